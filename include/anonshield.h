@@ -1,0 +1,203 @@
+/*
+ * anonshield.h — C ABI of the B300 pseudonymization hot path.
+ *
+ * The operation is the paper's problem statement (AnonShield, §2 "The
+ * AnonShield Framework"): records in, pseudonymised records plus an
+ * entity -> pseudonym map out, under an operator-defined key. One call runs,
+ * on one GPU:
+ *   byte tokenizer + pattern recognizers            (§2 stage (2))
+ *   encoder-only token-classification NER           (§2 stage (2))
+ *   argmax + BIO decoding + overlap rule + preserve (§2 stage (2), Appendix D)
+ *   HMAC-SHA256 slug substitution                   (§2 stage (3))
+ *   entity map update                               (§2 stage (4))
+ *   structure-preserving output                     (§2 stage (5))
+ *
+ * Conventions (every entry point):
+ *   - Return value: AS_OK (0) or a negative as_status; nothing is thrown.
+ *     as_last_error(ctx) gives a message for the last failing call on ctx.
+ *   - The caller owns every input buffer; the library reads it during the
+ *     call only. The library owns every as_output and every pointer it hands
+ *     out; they stay valid until the matching free call.
+ *   - One as_ctx per thread (or external locking).
+ *   - A ctx keeps one entity map under one key: calling with a different key
+ *     while the map is non-empty is AS_ERR_STATE (same entity + same key ->
+ *     same pseudonym; Fig. 1 caption).
+ *   - Record index = records processed by earlier calls on this ctx +
+ *     position in the call; it is the first_seen / last_seen value.
+ *   - All device work runs on the ctx's stream; calls are synchronous with
+ *     respect to the host (they return when results are ready).
+ */
+#ifndef ANONSHIELD_H
+#define ANONSHIELD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t as_status;
+#define AS_OK               0
+#define AS_ERR_ARG         -1  /* invalid argument, size or layout          */
+#define AS_ERR_OOM         -2  /* device or host allocation failed          */
+#define AS_ERR_CUDA        -3  /* a CUDA call failed                        */
+#define AS_ERR_TOO_LONG    -4  /* record longer than max_pos, no windows    */
+#define AS_ERR_TIMEOUT     -5  /* a bounded device wait ran out             */
+#define AS_ERR_STATE       -6  /* key changed on a non-empty map, etc.      */
+#define AS_ERR_UNSUPPORTED -7  /* configuration not built                   */
+#define AS_ERR_CAPACITY    -8  /* entity map or arena full                  */
+
+/* Encoder arithmetic. FP32: FP32 everywhere (SIMT GEMM). BF16: GEMM inputs
+ * rounded to BF16, FP32 accumulate; bias, residual, LayerNorm, softmax and
+ * logits in FP32. */
+#define AS_FP32 0
+#define AS_BF16 1
+
+/* Encoder batching. PACKED: all records of a call packed into large
+ * variable-length batches. PER_RECORD: one record per launch sequence. */
+#define AS_MODE_PACKED     0
+#define AS_MODE_PER_RECORD 1
+
+typedef struct as_ctx as_ctx;
+typedef struct as_output as_output;
+
+/* Model and runtime configuration, read by as_create only.
+ * weights: host FP32 blob, n = weights_len floats, in this order (row-major,
+ *   linear maps stored [out, in]):
+ *     tok_emb[vocab][d], pos_emb[max_pos][d], emb_ln_g[d], emb_ln_b[d],
+ *     per layer: w_qkv[3d][d] (rows 0..d-1 Q, d..2d-1 K, 2d..3d-1 V; head j
+ *                owns rows j*dh..(j+1)*dh-1 of each), b_qkv[3d], w_o[d][d],
+ *                b_o[d], ln1_g[d], ln1_b[d], w_1[f][d], b_1[f], w_2[d][f],
+ *                b_2[d], ln2_g[d], ln2_b[d],
+ *     cls_w[labels][d], cls_b[labels].
+ * vocab: the strings of token ids 257..vocab-1 (ids 1..256 are single bytes
+ *   0x00..0xFF, id 0 is padding): n_vocab_words = vocab - 257 strings of
+ *   2..12 bytes from [0-9A-Za-z], string k at
+ *   vocab_bytes[vocab_offsets[k] .. vocab_offsets[k+1]). Host memory. */
+typedef struct {
+  uint32_t vocab, d_model, n_heads, d_ffn, n_layers, n_labels, max_pos;
+  uint32_t precision;            /* AS_FP32 or AS_BF16                         */
+  uint32_t mode;                 /* AS_MODE_PACKED or AS_MODE_PER_RECORD       */
+  const float* weights;          /* host                                       */
+  uint64_t weights_len;          /* floats                                     */
+  const uint8_t* vocab_bytes;    /* host                                       */
+  const uint32_t* vocab_offsets; /* host, n_vocab_words + 1 entries            */
+  uint32_t n_vocab_words;
+  uint64_t max_chunk_tokens;     /* encoder rows per packed batch; 0 = 1<<20   */
+  uint64_t map_capacity;         /* entity-map slots (power of 2); 0 = 1<<22   */
+  uint64_t map_arena_bytes;      /* bytes for map originals; 0 = 256 MiB       */
+  int32_t device;                /* CUDA device ordinal                        */
+  uint32_t keep_trace;           /* 1: keep per-stage results for as_debug_*   */
+} as_config;
+
+/* Input records: one byte arena plus n_records + 1 offsets (offsets[0] = 0,
+ * non-decreasing, offsets[n] = total bytes < 2^32). on_device = 0: host
+ * pointers (copied to the GPU inside the call); 1: device pointers of the
+ * ctx's device (read in place). */
+typedef struct {
+  const uint8_t* bytes;
+  const uint64_t* offsets;
+  uint64_t n_records;
+  uint32_t on_device;
+} as_records;
+
+/* Replacement policy. type_names[t-1] is the name of entity type t
+ * (t = 1..n_types; label 2t-1 = B-t, 2t = I-t, 0 = O). Pattern recognizers
+ * emit types 1 IP_ADDRESS, 2 HOSTNAME, 3 CVE_ID, 4 MAC_ADDRESS.
+ * preserve_mask bit t set: type t is detected but passed through (the
+ * paper's --entities-to-preserve, §2). slug_hex_len: 0..64 hex characters
+ * (§2 stage (3)). window/stride: sliding windows for records longer than
+ * window tokens (0 = none: a record over max_pos tokens is AS_ERR_TOO_LONG);
+ * window <= max_pos, 0 < stride <= window, window - stride even. */
+typedef struct {
+  uint32_t n_types;
+  const char* const* type_names;
+  uint64_t preserve_mask;
+  uint32_t slug_hex_len;
+  uint32_t window, stride;
+} as_schema;
+
+/* One entity-map entry (§2 stage (4)): type, original bytes, full 64-hex
+ * HMAC, slug, first / last record index, occurrences. */
+typedef struct {
+  uint32_t type;
+  uint32_t original_len;
+  const uint8_t* original;
+  char full_hash[65];
+  char slug[65];
+  uint64_t first_seen, last_seen, count;
+} as_entity;
+
+/* Counters of one call. */
+typedef struct {
+  uint64_t n_records, n_bytes, n_tokens, n_encoded_tokens, n_sequences;
+  uint64_t n_regex_spans, n_ner_spans, n_final_spans, n_out_bytes;
+  uint64_t n_map_entries, n_new_entries;
+  uint64_t kernel_launches;
+} as_stats;
+
+/* Create a context: loads weights and vocabulary onto `device`, creates the
+ * ctx's stream. Errors: AS_ERR_ARG (shape mismatch, weights_len wrong,
+ * vocab strings invalid), AS_ERR_UNSUPPORTED (d_model % 64 != 0 in BF16,
+ * head dim != 64), AS_ERR_OOM, AS_ERR_CUDA. */
+as_status as_create(const as_config* cfg, as_ctx** out);
+void as_destroy(as_ctx* ctx);
+
+/* Pseudonymise a batch. key: key_len bytes (RFC 2104; > 64 bytes is hashed
+ * first). On success *out holds the output; free it with as_output_free.
+ * Output records live on the host when records->on_device == 0, else on the
+ * device. Errors: AS_ERR_ARG, AS_ERR_TOO_LONG, AS_ERR_STATE, AS_ERR_CAPACITY,
+ * AS_ERR_TIMEOUT, AS_ERR_OOM, AS_ERR_CUDA. On error the map may hold entries
+ * of records processed before the failure. */
+as_status as_anonymize(as_ctx* ctx, const as_records* records, const as_schema* schema,
+                       const uint8_t* key, size_t key_len, as_output** out);
+
+/* Output records: arena + n+1 offsets; *on_device tells where they live. */
+as_status as_output_records(const as_output* out, const uint8_t** bytes, const uint64_t** offsets,
+                            uint64_t* n_records, uint32_t* on_device);
+as_status as_output_stats(const as_output* out, as_stats* stats);
+/* Map entries touched by this call (new or updated), sorted by (type, bytes).
+ * Pointers valid until as_output_free. */
+as_status as_output_map(as_output* out, const as_entity** entries, uint64_t* n);
+void as_output_free(as_output* out);
+
+/* The whole map, sorted by type, then original bytes (lexicographic, a
+ * prefix first). *entries is one host allocation (entries followed by their
+ * original bytes); free it with as_free. */
+as_status as_map_export(as_ctx* ctx, as_entity** entries, uint64_t* n);
+/* Load entries (e.g. a previous export, or another shard's map): an entry
+ * already present keeps min first_seen, max last_seen, summed count. The
+ * entries' full_hash must be the HMAC under this ctx's key. */
+as_status as_map_import(as_ctx* ctx, const uint8_t* key, size_t key_len, const as_entity* entries, uint64_t n);
+/* Empty the map and forget the key. */
+as_status as_map_clear(as_ctx* ctx);
+
+/* Per-stage results of the last as_anonymize (needs keep_trace = 1). Host
+ * arrays owned by ctx, valid until the next call on ctx. Token arrays are in
+ * record order: tok_ids/tok_off(byte offset in the batch arena)/tok_len, and
+ * rec_tok[n+1] = first token of each record. Spans: start (byte offset in the
+ * batch arena), length, type. logits: n_tokens x n_labels FP32 (window-merged).
+ * labels: n_tokens. */
+typedef struct {
+  uint64_t n_records, n_tokens, n_regex, n_final;
+  const uint64_t* rec_tok;
+  const int32_t* tok_ids;
+  const uint32_t* tok_off;
+  const uint32_t* tok_len;
+  const uint32_t* regex_start; const uint32_t* regex_len; const uint8_t* regex_type;
+  const float* logits;
+  const uint8_t* labels;
+  const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
+} as_trace;
+as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+const char* as_last_error(const as_ctx* ctx);
+void as_free(void* p);
+/* Library version string. */
+const char* as_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANONSHIELD_H */

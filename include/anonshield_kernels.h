@@ -1,0 +1,63 @@
+/*
+ * anonshield_kernels.h — kernel-level entry points on device buffers.
+ *
+ * These expose the encoder's building blocks (AnonShield §2 stage (2): the
+ * transformer token classifier) one at a time so that each kernel can be
+ * checked against a plain reference of the same operation. All pointers are
+ * device pointers on the current device; `stream` is a cudaStream_t (NULL =
+ * legacy default stream). Calls are asynchronous on `stream` unless stated.
+ * Return AS_OK or a negative as_status; as_k_last_error() gives the message
+ * of the last failure on the calling thread.
+ */
+#ifndef ANONSHIELD_KERNELS_H
+#define ANONSHIELD_KERNELS_H
+
+#include "anonshield.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* GEMM epilogues: out = epi(A[M,K] . B[N,K]^T). */
+#define AS_EPI_BIAS       0  /* out = acc + bias[n]                (act type)  */
+#define AS_EPI_BIAS_GELU  1  /* out = gelu_erf(acc + bias[n])      (act type)  */
+#define AS_EPI_BIAS_RESID 2  /* out = acc + bias[n] + resid[m,n]   (FP32 out)  */
+
+/* GEMM engines. */
+#define AS_GEMM_AUTO     0   /* BF16 -> tcgen05, FP32 -> SIMT                   */
+#define AS_GEMM_TCGEN05  1   /* BF16 only: TMA + tcgen05.mma + TMEM, sm_103a    */
+#define AS_GEMM_SIMT     2   /* FP32 only: CUDA-core FP32                       */
+
+/* C = epi(A . B^T). Row-major A[M][K] and B[N][K] (B is an nn.Linear weight
+ * [out][in]); precision AS_FP32: A, B float, act type float; AS_BF16: A, B
+ * __nv_bfloat16, act type __nv_bfloat16, FP32 accumulation. bias: float[N]
+ * (may be NULL = 0). resid/out for AS_EPI_BIAS_RESID: float[M][N].
+ * Constraints: M >= 1; N % 128 == 0; K % 64 == 0 (BF16) or K % 8 == 0
+ * (FP32); 16-byte aligned base pointers. AS_ERR_ARG otherwise. */
+as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t N, int64_t K,
+                    const void* A, const void* B, const float* bias, const float* resid, void* out,
+                    void* stream);
+
+/* Multi-head self-attention over packed variable-length sequences.
+ * qkv: [rows][3*d] (Q | K | V column blocks; head j owns columns j*64..j*64+63
+ * of each), act type of `precision`; out: [rows][d] act type. Sequence s
+ * covers rows seq_start[s] .. seq_start[s]+seq_len[s]-1 (int32, device);
+ * tokens attend within their sequence only, scale 1/sqrt(64). Head dim 64,
+ * seq_len <= 4096. */
+as_status as_k_attention(int precision, const void* qkv, void* out, const int32_t* seq_start,
+                         const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model,
+                         int32_t n_heads, void* stream);
+
+/* Row LayerNorm (biased variance, eps 1e-5): out_f32 = LN(in) * g + b, and
+ * a BF16 copy in out_bf16 when it is not NULL. in/out_f32 may alias. */
+as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16,
+                         int64_t rows, int32_t d, void* stream);
+
+/* Device count of kernel launches made by this library since load. */
+uint64_t as_k_launch_count(void);
+const char* as_k_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANONSHIELD_KERNELS_H */

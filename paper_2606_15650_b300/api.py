@@ -1,0 +1,366 @@
+"""Thin Python binding of the C ABI (include/anonshield.h, anonshield_kernels.h).
+
+Argument marshalling only: every step of the pseudonymization path runs in
+the CUDA library. PyTorch tensors may be passed wherever the C ABI takes a
+device pointer (their data_ptr() is used); nothing here computes any part of
+the method. If the compiled library is missing, importing fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libanonshield.so")
+
+AS_OK = 0
+STATUS = {0: "AS_OK", -1: "AS_ERR_ARG", -2: "AS_ERR_OOM", -3: "AS_ERR_CUDA", -4: "AS_ERR_TOO_LONG",
+          -5: "AS_ERR_TIMEOUT", -6: "AS_ERR_STATE", -7: "AS_ERR_UNSUPPORTED", -8: "AS_ERR_CAPACITY"}
+PRECISION = {"fp32": 0, "bf16": 1}
+MODE = {"packed": 0, "per_record": 1}
+EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
+ENGINE = {"auto": 0, "tcgen05": 1, "simt": 2}
+
+
+class AnonShieldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("vocab", C.c_uint32), ("d_model", C.c_uint32), ("n_heads", C.c_uint32), ("d_ffn", C.c_uint32),
+                ("n_layers", C.c_uint32), ("n_labels", C.c_uint32), ("max_pos", C.c_uint32),
+                ("precision", C.c_uint32), ("mode", C.c_uint32),
+                ("weights", C.POINTER(C.c_float)), ("weights_len", C.c_uint64),
+                ("vocab_bytes", C.POINTER(C.c_uint8)), ("vocab_offsets", C.POINTER(C.c_uint32)),
+                ("n_vocab_words", C.c_uint32), ("max_chunk_tokens", C.c_uint64), ("map_capacity", C.c_uint64),
+                ("map_arena_bytes", C.c_uint64), ("device", C.c_int32), ("keep_trace", C.c_uint32)]
+
+
+class _Records(C.Structure):
+    _fields_ = [("bytes", C.c_void_p), ("offsets", C.c_void_p), ("n_records", C.c_uint64), ("on_device", C.c_uint32)]
+
+
+class _Schema(C.Structure):
+    _fields_ = [("n_types", C.c_uint32), ("type_names", C.POINTER(C.c_char_p)), ("preserve_mask", C.c_uint64),
+                ("slug_hex_len", C.c_uint32), ("window", C.c_uint32), ("stride", C.c_uint32)]
+
+
+class _Entity(C.Structure):
+    _fields_ = [("type", C.c_uint32), ("original_len", C.c_uint32), ("original", C.POINTER(C.c_uint8)),
+                ("full_hash", C.c_char * 65), ("slug", C.c_char * 65),
+                ("first_seen", C.c_uint64), ("last_seen", C.c_uint64), ("count", C.c_uint64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n_records", "n_bytes", "n_tokens", "n_encoded_tokens", "n_sequences",
+                                          "n_regex_spans", "n_ner_spans", "n_final_spans", "n_out_bytes",
+                                          "n_map_entries", "n_new_entries", "kernel_launches")]
+
+
+class _Trace(C.Structure):
+    _fields_ = [("n_records", C.c_uint64), ("n_tokens", C.c_uint64), ("n_regex", C.c_uint64), ("n_final", C.c_uint64),
+                ("rec_tok", C.POINTER(C.c_uint64)), ("tok_ids", C.POINTER(C.c_int32)),
+                ("tok_off", C.POINTER(C.c_uint32)), ("tok_len", C.POINTER(C.c_uint32)),
+                ("regex_start", C.POINTER(C.c_uint32)), ("regex_len", C.POINTER(C.c_uint32)),
+                ("regex_type", C.POINTER(C.c_uint8)), ("logits", C.POINTER(C.c_float)),
+                ("labels", C.POINTER(C.c_uint8)), ("final_start", C.POINTER(C.c_uint32)),
+                ("final_len", C.POINTER(C.c_uint32)), ("final_type", C.POINTER(C.c_uint8))]
+
+
+EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
+            "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
+            "as_free", "as_version", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
+            "as_k_last_error"]
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.as_create.argtypes = [C.POINTER(_Config), C.POINTER(P)]
+    lib.as_destroy.argtypes = [P]
+    lib.as_destroy.restype = None
+    lib.as_anonymize.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
+    lib.as_output_records.argtypes = [P, C.POINTER(P), C.POINTER(P), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
+    lib.as_output_stats.argtypes = [P, C.POINTER(_Stats)]
+    lib.as_output_map.argtypes = [P, C.POINTER(C.POINTER(_Entity)), C.POINTER(C.c_uint64)]
+    lib.as_output_free.argtypes = [P]
+    lib.as_output_free.restype = None
+    lib.as_map_export.argtypes = [P, C.POINTER(C.POINTER(_Entity)), C.POINTER(C.c_uint64)]
+    lib.as_map_import.argtypes = [P, C.c_char_p, C.c_size_t, C.POINTER(_Entity), C.c_uint64]
+    lib.as_map_clear.argtypes = [P]
+    lib.as_debug_trace.argtypes = [P, C.POINTER(_Trace)]
+    lib.as_last_error.argtypes = [P]
+    lib.as_last_error.restype = C.c_char_p
+    lib.as_free.argtypes = [P]
+    lib.as_free.restype = None
+    lib.as_version.restype = C.c_char_p
+    lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
+    lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
+    lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
+    lib.as_k_launch_count.restype = C.c_uint64
+    lib.as_k_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int | None:
+    """Device pointer of a torch tensor, or None."""
+    if x is None:
+        return None
+    return x.data_ptr()
+
+
+def _check_k(status: int):
+    if status != AS_OK:
+        raise AnonShieldError(status, (load().as_k_last_error() or b"").decode())
+
+
+# ------------------------------------------------------------ kernel level
+
+def gemm(precision: str, epilogue: str, A, B, bias=None, resid=None, out=None, engine: str = "auto", stream=None):
+    """out = epi(A @ B^T) on device tensors (A [M,K], B [N,K]); returns out."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check_k(load().as_k_gemm(PRECISION[precision], ENGINE[engine], EPI[epilogue], M, N, K, _ptr(A), _ptr(B),
+                              _ptr(bias), _ptr(resid), _ptr(out), stream))
+    return out
+
+
+def attention(precision: str, qkv, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
+    _check_k(load().as_k_attention(PRECISION[precision], _ptr(qkv), _ptr(out), _ptr(seq_start), _ptr(seq_len),
+                                   int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
+    return out
+
+
+def layernorm(x, g, b, out_f32, out_bf16=None, stream=None):
+    rows, d = x.shape
+    _check_k(load().as_k_layernorm(_ptr(x), _ptr(g), _ptr(b), _ptr(out_f32), _ptr(out_bf16), rows, d, stream))
+    return out_f32
+
+
+def launch_count() -> int:
+    return int(load().as_k_launch_count())
+
+
+# ------------------------------------------------------------ batch API
+
+@dataclass
+class Schema:
+    type_names: tuple[str, ...]
+    preserve_mask: int = 0
+    slug_hex_len: int = 10
+    window: int = 0
+    stride: int = 0
+
+
+@dataclass
+class Entity:
+    type: int
+    original: bytes
+    full_hash: str
+    slug: str
+    first_seen: int
+    last_seen: int
+    count: int
+
+
+def _entities(ptr, n) -> list[Entity]:
+    out = []
+    for i in range(n):
+        e = ptr[i]
+        out.append(Entity(int(e.type), C.string_at(e.original, e.original_len) if e.original_len else b"",
+                          e.full_hash.decode(), e.slug.decode(), int(e.first_seen), int(e.last_seen), int(e.count)))
+    return out
+
+
+class Output:
+    """Result of one anonymize call (owns the library's as_output)."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self._ctx = ctx
+        self._h = C.c_void_p(handle)
+
+    def _records(self):
+        b, o, n, dev = C.c_void_p(), C.c_void_p(), C.c_uint64(), C.c_uint32()
+        st = load().as_output_records(self._h, C.byref(b), C.byref(o), C.byref(n), C.byref(dev))
+        self._ctx._check(st)
+        return b.value, o.value, n.value, dev.value
+
+    def arrays(self) -> tuple[np.ndarray, np.ndarray]:
+        """(bytes uint8, offsets uint64) on the host (copied from the device if needed)."""
+        b, o, n, dev = self._records()
+        if dev:
+            raise ValueError("output lives on the device: use device_pointers()")
+        offs = np.ctypeslib.as_array(C.cast(o, C.POINTER(C.c_uint64)), shape=(n + 1,)).copy()
+        size = int(offs[-1])
+        data = np.ctypeslib.as_array(C.cast(b, C.POINTER(C.c_uint8)), shape=(max(size, 1),))[:size].copy()
+        return data, offs
+
+    def device_pointers(self) -> tuple[int, int, int]:
+        b, o, n, dev = self._records()
+        if not dev:
+            raise ValueError("output lives on the host")
+        return b, o, n
+
+    def records(self) -> list[bytes]:
+        data, offs = self.arrays()
+        return [data[offs[i]:offs[i + 1]].tobytes() for i in range(len(offs) - 1)]
+
+    def stats(self) -> dict:
+        s = _Stats()
+        self._ctx._check(load().as_output_stats(self._h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+    def map(self) -> list[Entity]:
+        p, n = C.POINTER(_Entity)(), C.c_uint64()
+        self._ctx._check(load().as_output_map(self._h, C.byref(p), C.byref(n)))
+        return _entities(p, n.value)
+
+    def free(self):
+        if self._h:
+            load().as_output_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One as_ctx: model weights, vocabulary and entity map on one GPU."""
+
+    def __init__(self, dims, weights_blob: np.ndarray, vocab_words: list[bytes], precision: str = "bf16",
+                 mode: str = "packed", max_chunk_tokens: int = 0, map_capacity: int = 0, map_arena_bytes: int = 0,
+                 keep_trace: bool = False, device: int = 0):
+        lib = load()
+        self.dims = dims
+        self.device = device
+        self._w = np.ascontiguousarray(weights_blob, dtype=np.float32)
+        vb = b"".join(vocab_words)
+        self._vb = np.frombuffer(vb, dtype=np.uint8).copy() if vb else np.zeros(1, np.uint8)
+        offs = np.zeros(len(vocab_words) + 1, dtype=np.uint32)
+        offs[1:] = np.cumsum([len(w) for w in vocab_words])
+        self._vo = offs
+        cfg = _Config(vocab=dims.vocab, d_model=dims.d_model, n_heads=dims.n_heads, d_ffn=dims.d_ffn,
+                      n_layers=dims.n_layers, n_labels=dims.n_labels, max_pos=dims.max_pos,
+                      precision=PRECISION[precision], mode=MODE[mode],
+                      weights=self._w.ctypes.data_as(C.POINTER(C.c_float)), weights_len=self._w.size,
+                      vocab_bytes=self._vb.ctypes.data_as(C.POINTER(C.c_uint8)),
+                      vocab_offsets=self._vo.ctypes.data_as(C.POINTER(C.c_uint32)),
+                      n_vocab_words=len(vocab_words), max_chunk_tokens=max_chunk_tokens,
+                      map_capacity=map_capacity, map_arena_bytes=map_arena_bytes, device=device,
+                      keep_trace=1 if keep_trace else 0)
+        h = C.c_void_p()
+        st = lib.as_create(C.byref(cfg), C.byref(h))
+        if st != AS_OK:
+            raise AnonShieldError(st, (lib.as_k_last_error() or b"").decode())
+        self._h = h
+        self.precision = precision
+
+    def _check(self, st: int):
+        if st != AS_OK:
+            raise AnonShieldError(st, (load().as_last_error(self._h) or b"").decode())
+
+    @staticmethod
+    def _schema(s: Schema):
+        names = (C.c_char_p * len(s.type_names))(*[n.encode() for n in s.type_names])
+        sc = _Schema(n_types=len(s.type_names), type_names=names, preserve_mask=s.preserve_mask,
+                     slug_hex_len=s.slug_hex_len, window=s.window, stride=s.stride)
+        return sc, names
+
+    def anonymize(self, data, offsets, schema: Schema, key: bytes) -> Output:
+        """data/offsets: numpy (host) or torch CUDA tensors (device, read in place)."""
+        on_dev = hasattr(data, "is_cuda") and data.is_cuda
+        if on_dev:
+            rec = _Records(bytes=data.data_ptr(), offsets=offsets.data_ptr(), n_records=offsets.numel() - 1,
+                           on_device=1)
+            keep = (data, offsets)
+        else:
+            d = np.ascontiguousarray(data, dtype=np.uint8)
+            o = np.ascontiguousarray(offsets, dtype=np.uint64)
+            rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
+                           on_device=0)
+            keep = (d, o)
+        sc, names = self._schema(schema)
+        out = C.c_void_p()
+        st = load().as_anonymize(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(out))
+        del keep, names
+        self._check(st)
+        return Output(self, out.value)
+
+    def map_export(self) -> list[Entity]:
+        p, n = C.POINTER(_Entity)(), C.c_uint64()
+        self._check(load().as_map_export(self._h, C.byref(p), C.byref(n)))
+        try:
+            return _entities(p, n.value)
+        finally:
+            load().as_free(C.cast(p, C.c_void_p))
+
+    def map_import(self, key: bytes, entries: list[Entity]):
+        arr = (_Entity * max(len(entries), 1))()
+        bufs = []
+        for i, e in enumerate(entries):
+            b = (C.c_uint8 * max(len(e.original), 1)).from_buffer_copy(e.original + b"\0")
+            bufs.append(b)
+            arr[i].type = e.type
+            arr[i].original_len = len(e.original)
+            arr[i].original = C.cast(b, C.POINTER(C.c_uint8))
+            arr[i].full_hash = e.full_hash.encode()
+            arr[i].slug = e.slug.encode()
+            arr[i].first_seen = e.first_seen
+            arr[i].last_seen = e.last_seen
+            arr[i].count = e.count
+        self._check(load().as_map_import(self._h, key, len(key), arr, len(entries)))
+
+    def map_clear(self):
+        self._check(load().as_map_clear(self._h))
+
+    def trace(self) -> dict:
+        t = _Trace()
+        self._check(load().as_debug_trace(self._h, C.byref(t)))
+        T, nr, nf, n = t.n_tokens, t.n_regex, t.n_final, t.n_records
+
+        def arr(p, k, dt):
+            if k == 0 or not p:
+                return np.zeros(0, dt)
+            return np.ctypeslib.as_array(p, shape=(k,)).astype(dt, copy=True)
+
+        C_ = self.dims.n_labels
+        logits = arr(t.logits, T * C_, np.float32).reshape(T, C_) if t.logits else None
+        return {"rec_tok": arr(t.rec_tok, n + 1, np.uint64), "tok_ids": arr(t.tok_ids, T, np.int32),
+                "tok_off": arr(t.tok_off, T, np.uint32), "tok_len": arr(t.tok_len, T, np.uint32),
+                "regex_start": arr(t.regex_start, nr, np.uint32), "regex_len": arr(t.regex_len, nr, np.uint32),
+                "regex_type": arr(t.regex_type, nr, np.uint8), "logits": logits,
+                "labels": arr(t.labels, T, np.uint8), "final_start": arr(t.final_start, nf, np.uint32),
+                "final_len": arr(t.final_len, nf, np.uint32), "final_type": arr(t.final_type, nf, np.uint8)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().as_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().as_version().decode()

@@ -1,0 +1,42 @@
+// Encoder kernels of the token classifier (AnonShield §2 stage (2)).
+#pragma once
+
+#include "../../include/anonshield_kernels.h"
+#include "common.cuh"
+
+namespace as {
+
+// C = epi(A . B^T) on tcgen05 (BF16 in, FP32 accumulate). See gemm_tc.cu.
+as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
+                       const float* resid, void* out, DevError* err, cudaStream_t st);
+// Same contract in FP32 on CUDA cores.
+as_status gemm_simt_f32(int epi, int64_t M, int64_t N, int64_t K, const float* A, const float* B, const float* bias,
+                        const float* resid, float* out, cudaStream_t st);
+
+// Self-attention over packed sequences (see anonshield_kernels.h).
+as_status attention_f32(const float* qkv, float* out, const int32_t* seq_start, const int32_t* seq_len, int32_t n_seq,
+                        int32_t max_len, int32_t d_model, int32_t n_heads, cudaStream_t st);
+as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
+                         const int32_t* seq_len, int32_t n_seq, int32_t max_len, int32_t d_model, int32_t n_heads,
+                         cudaStream_t st);
+
+// Row LayerNorm; writes FP32 and (optionally) BF16 copies.
+as_status layernorm_rows(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                         int64_t rows, int32_t d, cudaStream_t st);
+
+// X = LN(E[ids[row_tok[r]]] + P[row_pos[r]]) for each encoder row.
+as_status embed_ln(const int32_t* tok_ids, const int32_t* row_tok, const int32_t* row_pos, const float* tok_emb,
+                   const float* pos_emb, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                   int64_t rows, int32_t d, cudaStream_t st);
+
+// Last LayerNorm fused with the classifier: logits = LN(in) . Wc^T + bc, argmax
+// (lowest label wins ties). A row whose own flag is set writes its logits and
+// label to token row_tok[r] (window merge). C <= 32.
+as_status layernorm_classify(const float* in, const float* g, const float* b, const float* cls_w, const float* cls_b,
+                             int32_t C, const int32_t* row_tok, const uint8_t* row_own, float* logits,
+                             uint8_t* labels, int64_t rows, int32_t d, cudaStream_t st);
+
+// FP32 -> BF16 copy (round to nearest even).
+void convert_f32_bf16(const float* in, __nv_bfloat16* out, uint64_t n, cudaStream_t st);
+
+}  // namespace as

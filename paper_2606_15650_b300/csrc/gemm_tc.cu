@@ -1,0 +1,411 @@
+// BF16 GEMM on the 5th-generation tensor cores (sm_103a): C = epi(A . B^T).
+//
+// Encoder projections (QKV, output, FFN in/out) of the token classifier
+// (AnonShield §2 stage (2)). A = activations [M][K] BF16 row-major, B =
+// nn.Linear weight [N][K] BF16 row-major: both K-major, which is what the
+// tensor core reads directly.
+//
+// Structure (one CTA per SM, persistent over 128 x BN output tiles):
+//   warp 0, one lane : TMA producer, A and B tiles (64 K-elements, 128-byte
+//                      swizzle) into a STAGES-deep shared-memory ring
+//   warp 1, one lane : issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM
+//                      accumulator; tcgen05.commit frees ring slots and
+//                      signals a finished accumulator
+//   warps 2..5       : epilogue; tcgen05.ld of their 32 TMEM lanes, bias /
+//                      GELU / residual in FP32, stores
+// Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap
+// the main loop of tile i+1. Every mbarrier wait is bounded (globaltimer):
+// on timeout the kernel records the failure, every role leaves its loop,
+// TMEM is freed and the kernel returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "encoder.cuh"
+
+namespace as {
+namespace tc {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;             // one 128-byte swizzle atom of BF16
+constexpr int kThreads = 192;       // 6 warps
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+struct Params {
+  int M, N, K;
+  int n_tiles_n, n_tiles;
+  int epi;
+  const float* bias;
+  const float* resid;
+  void* out;
+  DevError* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait. Returns false when the kernel is aborting (timeout here or
+// elsewhere in the CTA).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, DevError* err,
+                                          uint32_t where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = globaltimer();
+  uint32_t n = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++n & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) {
+        report_error(err, kErrTimeout, where, blockIdx.x, parity);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// 8-row groups 1024 bytes apart (SBO), descriptor version 1 (tcgen05).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D FP32, A/B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+template <int BN, int STAGES>
+struct Smem {
+  static constexpr int kABytes = kBM * kBK * 2;   // 16 KB
+  static constexpr int kBBytes = BN * kBK * 2;    // 16 or 32 KB
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kBarOff = STAGES * kStageBytes;
+  // full[S], empty[S], tfull[2], tempty[2], then tmem slot + abort flag
+  static constexpr int kBytes = kBarOff + (2 * STAGES + 4) * 8 + 16;
+  static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+  using L = Smem<BN, STAGES>;
+  constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kBarOff + (2 * STAGES + 4) * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KB = p.K / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4 * 32);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+        const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.err, 10)) goto done;
+          mbar_expect_tx(full_bar(s), L::kStageBytes);
+          const uint32_t a_dst = sbase + s * L::kStageBytes;
+          tma_load_2d(a_dst, &tmA, full_bar(s), kb * kBK, m0);
+          tma_load_2d(a_dst + L::kABytes, &tmB, full_bar(s), kb * kBK, n0);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      uint32_t it = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
+        const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+        if (!mbar_wait(tempty_bar(acc), aph ^ 1u, abort_flag, p.err, 20)) goto done;
+        fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(full_bar(s), ph, abort_flag, p.err, 21)) goto done;
+          fence_after();
+          const uint32_t a_addr = sbase + s * L::kStageBytes;
+          const uint64_t adesc = sw128_desc(a_addr), bdesc = sw128_desc(a_addr + L::kABytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(empty_bar(s));
+        }
+        mma_commit(tfull_bar(acc));
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
+    const int sub = warp & 3;
+    const int row_in_tile = sub * 32 + lane;
+    uint32_t lt = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      if (!mbar_wait(tfull_bar(acc), aph, abort_flag, p.err, 30)) break;
+      fence_after();
+      const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
+      const int m = m0 + row_in_tile;
+      const bool row_ok = m < p.M;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN + c * 32, r);
+        const int n = n0 + c * 32;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[j + 0] = __uint_as_float(r[j + 0]) + b.x;
+          v[j + 1] = __uint_as_float(r[j + 1]) + b.y;
+          v[j + 2] = __uint_as_float(r[j + 2]) + b.z;
+          v[j + 3] = __uint_as_float(r[j + 3]) + b.w;
+        }
+        if (!row_ok) continue;
+        if (p.epi == AS_EPI_BIAS_RESID) {
+          const float* rs = p.resid + (size_t)m * p.N + n;
+          float* o = reinterpret_cast<float*>(p.out) + (size_t)m * p.N + n;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(rs + j));
+            *reinterpret_cast<float4*>(o + j) = make_float4(v[j] + q.x, v[j + 1] + q.y, v[j + 2] + q.z, v[j + 3] + q.w);
+          }
+        } else {
+          if (p.epi == AS_EPI_BIAS_GELU) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = gelu_erf(v[j]);
+          }
+          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(p.out) + (size_t)m * p.N + n;
+#pragma unroll
+          for (int j = 0; j < 32; j += 8) {
+            uint4 w;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[j + 0], v[j + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+            w.x = *reinterpret_cast<uint32_t*>(&h0);
+            w.y = *reinterpret_cast<uint32_t*>(&h1);
+            w.z = *reinterpret_cast<uint32_t*>(&h2);
+            w.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(o + j) = w;
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(tempty_bar(acc));
+    }
+  }
+done:
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+int g_num_sms = 0;
+
+as_status ensure_driver() {
+  if (g_encode) return AS_OK;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  AS_CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !fn) {
+    set_k_error("cuTensorMapEncodeTiled not available from the driver");
+    return AS_ERR_CUDA;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return AS_OK;
+}
+
+as_status make_map(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)tc::kBK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_k_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return AS_ERR_CUDA;
+  }
+  return AS_OK;
+}
+
+template <int BN, int STAGES>
+as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStream_t st) {
+  using L = tc::Smem<BN, STAGES>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!attr_set[dev & 63]) {
+    AS_CUDA_OK(cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
+    attr_set[dev & 63] = true;
+  }
+  CUtensorMap tmA, tmB;
+  as_status s = make_map(&tmA, A, (uint64_t)p0.M, (uint64_t)p0.K, tc::kBM);
+  if (s != AS_OK) return s;
+  s = make_map(&tmB, B, (uint64_t)p0.N, (uint64_t)p0.K, BN);
+  if (s != AS_OK) return s;
+  tc::Params p = p0;
+  p.n_tiles_n = p.N / BN;
+  p.n_tiles = p.n_tiles_n * ((p.M + tc::kBM - 1) / tc::kBM);
+  int grid = p.n_tiles < g_num_sms ? p.n_tiles : g_num_sms;
+  tc::gemm_kernel<BN, STAGES><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, p);
+  count_launch();
+  AS_CUDA_OK(cudaGetLastError());
+  return AS_OK;
+}
+
+}  // namespace
+
+as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
+                       const float* resid, void* out, DevError* err, cudaStream_t st) {
+  as_status s = ensure_driver();
+  if (s != AS_OK) return s;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = kDefaultSMs;
+  }
+  if (M < 1 || N % 128 != 0 || K % tc::kBK != 0 || K < tc::kBK || M > (1ll << 31) - 1 ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) {
+    set_k_error("gemm_tcgen05: unsupported shape or alignment");
+    return AS_ERR_ARG;
+  }
+  tc::Params p{};
+  p.M = (int)M;
+  p.N = (int)N;
+  p.K = (int)K;
+  p.epi = epi;
+  p.bias = bias;
+  p.resid = resid;
+  p.out = out;
+  p.err = err;
+  if (N % 256 == 0) return launch_bn<256, 4>(p, A, B, st);
+  return launch_bn<128, 6>(p, A, B, st);
+}
+
+}  // namespace as

@@ -1,0 +1,71 @@
+// Kernel-level entry points (include/anonshield_kernels.h): the encoder's
+// building blocks on caller-owned device buffers, for unit checks.
+#include <vector>
+
+#include "encoder.cuh"
+
+using namespace as;
+
+extern "C" {
+
+uint64_t as_k_launch_count(void) { return g_launches.load(); }
+
+as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t N, int64_t K, const void* A,
+                    const void* B, const float* bias, const float* resid, void* out, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (epilogue < AS_EPI_BIAS || epilogue > AS_EPI_BIAS_RESID) {
+    set_k_error("as_k_gemm: bad epilogue");
+    return AS_ERR_ARG;
+  }
+  if (epilogue == AS_EPI_BIAS_RESID && !resid) {
+    set_k_error("as_k_gemm: residual epilogue needs resid");
+    return AS_ERR_ARG;
+  }
+  if (precision == AS_BF16) {
+    if (engine != AS_GEMM_AUTO && engine != AS_GEMM_TCGEN05) {
+      set_k_error("as_k_gemm: BF16 runs on the tcgen05 engine");
+      return AS_ERR_UNSUPPORTED;
+    }
+    return gemm_tcgen05(epilogue, M, N, K, A, B, bias, resid, out, nullptr, st);
+  }
+  if (precision == AS_FP32) {
+    if (engine != AS_GEMM_AUTO && engine != AS_GEMM_SIMT) {
+      set_k_error("as_k_gemm: FP32 runs on the SIMT engine");
+      return AS_ERR_UNSUPPORTED;
+    }
+    return gemm_simt_f32(epilogue, M, N, K, static_cast<const float*>(A), static_cast<const float*>(B), bias, resid,
+                         static_cast<float*>(out), st);
+  }
+  set_k_error("as_k_gemm: precision must be AS_FP32 or AS_BF16");
+  return AS_ERR_ARG;
+}
+
+as_status as_k_attention(int precision, const void* qkv, void* out, const int32_t* seq_start, const int32_t* seq_len,
+                         int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads, void* stream) {
+  (void)rows;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the kernel needs the longest sequence for its grid: read it from the host copy
+  std::vector<int32_t> lens(n_seq > 0 ? n_seq : 0);
+  if (n_seq > 0) {
+    AS_CUDA_OK(cudaMemcpyAsync(lens.data(), seq_len, n_seq * 4, cudaMemcpyDeviceToHost, st));
+    AS_CUDA_OK(cudaStreamSynchronize(st));
+  }
+  int32_t mx = 0;
+  for (int32_t v : lens) mx = v > mx ? v : mx;
+  if (precision == AS_BF16)
+    return attention_bf16(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(out), seq_start,
+                          seq_len, n_seq, mx, d_model, n_heads, st);
+  if (precision == AS_FP32)
+    return attention_f32(static_cast<const float*>(qkv), static_cast<float*>(out), seq_start, seq_len, n_seq, mx,
+                         d_model, n_heads, st);
+  set_k_error("as_k_attention: precision must be AS_FP32 or AS_BF16");
+  return AS_ERR_ARG;
+}
+
+as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16, int64_t rows,
+                         int32_t d, void* stream) {
+  return layernorm_rows(in, g, b, out_f32, static_cast<__nv_bfloat16*>(out_bf16), rows, d,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

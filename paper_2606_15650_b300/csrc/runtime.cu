@@ -1,0 +1,1106 @@
+// Host runtime behind the C ABI (include/anonshield.h).
+//
+// One as_anonymize call runs the whole path on the ctx's stream:
+//   H2D (host inputs) -> tokenizer + recognizers -> [sync: token counts]
+//   -> windows / packing into encoder batches -> encoder per batch
+//   -> BIO decode -> overlap rule + preserve -> HMAC -> entity map
+//   -> substitution -> [sync: output size] -> D2H (host inputs).
+// Device buffers are owned by the ctx and only grow, so a steady stream of
+// calls allocates nothing after warm-up.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "encoder.cuh"
+#include "scan.cuh"
+#include "stages.cuh"
+
+namespace as {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_k_error;
+void set_k_error(const std::string& msg) { t_k_error = msg; }
+
+}  // namespace as
+
+using namespace as;
+
+namespace {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+as_status grow(DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return AS_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    set_k_error("cudaMalloc of " + std::to_string(want) + " bytes failed");
+    return AS_ERR_OOM;
+  }
+  b.cap = want;
+  return AS_OK;
+}
+
+void release(DBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+struct LayerW {
+  const float *w_qkv, *b_qkv, *w_o, *b_o, *ln1_g, *ln1_b, *w_1, *b_1, *w_2, *b_2, *ln2_g, *ln2_b;
+  __nv_bfloat16 *w_qkv16, *w_o16, *w_1_16, *w_2_16;
+};
+
+struct NonZeroU16 {
+  const uint16_t* p;
+  __device__ uint32_t operator()(uint64_t i) const { return p[i] != 0; }
+};
+struct NonZeroU8 {
+  const uint8_t* p;
+  __device__ uint32_t operator()(uint64_t i) const { return p[i] != 0; }
+};
+struct LoadI64 {
+  const int64_t* p;
+  __device__ int64_t operator()(uint64_t i) const { return p[i]; }
+};
+
+struct SeqDesc {
+  uint32_t src_tok;  // first token of the window (global token index)
+  uint32_t len;
+  uint32_t row;      // first encoder row, relative to its batch
+  uint16_t own_lo, own_hi;
+};
+
+struct Chunk {
+  uint64_t s0, s1;   // sequences
+  uint64_t rows;
+  uint32_t max_len;
+};
+
+// cnt[5] = cnt[3] + cnt[4] (kept spans: recognizer + NER), on the device.
+__global__ void sum_kept_kernel(uint32_t* cnt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cnt[5] = cnt[3] + cnt[4];
+}
+
+__global__ void expand_rows_kernel(const SeqDesc* __restrict__ seqs, int32_t* row_tok, int32_t* row_pos,
+                                   uint8_t* row_own, int32_t* seq_start, int32_t* seq_len) {
+  const SeqDesc d = seqs[blockIdx.x];
+  if (threadIdx.x == 0) {
+    seq_start[blockIdx.x] = (int32_t)d.row;
+    seq_len[blockIdx.x] = (int32_t)d.len;
+  }
+  for (uint32_t j = threadIdx.x; j < d.len; j += blockDim.x) {
+    row_tok[d.row + j] = (int32_t)(d.src_tok + j);
+    row_pos[d.row + j] = (int32_t)j;
+    row_own[d.row + j] = (j >= d.own_lo && j < d.own_hi) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+struct as_ctx {
+  as_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // weights
+  DBuf w32, w16;
+  const float *tok_emb = nullptr, *pos_emb = nullptr, *emb_g = nullptr, *emb_b = nullptr;
+  const float *cls_w = nullptr, *cls_b = nullptr;
+  std::vector<LayerW> layers;
+  // vocab
+  DBuf vocab_slots;
+  uint32_t vocab_mask = 0;
+  // map
+  DBuf map_slots, map_arena, map_ctr;  // map_ctr: arena_used, n_entries
+  uint64_t map_mask = 0;
+  std::vector<uint8_t> key;
+  bool key_set = false;
+  DBuf key_dev, key_state;
+  uint32_t call_id = 0;
+  uint64_t records_done = 0;
+  uint32_t slug_len = 10;
+  DBuf dev_err;
+  // per-call buffers
+  DBuf in_bytes, in_off, rs_bits, tok_at, pos_b, scan_tiles, counters, delta_total;
+  DBuf tok_ids, tok_off, tok_len, rec_tok;
+  DBuf rx_len_b, rx_type_b, rx_s, rx_l, rx_t;
+  DBuf labels, logits, tok_flags, rx_pos, bio_start, bio_end, pos_t;
+  DBuf ner_s, ner_l, ner_t, keep, pos_k, nk_s, nk_l, nk_t, rk_s, rk_l, rk_t;
+  DBuf fin_s, fin_l, fin_t, digests, delta, shift;
+  DBuf names, name_off, name_len;
+  DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len;
+  DBuf X32, X16, QKV, ATT, Y32, H;
+  // last call results kept for as_debug_trace
+  uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
+  bool last_logits = false;
+  std::vector<uint64_t> h_rec_tok;
+  std::vector<int32_t> h_tok_ids;
+  std::vector<uint32_t> h_tok_off, h_tok_len, h_rx_s, h_rx_l, h_fin_s, h_fin_l;
+  std::vector<uint8_t> h_rx_t, h_labels, h_fin_t;
+  std::vector<float> h_logits;
+};
+
+struct as_output {
+  as_ctx* ctx = nullptr;
+  uint32_t call_id = 0;
+  uint32_t on_device = 0;
+  std::vector<uint8_t> h_bytes;
+  std::vector<uint64_t> h_off;
+  void* d_bytes = nullptr;
+  uint64_t* d_off = nullptr;
+  uint64_t n = 0;
+  as_stats stats{};
+  bool map_loaded = false;
+  std::vector<as_entity> map;
+  std::vector<uint8_t> map_orig;
+};
+
+namespace {
+
+as_status fail(as_ctx* c, as_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(expr)                                                                                   \
+  do {                                                                                             \
+    cudaError_t _e = (expr);                                                                       \
+    if (_e != cudaSuccess) return fail(c, AS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+#define CKS(expr)                                                      \
+  do {                                                                 \
+    as_status _s = (expr);                                             \
+    if (_s != AS_OK) return fail(c, _s, t_k_error_or(#expr));          \
+  } while (0)
+
+#define CKI(expr)                  \
+  do {                             \
+    as_status _s = (expr);         \
+    if (_s != AS_OK) return _s;    \
+  } while (0)
+
+std::string t_k_error_or(const char* what) {
+  const char* e = as_k_last_error();
+  return std::string(what) + ": " + (e ? e : "");
+}
+
+MapView map_view(as_ctx* c) {
+  MapView m;
+  m.slots = c->map_slots.as<MapSlot>();
+  m.mask = c->map_mask;
+  m.arena = c->map_arena.as<uint8_t>();
+  m.arena_used = c->map_ctr.as<unsigned long long>();
+  m.arena_cap = c->map_arena.cap;
+  m.n_entries = c->map_ctr.as<unsigned long long>() + 1;
+  return m;
+}
+
+as_status check_dev_error(as_ctx* c) {
+  DevError e{};
+  CK(cudaMemcpyAsync(&e, c->dev_err.p, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (e.code == 0) return AS_OK;
+  cudaMemsetAsync(c->dev_err.p, 0, sizeof(DevError), c->stream);
+  if (e.code == kErrTimeout)
+    return fail(c, AS_ERR_TIMEOUT, "a bounded device wait ran out (site " + std::to_string(e.where) + ")");
+  if (e.code == kErrCapacity)
+    return fail(c, AS_ERR_CAPACITY, "entity map full (site " + std::to_string(e.where) + "); raise map_capacity / map_arena_bytes");
+  return fail(c, AS_ERR_CUDA, "device error code " + std::to_string(e.code));
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+as_status build_vocab(as_ctx* c) {
+  const as_config& g = c->cfg;
+  uint64_t n = g.n_vocab_words;
+  uint64_t size = std::max<uint64_t>(1024, pow2_at_least(2 * n + 1));
+  std::vector<uint4> slots(size, make_uint4(0, 0, 0, 0));
+  for (uint64_t k = 0; k < n; ++k) {
+    uint32_t a = g.vocab_offsets[k], b = g.vocab_offsets[k + 1];
+    if (b <= a) return fail(c, AS_ERR_ARG, "vocab offsets must increase");
+    uint32_t len = b - a;
+    if (len < 2 || len > (uint32_t)kMaxPiece) return fail(c, AS_ERR_ARG, "vocab strings must be 2..12 bytes");
+    uint32_t w[3] = {0, 0, 0};
+    for (uint32_t i = 0; i < len; ++i) {
+      uint8_t ch = g.vocab_bytes[a + i];
+      bool an = (ch >= '0' && ch <= '9') || (ch >= 'A' && ch <= 'Z') || (ch >= 'a' && ch <= 'z');
+      if (!an) return fail(c, AS_ERR_ARG, "vocab strings must be [0-9A-Za-z]");
+      w[i >> 2] |= (uint32_t)ch << (8 * (i & 3));
+    }
+    uint32_t id = (uint32_t)(257 + k);
+    uint32_t h = vocab_hash(w[0], w[1], w[2], len) & (uint32_t)(size - 1);
+    while (true) {
+      uint4& s = slots[h];
+      if (s.w == 0) {
+        s = make_uint4(w[0], w[1], w[2], len | (id << 16));
+        break;
+      }
+      if ((s.w & 0xFFFFu) == len && s.x == w[0] && s.y == w[1] && s.z == w[2])
+        return fail(c, AS_ERR_ARG, "duplicate vocab string at id " + std::to_string(id));
+      h = (h + 1) & (uint32_t)(size - 1);
+    }
+  }
+  CKS(grow(c->vocab_slots, size * sizeof(uint4)));
+  CK(cudaMemcpy(c->vocab_slots.p, slots.data(), size * sizeof(uint4), cudaMemcpyHostToDevice));
+  c->vocab_mask = (uint32_t)(size - 1);
+  return AS_OK;
+}
+
+uint64_t expected_weights(const as_config& g) {
+  uint64_t d = g.d_model, f = g.d_ffn;
+  uint64_t per_layer = 3 * d * d + 3 * d + d * d + d + 2 * d + f * d + f + d * f + d + 2 * d;
+  return (uint64_t)g.vocab * d + (uint64_t)g.max_pos * d + 2 * d + g.n_layers * per_layer + (uint64_t)g.n_labels * d +
+         g.n_labels;
+}
+
+as_status load_weights(as_ctx* c) {
+  const as_config& g = c->cfg;
+  uint64_t n = g.weights_len;
+  CKS(grow(c->w32, n * 4));
+  CK(cudaMemcpy(c->w32.p, g.weights, n * 4, cudaMemcpyHostToDevice));
+  const float* p = c->w32.as<float>();
+  uint64_t d = g.d_model, f = g.d_ffn;
+  auto take = [&](uint64_t k) { const float* q = p; p += k; return q; };
+  c->tok_emb = take((uint64_t)g.vocab * d);
+  c->pos_emb = take((uint64_t)g.max_pos * d);
+  c->emb_g = take(d);
+  c->emb_b = take(d);
+  c->layers.resize(g.n_layers);
+  for (auto& L : c->layers) {
+    L.w_qkv = take(3 * d * d); L.b_qkv = take(3 * d);
+    L.w_o = take(d * d); L.b_o = take(d);
+    L.ln1_g = take(d); L.ln1_b = take(d);
+    L.w_1 = take(f * d); L.b_1 = take(f);
+    L.w_2 = take(d * f); L.b_2 = take(d);
+    L.ln2_g = take(d); L.ln2_b = take(d);
+  }
+  c->cls_w = take((uint64_t)g.n_labels * d);
+  c->cls_b = take(g.n_labels);
+  if (g.precision == AS_BF16) {
+    uint64_t per = 3 * d * d + d * d + f * d + d * f;
+    CKS(grow(c->w16, per * g.n_layers * 2));
+    __nv_bfloat16* q = c->w16.as<__nv_bfloat16>();
+    for (auto& L : c->layers) {
+      L.w_qkv16 = q; convert_f32_bf16(L.w_qkv, q, 3 * d * d, c->stream); q += 3 * d * d;
+      L.w_o16 = q; convert_f32_bf16(L.w_o, q, d * d, c->stream); q += d * d;
+      L.w_1_16 = q; convert_f32_bf16(L.w_1, q, f * d, c->stream); q += f * d;
+      L.w_2_16 = q; convert_f32_bf16(L.w_2, q, d * f, c->stream); q += d * f;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return AS_OK;
+}
+
+// ---------------------------------------------------------------- encoder
+
+as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, bool want_logits) {
+  const as_config& g = c->cfg;
+  const int64_t R = (int64_t)ch.rows;
+  const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
+  const int32_t ns = (int32_t)(ch.s1 - ch.s0);
+  cudaStream_t st = c->stream;
+  expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(),
+                                         c->row_own.as<uint8_t>(), c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>());
+  count_launch();
+  float* X32 = c->X32.as<float>();
+  float* Y32 = c->Y32.as<float>();
+  const bool bf = g.precision == AS_BF16;
+  __nv_bfloat16* X16 = bf ? c->X16.as<__nv_bfloat16>() : nullptr;
+  CKS(embed_ln(c->tok_ids.as<int32_t>(), c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(), c->tok_emb, c->pos_emb,
+               c->emb_g, c->emb_b, X32, X16, R, d, st));
+  DevError* err = c->dev_err.as<DevError>();
+  for (uint32_t l = 0; l < g.n_layers; ++l) {
+    const LayerW& L = c->layers[l];
+    const bool last = l + 1 == g.n_layers;
+    if (bf) {
+      __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
+      __nv_bfloat16* ATT = c->ATT.as<__nv_bfloat16>();
+      __nv_bfloat16* H = c->H.as<__nv_bfloat16>();
+      CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st));
+      CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+                         (int32_t)g.n_heads, st));
+      CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st));
+      CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
+      CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st));
+      CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st));
+    } else {
+      float* QKV = c->QKV.as<float>();
+      float* ATT = c->ATT.as<float>();
+      float* H = c->H.as<float>();
+      CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st));
+      CKS(attention_f32(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+                        (int32_t)g.n_heads, st));
+      CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st));
+      CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, nullptr, R, d, st));
+      CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st));
+      CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st));
+    }
+    if (!last) {
+      CKS(layernorm_rows(Y32, L.ln2_g, L.ln2_b, X32, X16, R, d, st));
+    } else {
+      CKS(layernorm_classify(Y32, L.ln2_g, L.ln2_b, c->cls_w, c->cls_b, (int32_t)g.n_labels, c->row_tok.as<int32_t>(),
+                             c->row_own.as<uint8_t>(), want_logits ? c->logits.as<float>() : nullptr,
+                             c->labels.as<uint8_t>(), R, d, st));
+    }
+  }
+  return AS_OK;
+}
+
+as_status ensure_encoder_buffers(as_ctx* c, uint64_t rows, uint64_t n_seq) {
+  const as_config& g = c->cfg;
+  const uint64_t d = g.d_model, f = g.d_ffn;
+  const bool bf = g.precision == AS_BF16;
+  const size_t act = bf ? 2 : 4;
+  CKS(grow(c->row_tok, rows * 4));
+  CKS(grow(c->row_pos, rows * 4));
+  CKS(grow(c->row_own, rows));
+  CKS(grow(c->seq_start, n_seq * 4));
+  CKS(grow(c->seq_len, n_seq * 4));
+  CKS(grow(c->X32, rows * d * 4));
+  CKS(grow(c->Y32, rows * d * 4));
+  if (bf) CKS(grow(c->X16, rows * d * 2));
+  CKS(grow(c->QKV, rows * 3 * d * act));
+  CKS(grow(c->ATT, rows * d * act));
+  CKS(grow(c->H, rows * f * act));
+  return AS_OK;
+}
+
+as_status validate_schema(as_ctx* c, const as_schema* s) {
+  if (!s) return fail(c, AS_ERR_ARG, "schema is NULL");
+  const as_config& g = c->cfg;
+  if (s->n_types < 1 || s->n_types > 62) return fail(c, AS_ERR_ARG, "n_types must be 1..62");
+  if (2 * s->n_types + 1 != g.n_labels)
+    return fail(c, AS_ERR_ARG, "n_labels must equal 2 * n_types + 1 (O, B-t, I-t)");
+  if (s->n_types < 4) return fail(c, AS_ERR_ARG, "the pattern recognizers need entity types 1..4");
+  if (!s->type_names) return fail(c, AS_ERR_ARG, "type_names is NULL");
+  for (uint32_t t = 0; t < s->n_types; ++t)
+    if (!s->type_names[t] || !s->type_names[t][0]) return fail(c, AS_ERR_ARG, "empty type name");
+  if (s->slug_hex_len > 64) return fail(c, AS_ERR_ARG, "slug_hex_len must be 0..64");
+  if (s->window) {
+    if (s->window > g.max_pos) return fail(c, AS_ERR_ARG, "window exceeds max_pos");
+    if (s->stride == 0 || s->stride > s->window || (s->window - s->stride) % 2)
+      return fail(c, AS_ERR_ARG, "need 0 < stride <= window and window - stride even");
+  }
+  return AS_OK;
+}
+
+as_status set_key(as_ctx* c, const uint8_t* key, size_t key_len) {
+  if (!key && key_len) return fail(c, AS_ERR_ARG, "key is NULL");
+  std::vector<uint8_t> k(key, key + key_len);
+  if (c->key_set && k == c->key) return AS_OK;
+  uint64_t n_entries = 0;
+  CK(cudaMemcpyAsync(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->key_set && n_entries > 0)
+    return fail(c, AS_ERR_STATE, "key differs from the key of the non-empty entity map (clear the map first)");
+  c->key = k;
+  c->key_set = true;
+  CKS(grow(c->key_dev, key_len + 1));
+  if (key_len) CK(cudaMemcpyAsync(c->key_dev.p, key, key_len, cudaMemcpyHostToDevice, c->stream));
+  CKS(grow(c->key_state, 16 * 4));
+  launch_hmac_key_setup(c->key_dev.as<uint8_t>(), (uint32_t)key_len, c->key_state.as<uint32_t>(), c->stream);
+  CK(cudaStreamSynchronize(c->stream));
+  return AS_OK;
+}
+
+template <typename T>
+as_status d2h_vec(as_ctx* c, std::vector<T>& v, const void* src, uint64_t n) {
+  v.resize(n);
+  if (n) CK(cudaMemcpyAsync(v.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  return AS_OK;
+}
+
+as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch, const uint8_t* key, size_t key_len,
+                         as_output** out) {
+  const as_config& g = c->cfg;
+  cudaStream_t st = c->stream;
+  if (!rec || !out) return fail(c, AS_ERR_ARG, "records / out is NULL");
+  *out = nullptr;
+  CKI(validate_schema(c, sch));
+  CKI(set_key(c, key, key_len));
+  c->slug_len = sch->slug_hex_len;
+  const uint64_t n = rec->n_records;
+  if (n > 0 && (!rec->offsets)) return fail(c, AS_ERR_ARG, "offsets is NULL");
+  // ---- inputs
+  uint64_t N = 0;
+  std::vector<uint64_t> h_off_in;
+  if (n > 0) {
+    if (rec->on_device) {
+      CK(cudaMemcpyAsync(&N, rec->offsets + n, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      N = rec->offsets[n];
+      if (rec->offsets[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
+      for (uint64_t r = 0; r < n; ++r)
+        if (rec->offsets[r + 1] < rec->offsets[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
+    }
+  }
+  if (N >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "a call takes less than 4 GiB of text");
+  if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
+  const uint8_t* d_bytes;
+  const uint64_t* d_off;
+  CKS(grow(c->in_off, (n + 1) * 8));
+  if (rec->on_device) {
+    d_bytes = rec->bytes;
+    d_off = rec->offsets;
+  } else {
+    CKS(grow(c->in_bytes, N + 16));
+    if (N) CK(cudaMemcpyAsync(c->in_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+    uint64_t zero = 0;
+    if (n) CK(cudaMemcpyAsync(c->in_off.p, rec->offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemcpyAsync(c->in_off.p, &zero, 8, cudaMemcpyHostToDevice, st));
+    d_bytes = c->in_bytes.as<uint8_t>();
+    d_off = c->in_off.as<uint64_t>();
+  }
+  if (n == 0) {
+    static const uint64_t zero_off = 0;
+    CK(cudaMemcpyAsync(c->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
+    d_off = c->in_off.as<uint64_t>();
+  }
+  const uint32_t N32 = (uint32_t)N;
+  const uint64_t launches0 = g_launches.load();
+  ++c->call_id;
+  const uint32_t call_id = c->call_id;
+  // ---- tokenizer + recognizers
+  CKS(grow(c->counters, 64));
+  uint32_t* cnt = c->counters.as<uint32_t>();  // 0 T, 1 n_rx, 2 n_ner, 3 n_nerk, 4 n_rxk, 5 n_fin
+  CK(cudaMemsetAsync(cnt, 0, 64, st));
+  CKS(grow(c->rs_bits, ((size_t)N / 32 + 1) * 4));
+  CKS(grow(c->tok_at, N * 2));
+  CKS(grow(c->pos_b, (N + 1) * 4));
+  CKS(grow(c->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(N + 1, 1) * 2) + 16) * 8));
+  CKS(grow(c->tok_ids, N * 4));
+  CKS(grow(c->tok_off, N * 4));
+  CKS(grow(c->tok_len, N * 4));
+  CKS(grow(c->rec_tok, (n + 1) * 8));
+  VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask};
+  launch_mark_record_starts(d_off, n, N32, c->rs_bits.as<uint32_t>(), st);
+  launch_tokenize_mark(d_bytes, N32, c->rs_bits.as<uint32_t>(), vt, c->tok_at.as<uint16_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU16{c->tok_at.as<uint16_t>()}, N, c->pos_b.as<uint32_t>(), cnt + 0,
+                           c->scan_tiles.as<uint32_t>(), st);
+  launch_tokenize_emit(c->tok_at.as<uint16_t>(), c->pos_b.as<uint32_t>(), N32, c->tok_ids.as<int32_t>(),
+                       c->tok_off.as<uint32_t>(), st);
+  launch_record_token_offsets(d_off, n, c->pos_b.as<uint32_t>(), N32, cnt + 0, c->rec_tok.as<uint64_t>(), st);
+  // recognizers (pos_b reused after the token emit above)
+  CKS(grow(c->rx_len_b, N * 4));
+  CKS(grow(c->rx_type_b, N + 16));
+  launch_recognize_mark(d_bytes, N32, c->rs_bits.as<uint32_t>(), c->rx_len_b.as<uint32_t>(), c->rx_type_b.as<uint8_t>(),
+                        st);
+  CKS(grow(c->rx_pos, (N + 1) * 4));
+  exclusive_scan<uint32_t>(NonZeroU8{c->rx_type_b.as<uint8_t>()}, N, c->rx_pos.as<uint32_t>(), cnt + 1,
+                           c->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(c->rx_s, (N / 2 + 2) * 4));
+  CKS(grow(c->rx_l, (N / 2 + 2) * 4));
+  CKS(grow(c->rx_t, N / 2 + 2));
+  launch_recognize_emit(c->rx_len_b.as<uint32_t>(), c->rx_type_b.as<uint8_t>(), c->rx_pos.as<uint32_t>(), N32,
+                        c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), c->rx_t.as<uint8_t>(), st);
+  // ---- sync 1: token counts
+  uint32_t h_cnt[2] = {0, 0};
+  CK(cudaMemcpyAsync(h_cnt, cnt, 8, cudaMemcpyDeviceToHost, st));
+  std::vector<uint64_t>& rt = c->h_rec_tok;
+  rt.resize(n + 1);
+  CK(cudaMemcpyAsync(rt.data(), c->rec_tok.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t T = h_cnt[0], n_rx = h_cnt[1];
+  launch_token_lengths(c->tok_off.as<uint32_t>(), (uint32_t)T, N32, c->tok_len.as<uint32_t>(), st);
+  // ---- sequences (windows) and encoder batches
+  const uint32_t W = sch->window, S = sch->stride;
+  std::vector<SeqDesc> seqs;
+  seqs.reserve(n);
+  uint64_t enc_tokens = 0;
+  for (uint64_t r = 0; r < n; ++r) {
+    const uint64_t a = rt[r], L = rt[r + 1] - rt[r];
+    if (L == 0) continue;
+    if (W == 0 || L <= W) {
+      if (L > g.max_pos)
+        return fail(c, AS_ERR_TOO_LONG, "record " + std::to_string(r) + " has " + std::to_string(L) +
+                                            " tokens, more than max_pos without windows");
+      seqs.push_back(SeqDesc{(uint32_t)a, (uint32_t)L, 0, 0, (uint16_t)L});
+      enc_tokens += L;
+      continue;
+    }
+    const uint32_t half = (W - S) / 2;
+    std::vector<uint64_t> starts{0};
+    while (starts.back() + W < L) starts.push_back(starts.back() + S);
+    for (size_t w = 0; w < starts.size(); ++w) {
+      const uint64_t s0 = starts[w];
+      const uint32_t len = (uint32_t)std::min<uint64_t>(W, L - s0);
+      const uint16_t lo = w == 0 ? 0 : (uint16_t)half;
+      const uint16_t hi = w + 1 == starts.size() ? (uint16_t)len : (uint16_t)(S + half);
+      seqs.push_back(SeqDesc{(uint32_t)(a + s0), len, 0, lo, hi});
+      enc_tokens += len;
+    }
+  }
+  // batches: whole sequences up to max_chunk_tokens rows (PACKED), or all
+  // windows of one record (PER_RECORD: one record per launch sequence)
+  std::vector<Chunk> chunks;
+  if (g.mode == AS_MODE_PER_RECORD) {
+    uint64_t i = 0;
+    for (uint64_t r = 0; r < n && i < seqs.size(); ++r) {
+      const uint64_t a = rt[r], b = rt[r + 1];
+      if (a == b) continue;
+      Chunk ch{i, i, 0, 0};
+      while (i < seqs.size() && seqs[i].src_tok >= a && seqs[i].src_tok < b) {
+        seqs[i].row = (uint32_t)ch.rows;
+        ch.rows += seqs[i].len;
+        ch.max_len = std::max(ch.max_len, seqs[i].len);
+        ch.s1 = ++i;
+      }
+      chunks.push_back(ch);
+    }
+  } else {
+    const uint64_t cap = g.max_chunk_tokens ? g.max_chunk_tokens : (1ull << 19);
+    Chunk cur{0, 0, 0, 0};
+    for (uint64_t i = 0; i < seqs.size(); ++i) {
+      if (cur.rows > 0 && cur.rows + seqs[i].len > cap) {
+        chunks.push_back(cur);
+        cur = Chunk{i, i, 0, 0};
+      }
+      seqs[i].row = (uint32_t)cur.rows;
+      cur.s1 = i + 1;
+      cur.rows += seqs[i].len;
+      cur.max_len = std::max(cur.max_len, seqs[i].len);
+    }
+    if (cur.rows) chunks.push_back(cur);
+  }
+  uint64_t max_rows = 0, max_seqs = 0;
+  for (auto& ch : chunks) {
+    max_rows = std::max(max_rows, ch.rows);
+    max_seqs = std::max<uint64_t>(max_seqs, ch.s1 - ch.s0);
+  }
+  CKS(grow(c->seqs, std::max<size_t>(1, seqs.size()) * sizeof(SeqDesc)));
+  if (!seqs.empty()) CK(cudaMemcpyAsync(c->seqs.p, seqs.data(), seqs.size() * sizeof(SeqDesc), cudaMemcpyHostToDevice, st));
+  CKI(ensure_encoder_buffers(c, std::max<uint64_t>(max_rows, 1), std::max<uint64_t>(max_seqs, 1)));
+  const bool want_logits = g.keep_trace != 0;
+  CKS(grow(c->labels, T + 16));
+  if (want_logits) CKS(grow(c->logits, (T + 1) * g.n_labels * 4));
+  CK(cudaMemsetAsync(c->labels.p, 0, T + 16, st));
+  for (const Chunk& ch : chunks) CKI(run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), want_logits));
+  // ---- BIO decode
+  CKS(grow(c->tok_flags, T + 16));
+  CK(cudaMemsetAsync(c->tok_flags.p, 0, T + 1, st));
+  launch_token_flags(c->rec_tok.as<uint64_t>(), n, c->tok_flags.as<uint8_t>(), st);
+  CKS(grow(c->bio_start, T + 16));
+  CKS(grow(c->bio_end, T + 16));
+  CKS(grow(c->pos_t, (T + 1) * 4));
+  launch_bio_mark(c->labels.as<uint8_t>(), c->tok_flags.as<uint8_t>(), (uint32_t)T, c->bio_start.as<uint8_t>(),
+                  c->bio_end.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{c->bio_start.as<uint8_t>()}, T, c->pos_t.as<uint32_t>(), cnt + 2,
+                           c->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(c->ner_s, (T + 1) * 4));
+  CKS(grow(c->ner_l, (T + 1) * 4));
+  CKS(grow(c->ner_t, T + 16));
+  launch_bio_emit(c->labels.as<uint8_t>(), c->bio_start.as<uint8_t>(), c->bio_end.as<uint8_t>(), c->pos_t.as<uint32_t>(),
+                  (uint32_t)T, c->tok_off.as<uint32_t>(), c->tok_len.as<uint32_t>(), d_bytes, c->ner_s.as<uint32_t>(),
+                  c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), st);
+  launch_bio_to_bytes(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), cnt + 2, (uint32_t)T, c->tok_off.as<uint32_t>(),
+                      c->tok_len.as<uint32_t>(), d_bytes, st);
+  // ---- overlap rule + preserve
+  const uint32_t ner_cap = (uint32_t)T, rx_cap = (uint32_t)n_rx;
+  CKS(grow(c->pos_k, (T + n_rx + 2) * 4));
+  DBuf& keep = c->keep;
+  CKS(grow(keep, T + n_rx + 16));
+  launch_ner_keep(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), cnt + 2, ner_cap,
+                  c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), cnt + 1, sch->preserve_mask, keep.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, ner_cap, c->pos_k.as<uint32_t>(), cnt + 3,
+                           c->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(c->nk_s, (T + 1) * 4));
+  CKS(grow(c->nk_l, (T + 1) * 4));
+  CKS(grow(c->nk_t, T + 16));
+  launch_compact_spans(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), keep.as<uint8_t>(),
+                       c->pos_k.as<uint32_t>(), cnt + 2, ner_cap, c->nk_s.as<uint32_t>(), c->nk_l.as<uint32_t>(),
+                       c->nk_t.as<uint8_t>(), st);
+  launch_rx_keep(c->rx_t.as<uint8_t>(), cnt + 1, rx_cap, sch->preserve_mask, keep.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, rx_cap, c->pos_k.as<uint32_t>(), cnt + 4,
+                           c->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(c->rk_s, (n_rx + 1) * 4));
+  CKS(grow(c->rk_l, (n_rx + 1) * 4));
+  CKS(grow(c->rk_t, n_rx + 16));
+  launch_compact_spans(c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), c->rx_t.as<uint8_t>(), keep.as<uint8_t>(),
+                       c->pos_k.as<uint32_t>(), cnt + 1, rx_cap, c->rk_s.as<uint32_t>(), c->rk_l.as<uint32_t>(),
+                       c->rk_t.as<uint8_t>(), st);
+  const uint32_t fin_cap = ner_cap + rx_cap;
+  CKS(grow(c->fin_s, (fin_cap + 1) * 4));
+  CKS(grow(c->fin_l, (fin_cap + 1) * 4));
+  CKS(grow(c->fin_t, fin_cap + 16));
+  launch_merge_spans(c->rk_s.as<uint32_t>(), c->rk_l.as<uint32_t>(), c->rk_t.as<uint8_t>(), cnt + 4, rx_cap,
+                     c->nk_s.as<uint32_t>(), c->nk_l.as<uint32_t>(), c->nk_t.as<uint8_t>(), cnt + 3, ner_cap,
+                     c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), c->fin_t.as<uint8_t>(), st);
+  // the HMAC / map / substitution kernels read the final span count from cnt[5]
+  sum_kept_kernel<<<1, 32, 0, st>>>(cnt);
+  count_launch();
+  // ---- HMAC + map
+  CKS(grow(c->digests, (size_t)(fin_cap + 1) * 32));
+  launch_hmac_spans(d_bytes, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), cnt + 5, fin_cap,
+                    c->key_state.as<uint32_t>(), c->digests.as<uint32_t>(), st);
+  launch_map_insert_spans(map_view(c), d_bytes, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(),
+                          c->fin_t.as<uint8_t>(), c->digests.as<uint32_t>(), cnt + 5, fin_cap, d_off, n,
+                          c->records_done, call_id, c->dev_err.as<DevError>(), st);
+  // ---- substitution
+  {
+    std::vector<uint32_t> noff(sch->n_types + 2, 0), nlen(sch->n_types + 1, 0);
+    std::string all;
+    for (uint32_t t = 1; t <= sch->n_types; ++t) {
+      noff[t] = (uint32_t)all.size();
+      all += sch->type_names[t - 1];
+      noff[t + 1] = (uint32_t)all.size();
+      nlen[t] = noff[t + 1] - noff[t];
+    }
+    CKS(grow(c->names, all.size() + 16));
+    CKS(grow(c->name_off, noff.size() * 4));
+    CKS(grow(c->name_len, nlen.size() * 4));
+    CK(cudaMemcpyAsync(c->names.p, all.data(), all.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->name_off.p, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+  }
+  CKS(grow(c->delta, (size_t)(fin_cap + 1) * 8));
+  CKS(grow(c->shift, (size_t)(fin_cap + 1) * 8));
+  CKS(grow(c->delta_total, 16));
+  launch_sub_delta(c->fin_l.as<uint32_t>(), c->fin_t.as<uint8_t>(), cnt + 5, fin_cap + 1, c->name_len.as<uint32_t>(),
+                   sch->slug_hex_len, c->delta.as<int64_t>(), st);
+  exclusive_scan<int64_t>(LoadI64{c->delta.as<int64_t>()}, fin_cap + 1, c->shift.as<int64_t>(),
+                          c->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(c->scan_tiles.p), st);
+  // ---- sync 2: output size and counts
+  int64_t total_delta = 0;
+  uint32_t h_cnt2[6];
+  CK(cudaMemcpyAsync(&total_delta, c->delta_total.p, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_cnt2, cnt, 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t out_size = (uint64_t)((int64_t)N + total_delta);
+  as_output* o = new as_output();
+  o->ctx = c;
+  o->call_id = call_id;
+  o->on_device = rec->on_device;
+  o->n = n;
+  void* d_out = nullptr;
+  uint64_t* d_out_off = nullptr;
+  if (cudaMallocAsync(&d_out, out_size + 16, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&d_out_off), (n + 1) * 8, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_out) cudaFreeAsync(d_out, st);
+    delete o;
+    return fail(c, AS_ERR_OOM, "output allocation failed");
+  }
+  launch_sub_copy(d_bytes, N32, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), cnt + 5, c->shift.as<int64_t>(),
+                  reinterpret_cast<uint8_t*>(d_out), st);
+  launch_sub_replace(c->fin_s.as<uint32_t>(), c->fin_t.as<uint8_t>(), cnt + 5, fin_cap, c->shift.as<int64_t>(),
+                     c->digests.as<uint32_t>(), c->names.as<char>(), c->name_off.as<uint32_t>(), sch->slug_hex_len,
+                     reinterpret_cast<uint8_t*>(d_out), st);
+  launch_sub_offsets(d_off, n, c->fin_s.as<uint32_t>(), cnt + 5, c->shift.as<int64_t>(), d_out_off, st);
+  if (rec->on_device) {
+    o->d_bytes = d_out;
+    o->d_off = d_out_off;
+  } else {
+    o->h_bytes.resize(out_size);
+    o->h_off.resize(n + 1);
+    cudaMemcpyAsync(o->h_bytes.data(), d_out, out_size, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(o->h_off.data(), d_out_off, (n + 1) * 8, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_out, st);
+    cudaFreeAsync(d_out_off, st);
+  }
+  // ---- trace for as_debug_trace
+  c->last_n = n;
+  c->last_T = T;
+  c->last_nrx = n_rx;
+  c->last_nfin = h_cnt2[5];
+  c->last_logits = want_logits;
+  if (g.keep_trace) {
+    CKS(d2h_vec(c, c->h_tok_ids, c->tok_ids.p, T));
+    CKS(d2h_vec(c, c->h_tok_off, c->tok_off.p, T));
+    CKS(d2h_vec(c, c->h_tok_len, c->tok_len.p, T));
+    CKS(d2h_vec(c, c->h_rx_s, c->rx_s.p, n_rx));
+    CKS(d2h_vec(c, c->h_rx_l, c->rx_l.p, n_rx));
+    CKS(d2h_vec(c, c->h_rx_t, c->rx_t.p, n_rx));
+    CKS(d2h_vec(c, c->h_labels, c->labels.p, T));
+    CKS(d2h_vec(c, c->h_logits, c->logits.p, T * g.n_labels));
+    CKS(d2h_vec(c, c->h_fin_s, c->fin_s.p, h_cnt2[5]));
+    CKS(d2h_vec(c, c->h_fin_l, c->fin_l.p, h_cnt2[5]));
+    CKS(d2h_vec(c, c->h_fin_t, c->fin_t.p, h_cnt2[5]));
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    as_output_free(o);
+    return fail(c, AS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  }
+  as_status ds = check_dev_error(c);
+  if (ds != AS_OK) {
+    as_output_free(o);
+    return ds;
+  }
+  uint64_t n_entries = 0;
+  cudaMemcpy(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost);
+  as_stats& s = o->stats;
+  s.n_records = n;
+  s.n_bytes = N;
+  s.n_tokens = T;
+  s.n_encoded_tokens = enc_tokens;
+  s.n_sequences = seqs.size();
+  s.n_regex_spans = n_rx;
+  s.n_ner_spans = h_cnt2[2];
+  s.n_final_spans = h_cnt2[5];
+  s.n_out_bytes = out_size;
+  s.n_map_entries = n_entries;
+  s.kernel_launches = g_launches.load() - launches0;
+  c->records_done += n;
+  *out = o;
+  return AS_OK;
+}
+
+as_status map_collect(as_ctx* c, uint32_t call_id, std::vector<as_entity>& ents, std::vector<uint8_t>& orig) {
+  cudaStream_t st = c->stream;
+  const uint64_t slots = c->map_mask + 1;
+  DBuf keep, pos, idx, tiles, total;
+  auto cleanup = [&]() { release(keep); release(pos); release(idx); release(tiles); release(total); };
+  if (grow(keep, slots) || grow(pos, slots * 4) || grow(tiles, (scan_tiles_needed(slots) + 4) * 4) ||
+      grow(total, 16)) {
+    cleanup();
+    return fail(c, AS_ERR_OOM, "map export scratch");
+  }
+  MapView m = map_view(c);
+  launch_map_select(m, call_id, keep.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, slots, pos.as<uint32_t>(), total.as<uint32_t>(),
+                           tiles.as<uint32_t>(), st);
+  uint32_t cnt = 0;
+  cudaMemcpyAsync(&cnt, total.p, 4, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (grow(idx, (size_t)(cnt + 1) * 4)) { cleanup(); return fail(c, AS_ERR_OOM, "map export scratch"); }
+  launch_map_gather(m, keep.as<uint8_t>(), pos.as<uint32_t>(), idx.as<uint32_t>(), st);
+  uint64_t used = 0;
+  cudaMemcpyAsync(&used, c->map_ctr.p, 8, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  std::vector<MapSlot> hs(cnt);
+  DBuf gathered;
+  if (grow(gathered, (size_t)(cnt + 1) * sizeof(MapSlot))) { cleanup(); return fail(c, AS_ERR_OOM, "map export scratch"); }
+  launch_map_gather_slots(m, idx.as<uint32_t>(), cnt, gathered.as<MapSlot>(), st);
+  if (cnt) cudaMemcpyAsync(hs.data(), gathered.p, cnt * sizeof(MapSlot), cudaMemcpyDeviceToHost, st);
+  std::vector<uint8_t> arena(used);
+  if (used) cudaMemcpyAsync(arena.data(), c->map_arena.p, used, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  release(gathered);
+  if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, std::string("map export: ") + cudaGetErrorString(e));
+  std::vector<uint32_t> order(cnt);
+  for (uint32_t i = 0; i < cnt; ++i) order[i] = i;
+  auto bytes_of = [&](const MapSlot& s) { return arena.data() + s.arena_off; };
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    const MapSlot &x = hs[a], &y = hs[b];
+    if (x.type != y.type) return x.type < y.type;
+    int r = memcmp(bytes_of(x), bytes_of(y), std::min(x.len, y.len));
+    if (r != 0) return r < 0;
+    return x.len < y.len;
+  });
+  uint64_t total_len = 0;
+  for (auto& s : hs) total_len += s.len;
+  orig.resize(total_len + 1);
+  ents.resize(cnt);
+  uint64_t p = 0;
+  static const char* hex = "0123456789abcdef";
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const MapSlot& s = hs[order[i]];
+    as_entity& en = ents[i];
+    memset(&en, 0, sizeof(en));
+    en.type = s.type;
+    en.original_len = s.len;
+    if (s.arena_off != ~0ull) memcpy(orig.data() + p, bytes_of(s), s.len);
+    en.original = nullptr;
+    for (int k = 0; k < 64; ++k) en.full_hash[k] = hex[(s.digest[k >> 3] >> (28 - 4 * (k & 7))) & 15];
+    en.full_hash[64] = 0;
+    memcpy(en.slug, en.full_hash, c->slug_len);
+    en.slug[c->slug_len] = 0;
+    en.first_seen = s.first_seen;
+    en.last_seen = s.last_seen;
+    en.count = s.count;
+    reinterpret_cast<uint64_t&>(en.original) = p;  // fixed up by the caller
+    p += s.len;
+  }
+  return AS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* as_k_last_error(void) { return as::t_k_error.c_str(); }
+
+const char* as_version(void) { return "anonshield-b300 0.1 (sm_103a)"; }
+
+const char* as_last_error(const as_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+void as_free(void* p) { free(p); }
+
+as_status as_create(const as_config* cfg, as_ctx** out) {
+  if (!cfg || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  as_ctx* c = new as_ctx();
+  c->cfg = *cfg;
+  const as_config& g = c->cfg;
+  auto bail = [&](as_status s) {
+    std::string m = c->err;
+    as_destroy(c);
+    set_k_error(m);
+    return s;
+  };
+  if (g.vocab < 258 || g.n_vocab_words != g.vocab - 257 || !g.vocab_bytes || !g.vocab_offsets) {
+    c->err = "vocab must be > 257 with vocab - 257 strings";
+    return bail(AS_ERR_ARG);
+  }
+  if (g.d_model == 0 || g.n_heads == 0 || g.d_model != g.n_heads * 64) {
+    c->err = "head dim must be 64 (d_model = 64 * n_heads)";
+    return bail(AS_ERR_UNSUPPORTED);
+  }
+  if (g.d_model % 128 || g.d_model > 1024 || g.d_ffn % 128 || g.d_ffn == 0 || g.n_layers == 0 || g.n_labels < 9 ||
+      g.n_labels > 32 || g.max_pos == 0 || g.max_pos > 4096) {
+    c->err = "unsupported dimensions (d_model multiple of 128 up to 1024, d_ffn multiple of 128, 9..32 labels)";
+    return bail(AS_ERR_UNSUPPORTED);
+  }
+  if (g.precision != AS_FP32 && g.precision != AS_BF16) {
+    c->err = "precision must be AS_FP32 or AS_BF16";
+    return bail(AS_ERR_UNSUPPORTED);
+  }
+  if (g.mode != AS_MODE_PACKED && g.mode != AS_MODE_PER_RECORD) {
+    c->err = "mode must be AS_MODE_PACKED or AS_MODE_PER_RECORD";
+    return bail(AS_ERR_ARG);
+  }
+  if (!g.weights || g.weights_len != expected_weights(g)) {
+    c->err = "weights_len " + std::to_string(g.weights_len) + " != expected " + std::to_string(expected_weights(g));
+    return bail(AS_ERR_ARG);
+  }
+  c->device = g.device;
+  if (cudaSetDevice(g.device) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaSetDevice failed";
+    return bail(AS_ERR_CUDA);
+  }
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->err = "stream creation failed";
+    return bail(AS_ERR_CUDA);
+  }
+  sha256_init_constants();
+  as_status s;
+  if ((s = build_vocab(c)) != AS_OK) return bail(s);
+  if ((s = load_weights(c)) != AS_OK) return bail(s);
+  uint64_t cap = g.map_capacity ? pow2_at_least(g.map_capacity) : (1ull << 22);
+  uint64_t arena = g.map_arena_bytes ? g.map_arena_bytes : (256ull << 20);
+  if (grow(c->map_slots, cap * sizeof(MapSlot)) || grow(c->map_arena, arena) || grow(c->map_ctr, 16) ||
+      grow(c->dev_err, sizeof(DevError))) {
+    c->err = "map allocation failed";
+    return bail(AS_ERR_OOM);
+  }
+  c->map_arena.cap = arena;
+  c->map_mask = cap - 1;
+  cudaMemsetAsync(c->dev_err.p, 0, sizeof(DevError), c->stream);
+  launch_map_init(map_view(c), c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    c->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
+    return bail(AS_ERR_CUDA);
+  }
+  *out = c;
+  return AS_OK;
+}
+
+void as_destroy(as_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DBuf* all[] = {&c->w32, &c->w16, &c->vocab_slots, &c->map_slots, &c->map_arena, &c->map_ctr, &c->key_dev,
+                 &c->key_state, &c->dev_err, &c->in_bytes, &c->in_off, &c->rs_bits, &c->tok_at, &c->pos_b,
+                 &c->scan_tiles, &c->counters, &c->delta_total, &c->tok_ids, &c->tok_off, &c->tok_len, &c->rec_tok,
+                 &c->rx_len_b, &c->rx_type_b, &c->rx_s, &c->rx_l, &c->rx_t, &c->labels, &c->logits, &c->tok_flags,
+                 &c->rx_pos, &c->bio_start, &c->bio_end, &c->pos_t, &c->ner_s, &c->ner_l, &c->ner_t, &c->keep, &c->pos_k,
+                 &c->nk_s, &c->nk_l, &c->nk_t, &c->rk_s, &c->rk_l, &c->rk_t, &c->fin_s, &c->fin_l, &c->fin_t,
+                 &c->digests, &c->delta, &c->shift, &c->names, &c->name_off, &c->name_len, &c->seqs, &c->row_tok,
+                 &c->row_pos, &c->row_own, &c->seq_start, &c->seq_len, &c->X32, &c->X16, &c->QKV, &c->ATT, &c->Y32,
+                 &c->H};
+  for (DBuf* b : all) release(*b);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+as_status as_anonymize(as_ctx* ctx, const as_records* records, const as_schema* schema, const uint8_t* key,
+                       size_t key_len, as_output** out) {
+  if (!ctx) return AS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, AS_ERR_CUDA, "cudaSetDevice failed");
+  as_status s = anonymize_impl(ctx, records, schema, key, key_len, out);
+  if (s == AS_ERR_CUDA) cudaGetLastError();
+  return s;
+}
+
+as_status as_output_records(const as_output* o, const uint8_t** bytes, const uint64_t** offsets, uint64_t* n,
+                            uint32_t* on_device) {
+  if (!o || !bytes || !offsets || !n) return AS_ERR_ARG;
+  if (o->on_device) {
+    *bytes = reinterpret_cast<const uint8_t*>(o->d_bytes);
+    *offsets = o->d_off;
+  } else {
+    *bytes = o->h_bytes.data();
+    *offsets = o->h_off.data();
+  }
+  *n = o->n;
+  if (on_device) *on_device = o->on_device;
+  return AS_OK;
+}
+
+as_status as_output_stats(const as_output* o, as_stats* s) {
+  if (!o || !s) return AS_ERR_ARG;
+  *s = o->stats;
+  return AS_OK;
+}
+
+as_status as_output_map(as_output* o, const as_entity** entries, uint64_t* n) {
+  if (!o || !entries || !n) return AS_ERR_ARG;
+  if (!o->map_loaded) {
+    as_ctx* c = o->ctx;
+    cudaSetDevice(c->device);
+    as_status s = map_collect(c, o->call_id, o->map, o->map_orig);
+    if (s != AS_OK) return s;
+    for (auto& e : o->map) e.original = o->map_orig.data() + reinterpret_cast<uint64_t&>(e.original);
+    o->map_loaded = true;
+  }
+  *entries = o->map.data();
+  *n = o->map.size();
+  return AS_OK;
+}
+
+void as_output_free(as_output* o) {
+  if (!o) return;
+  if (o->d_bytes || o->d_off) {
+    cudaSetDevice(o->ctx->device);
+    cudaStreamSynchronize(o->ctx->stream);
+    if (o->d_bytes) cudaFree(o->d_bytes);
+    if (o->d_off) cudaFree(o->d_off);
+  }
+  delete o;
+}
+
+as_status as_map_export(as_ctx* c, as_entity** entries, uint64_t* n) {
+  if (!c || !entries || !n) return AS_ERR_ARG;
+  cudaSetDevice(c->device);
+  std::vector<as_entity> ents;
+  std::vector<uint8_t> orig;
+  as_status s = map_collect(c, 0, ents, orig);
+  if (s != AS_OK) return s;
+  size_t bytes = ents.size() * sizeof(as_entity) + orig.size() + 1;
+  uint8_t* blob = static_cast<uint8_t*>(malloc(bytes));
+  if (!blob) return fail(c, AS_ERR_OOM, "host allocation");
+  as_entity* e = reinterpret_cast<as_entity*>(blob);
+  uint8_t* o = blob + ents.size() * sizeof(as_entity);
+  if (!orig.empty()) memcpy(o, orig.data(), orig.size());
+  for (size_t i = 0; i < ents.size(); ++i) {
+    e[i] = ents[i];
+    e[i].original = o + reinterpret_cast<uint64_t&>(ents[i].original);
+  }
+  *entries = e;
+  *n = ents.size();
+  return AS_OK;
+}
+
+as_status as_map_import(as_ctx* c, const uint8_t* key, size_t key_len, const as_entity* entries, uint64_t n) {
+  if (!c || (n && !entries)) return AS_ERR_ARG;
+  cudaSetDevice(c->device);
+  as_status ks = set_key(c, key, key_len);
+  if (ks != AS_OK) return ks;
+  if (n == 0) return AS_OK;
+  std::vector<uint8_t> orig;
+  std::vector<uint64_t> off(n), first(n), last(n), count(n);
+  std::vector<uint32_t> len(n), type(n), dig(n * 8);
+  for (uint64_t i = 0; i < n; ++i) {
+    const as_entity& e = entries[i];
+    off[i] = orig.size();
+    orig.insert(orig.end(), e.original, e.original + e.original_len);
+    len[i] = e.original_len;
+    type[i] = e.type;
+    first[i] = e.first_seen;
+    last[i] = e.last_seen;
+    count[i] = e.count;
+    for (int k = 0; k < 8; ++k) {
+      uint32_t v = 0;
+      for (int j = 0; j < 8; ++j) {
+        char ch = e.full_hash[k * 8 + j];
+        uint32_t nib = (ch >= '0' && ch <= '9') ? ch - '0' : (ch >= 'a' && ch <= 'f') ? ch - 'a' + 10 : 99;
+        if (nib > 15) return fail(c, AS_ERR_ARG, "full_hash must be 64 lower-case hex characters");
+        v = (v << 4) | nib;
+      }
+      dig[i * 8 + k] = v;
+    }
+  }
+  DBuf b_orig, b_off, b_len, b_type, b_dig, b_first, b_last, b_count;
+  DBuf* bs[] = {&b_orig, &b_off, &b_len, &b_type, &b_dig, &b_first, &b_last, &b_count};
+  auto cleanup = [&]() { for (DBuf* b : bs) release(*b); };
+  if (grow(b_orig, orig.size() + 1) || grow(b_off, n * 8) || grow(b_len, n * 4) || grow(b_type, n * 4) ||
+      grow(b_dig, n * 32) || grow(b_first, n * 8) || grow(b_last, n * 8) || grow(b_count, n * 8)) {
+    cleanup();
+    return fail(c, AS_ERR_OOM, "import staging");
+  }
+  cudaStream_t st = c->stream;
+  if (!orig.empty()) cudaMemcpyAsync(b_orig.p, orig.data(), orig.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_off.p, off.data(), n * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_len.p, len.data(), n * 4, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_type.p, type.data(), n * 4, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_dig.p, dig.data(), n * 32, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_first.p, first.data(), n * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_last.p, last.data(), n * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b_count.p, count.data(), n * 8, cudaMemcpyHostToDevice, st);
+  ++c->call_id;
+  launch_map_import(map_view(c), b_orig.as<uint8_t>(), b_off.as<uint64_t>(), b_len.as<uint32_t>(),
+                    b_type.as<uint32_t>(), b_dig.as<uint32_t>(), b_first.as<uint64_t>(), b_last.as<uint64_t>(),
+                    b_count.as<uint64_t>(), n, c->call_id, c->dev_err.as<DevError>(), st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
+  return check_dev_error(c);
+}
+
+as_status as_map_clear(as_ctx* c) {
+  if (!c) return AS_ERR_ARG;
+  cudaSetDevice(c->device);
+  launch_map_init(map_view(c), c->stream);
+  c->key_set = false;
+  c->key.clear();
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, AS_ERR_CUDA, "map clear");
+  return AS_OK;
+}
+
+as_status as_debug_trace(as_ctx* c, as_trace* t) {
+  if (!c || !t) return AS_ERR_ARG;
+  if (!c->cfg.keep_trace) return fail(c, AS_ERR_STATE, "create the context with keep_trace = 1");
+  t->n_records = c->last_n;
+  t->n_tokens = c->last_T;
+  t->n_regex = c->last_nrx;
+  t->n_final = c->last_nfin;
+  t->rec_tok = c->h_rec_tok.data();
+  t->tok_ids = c->h_tok_ids.data();
+  t->tok_off = c->h_tok_off.data();
+  t->tok_len = c->h_tok_len.data();
+  t->regex_start = c->h_rx_s.data();
+  t->regex_len = c->h_rx_l.data();
+  t->regex_type = c->h_rx_t.data();
+  t->logits = c->last_logits ? c->h_logits.data() : nullptr;
+  t->labels = c->h_labels.data();
+  t->final_start = c->h_fin_s.data();
+  t->final_len = c->h_fin_l.data();
+  t->final_type = c->h_fin_t.data();
+  return AS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Device-wide exclusive prefix sum in three passes (tile sums, scan of tile
+// sums, tile scan with offsets). Values come from a load functor so callers
+// can scan predicates (e.g. "byte starts a token") without materialising them.
+#pragma once
+
+#include "common.cuh"
+
+namespace as {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T, typename Load>
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums(Load load, uint64_t n, T* tile_sums) {
+  __shared__ T sm[33];
+  uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    if (i < n) s += load(i);
+  }
+  T tot;
+  block_exclusive_scan(s, sm, &tot);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// One block scans all tile sums in place (exclusive) and writes the total.
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_tile_offsets(T* tile_sums, uint64_t n_tiles, T* total) {
+  __shared__ T sm[33];
+  T carry = 0;
+  for (uint64_t b = 0; b < n_tiles; b += blockDim.x) {
+    uint64_t i = b + threadIdx.x;
+    T v = i < n_tiles ? tile_sums[i] : T(0);
+    T tot;
+    T ex = block_exclusive_scan(v, sm, &tot);
+    if (i < n_tiles) tile_sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total != nullptr) *total = carry;
+}
+
+template <typename T, typename Load>
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(Load load, uint64_t n, const T* tile_offsets, T* out) {
+  __shared__ T sm[33];
+  uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    v[k] = i < n ? load(i) : T(0);
+    s += v[k];
+  }
+  T tot;
+  T run = block_exclusive_scan(s, sm, &tot) + tile_offsets[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+}
+
+inline uint64_t scan_tiles_needed(uint64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// out[i] = sum_{j<i} load(j); *total_dev = sum of all. tile_scratch needs
+// scan_tiles_needed(n) elements. n may be 0 (then only *total_dev = 0).
+template <typename T, typename Load>
+inline void exclusive_scan(Load load, uint64_t n, T* out, T* total_dev, T* tile_scratch, cudaStream_t st) {
+  uint64_t tiles = scan_tiles_needed(n);
+  if (tiles == 0) {
+    cudaMemsetAsync(total_dev, 0, sizeof(T), st);
+    return;
+  }
+  scan_tile_sums<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch);
+  scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_scratch, tiles, total_dev);
+  scan_tiles<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, out);
+  count_launch(3);
+}
+
+}  // namespace as

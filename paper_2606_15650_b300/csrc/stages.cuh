@@ -1,0 +1,131 @@
+// Declarations of the batch stages (tokenizer, recognizers, BIO decode,
+// span merge, HMAC, entity map, substitution) launched by the runtime.
+#pragma once
+
+#include "common.cuh"
+
+namespace as {
+
+// ---- vocabulary hash table (greedy longest-match lookups) ----
+// A slot holds up to 12 bytes packed little-endian in x, y, z and
+// w = length | id << 16 (w == 0: empty). Open addressing, linear probing.
+constexpr int kMaxPiece = 12;
+
+__host__ __device__ inline uint32_t vocab_hash(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t len) {
+  uint32_t h = len * 0x9E3779B1u;
+  h ^= w0; h *= 0x85EBCA77u; h ^= h >> 13;
+  h ^= w1; h *= 0xC2B2AE3Du; h ^= h >> 16;
+  h ^= w2; h *= 0x27D4EB2Fu; h ^= h >> 15;
+  return h;
+}
+
+struct VocabTable {
+  const uint4* slots;
+  uint32_t mask;
+};
+
+// ---- stage launchers (all asynchronous on `st`) ----
+// Bit r of the bitmap is set when a record starts at byte r (n_words = N/32 + 1).
+void launch_mark_record_starts(const uint64_t* offsets, uint64_t n_records, uint32_t N, uint32_t* rs_bits,
+                               cudaStream_t st);
+// tok_at[i] = token id when a token starts at byte i, else 0.
+void launch_tokenize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, VocabTable vt,
+                          uint16_t* tok_at, cudaStream_t st);
+// Compact token starts: ids/offsets in byte order; pos[] is the exclusive scan.
+void launch_tokenize_emit(const uint16_t* tok_at, const uint32_t* pos, uint32_t N, int32_t* tok_ids,
+                          uint32_t* tok_off, cudaStream_t st);
+void launch_token_lengths(const uint32_t* tok_off, uint32_t T, uint32_t N, uint32_t* tok_len, cudaStream_t st);
+void launch_record_token_offsets(const uint64_t* offsets, uint64_t n_records, const uint32_t* pos, uint32_t N,
+                                 const uint32_t* total_T, uint64_t* rec_tok, cudaStream_t st);
+
+// Pattern recognizers: rx_len[i] / rx_type[i] at each word start that is an entity.
+void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, uint32_t* rx_len,
+                           uint8_t* rx_type, cudaStream_t st);
+void launch_recognize_emit(const uint32_t* rx_len, const uint8_t* rx_type, const uint32_t* pos, uint32_t N,
+                           uint32_t* sp_start, uint32_t* sp_len, uint8_t* sp_type, cudaStream_t st);
+
+// BIO decode: token flags (bit0 first token of record, bit1 last).
+void launch_token_flags(const uint64_t* rec_tok, uint64_t n_records, uint8_t* tok_flags, cudaStream_t st);
+// start[t] = 1 when a span starts at token t; is_end[t] = 1 when one ends there.
+void launch_bio_mark(const uint8_t* labels, const uint8_t* tok_flags, uint32_t T, uint8_t* is_start,
+                     uint8_t* is_end, cudaStream_t st);
+// Token spans: ner_start / ner_len receive the first / last token of each span.
+void launch_bio_emit(const uint8_t* labels, const uint8_t* is_start, const uint8_t* is_end, const uint32_t* pos,
+                     uint32_t T, const uint32_t* tok_off, const uint32_t* tok_len, const uint8_t* bytes,
+                     uint32_t* ner_start, uint32_t* ner_len, uint8_t* ner_type, cudaStream_t st);
+// In place: (first token, last token) -> trimmed byte span (length 0 = dropped).
+void launch_bio_to_bytes(uint32_t* ner_start, uint32_t* ner_len, const uint32_t* n_dev, uint32_t cap,
+                         const uint32_t* tok_off, const uint32_t* tok_len, const uint8_t* bytes, cudaStream_t st);
+// keep[k] for NER spans: non-empty, not overlapping any recognizer span, type not preserved.
+void launch_ner_keep(const uint32_t* ner_start, const uint32_t* ner_len, const uint8_t* ner_type,
+                     const uint32_t* n_ner_dev, uint32_t ner_cap, const uint32_t* rx_start, const uint32_t* rx_len,
+                     const uint32_t* n_rx_dev, uint64_t preserve_mask, uint8_t* keep, cudaStream_t st);
+void launch_rx_keep(const uint8_t* rx_type, const uint32_t* n_rx_dev, uint32_t rx_cap, uint64_t preserve_mask,
+                    uint8_t* keep, cudaStream_t st);
+// Compact a span list by keep[] (pos = exclusive scan of keep).
+void launch_compact_spans(const uint32_t* s, const uint32_t* l, const uint8_t* t, const uint8_t* keep,
+                          const uint32_t* pos, const uint32_t* n_dev, uint32_t cap, uint32_t* os, uint32_t* ol,
+                          uint8_t* ot, cudaStream_t st);
+// Merge two sorted disjoint lists into one sorted list.
+void launch_merge_spans(const uint32_t* a_s, const uint32_t* a_l, const uint8_t* a_t, const uint32_t* n_a_dev,
+                        uint32_t a_cap, const uint32_t* b_s, const uint32_t* b_l, const uint8_t* b_t,
+                        const uint32_t* n_b_dev, uint32_t b_cap, uint32_t* o_s, uint32_t* o_l, uint8_t* o_t,
+                        cudaStream_t st);
+
+// ---- HMAC-SHA256 ----
+void sha256_init_constants();  // uploads FIPS 180-4 constants (derived on the host)
+// key_state[0..7] = inner midstate, [8..15] = outer midstate.
+void launch_hmac_key_setup(const uint8_t* key, uint32_t key_len, uint32_t* key_state, cudaStream_t st);
+void launch_hmac_spans(const uint8_t* bytes, const uint32_t* sp_start, const uint32_t* sp_len,
+                       const uint32_t* n_dev, uint32_t cap, const uint32_t* key_state, uint32_t* digests,
+                       cudaStream_t st);
+
+// ---- entity map ----
+struct MapSlot {
+  unsigned long long key;         // 0 = empty; type << 56 | 56 bits of the digest
+  unsigned long long first_seen;  // atomicMin
+  unsigned long long last_seen;   // atomicMax
+  unsigned long long count;       // atomicAdd
+  uint32_t digest[8];             // full HMAC (written by the inserting thread)
+  unsigned long long arena_off;   // original bytes in the arena
+  uint32_t len;
+  uint32_t type;
+  uint32_t first_call;            // call id that created the entry
+  uint32_t last_call;             // atomicMax of call ids that touched it
+};
+struct MapView {
+  MapSlot* slots;
+  uint64_t mask;
+  uint8_t* arena;
+  unsigned long long* arena_used;
+  uint64_t arena_cap;
+  unsigned long long* n_entries;
+};
+void launch_map_init(MapView m, cudaStream_t st);
+// Insert/update one entry per final span; record index = rec_base + record of the span.
+void launch_map_insert_spans(MapView m, const uint8_t* bytes, const uint32_t* sp_start, const uint32_t* sp_len,
+                             const uint8_t* sp_type, const uint32_t* digests, const uint32_t* n_dev, uint32_t cap,
+                             const uint64_t* offsets, uint64_t n_records, uint64_t rec_base, uint32_t call_id,
+                             DevError* err, cudaStream_t st);
+// Import entries (host-prepared arrays already on the device).
+void launch_map_import(MapView m, const uint8_t* orig, const uint64_t* orig_off, const uint32_t* orig_len,
+                       const uint32_t* type, const uint32_t* digests, const uint64_t* first, const uint64_t* last,
+                       const uint64_t* count, uint64_t n, uint32_t call_id, DevError* err, cudaStream_t st);
+// keep[i] = slot i occupied and (call_id == 0 or touched by call_id).
+void launch_map_select(MapView m, uint32_t call_id, uint8_t* keep, cudaStream_t st);
+void launch_map_gather(MapView m, const uint8_t* keep, const uint32_t* pos, uint32_t* idx, cudaStream_t st);
+void launch_map_gather_slots(MapView m, const uint32_t* idx, uint32_t n, MapSlot* out, cudaStream_t st);
+
+// ---- substitution ----
+// delta[k] = replacement length - span length (int64).
+void launch_sub_delta(const uint32_t* sp_len, const uint8_t* sp_type, const uint32_t* n_dev, uint32_t cap,
+                      const uint32_t* name_len, uint32_t slug_len, int64_t* delta, cudaStream_t st);
+void launch_sub_copy(const uint8_t* bytes, uint32_t N, const uint32_t* sp_start, const uint32_t* sp_len,
+                     const uint32_t* n_dev, const int64_t* shift, uint8_t* out, cudaStream_t st);
+void launch_sub_replace(const uint32_t* sp_start, const uint8_t* sp_type, const uint32_t* n_dev, uint32_t cap,
+                        const int64_t* shift, const uint32_t* digests, const char* names, const uint32_t* name_off,
+                        uint32_t slug_len, uint8_t* out, cudaStream_t st);
+void launch_sub_offsets(const uint64_t* offsets, uint64_t n_records, const uint32_t* sp_start,
+                        const uint32_t* n_dev, const int64_t* shift, uint64_t* out_off, cudaStream_t st);
+
+}  // namespace as

@@ -1,0 +1,107 @@
+"""Encoder kernels against plain PyTorch references of the same operation.
+
+GEMM (tcgen05 BF16 and SIMT FP32) against torch matmul in FP32 on the same
+(BF16-rounded) operands; attention against a per-sequence softmax(QK^T/8)V
+in FP32; LayerNorm against torch.nn.functional.layer_norm. Shapes cover
+several tiles, ragged M tails, both N tile widths and all epilogues.
+"""
+import math
+
+import pytest
+import torch
+
+import paper_2606_15650_b300.api as api
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _ref_gemm(A, B, bias, resid, epi):
+    y = A.float() @ B.float().T
+    if bias is not None:
+        y = y + bias
+    if epi == "bias_gelu":
+        y = torch.nn.functional.gelu(y, approximate="none")
+    if epi == "bias_resid":
+        y = y + resid
+    return y
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 128, 64), (128, 256, 64), (200, 384, 128), (1000, 768, 768),
+                                   (4096, 2304, 768), (777, 768, 3072), (300, 3072, 768), (129, 128, 512)])
+@pytest.mark.parametrize("epi", ["bias", "bias_gelu", "bias_resid"])
+def test_gemm_tcgen05_bf16(M, N, K, epi):
+    g = torch.Generator(device=DEV).manual_seed(M * 7 + N + K)
+    A = torch.randn(M, K, device=DEV, generator=g).to(torch.bfloat16)
+    B = (0.05 * torch.randn(N, K, device=DEV, generator=g)).to(torch.bfloat16)
+    bias = torch.randn(N, device=DEV, generator=g)
+    resid = torch.randn(M, N, device=DEV, generator=g) if epi == "bias_resid" else None
+    out = torch.empty(M, N, device=DEV, dtype=torch.float32 if epi == "bias_resid" else torch.bfloat16)
+    api.gemm("bf16", epi, A, B, bias, resid, out, engine="tcgen05")
+    torch.cuda.synchronize()
+    ref = _ref_gemm(A, B, bias, resid, epi)
+    tol = 2e-3 * math.sqrt(K) * 0.05 * 4 + (8e-3 * ref.abs() if out.dtype == torch.bfloat16 else 0)
+    err = (out.float() - ref).abs()
+    assert bool((err <= tol + 1e-4).all()), f"max err {err.max().item()} at {divmod(int(err.argmax()), N)}"
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 128, 8), (130, 256, 64), (300, 384, 128), (517, 768, 768)])
+@pytest.mark.parametrize("epi", ["bias", "bias_gelu", "bias_resid"])
+def test_gemm_simt_fp32(M, N, K, epi):
+    g = torch.Generator(device=DEV).manual_seed(M + N + K)
+    A = torch.randn(M, K, device=DEV, generator=g)
+    B = 0.05 * torch.randn(N, K, device=DEV, generator=g)
+    bias = torch.randn(N, device=DEV, generator=g)
+    resid = torch.randn(M, N, device=DEV, generator=g) if epi == "bias_resid" else None
+    out = torch.empty(M, N, device=DEV)
+    api.gemm("fp32", epi, A, B, bias, resid, out, engine="simt")
+    torch.cuda.synchronize()
+    ref = _ref_gemm(A.double(), B.double(), bias.double(), None if resid is None else resid.double(), epi)
+    assert torch.allclose(out.double(), ref, atol=1e-4, rtol=1e-5)
+
+
+def _ref_attention(qkv, starts, lens, d, h):
+    out = torch.zeros(qkv.shape[0], d, device=qkv.device, dtype=torch.float32)
+    for s, L in zip(starts.tolist(), lens.tolist()):
+        x = qkv[s:s + L].float()
+        q = x[:, :d].view(L, h, 64).transpose(0, 1)
+        k = x[:, d:2 * d].view(L, h, 64).transpose(0, 1)
+        v = x[:, 2 * d:].view(L, h, 64).transpose(0, 1)
+        p = torch.softmax(q @ k.transpose(1, 2) / 8.0, dim=-1)
+        out[s:s + L] = (p @ v).transpose(0, 1).reshape(L, d)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("d,h", [(128, 2), (768, 12)])
+def test_attention(prec, d, h):
+    g = torch.Generator(device="cpu").manual_seed(d)
+    lens = torch.tensor([1, 5, 64, 65, 300, 512, 17, 128], dtype=torch.int32)
+    starts = torch.zeros_like(lens)
+    starts[1:] = torch.cumsum(lens, 0)[:-1]
+    rows = int(lens.sum())
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    qkv = torch.randn(rows, 3 * d, generator=g).to(DEV).to(dt)
+    out = torch.full((rows, d), float("nan"), device=DEV, dtype=dt)
+    api.attention(prec, qkv, out, starts.to(DEV), lens.to(DEV), d, h)
+    torch.cuda.synchronize()
+    ref = _ref_attention(qkv, starts, lens, d, h)
+    tol = 2.5e-2 if prec == "bf16" else 1e-5
+    assert torch.isfinite(out.float()).all()
+    assert (out.float() - ref).abs().max().item() < tol
+
+
+@pytest.mark.parametrize("d", [128, 768, 1024])
+def test_layernorm(d):
+    g = torch.Generator(device=DEV).manual_seed(d)
+    x = 3 * torch.randn(1000, d, device=DEV, generator=g) + 1
+    gam = 1 + 0.1 * torch.randn(d, device=DEV, generator=g)
+    bet = 0.1 * torch.randn(d, device=DEV, generator=g)
+    out = torch.empty_like(x)
+    out16 = torch.empty(1000, d, device=DEV, dtype=torch.bfloat16)
+    api.layernorm(x, gam, bet, out, out16)
+    torch.cuda.synchronize()
+    ref = torch.nn.functional.layer_norm(x.double(), (d,), gam.double(), bet.double(), eps=1e-5)
+    assert (out.double() - ref).abs().max().item() < 2e-5
+    assert torch.equal(out16, out.to(torch.bfloat16))
