@@ -84,7 +84,7 @@ typedef struct {
   const uint8_t* vocab_bytes;    /* host                                       */
   const uint32_t* vocab_offsets; /* host, n_vocab_words + 1 entries            */
   uint32_t n_vocab_words;
-  uint64_t max_chunk_tokens;     /* encoder rows per packed batch; 0 = 1<<20   */
+  uint64_t max_chunk_tokens;     /* encoder rows per packed batch; 0 = 1<<19   */
   uint64_t map_capacity;         /* entity-map slots (power of 2); 0 = 1<<22   */
   uint64_t map_arena_bytes;      /* bytes for map originals; 0 = 256 MiB       */
   int32_t device;                /* CUDA device ordinal                        */
@@ -191,6 +191,24 @@ typedef struct {
   const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+/* The ctx's CUDA stream (a cudaStream_t): every kernel of the ctx runs on
+ * it, so a caller can time a call with CUDA events recorded on it. */
+as_status as_get_stream(as_ctx* ctx, void** stream);
+
+/* Opt-in launch timing. enable = 1 records a CUDA event pair around every
+ * encoder GEMM and attention launch of later calls and accumulates their
+ * device time and algorithmic FLOPs (GEMM 2*M*N*K; attention 4*L^2*d per
+ * sequence of L tokens); enable = 0 stops and clears. Timing adds a few
+ * microseconds per launch. */
+typedef struct {
+  uint64_t gemm_launches;
+  double gemm_ms, gemm_flops;
+  uint64_t attn_launches;
+  double attn_ms, attn_flops;
+} as_profile_stats;
+as_status as_profile(as_ctx* ctx, uint32_t enable);
+as_status as_profile_read(as_ctx* ctx, as_profile_stats* stats);
 
 const char* as_last_error(const as_ctx* ctx);
 void as_free(void* p);

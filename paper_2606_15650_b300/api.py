@@ -72,9 +72,14 @@ class _Trace(C.Structure):
                 ("final_len", C.POINTER(C.c_uint32)), ("final_type", C.POINTER(C.c_uint8))]
 
 
+class _Profile(C.Structure):
+    _fields_ = [("gemm_launches", C.c_uint64), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
+                ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double)]
+
+
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
-            "as_free", "as_version", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
+            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -108,6 +113,9 @@ def load() -> C.CDLL:
     lib.as_free.argtypes = [P]
     lib.as_free.restype = None
     lib.as_version.restype = C.c_char_p
+    lib.as_get_stream.argtypes = [P, C.POINTER(P)]
+    lib.as_profile.argtypes = [P, C.c_uint32]
+    lib.as_profile_read.argtypes = [P, C.POINTER(_Profile)]
     lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
@@ -122,6 +130,22 @@ def _ptr(x) -> int | None:
     if x is None:
         return None
     return x.data_ptr()
+
+
+_rt = None
+
+
+def _cudart():
+    """The CUDA runtime the library links (for plain device-to-host copies)."""
+    global _rt
+    if _rt is None:
+        _rt = C.CDLL("libcudart.so.13")
+    return _rt
+
+
+def _check_rt(err: int):
+    if err != 0:
+        raise AnonShieldError(-3, f"cudaMemcpy failed with error {err}")
 
 
 def _check_k(status: int):
@@ -207,7 +231,9 @@ class Output:
             raise ValueError("output lives on the device: use device_pointers()")
         offs = np.ctypeslib.as_array(C.cast(o, C.POINTER(C.c_uint64)), shape=(n + 1,)).copy()
         size = int(offs[-1])
-        data = np.ctypeslib.as_array(C.cast(b, C.POINTER(C.c_uint8)), shape=(max(size, 1),))[:size].copy()
+        if size == 0 or not b:
+            return np.zeros(0, np.uint8), offs
+        data = np.ctypeslib.as_array(C.cast(b, C.POINTER(C.c_uint8)), shape=(size,)).copy()
         return data, offs
 
     def device_pointers(self) -> tuple[int, int, int]:
@@ -215,6 +241,18 @@ class Output:
         if not dev:
             raise ValueError("output lives on the host")
         return b, o, n
+
+    def copy_to_host(self) -> list[bytes]:
+        """Records of a device-resident output, copied to the host (cudaMemcpy)."""
+        b, o, n = self.device_pointers()
+        rt = _cudart()
+        offs = np.empty(n + 1, np.uint64)
+        _check_rt(rt.cudaMemcpy(C.c_void_p(offs.ctypes.data), C.c_void_p(o), C.c_size_t((n + 1) * 8), 2))
+        size = int(offs[-1])
+        data = np.empty(max(size, 1), np.uint8)
+        if size:
+            _check_rt(rt.cudaMemcpy(C.c_void_p(data.ctypes.data), C.c_void_p(b), C.c_size_t(size), 2))
+        return [data[offs[i]:offs[i + 1]].tobytes() for i in range(n)]
 
     def records(self) -> list[bytes]:
         data, offs = self.arrays()
@@ -327,6 +365,20 @@ class Context:
             arr[i].last_seen = e.last_seen
             arr[i].count = e.count
         self._check(load().as_map_import(self._h, key, len(key), arr, len(entries)))
+
+    def stream(self) -> int:
+        """The ctx's cudaStream_t (as an int), for torch.cuda.ExternalStream."""
+        p = C.c_void_p()
+        self._check(load().as_get_stream(self._h, C.byref(p)))
+        return p.value or 0
+
+    def profile(self, enable: bool):
+        self._check(load().as_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        s = _Profile()
+        self._check(load().as_profile_read(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _Profile._fields_}
 
     def map_clear(self):
         self._check(load().as_map_clear(self._h))

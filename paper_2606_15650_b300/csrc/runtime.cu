@@ -132,6 +132,7 @@ struct as_ctx {
   uint32_t call_id = 0;
   uint64_t records_done = 0;
   uint32_t slug_len = 10;
+  uint64_t n_entries_seen = 0;  // map size after the previous call
   DBuf dev_err;
   // per-call buffers
   DBuf in_bytes, in_off, rs_bits, tok_at, pos_b, scan_tiles, counters, delta_total;
@@ -151,6 +152,12 @@ struct as_ctx {
   std::vector<uint32_t> h_tok_off, h_tok_len, h_rx_s, h_rx_l, h_fin_s, h_fin_l;
   std::vector<uint8_t> h_rx_t, h_labels, h_fin_t;
   std::vector<float> h_logits;
+  // launch timing (as_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, double>> ev_pending;  // (kind, flops) per event pair
+  as_profile_stats prof_acc{};
 };
 
 struct as_output {
@@ -311,7 +318,50 @@ as_status load_weights(as_ctx* c) {
 
 // ---------------------------------------------------------------- encoder
 
-as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, bool want_logits) {
+// Event pair around one launch when profiling is on (kind 0 GEMM, 1 attention).
+struct ProfScope {
+  as_ctx* c;
+  bool on;
+  ProfScope(as_ctx* c_, int kind, double flops) : c(c_), on(c_->prof) {
+    if (!on) return;
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+      }
+    }
+    cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+    c->ev_pending.push_back({kind, flops});
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
+    c->ev_used += 2;
+  }
+};
+
+// After a stream sync: fold the recorded event pairs into the totals.
+void prof_collect(as_ctx* c) {
+  for (size_t i = 0; i < c->ev_pending.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]);
+    if (c->ev_pending[i].first == 0) {
+      c->prof_acc.gemm_launches++;
+      c->prof_acc.gemm_ms += ms;
+      c->prof_acc.gemm_flops += c->ev_pending[i].second;
+    } else {
+      c->prof_acc.attn_launches++;
+      c->prof_acc.attn_ms += ms;
+      c->prof_acc.attn_flops += c->ev_pending[i].second;
+    }
+  }
+  c->ev_pending.clear();
+  c->ev_used = 0;
+}
+
+as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
+                            bool want_logits) {
   const as_config& g = c->cfg;
   const int64_t R = (int64_t)ch.rows;
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
@@ -334,24 +384,26 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
       __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
       __nv_bfloat16* ATT = c->ATT.as<__nv_bfloat16>();
       __nv_bfloat16* H = c->H.as<__nv_bfloat16>();
-      CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st));
-      CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
-                         (int32_t)g.n_heads, st));
-      CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st));
+      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
+      { ProfScope ps(c, 1, attn_flops);
+        CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+                           (int32_t)g.n_heads, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
-      CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st));
-      CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st));
+      { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st)); }
     } else {
       float* QKV = c->QKV.as<float>();
       float* ATT = c->ATT.as<float>();
       float* H = c->H.as<float>();
-      CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st));
-      CKS(attention_f32(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
-                        (int32_t)g.n_heads, st));
-      CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st));
+      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
+      { ProfScope ps(c, 1, attn_flops);
+        CKS(attention_f32(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+                          (int32_t)g.n_heads, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, nullptr, R, d, st));
-      CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st));
-      CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st));
+      { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
     }
     if (!last) {
       CKS(layernorm_rows(Y32, L.ln2_g, L.ln2_b, X32, X16, R, d, st));
@@ -593,7 +645,15 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   CKS(grow(c->labels, T + 16));
   if (want_logits) CKS(grow(c->logits, (T + 1) * g.n_labels * 4));
   CK(cudaMemsetAsync(c->labels.p, 0, T + 16, st));
-  for (const Chunk& ch : chunks) CKI(run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), want_logits));
+  for (const Chunk& ch : chunks) {
+    double af = 0;  // attention FLOPs of the batch: QK^T and PV, 2 * 2 * L^2 * d per sequence
+    for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
+    CKI(run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), af, want_logits));
+    if (c->prof && c->ev_used > 4096) {  // bound the event pool
+      CK(cudaStreamSynchronize(st));
+      prof_collect(c);
+    }
+  }
   // ---- BIO decode
   CKS(grow(c->tok_flags, T + 16));
   CK(cudaMemsetAsync(c->tok_flags.p, 0, T + 1, st));
@@ -741,6 +801,7 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     as_output_free(o);
     return fail(c, AS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
   }
+  if (c->prof) prof_collect(c);
   as_status ds = check_dev_error(c);
   if (ds != AS_OK) {
     as_output_free(o);
@@ -759,6 +820,8 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   s.n_final_spans = h_cnt2[5];
   s.n_out_bytes = out_size;
   s.n_map_entries = n_entries;
+  s.n_new_entries = n_entries >= c->n_entries_seen ? n_entries - c->n_entries_seen : 0;
+  c->n_entries_seen = n_entries;
   s.kernel_launches = g_launches.load() - launches0;
   c->records_done += n;
   *out = o;
@@ -933,6 +996,7 @@ void as_destroy(as_ctx* c) {
                  &c->row_pos, &c->row_own, &c->seq_start, &c->seq_len, &c->X32, &c->X16, &c->QKV, &c->ATT, &c->Y32,
                  &c->H};
   for (DBuf* b : all) release(*b);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1075,9 +1139,33 @@ as_status as_map_clear(as_ctx* c) {
   if (!c) return AS_ERR_ARG;
   cudaSetDevice(c->device);
   launch_map_init(map_view(c), c->stream);
+  c->n_entries_seen = 0;
   c->key_set = false;
   c->key.clear();
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, AS_ERR_CUDA, "map clear");
+  return AS_OK;
+}
+
+as_status as_get_stream(as_ctx* c, void** stream) {
+  if (!c || !stream) return AS_ERR_ARG;
+  *stream = reinterpret_cast<void*>(c->stream);
+  return AS_OK;
+}
+
+as_status as_profile(as_ctx* c, uint32_t enable) {
+  if (!c) return AS_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->ev_pending.clear();
+  c->ev_used = 0;
+  c->prof_acc = as_profile_stats{};
+  c->prof = enable != 0;
+  return AS_OK;
+}
+
+as_status as_profile_read(as_ctx* c, as_profile_stats* s) {
+  if (!c || !s) return AS_ERR_ARG;
+  *s = c->prof_acc;
   return AS_OK;
 }
 
