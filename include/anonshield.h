@@ -210,6 +210,28 @@ typedef struct {
 as_status as_profile(as_ctx* ctx, uint32_t enable);
 as_status as_profile_read(as_ctx* ctx, as_profile_stats* stats);
 
+/* Tokenizer that allocates no memory. The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc, such as code running while a CUDA
+ * graph is being captured, hosts whose device memory belongs to their own
+ * allocator, or latency-bound loops where an allocation would synchronize
+ * the device. It runs the same tokenizer as as_anonymize, with its scratch
+ * memory in a fixed-size array inside the library instead of ctx buffers.
+ * All pointers are device pointers on the ctx's device:
+ *   bytes[n_bytes], offsets[n_records + 1] (offsets[n_records] == n_bytes),
+ *   outputs tok_ids / tok_off (byte offset in `bytes`) / tok_len with room
+ *   for n_bytes tokens, rec_tok[n_records + 1] (first token of each record),
+ *   *n_tokens (token count).
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Limits: n_bytes <= AS_STATIC_MAX_BYTES, else AS_ERR_ARG. The array (about
+ * 6.4 MB) stays on every device that loads the library until exit. The first
+ * call on a device looks the array up (cudaGetSymbolAddress): make it before
+ * any stream capture. Every call reuses the same array, so calls that overlap
+ * on the GPU (other streams or host threads) race: serialize them. */
+#define AS_STATIC_MAX_BYTES (1u << 20)
+as_status as_tokenize_static(as_ctx* ctx, const uint8_t* bytes, const uint64_t* offsets, uint64_t n_records,
+                             uint64_t n_bytes, int32_t* tok_ids, uint32_t* tok_off, uint32_t* tok_len,
+                             uint64_t* rec_tok, uint32_t* n_tokens, void* stream);
+
 const char* as_last_error(const as_ctx* ctx);
 void as_free(void* p);
 /* Library version string. */

@@ -79,7 +79,7 @@ class _Profile(C.Structure):
 
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
-            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
+            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -116,6 +116,7 @@ def load() -> C.CDLL:
     lib.as_get_stream.argtypes = [P, C.POINTER(P)]
     lib.as_profile.argtypes = [P, C.c_uint32]
     lib.as_profile_read.argtypes = [P, C.POINTER(_Profile)]
+    lib.as_tokenize_static.argtypes = [P, P, P, C.c_uint64, C.c_uint64, P, P, P, P, P, P]
     lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
@@ -412,6 +413,31 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+STATIC_MAX_BYTES = 1 << 20
+
+
+def tokenize_static(ctx: "Context", data, offsets, stream=None) -> dict:
+    """Tokenize device-resident records without any allocation inside the call.
+
+    data (uint8) and offsets (int64/uint64, n+1) are CUDA tensors. The output
+    tensors are allocated here, by the caller side, before the call; the
+    library call itself allocates nothing. Returns the outputs as tensors."""
+    import torch
+    n = offsets.numel() - 1
+    n_bytes = int(data.numel())
+    dev = data.device
+    out = {"tok_ids": torch.empty(max(n_bytes, 1), dtype=torch.int32, device=dev),
+           "tok_off": torch.empty(max(n_bytes, 1), dtype=torch.int32, device=dev),
+           "tok_len": torch.empty(max(n_bytes, 1), dtype=torch.int32, device=dev),
+           "rec_tok": torch.empty(n + 1, dtype=torch.int64, device=dev),
+           "n_tokens": torch.zeros(1, dtype=torch.int32, device=dev)}
+    st = load().as_tokenize_static(ctx._h, _ptr(data), _ptr(offsets), n, n_bytes, _ptr(out["tok_ids"]),
+                                   _ptr(out["tok_off"]), _ptr(out["tok_len"]), _ptr(out["rec_tok"]),
+                                   _ptr(out["n_tokens"]), stream)
+    _check_k(st)
+    return out
 
 
 def version() -> str:

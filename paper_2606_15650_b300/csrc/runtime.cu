@@ -900,6 +900,17 @@ as_status map_collect(as_ctx* c, uint32_t call_id, std::vector<as_entity>& ents,
 
 }  // namespace
 
+namespace as {
+// Vocabulary table and device of a ctx, for entry points defined in other files.
+bool ctx_vocab(const as_ctx* ctx, VocabTable* vt, int* device) {
+  if (!ctx || !ctx->vocab_slots.p) return false;
+  vt->slots = ctx->vocab_slots.as<uint4>();
+  vt->mask = ctx->vocab_mask;
+  *device = ctx->device;
+  return true;
+}
+}  // namespace as
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
