@@ -208,20 +208,69 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// 4 warps x 16 query rows; 64-key tiles of K (row-major) and V (transposed)
-// in shared memory; S = Q K^T and O += P V on m16n8k16 BF16 tensor cores.
-__global__ void __launch_bounds__(128) attn_bf16_kernel(const __nv_bfloat16* __restrict__ qkv,
-                                                       __nv_bfloat16* __restrict__ out,
-                                                       const int32_t* __restrict__ seq_start,
-                                                       const int32_t* __restrict__ seq_len, int d) {
-  constexpr int P = 72;  // padded row (bf16): conflict-free fragment reads
-  __shared__ __align__(16) __nv_bfloat16 Ks[64][P];
-  __shared__ __align__(16) __nv_bfloat16 Vt[64][P];
-  const int s = blockIdx.x, h = blockIdx.y, L = seq_len[s], q0 = blockIdx.z * 64;
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  // src-size 0 zero-fills the 16 destination bytes (keys past the sequence end)
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+// 2^x with the hardware approximation (MUFU.EX2); exact enough for an FP32
+// softmax whose inputs were rounded to BF16.
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Flash-style attention, one block per (sequence, head, 64-query tile); the
+// blocks of one (sequence, head) are consecutive so that K and V are read
+// from DRAM once and then served from L2. 4 warps x 16 query rows. K and V
+// tiles of 64 keys are double-buffered in shared memory with cp.async;
+// B fragments come from ldmatrix (K) and ldmatrix.trans (V); S = Q K^T and
+// O += P V run on m16n8k16 BF16 tensor cores; softmax statistics in FP32.
+__global__ void __launch_bounds__(128, 4) attn_bf16_kernel(const __nv_bfloat16* __restrict__ qkv,
+                                                          __nv_bfloat16* __restrict__ out,
+                                                          const int32_t* __restrict__ seq_start,
+                                                          const int32_t* __restrict__ seq_len, int d, int n_heads,
+                                                          int q_tiles) {
+  constexpr int P = 72;  // padded row (bf16): 144 B, conflict-free ldmatrix rows
+  __shared__ __align__(128) __nv_bfloat16 Ks[2][64][P];
+  __shared__ __align__(128) __nv_bfloat16 Vs[2][64][P];
+  const int qt = blockIdx.x % q_tiles;
+  const int rest = blockIdx.x / q_tiles;
+  const int h = rest % n_heads, s = rest / n_heads;
+  const int L = seq_len[s], q0 = qt * 64;
   if (q0 >= L) return;
   const size_t ld = 3 * (size_t)d;
   const __nv_bfloat16* base = qkv + (size_t)seq_start[s] * ld + h * 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mi = lane >> 3, mr = lane & 7;
+  const int n_tiles = (L + 63) / 64;
+
+  auto load_tile = [&](int buf, int k0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = threadIdx.x + i * 128;
+      const int key = idx >> 3, c8 = (idx & 7) * 8;
+      const bool v = k0 + key < L;
+      const __nv_bfloat16* src = base + (size_t)(v ? k0 + key : 0) * ld;
+      cp_async16((uint32_t)__cvta_generic_to_shared(&Ks[buf][key][c8]), src + d + c8, v);
+      cp_async16((uint32_t)__cvta_generic_to_shared(&Vs[buf][key][c8]), src + 2 * d + c8, v);
+    }
+    cp_async_commit();
+  };
+  load_tile(0, 0);
+
   const int qr0 = q0 + warp * 16 + g, qr1 = qr0 + 8;
   uint32_t qa[4][4];
 #pragma unroll
@@ -237,21 +286,14 @@ __global__ void __launch_bounds__(128) attn_bf16_kernel(const __nv_bfloat16* __r
   for (int i = 0; i < 8; ++i) o[i][0] = o[i][1] = o[i][2] = o[i][3] = 0.f;
   float m0 = -INFINITY, m1 = -INFINITY, l0 = 0.f, l1 = 0.f;
   const float sl2 = 0.125f * 1.4426950408889634f;  // 1/sqrt(64) * log2(e)
-  for (int k0 = 0; k0 < L; k0 += 64) {
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int idx = threadIdx.x + i * 128;
-      const int key = idx >> 3, c8 = (idx & 7) * 8;
-      uint4 kv = make_uint4(0, 0, 0, 0), vv = make_uint4(0, 0, 0, 0);
-      if (k0 + key < L) {
-        kv = *reinterpret_cast<const uint4*>(base + (size_t)(k0 + key) * ld + d + c8);
-        vv = *reinterpret_cast<const uint4*>(base + (size_t)(k0 + key) * ld + 2 * d + c8);
-      }
-      *reinterpret_cast<uint4*>(&Ks[key][c8]) = kv;
-      const __nv_bfloat16* ve = reinterpret_cast<const __nv_bfloat16*>(&vv);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) Vt[c8 + j][key] = ve[j];
+
+  for (int it = 0; it < n_tiles; ++it) {
+    const int buf = it & 1, k0 = it * 64;
+    if (it + 1 < n_tiles) {
+      load_tile(buf ^ 1, k0 + 64);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
     float sf[8][4];
@@ -260,10 +302,12 @@ __global__ void __launch_bounds__(128) attn_bf16_kernel(const __nv_bfloat16* __r
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Ks[nt * 8 + g][ks * 16 + 2 * t]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Ks[nt * 8 + g][ks * 16 + 8 + 2 * t]);
-        mma16816(sf[nt], qa[ks], b0, b1);
+      for (int np = 0; np < 4; ++np) {
+        uint32_t b0a, b1a, b0b, b1b;
+        ldsm_x4((uint32_t)__cvta_generic_to_shared(&Ks[buf][np * 16 + (mi >> 1) * 8 + mr][ks * 16 + (mi & 1) * 8]),
+                b0a, b1a, b0b, b1b);
+        mma16816(sf[2 * np], qa[ks], b0a, b1a);
+        mma16816(sf[2 * np + 1], qa[ks], b0b, b1b);
       }
     float mx0 = -INFINITY, mx1 = -INFINITY;
 #pragma unroll
@@ -280,14 +324,14 @@ __global__ void __launch_bounds__(128) attn_bf16_kernel(const __nv_bfloat16* __r
     mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
     mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 2));
     const float mn0 = fmaxf(m0, mx0), mn1 = fmaxf(m1, mx1);
-    const float c0 = exp2f(m0 - mn0), c1 = exp2f(m1 - mn1);
+    const float c0 = ex2(m0 - mn0), c1 = ex2(m1 - mn1);
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      sf[nt][0] = exp2f(sf[nt][0] - mn0);
-      sf[nt][1] = exp2f(sf[nt][1] - mn0);
-      sf[nt][2] = exp2f(sf[nt][2] - mn1);
-      sf[nt][3] = exp2f(sf[nt][3] - mn1);
+      sf[nt][0] = ex2(sf[nt][0] - mn0);
+      sf[nt][1] = ex2(sf[nt][1] - mn0);
+      sf[nt][2] = ex2(sf[nt][2] - mn1);
+      sf[nt][3] = ex2(sf[nt][3] - mn1);
       s0 += sf[nt][0] + sf[nt][1];
       s1 += sf[nt][2] + sf[nt][3];
     }
@@ -311,12 +355,15 @@ __global__ void __launch_bounds__(128) attn_bf16_kernel(const __nv_bfloat16* __r
       pa[2] = pack_bf16(sf[2 * kk + 1][0], sf[2 * kk + 1][1]);
       pa[3] = pack_bf16(sf[2 * kk + 1][2], sf[2 * kk + 1][3]);
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Vt[nt * 8 + g][kk * 16 + 2 * t]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Vt[nt * 8 + g][kk * 16 + 8 + 2 * t]);
-        mma16816(o[nt], pa, b0, b1);
+      for (int dp = 0; dp < 4; ++dp) {
+        uint32_t b0a, b1a, b0b, b1b;
+        ldsm_x4_t((uint32_t)__cvta_generic_to_shared(&Vs[buf][kk * 16 + (mi & 1) * 8 + mr][dp * 16 + (mi >> 1) * 8]),
+                  b0a, b1a, b0b, b1b);
+        mma16816(o[2 * dp], pa, b0a, b1a);
+        mma16816(o[2 * dp + 1], pa, b0b, b1b);
       }
     }
+    __syncthreads();  // the next iteration refills this buffer
   }
   const float i0 = 1.f / l0, i1 = 1.f / l1;
   const size_t row0 = (size_t)seq_start[s];
@@ -334,12 +381,17 @@ as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int
                          const int32_t* seq_len, int32_t n_seq, int32_t max_len, int32_t d_model, int32_t n_heads,
                          cudaStream_t st) {
   if (n_seq == 0 || max_len == 0) return AS_OK;
-  if (d_model != n_heads * 64 || max_len > 4096 || n_heads > 65535) {
+  if (d_model != n_heads * 64 || max_len > 4096) {
     set_k_error("attention_bf16: head dim must be 64 and sequences at most 4096 tokens");
     return AS_ERR_ARG;
   }
-  dim3 grid((unsigned)n_seq, (unsigned)n_heads, (unsigned)((max_len + 63) / 64));
-  attn_bf16_kernel<<<grid, 128, 0, st>>>(qkv, out, seq_start, seq_len, d_model);
+  const int q_tiles = (max_len + 63) / 64;
+  const uint64_t blocks = (uint64_t)n_seq * n_heads * q_tiles;
+  if (blocks > 0x7FFFFFFFull) {
+    set_k_error("attention_bf16: too many sequences in one batch");
+    return AS_ERR_ARG;
+  }
+  attn_bf16_kernel<<<(unsigned)blocks, 128, 0, st>>>(qkv, out, seq_start, seq_len, d_model, n_heads, q_tiles);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;

@@ -11,8 +11,11 @@
 //   warp 1, one lane : issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM
 //                      accumulator; tcgen05.commit frees ring slots and
 //                      signals a finished accumulator
-//   warps 2..5       : epilogue; tcgen05.ld of their 32 TMEM lanes, bias /
-//                      GELU / residual in FP32, stores
+//   warps 2..9       : epilogue; two warps per TMEM lane quarter (32 rows),
+//                      each taking half of the tile's columns: tcgen05.ld,
+//                      bias / GELU / residual in FP32, then 32x32 chunks
+//                      through swizzled shared memory and TMA tensor stores
+//                      (the FP32 residual comes in by TMA the same way)
 // Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap
 // the main loop of tile i+1. Every mbarrier wait is bounded (globaltimer):
 // on timeout the kernel records the failure, every role leaves its loop,
@@ -28,7 +31,8 @@ namespace tc {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;             // one 128-byte swizzle atom of BF16
-constexpr int kThreads = 192;       // 6 warps
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer + MMA + epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 struct Params {
@@ -146,25 +150,85 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU 0.5 x (1 + erf(x / sqrt 2)) for the BF16 epilogue. erf uses the
+// rational approximation of Abramowitz & Stegun, Handbook of Mathematical
+// Functions, eq. 7.1.26 (|error| <= 1.5e-7): erf(z) = 1 - t (a1 + t (a2 + t (a3
+// + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z), z >= 0, odd extension. The
+// result is rounded to BF16 (relative 2^-9) right after, so the approximation
+// error does not show; it costs about a third of a full-precision erf.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu_erf(float x) {
+  const float z = fabsf(x) * 0.70710678118654752f;
+  const float t = rcp_approx(fmaf(0.3275911f, z, 1.0f));
+  float poly = fmaf(t, 1.061405429f, -1.453152027f);
+  poly = fmaf(t, poly, 1.421413741f);
+  poly = fmaf(t, poly, -0.284496736f);
+  poly = fmaf(t, poly, 0.254829592f);
+  const float e = ex2_approx(-z * z * 1.4426950408889634f);
+  const float erf_abs = fmaf(-poly * t, e, 1.0f);
+  const float erf_x = copysignf(erf_abs, x);
+  return 0.5f * x * (1.0f + erf_x);
+}
 
-template <int BN, int STAGES>
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// TMA tensor store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Epilogue staging: each epilogue warp owns two 32x32 chunk buffers. BF16
+// chunks have 64-byte rows stored with the 64-byte TMA swizzle (16-byte
+// piece j of row r at j ^ ((r >> 1) & 3)); FP32 chunks have 128-byte rows
+// with the 128-byte swizzle (piece j at j ^ (r & 7)). The warp writes (and,
+// for the residual, reads) one row per lane without bank conflicts, and the
+// TMA engine moves whole lines to and from global memory.
+template <int EPI>
+struct EpiTraits {
+  static constexpr bool kF32 = EPI == AS_EPI_BIAS_RESID;
+  static constexpr int kChunkBytes = 32 * 32 * (kF32 ? 4 : 2);
+};
+
+template <int BN, int STAGES, int EPI>
 struct Smem {
   static constexpr int kABytes = kBM * kBK * 2;   // 16 KB
   static constexpr int kBBytes = BN * kBK * 2;    // 16 or 32 KB
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kBarOff = STAGES * kStageBytes;
-  // full[S], empty[S], tfull[2], tempty[2], then tmem slot + abort flag
-  static constexpr int kBytes = kBarOff + (2 * STAGES + 4) * 8 + 16;
+  static constexpr int kStgOff = STAGES * kStageBytes;                       // 1024-aligned
+  static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<EPI>::kChunkBytes;
+  static constexpr int kBarOff = kStgOff + kStgBytes;
+  // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][2]; tmem slot + abort flag
+  static constexpr int kNumBars = 2 * STAGES + 4 + 2 * kEpiWarps;
+  static constexpr int kBytes = kBarOff + kNumBars * 8 + 16;
   static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
-  using L = Smem<BN, STAGES>;
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR, Params p) {
+  using L = Smem<BN, STAGES, EPI>;
+  using E = EpiTraits<EPI>;
   constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
   constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+  constexpr int CH = BN / 64;              // 32-column chunks per epilogue warp and tile
+  static_assert(CH % 2 == 0, "chunks alternate between two staging buffers");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -174,7 +238,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
   auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kBarOff + (2 * STAGES + 4) * 8);
+  auto resid_bar = [&](int w, int b) { return bar0 + 8u * (2 * STAGES + 4 + 2 * w + b); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kBarOff + L::kNumBars * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,12 +252,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 4 * 32);
+      mbar_init(tempty_bar(a), kEpiWarps * 32);
+    }
+    for (int w = 0; w < kEpiWarps; ++w) {
+      mbar_init(resid_bar(w, 0), 1);
+      mbar_init(resid_bar(w, 1), 1);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
+    if (E::kF32) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -247,64 +318,99 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
+    // ---------------- epilogue: warp w owns TMEM lanes 32*(w%4) .. +31 (a
+    // warp can reach only its own lane quarter) and column half (w-2)/4
+    const int ew = warp - 2;
     const int sub = warp & 3;
-    const int row_in_tile = sub * 32 + lane;
+    const int half = ew >> 2;
+    const uint32_t stg = sbase + L::kStgOff + ew * 2 * E::kChunkBytes;
+    uint8_t* stg_ptr = smem + L::kStgOff + ew * 2 * E::kChunkBytes;
+    const int r = lane;
     uint32_t lt = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
+      const int row0 = m0 + sub * 32;
+      if (E::kF32) {
+        // residual chunks of this tile: fetched before the accumulator is ready
+        if (lane == 0) {
+          bulk_wait_read<0>();  // earlier stores have left the staging buffers
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            mbar_expect_tx(resid_bar(ew, i), E::kChunkBytes);
+            tma_load_2d(stg + i * E::kChunkBytes, &tmR, resid_bar(ew, i), n0 + (half * CH + i) * 32, row0);
+          }
+        }
+        __syncwarp();
+      }
       if (!mbar_wait(tfull_bar(acc), aph, abort_flag, p.err, 30)) break;
       fence_after();
-      const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
-      const int m = m0 + row_in_tile;
-      const bool row_ok = m < p.M;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN + c * 32, r);
+      for (int i = 0; i < CH; ++i) {
+        const int c = half * CH + i;
+        const int buf = i & 1;
+        uint32_t rr[32];
+        tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN + c * 32, rr);
         const int n = n0 + c * 32;
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
-          v[j + 0] = __uint_as_float(r[j + 0]) + b.x;
-          v[j + 1] = __uint_as_float(r[j + 1]) + b.y;
-          v[j + 2] = __uint_as_float(r[j + 2]) + b.z;
-          v[j + 3] = __uint_as_float(r[j + 3]) + b.w;
+          v[j + 0] = __uint_as_float(rr[j + 0]) + b.x;
+          v[j + 1] = __uint_as_float(rr[j + 1]) + b.y;
+          v[j + 2] = __uint_as_float(rr[j + 2]) + b.z;
+          v[j + 3] = __uint_as_float(rr[j + 3]) + b.w;
         }
-        if (!row_ok) continue;
-        if (p.epi == AS_EPI_BIAS_RESID) {
-          const float* rs = p.resid + (size_t)m * p.N + n;
-          float* o = reinterpret_cast<float*>(p.out) + (size_t)m * p.N + n;
+        uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
+        if (E::kF32) {
+          // residual rows arrived by TMA; each buffer is filled CH/2 times per tile
+          const uint32_t par = (lt * (CH / 2) + (i >> 1)) & 1u;
+          if (!mbar_wait(resid_bar(ew, buf), par, abort_flag, p.err, 31)) break;
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 q = __ldg(reinterpret_cast<const float4*>(rs + j));
-            *reinterpret_cast<float4*>(o + j) = make_float4(v[j] + q.x, v[j + 1] + q.y, v[j + 2] + q.z, v[j + 3] + q.w);
+          for (int j = 0; j < 8; ++j) {
+            float4* q = reinterpret_cast<float4*>(cb + r * 128 + ((j ^ (r & 7)) << 4));
+            float4 x = *q;
+            *q = make_float4(v[4 * j] + x.x, v[4 * j + 1] + x.y, v[4 * j + 2] + x.z, v[4 * j + 3] + x.w);
           }
         } else {
-          if (p.epi == AS_EPI_BIAS_GELU) {
+          if (EPI == AS_EPI_BIAS_GELU) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = gelu_erf(v[j]);
           }
-          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(p.out) + (size_t)m * p.N + n;
+          if (lane == 0) bulk_wait_read<1>();  // the store two chunks back has read this buffer
+          __syncwarp();
 #pragma unroll
-          for (int j = 0; j < 32; j += 8) {
+          for (int j = 0; j < 4; ++j) {
             uint4 w;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[j + 0], v[j + 1]);
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
-            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * j + 0], v[8 * j + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * j + 2], v[8 * j + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 4], v[8 * j + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * j + 6], v[8 * j + 7]);
             w.x = *reinterpret_cast<uint32_t*>(&h0);
             w.y = *reinterpret_cast<uint32_t*>(&h1);
             w.z = *reinterpret_cast<uint32_t*>(&h2);
             w.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(o + j) = w;
+            *reinterpret_cast<uint4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4)) = w;
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmC, stg + buf * E::kChunkBytes, n, row0);
+          bulk_commit();
+          if (E::kF32 && i + 2 < CH) {
+            // refill this buffer with the residual of chunk i + 2 once the
+            // store has read it
+            bulk_wait_read<0>();
+            mbar_expect_tx(resid_bar(ew, buf), E::kChunkBytes);
+            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + 64, row0);
           }
         }
       }
       fence_before();
       mbar_arrive(tempty_bar(acc));
     }
+    if (lane == 0) bulk_wait_all();
   }
 done:
   fence_before();
@@ -338,14 +444,15 @@ as_status ensure_driver() {
   return AS_OK;
 }
 
-as_status make_map(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows) {
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)tc::kBK, box_rows};
+// 2D row-major tensor map [rows][cols] of `dtype` with box {box_cols, box_rows}.
+as_status make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dtype, uint32_t esize, uint64_t rows,
+                   uint64_t cols, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * esize)};
+  cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = g_encode(tm, dtype, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_k_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
     return AS_ERR_CUDA;
@@ -353,26 +460,39 @@ as_status make_map(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_t K, 
   return AS_OK;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int EPI>
 as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStream_t st) {
-  using L = tc::Smem<BN, STAGES>;
+  using L = tc::Smem<BN, STAGES, EPI>;
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
-    AS_CUDA_OK(cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
+    AS_CUDA_OK(
+        cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
     attr_set[dev & 63] = true;
   }
-  CUtensorMap tmA, tmB;
-  as_status s = make_map(&tmA, A, (uint64_t)p0.M, (uint64_t)p0.K, tc::kBM);
-  if (s != AS_OK) return s;
-  s = make_map(&tmB, B, (uint64_t)p0.N, (uint64_t)p0.K, BN);
+  CUtensorMap tmA, tmB, tmC, tmR;
+  const auto bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  as_status s = make_map(&tmA, A, bf, 2, (uint64_t)p0.M, (uint64_t)p0.K, tc::kBK, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK) s = make_map(&tmB, B, bf, 2, (uint64_t)p0.N, (uint64_t)p0.K, tc::kBK, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK) {
+    if (tc::EpiTraits<EPI>::kF32) {
+      s = make_map(&tmC, p0.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
+                   CU_TENSOR_MAP_SWIZZLE_128B);
+      if (s == AS_OK)
+        s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
+                     CU_TENSOR_MAP_SWIZZLE_128B);
+    } else {
+      s = make_map(&tmC, p0.out, bf, 2, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B);
+      tmR = tmC;  // unused
+    }
+  }
   if (s != AS_OK) return s;
   tc::Params p = p0;
   p.n_tiles_n = p.N / BN;
   p.n_tiles = p.n_tiles_n * ((p.M + tc::kBM - 1) / tc::kBM);
   int grid = p.n_tiles < g_num_sms ? p.n_tiles : g_num_sms;
-  tc::gemm_kernel<BN, STAGES><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, p);
+  tc::gemm_kernel<BN, STAGES, EPI><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
@@ -391,7 +511,9 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
     if (g_num_sms <= 0) g_num_sms = kDefaultSMs;
   }
   if (M < 1 || N % 128 != 0 || K % tc::kBK != 0 || K < tc::kBK || M > (1ll << 31) - 1 ||
-      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) {
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
+      (reinterpret_cast<uintptr_t>(out) & 15) || (epi == AS_EPI_BIAS_RESID && (reinterpret_cast<uintptr_t>(resid) & 15)) ||
+      (bias && (reinterpret_cast<uintptr_t>(bias) & 15))) {
     set_k_error("gemm_tcgen05: unsupported shape or alignment");
     return AS_ERR_ARG;
   }
@@ -404,8 +526,19 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
   p.resid = resid;
   p.out = out;
   p.err = err;
-  if (N % 256 == 0) return launch_bn<256, 4>(p, A, B, st);
-  return launch_bn<128, 6>(p, A, B, st);
+  switch (epi) {
+    case AS_EPI_BIAS:
+      return N % 256 == 0 ? launch_bn<256, 4, AS_EPI_BIAS>(p, A, B, st) : launch_bn<128, 6, AS_EPI_BIAS>(p, A, B, st);
+    case AS_EPI_BIAS_GELU:
+      return N % 256 == 0 ? launch_bn<256, 4, AS_EPI_BIAS_GELU>(p, A, B, st)
+                          : launch_bn<128, 6, AS_EPI_BIAS_GELU>(p, A, B, st);
+    case AS_EPI_BIAS_RESID:
+      return N % 256 == 0 ? launch_bn<256, 3, AS_EPI_BIAS_RESID>(p, A, B, st)
+                          : launch_bn<128, 4, AS_EPI_BIAS_RESID>(p, A, B, st);
+    default:
+      set_k_error("gemm_tcgen05: bad epilogue");
+      return AS_ERR_ARG;
+  }
 }
 
 }  // namespace as
