@@ -48,6 +48,14 @@ as_status as_k_attention(int precision, const void* qkv, void* out, const int32_
                          const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model,
                          int32_t n_heads, void* stream);
 
+/* The same attention (BF16) on the tcgen05 tensor cores: S = Q K^T and
+ * O = P V in TMEM, softmax in four warps. Every seq_start must be a multiple
+ * of 8 (AS_ERR_ARG otherwise); vt_scratch must hold d_model * round8(rows)
+ * BF16 elements (the kernel writes V transposed there first). */
+as_status as_k_attention_tc(const void* qkv, void* vt_scratch, void* out, const int32_t* seq_start,
+                            const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
+                            void* stream);
+
 /* Row LayerNorm (biased variance, eps 1e-5): out_f32 = LN(in) * g + b, and
  * a BF16 copy in out_bf16 when it is not NULL. in/out_f32 may alias. */
 as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16,

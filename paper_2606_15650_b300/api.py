@@ -23,6 +23,7 @@ PRECISION = {"fp32": 0, "bf16": 1}
 MODE = {"packed": 0, "per_record": 1}
 EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
 ENGINE = {"auto": 0, "tcgen05": 1, "simt": 2}
+ATTENTION = {"mma_sync": 0, "tcgen05": 1}
 
 
 class AnonShieldError(RuntimeError):
@@ -38,7 +39,8 @@ class _Config(C.Structure):
                 ("weights", C.POINTER(C.c_float)), ("weights_len", C.c_uint64),
                 ("vocab_bytes", C.POINTER(C.c_uint8)), ("vocab_offsets", C.POINTER(C.c_uint32)),
                 ("n_vocab_words", C.c_uint32), ("max_chunk_tokens", C.c_uint64), ("map_capacity", C.c_uint64),
-                ("map_arena_bytes", C.c_uint64), ("device", C.c_int32), ("keep_trace", C.c_uint32)]
+                ("map_arena_bytes", C.c_uint64), ("device", C.c_int32), ("keep_trace", C.c_uint32),
+                ("attention", C.c_uint32)]
 
 
 class _Records(C.Structure):
@@ -79,7 +81,7 @@ class _Profile(C.Structure):
 
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
-            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_k_gemm", "as_k_attention", "as_k_layernorm", "as_k_launch_count",
+            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_k_gemm", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -119,6 +121,7 @@ def load() -> C.CDLL:
     lib.as_tokenize_static.argtypes = [P, P, P, C.c_uint64, C.c_uint64, P, P, P, P, P, P]
     lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
+    lib.as_k_attention_tc.argtypes = [P, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
     lib.as_k_launch_count.restype = C.c_uint64
     lib.as_k_last_error.restype = C.c_char_p
@@ -168,6 +171,13 @@ def gemm(precision: str, epilogue: str, A, B, bias=None, resid=None, out=None, e
 def attention(precision: str, qkv, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
     _check_k(load().as_k_attention(PRECISION[precision], _ptr(qkv), _ptr(out), _ptr(seq_start), _ptr(seq_len),
                                    int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
+    return out
+
+
+def attention_tc(qkv, vt_scratch, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
+    """tcgen05 attention (BF16); sequence starts must be multiples of 8."""
+    _check_k(load().as_k_attention_tc(_ptr(qkv), _ptr(vt_scratch), _ptr(out), _ptr(seq_start), _ptr(seq_len),
+                                      int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
     return out
 
 
@@ -286,7 +296,7 @@ class Context:
 
     def __init__(self, dims, weights_blob: np.ndarray, vocab_words: list[bytes], precision: str = "bf16",
                  mode: str = "packed", max_chunk_tokens: int = 0, map_capacity: int = 0, map_arena_bytes: int = 0,
-                 keep_trace: bool = False, device: int = 0):
+                 keep_trace: bool = False, device: int = 0, attention: str = "mma_sync"):
         lib = load()
         self.dims = dims
         self.device = device
@@ -304,7 +314,7 @@ class Context:
                       vocab_offsets=self._vo.ctypes.data_as(C.POINTER(C.c_uint32)),
                       n_vocab_words=len(vocab_words), max_chunk_tokens=max_chunk_tokens,
                       map_capacity=map_capacity, map_arena_bytes=map_arena_bytes, device=device,
-                      keep_trace=1 if keep_trace else 0)
+                      keep_trace=1 if keep_trace else 0, attention=ATTENTION[attention])
         h = C.c_void_p()
         st = lib.as_create(C.byref(cfg), C.byref(h))
         if st != AS_OK:

@@ -97,6 +97,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return true;
 }
 
+// Warp-uniform wait for warps that go on to the warp-collective tcgen05.ld.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, DevError* err,
+                                          uint32_t where) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, err, where);
+  return __all_sync(0xffffffffu, ok);
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
       }
-      if (!mbar_wait(tfull_bar(acc), aph, abort_flag, p.err, 30)) break;
+      if (!warp_wait(tfull_bar(acc), aph, abort_flag, p.err, 30)) break;
       fence_after();
 #pragma unroll 1
       for (int i = 0; i < CH; ++i) {
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (E::kF32) {
           // residual rows arrived by TMA; each buffer is filled CH/2 times per tile
           const uint32_t par = (lt * (CH / 2) + (i >> 1)) & 1u;
-          if (!mbar_wait(resid_bar(ew, buf), par, abort_flag, p.err, 31)) break;
+          if (!warp_wait(resid_bar(ew, buf), par, abort_flag, p.err, 31)) break;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float4* q = reinterpret_cast<float4*>(cb + r * 128 + ((j ^ (r & 7)) << 4));

@@ -62,6 +62,29 @@ as_status as_k_attention(int precision, const void* qkv, void* out, const int32_
   return AS_ERR_ARG;
 }
 
+as_status as_k_attention_tc(const void* qkv, void* vt_scratch, void* out, const int32_t* seq_start,
+                            const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
+                            void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<int32_t> lens(n_seq > 0 ? n_seq : 0), starts(n_seq > 0 ? n_seq : 0);
+  if (n_seq > 0) {
+    AS_CUDA_OK(cudaMemcpyAsync(lens.data(), seq_len, n_seq * 4, cudaMemcpyDeviceToHost, st));
+    AS_CUDA_OK(cudaMemcpyAsync(starts.data(), seq_start, n_seq * 4, cudaMemcpyDeviceToHost, st));
+    AS_CUDA_OK(cudaStreamSynchronize(st));
+  }
+  int32_t mx = 0;
+  for (int32_t i = 0; i < n_seq; ++i) {
+    if (starts[i] % 8 != 0 || starts[i] < 0 || (int64_t)starts[i] + lens[i] > rows) {
+      set_k_error("as_k_attention_tc: sequence starts must be multiples of 8 inside the rows");
+      return AS_ERR_ARG;
+    }
+    mx = lens[i] > mx ? lens[i] : mx;
+  }
+  return attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(vt_scratch),
+                           static_cast<__nv_bfloat16*>(out), seq_start, seq_len, n_seq, mx, rows, d_model, n_heads,
+                           nullptr, st);
+}
+
 as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16, int64_t rows,
                          int32_t d, void* stream) {
   return layernorm_rows(in, g, b, out_f32, static_cast<__nv_bfloat16*>(out_bf16), rows, d,

@@ -143,7 +143,7 @@ struct as_ctx {
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
   DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len;
-  DBuf X32, X16, QKV, ATT, Y32, H;
+  DBuf X32, X16, QKV, ATT, Y32, H, VT;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
   bool last_logits = false;
@@ -367,6 +367,10 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
   const int32_t ns = (int32_t)(ch.s1 - ch.s0);
   cudaStream_t st = c->stream;
+  // padding rows between sequences: token 0, position 0, owned by nobody
+  CK(cudaMemsetAsync(c->row_tok.p, 0, R * 4, st));
+  CK(cudaMemsetAsync(c->row_pos.p, 0, R * 4, st));
+  CK(cudaMemsetAsync(c->row_own.p, 0, R, st));
   expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(),
                                          c->row_own.as<uint8_t>(), c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>());
   count_launch();
@@ -385,9 +389,15 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
       __nv_bfloat16* ATT = c->ATT.as<__nv_bfloat16>();
       __nv_bfloat16* H = c->H.as<__nv_bfloat16>();
       { ProfScope ps(c, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
-      { ProfScope ps(c, 1, attn_flops);
+      if (g.attention == AS_ATTN_TCGEN05) {
+        ProfScope ps(c, 1, attn_flops);
+        CKS(attention_tcgen05(QKV, c->VT.as<__nv_bfloat16>(), ATT, c->seq_start.as<int32_t>(),
+                              c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+      } else {
+        ProfScope ps(c, 1, attn_flops);
         CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
-                           (int32_t)g.n_heads, st)); }
+                           (int32_t)g.n_heads, st));
+      }
       { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
       { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
@@ -430,7 +440,11 @@ as_status ensure_encoder_buffers(as_ctx* c, uint64_t rows, uint64_t n_seq) {
   CKS(grow(c->Y32, rows * d * 4));
   if (bf) CKS(grow(c->X16, rows * d * 2));
   CKS(grow(c->QKV, rows * 3 * d * act));
+  const void* att_before = c->ATT.p;
   CKS(grow(c->ATT, rows * d * act));
+  // rows no sequence covers are never written by attention: keep them finite
+  if (c->ATT.p != att_before) CK(cudaMemsetAsync(c->ATT.p, 0, c->ATT.cap, c->stream));
+  if (bf && g.attention == AS_ATTN_TCGEN05) CKS(grow(c->VT, attention_vt_elems((int64_t)rows, (int32_t)d) * 2));
   CKS(grow(c->H, rows * f * act));
   return AS_OK;
 }
@@ -611,24 +625,27 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
       if (a == b) continue;
       Chunk ch{i, i, 0, 0};
       while (i < seqs.size() && seqs[i].src_tok >= a && seqs[i].src_tok < b) {
-        seqs[i].row = (uint32_t)ch.rows;
-        ch.rows += seqs[i].len;
+        seqs[i].row = (uint32_t)((ch.rows + 7) & ~7ull);
+        ch.rows = seqs[i].row + seqs[i].len;
         ch.max_len = std::max(ch.max_len, seqs[i].len);
         ch.s1 = ++i;
       }
       chunks.push_back(ch);
     }
   } else {
+    // every sequence starts on a row that is a multiple of 8 (the padding rows
+    // in between belong to no sequence and are never written out)
     const uint64_t cap = g.max_chunk_tokens ? g.max_chunk_tokens : (1ull << 19);
     Chunk cur{0, 0, 0, 0};
     for (uint64_t i = 0; i < seqs.size(); ++i) {
-      if (cur.rows > 0 && cur.rows + seqs[i].len > cap) {
+      const uint64_t start = (cur.rows + 7) & ~7ull;
+      if (cur.rows > 0 && start + seqs[i].len > cap) {
         chunks.push_back(cur);
         cur = Chunk{i, i, 0, 0};
       }
-      seqs[i].row = (uint32_t)cur.rows;
+      seqs[i].row = (uint32_t)((cur.rows + 7) & ~7ull);
       cur.s1 = i + 1;
-      cur.rows += seqs[i].len;
+      cur.rows = seqs[i].row + seqs[i].len;
       cur.max_len = std::max(cur.max_len, seqs[i].len);
     }
     if (cur.rows) chunks.push_back(cur);
@@ -952,6 +969,10 @@ as_status as_create(const as_config* cfg, as_ctx** out) {
     c->err = "precision must be AS_FP32 or AS_BF16";
     return bail(AS_ERR_UNSUPPORTED);
   }
+  if (g.attention != AS_ATTN_MMA_SYNC && g.attention != AS_ATTN_TCGEN05) {
+    c->err = "attention must be AS_ATTN_MMA_SYNC or AS_ATTN_TCGEN05";
+    return bail(AS_ERR_ARG);
+  }
   if (g.mode != AS_MODE_PACKED && g.mode != AS_MODE_PER_RECORD) {
     c->err = "mode must be AS_MODE_PACKED or AS_MODE_PER_RECORD";
     return bail(AS_ERR_ARG);
@@ -1005,7 +1026,7 @@ void as_destroy(as_ctx* c) {
                  &c->nk_s, &c->nk_l, &c->nk_t, &c->rk_s, &c->rk_l, &c->rk_t, &c->fin_s, &c->fin_l, &c->fin_t,
                  &c->digests, &c->delta, &c->shift, &c->names, &c->name_off, &c->name_len, &c->seqs, &c->row_tok,
                  &c->row_pos, &c->row_own, &c->seq_start, &c->seq_len, &c->X32, &c->X16, &c->QKV, &c->ATT, &c->Y32,
-                 &c->H};
+                 &c->H, &c->VT};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);

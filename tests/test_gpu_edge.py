@@ -39,6 +39,14 @@ def _ctx(model, words, prec="fp32", **kw):
     return api.Context(DIMS, model[1], words, precision=prec, keep_trace=True, **kw)
 
 
+@pytest.mark.parametrize("attention", ["mma_sync", "tcgen05"])
+def test_windows_both_attention_engines(model, vocab_words, vocab_index, c1_records, attention):
+    recs = c1_records.records()[40:70]
+    ctx = _ctx(model, vocab_words, prec="bf16", attention=attention)
+    win = api.Schema(synth.TYPE_NAMES_4, window=128, stride=96)
+    _check_full(ctx, recs, win, synth.make_key(), model, vocab_index)
+
+
 def _check_full(ctx, recs, schema, key, model, vocab_index, record_base=0, emap=None):
     data, offs = _arrays(recs)
     out = ctx.anonymize(data, offs, schema, key)

@@ -92,6 +92,37 @@ def test_attention(prec, d, h):
     assert (out.float() - ref).abs().max().item() < tol
 
 
+@pytest.mark.parametrize("d,h", [(128, 2), (768, 12), (1024, 16)])
+@pytest.mark.parametrize("lens", [[1, 5, 64, 65, 300, 512, 17, 128], [127, 128, 129, 255, 256, 257, 1000, 8, 2048]])
+def test_attention_tcgen05(d, h, lens):
+    """tcgen05 attention against the per-sequence softmax reference; starts on multiples of 8."""
+    g = torch.Generator(device="cpu").manual_seed(d + len(lens))
+    lens = torch.tensor(lens, dtype=torch.int32)
+    starts = torch.zeros_like(lens)
+    for i in range(1, len(lens)):
+        starts[i] = ((int(starts[i - 1]) + int(lens[i - 1]) + 7) // 8) * 8 + 8 * (i % 3)
+    rows = int(starts[-1] + lens[-1]) + 5
+    qkv = torch.randn(rows, 3 * d, generator=g).to(DEV).to(torch.bfloat16)
+    out = torch.full((rows, d), float("nan"), device=DEV, dtype=torch.bfloat16)
+    vt = torch.empty(d * ((rows + 7) // 8) * 8, device=DEV, dtype=torch.bfloat16)
+    api.attention_tc(qkv, vt, out, starts.to(DEV), lens.to(DEV), d, h)
+    torch.cuda.synchronize()
+    ref = _ref_attention(qkv, starts, lens, d, h)
+    for s0, L in zip(starts.tolist(), lens.tolist()):
+        got = out[s0:s0 + L].float()
+        assert torch.isfinite(got).all()
+        assert (got - ref[s0:s0 + L]).abs().max().item() < 2.5e-2
+
+
+def test_attention_tcgen05_rejects_unaligned():
+    qkv = torch.zeros(64, 3 * 128, device=DEV, dtype=torch.bfloat16)
+    out = torch.zeros(64, 128, device=DEV, dtype=torch.bfloat16)
+    vt = torch.zeros(128 * 64, device=DEV, dtype=torch.bfloat16)
+    with pytest.raises(api.AnonShieldError):
+        api.attention_tc(qkv, vt, out, torch.tensor([0, 13], dtype=torch.int32, device=DEV),
+                         torch.tensor([10, 20], dtype=torch.int32, device=DEV), 128, 2)
+
+
 @pytest.mark.parametrize("d", [128, 768, 1024])
 def test_layernorm(d):
     g = torch.Generator(device=DEV).manual_seed(d)

@@ -34,17 +34,20 @@ def c1(vocab_words, vocab_index):
     return recs, w, key, ref
 
 
-def _run(c1, vocab_words, prec, mode):
+def _run(c1, vocab_words, prec, mode, attention="mma_sync"):
     recs, w, key, ref = c1
-    ctx = api.Context(DIMS, synth.pack_blob(DIMS, w), vocab_words, precision=prec, mode=mode, keep_trace=True)
+    ctx = api.Context(DIMS, synth.pack_blob(DIMS, w), vocab_words, precision=prec, mode=mode, keep_trace=True,
+                      attention=attention)
     out = ctx.anonymize(recs.data, recs.offsets, SCHEMA, key)
     return ctx, out, ctx.trace()
 
 
-@pytest.mark.parametrize("prec,mode", [("fp32", "packed"), ("fp32", "per_record"), ("bf16", "packed")])
-def test_c1_parity(c1, vocab_words, vocab_index, prec, mode):
+@pytest.mark.parametrize("prec,mode,attention", [("fp32", "packed", "mma_sync"), ("fp32", "per_record", "mma_sync"),
+                                                ("bf16", "packed", "mma_sync"), ("bf16", "packed", "tcgen05"),
+                                                ("bf16", "per_record", "tcgen05")])
+def test_c1_parity(c1, vocab_words, vocab_index, prec, mode, attention):
     recs, w, key, ref = c1
-    ctx, out, tr = _run(c1, vocab_words, prec, mode)
+    ctx, out, tr = _run(c1, vocab_words, prec, mode, attention)
     records = recs.records()
     U.check_tokens(tr, records, recs.offsets, ref.traces)
     U.check_regex(tr, recs.offsets, ref.traces)
