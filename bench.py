@@ -345,6 +345,7 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
     o.free()
     tr32 = f32.trace()
     f32.close()
+    # (tr32 is also the reference of the FP8 leg)
     bf = api.Context(w.dims, blob, words, precision="bf16", mode="packed", keep_trace=True, device=local)
     bf.anonymize(sample.data, sample.offsets, schema, key).free()
     tr16 = bf.trace()
@@ -359,8 +360,50 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
            "label_agreement_bf16_vs_fp32": {"agreement": agree, "confident_tokens": int(conf.sum()),
                                             "max_abs_logit_diff": max_dlogit,
                                             "sample": f"first {sample.n} records, FP32 margin > 0.05"}}
+    out["fp8"] = fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32)
     out["cpu_baseline"] = cpu_baseline(w, words, recs, weights, key)
     return out
+
+
+def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32) -> dict:
+    """FP8 e4m3 GEMMs (static scales from 64 calibration records) on the same workload."""
+    import torch
+    import paper_2606_15650_b300.api as api
+    ctx = api.Context(w.dims, blob, words, precision="fp8", mode="packed", keep_trace=True, device=local)
+    cal = synth.make_records(synth.scaled(w, 64).records, words, seed=synth.SEED_CALIB)
+    ctx.calibrate(cal.data, cal.offsets, schema)
+    ctx.anonymize(sample.data, sample.offsets, schema, key).free()
+    tr8 = ctx.trace()
+    lg = tr32["logits"]
+    srt = np.sort(lg, axis=1)
+    conf = (srt[:, -1] - srt[:, -2]) > 0.05
+    agree = float(np.mean(tr8["labels"][conf] == tr32["labels"][conf]))
+    max_d = float(np.max(np.abs(tr8["logits"] - lg)))
+    ctx.close()
+    ctx = api.Context(w.dims, blob, words, precision="fp8", mode="packed", device=local)
+    ctx.calibrate(cal.data, cal.offsets, schema)
+    stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{local}")
+    d_data = torch.from_numpy(recs.data).to(f"cuda:{local}")
+    d_offs = torch.from_numpy(recs.offsets.astype(np.int64)).to(f"cuda:{local}")
+    ctx.anonymize(d_data, d_offs, schema, key).free()
+    ctx.profile(True)
+    ms = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = ctx.anonymize(d_data, d_offs, schema, key)
+        e1.record(stream)
+        e1.synchronize()
+        st = o.stats()
+        o.free()
+        ms.append(e0.elapsed_time(e1))
+    prof = ctx.profile_read()
+    ctx.close()
+    return {"value": st["n_encoded_tokens"] / (np.mean(ms) / 1e3), "unit": "tokens/s", "steps": len(ms),
+            "gemm_tflops": prof["gemm_flops"] / max(prof["gemm_ms"], 1e-9) / 1e9,
+            "label_agreement_vs_fp32": agree, "max_abs_logit_diff_vs_fp32": max_d,
+            "sample": f"agreement on the first {sample.n} records; timing on the whole workload; "
+                      f"scales from 64 calibration records (seed {synth.SEED_CALIB})"}
 
 
 def main():

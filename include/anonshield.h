@@ -50,9 +50,13 @@ typedef int32_t as_status;
 
 /* Encoder arithmetic. FP32: FP32 everywhere (SIMT GEMM). BF16: GEMM inputs
  * rounded to BF16, FP32 accumulate; bias, residual, LayerNorm, softmax and
- * logits in FP32. */
+ * logits in FP32. FP8: GEMM inputs in E4M3 with static per-tensor scales
+ * (weights: amax / 448 at as_create; activations: amax / 448 over a
+ * calibration set, see as_calibrate), FP32 accumulate; Q/K/V and attention
+ * in BF16/FP32; bias, residual, LayerNorm, softmax and logits in FP32. */
 #define AS_FP32 0
 #define AS_BF16 1
+#define AS_FP8  2
 
 /* Encoder batching. PACKED: all records of a call packed into large
  * variable-length batches. PER_RECORD: one record per launch sequence. */
@@ -77,7 +81,7 @@ typedef struct as_output as_output;
  *   vocab_bytes[vocab_offsets[k] .. vocab_offsets[k+1]). Host memory. */
 typedef struct {
   uint32_t vocab, d_model, n_heads, d_ffn, n_layers, n_labels, max_pos;
-  uint32_t precision;            /* AS_FP32 or AS_BF16                         */
+  uint32_t precision;            /* AS_FP32, AS_BF16 or AS_FP8                 */
   uint32_t mode;                 /* AS_MODE_PACKED or AS_MODE_PER_RECORD       */
   const float* weights;          /* host                                       */
   uint64_t weights_len;          /* floats                                     */
@@ -198,6 +202,19 @@ typedef struct {
   const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+/* FP8 contexts: set the static activation scales from a calibration set.
+ * Runs the tokenizer and the BF16 encoder over `records` (same layout rules
+ * as as_anonymize) and records, for each FP8 GEMM input (per layer: the QKV,
+ * output, FFN-in and FFN-out projection inputs), the largest magnitude; each
+ * scale is that amax / 448 (the E4M3 maximum). Fixed scales make a record's
+ * result independent of the batch it arrives in. Touches neither the map nor
+ * the key. Errors: AS_ERR_STATE (not an FP8 context), as as_anonymize. */
+as_status as_calibrate(as_ctx* ctx, const as_records* records, const as_schema* schema);
+/* Read / load the activation scales (4 per layer, order above) so that a
+ * calibration can be stored with the weights and reused. */
+as_status as_get_scales(as_ctx* ctx, float* scales, uint64_t n);
+as_status as_set_scales(as_ctx* ctx, const float* scales, uint64_t n);
 
 /* The ctx's CUDA stream (a cudaStream_t): every kernel of the ctx runs on
  * it, so a caller can time a call with CUDA events recorded on it. */

@@ -38,6 +38,14 @@ as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t 
                     const void* A, const void* B, const float* bias, const float* resid, void* out,
                     void* stream);
 
+/* E4M3 GEMM on tcgen05 (kind::f8f6f4): out = epi(alpha * (A8 . B8^T)), A8
+ * [M][K] and B8 [N][K] E4M3 bytes, FP32 accumulation. Outputs as for
+ * AS_EPI_* in BF16 (FP32 for AS_EPI_BIAS_RESID); with out_e4m3 = 1
+ * (AS_EPI_BIAS_GELU only) the output is E4M3 of value / out_scale, rounded
+ * to nearest even and saturated to +-448. K % 128 == 0, N % 128 == 0. */
+as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_t K, const void* A8, const void* B8,
+                        float alpha, float out_scale, const float* bias, const float* resid, void* out, void* stream);
+
 /* Multi-head self-attention over packed variable-length sequences.
  * qkv: [rows][3*d] (Q | K | V column blocks; head j owns columns j*64..j*64+63
  * of each), act type of `precision`; out: [rows][d] act type. Sequence s

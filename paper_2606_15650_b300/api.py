@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libanonshield.so")
 AS_OK = 0
 STATUS = {0: "AS_OK", -1: "AS_ERR_ARG", -2: "AS_ERR_OOM", -3: "AS_ERR_CUDA", -4: "AS_ERR_TOO_LONG",
           -5: "AS_ERR_TIMEOUT", -6: "AS_ERR_STATE", -7: "AS_ERR_UNSUPPORTED", -8: "AS_ERR_CAPACITY"}
-PRECISION = {"fp32": 0, "bf16": 1}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 MODE = {"packed": 0, "per_record": 1}
 EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
 ENGINE = {"auto": 0, "tcgen05": 1, "simt": 2}
@@ -81,7 +81,8 @@ class _Profile(C.Structure):
 
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
-            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_k_gemm", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
+            "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
+            "as_get_scales", "as_set_scales", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -116,10 +117,15 @@ def load() -> C.CDLL:
     lib.as_free.restype = None
     lib.as_version.restype = C.c_char_p
     lib.as_get_stream.argtypes = [P, C.POINTER(P)]
+    lib.as_calibrate.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema)]
+    lib.as_get_scales.argtypes = [P, P, C.c_uint64]
+    lib.as_set_scales.argtypes = [P, P, C.c_uint64]
     lib.as_profile.argtypes = [P, C.c_uint32]
     lib.as_profile_read.argtypes = [P, C.POINTER(_Profile)]
     lib.as_tokenize_static.argtypes = [P, P, P, C.c_uint64, C.c_uint64, P, P, P, P, P, P]
     lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
+    lib.as_k_gemm_fp8.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, C.c_float, C.c_float,
+                                  P, P, P, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_attention_tc.argtypes = [P, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
@@ -165,6 +171,17 @@ def gemm(precision: str, epilogue: str, A, B, bias=None, resid=None, out=None, e
     N = B.shape[0]
     _check_k(load().as_k_gemm(PRECISION[precision], ENGINE[engine], EPI[epilogue], M, N, K, _ptr(A), _ptr(B),
                               _ptr(bias), _ptr(resid), _ptr(out), stream))
+    return out
+
+
+def gemm_fp8(epilogue: str, A8, B8, alpha: float, bias=None, resid=None, out=None, out_scale: float = 0.0,
+             stream=None):
+    """out = epi(alpha * A8 @ B8^T) with E4M3 operands (torch.float8_e4m3fn or uint8 tensors)."""
+    M, K = A8.shape
+    N = B8.shape[0]
+    out_e4m3 = 1 if out_scale > 0 else 0
+    _check_k(load().as_k_gemm_fp8(EPI[epilogue], out_e4m3, M, N, K, _ptr(A8), _ptr(B8), alpha, out_scale or 1.0,
+                                  _ptr(bias), _ptr(resid), _ptr(out), stream))
     return out
 
 
@@ -352,6 +369,25 @@ class Context:
         del keep, names
         self._check(st)
         return Output(self, out.value)
+
+    def calibrate(self, data, offsets, schema: Schema):
+        """FP8: set static activation scales from calibration records (host arrays)."""
+        d = np.ascontiguousarray(data, dtype=np.uint8)
+        o = np.ascontiguousarray(offsets, dtype=np.uint64)
+        rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
+                       on_device=0)
+        sc, names = self._schema(schema)
+        self._check(load().as_calibrate(self._h, C.byref(rec), C.byref(sc)))
+        del names
+
+    def scales(self) -> np.ndarray:
+        out = np.zeros(4 * self.dims.n_layers, np.float32)
+        self._check(load().as_get_scales(self._h, out.ctypes.data, out.size))
+        return out
+
+    def set_scales(self, scales: np.ndarray):
+        sc = np.ascontiguousarray(scales, dtype=np.float32)
+        self._check(load().as_set_scales(self._h, sc.ctypes.data, sc.size))
 
     def map_export(self) -> list[Entity]:
         p, n = C.POINTER(_Entity)(), C.c_uint64()

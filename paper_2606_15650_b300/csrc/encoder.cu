@@ -208,6 +208,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Two FP32 values to E4M3 (round to nearest even, saturate to +-448), first
+// value in the low byte.
+__device__ __forceinline__ uint16_t pack_e4m3(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   // src-size 0 zero-fills the 16 destination bytes (keys past the sequence end)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
@@ -238,11 +246,12 @@ __device__ __forceinline__ float ex2(float x) {
 // tiles of 64 keys are double-buffered in shared memory with cp.async;
 // B fragments come from ldmatrix (K) and ldmatrix.trans (V); S = Q K^T and
 // O += P V run on m16n8k16 BF16 tensor cores; softmax statistics in FP32.
+template <bool OUT8>
 __global__ void __launch_bounds__(128, 4) attn_bf16_kernel(const __nv_bfloat16* __restrict__ qkv,
-                                                          __nv_bfloat16* __restrict__ out,
+                                                          void* __restrict__ out_v,
                                                           const int32_t* __restrict__ seq_start,
                                                           const int32_t* __restrict__ seq_len, int d, int n_heads,
-                                                          int q_tiles) {
+                                                          int q_tiles, float out_inv_scale) {
   constexpr int P = 72;  // padded row (bf16): 144 B, conflict-free ldmatrix rows
   __shared__ __align__(128) __nv_bfloat16 Ks[2][64][P];
   __shared__ __align__(128) __nv_bfloat16 Vs[2][64][P];
@@ -370,11 +379,40 @@ __global__ void __launch_bounds__(128, 4) attn_bf16_kernel(const __nv_bfloat16* 
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const int c = h * 64 + nt * 8 + 2 * t;
-    if (qr0 < L)
-      *reinterpret_cast<uint32_t*>(out + (row0 + qr0) * d + c) = pack_bf16(o[nt][0] * i0, o[nt][1] * i0);
-    if (qr1 < L)
-      *reinterpret_cast<uint32_t*>(out + (row0 + qr1) * d + c) = pack_bf16(o[nt][2] * i1, o[nt][3] * i1);
+    if (OUT8) {
+      uint8_t* out = static_cast<uint8_t*>(out_v);
+      const float a0 = i0 * out_inv_scale, a1 = i1 * out_inv_scale;
+      if (qr0 < L) *reinterpret_cast<uint16_t*>(out + (row0 + qr0) * d + c) = pack_e4m3(o[nt][0] * a0, o[nt][1] * a0);
+      if (qr1 < L) *reinterpret_cast<uint16_t*>(out + (row0 + qr1) * d + c) = pack_e4m3(o[nt][2] * a1, o[nt][3] * a1);
+    } else {
+      __nv_bfloat16* out = static_cast<__nv_bfloat16*>(out_v);
+      if (qr0 < L)
+        *reinterpret_cast<uint32_t*>(out + (row0 + qr0) * d + c) = pack_bf16(o[nt][0] * i0, o[nt][1] * i0);
+      if (qr1 < L)
+        *reinterpret_cast<uint32_t*>(out + (row0 + qr1) * d + c) = pack_bf16(o[nt][2] * i1, o[nt][3] * i1);
+    }
   }
+}
+
+as_status attention_bf16_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* seq_start,
+                              const int32_t* seq_len, int32_t n_seq, int32_t max_len, int32_t d_model,
+                              int32_t n_heads, cudaStream_t st) {
+  if (n_seq == 0 || max_len == 0) return AS_OK;
+  if (d_model != n_heads * 64 || max_len > 4096 || !(out_scale > 0.f)) {
+    set_k_error("attention: head dim must be 64, sequences at most 4096 tokens, scale > 0");
+    return AS_ERR_ARG;
+  }
+  const int q_tiles = (max_len + 63) / 64;
+  const uint64_t blocks = (uint64_t)n_seq * n_heads * q_tiles;
+  if (blocks > 0x7FFFFFFFull) {
+    set_k_error("attention: too many sequences in one batch");
+    return AS_ERR_ARG;
+  }
+  attn_bf16_kernel<true><<<(unsigned)blocks, 128, 0, st>>>(qkv, out, seq_start, seq_len, d_model, n_heads, q_tiles,
+                                                           1.0f / out_scale);
+  count_launch();
+  AS_CUDA_OK(cudaGetLastError());
+  return AS_OK;
 }
 
 as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
@@ -391,7 +429,8 @@ as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int
     set_k_error("attention_bf16: too many sequences in one batch");
     return AS_ERR_ARG;
   }
-  attn_bf16_kernel<<<(unsigned)blocks, 128, 0, st>>>(qkv, out, seq_start, seq_len, d_model, n_heads, q_tiles);
+  attn_bf16_kernel<false><<<(unsigned)blocks, 128, 0, st>>>(qkv, out, seq_start, seq_len, d_model, n_heads, q_tiles,
+                                                            1.0f);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
@@ -425,25 +464,37 @@ __device__ __forceinline__ void ln_row(float4 (&v)[CH], int d, const float* __re
   }
 }
 
+// Second output copy of a normalized row: BF16, or E4M3 of value * inv8.
+struct Out2 {
+  __nv_bfloat16* bf16;
+  uint8_t* e4m3;
+  float inv8;
+};
+
 template <int CH>
-__device__ __forceinline__ void store_row(const float4 (&v)[CH], float* out_f32, __nv_bfloat16* out_bf16, int lane) {
+__device__ __forceinline__ void store_row(const float4 (&v)[CH], float* out_f32, Out2 o2, int64_t row, int d, int lane) {
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int col = (c * 32 + lane) * 4;
-    if (out_f32) *reinterpret_cast<float4*>(out_f32 + col) = v[c];
-    if (out_bf16) {
+    if (out_f32) *reinterpret_cast<float4*>(out_f32 + row * d + col) = v[c];
+    if (o2.bf16) {
       uint2 w;
       w.x = pack_bf16(v[c].x, v[c].y);
       w.y = pack_bf16(v[c].z, v[c].w);
-      *reinterpret_cast<uint2*>(out_bf16 + col) = w;
+      *reinterpret_cast<uint2*>(o2.bf16 + row * d + col) = w;
+    }
+    if (o2.e4m3) {
+      const uint32_t w = (uint32_t)pack_e4m3(v[c].x * o2.inv8, v[c].y * o2.inv8) |
+                         ((uint32_t)pack_e4m3(v[c].z * o2.inv8, v[c].w * o2.inv8) << 16);
+      *reinterpret_cast<uint32_t*>(o2.e4m3 + row * d + col) = w;
     }
   }
 }
 
 template <int CH>
 __global__ void __launch_bounds__(256) ln_kernel(const float* in, const float* __restrict__ g,
-                                                 const float* __restrict__ b, float* out_f32,
-                                                 __nv_bfloat16* out_bf16, int64_t rows, int d) {
+                                                 const float* __restrict__ b, float* out_f32, Out2 o2,
+                                                 int64_t rows, int d) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= rows) return;
@@ -452,7 +503,7 @@ __global__ void __launch_bounds__(256) ln_kernel(const float* in, const float* _
 #pragma unroll
   for (int c = 0; c < CH; ++c) v[c] = *reinterpret_cast<const float4*>(x + (c * 32 + lane) * 4);
   ln_row<CH>(v, d, g, b, lane);
-  store_row<CH>(v, out_f32 ? out_f32 + row * d : nullptr, out_bf16 ? out_bf16 + row * d : nullptr, lane);
+  store_row<CH>(v, out_f32, o2, row, d, lane);
 }
 
 template <int CH>
@@ -461,7 +512,7 @@ __global__ void __launch_bounds__(256) embed_ln_kernel(const int32_t* __restrict
                                                        const int32_t* __restrict__ row_pos,
                                                        const float* __restrict__ E, const float* __restrict__ P,
                                                        const float* __restrict__ g, const float* __restrict__ b,
-                                                       float* out_f32, __nv_bfloat16* out_bf16, int64_t rows, int d) {
+                                                       float* out_f32, Out2 o2, int64_t rows, int d) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= rows) return;
@@ -476,7 +527,7 @@ __global__ void __launch_bounds__(256) embed_ln_kernel(const int32_t* __restrict
     v[c] = make_float4(e.x + p.x, e.y + p.y, e.z + p.z, e.w + p.w);
   }
   ln_row<CH>(v, d, g, b, lane);
-  store_row<CH>(v, out_f32 ? out_f32 + row * d : nullptr, out_bf16 ? out_bf16 + row * d : nullptr, lane);
+  store_row<CH>(v, out_f32, o2, row, d, lane);
 }
 
 template <int CH>
@@ -533,10 +584,16 @@ __global__ void __launch_bounds__(256) ln_classify_kernel(const float* in, const
 
 as_status layernorm_rows(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
                          int64_t rows, int32_t d, cudaStream_t st) {
+  return layernorm_rows_ex(in, g, b, out_f32, out_bf16, nullptr, 1.0f, rows, d, st);
+}
+
+as_status layernorm_rows_ex(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                            uint8_t* out_e4m3, float e4m3_scale, int64_t rows, int32_t d, cudaStream_t st) {
   if (rows == 0) return AS_OK;
   if (d % 128) { set_k_error("layernorm: d must be a multiple of 128"); return AS_ERR_ARG; }
   const unsigned grid = (unsigned)((rows + 7) / 8);
-  AS_CH_DISPATCH(d, ln_kernel<CH><<<grid, 256, 0, st>>>(in, g, b, out_f32, out_bf16, rows, d));
+  const Out2 o2{out_bf16, out_e4m3, 1.0f / e4m3_scale};
+  AS_CH_DISPATCH(d, ln_kernel<CH><<<grid, 256, 0, st>>>(in, g, b, out_f32, o2, rows, d));
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
@@ -545,10 +602,17 @@ as_status layernorm_rows(const float* in, const float* g, const float* b, float*
 as_status embed_ln(const int32_t* tok_ids, const int32_t* row_tok, const int32_t* row_pos, const float* tok_emb,
                    const float* pos_emb, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
                    int64_t rows, int32_t d, cudaStream_t st) {
+  return embed_ln_ex(tok_ids, row_tok, row_pos, tok_emb, pos_emb, g, b, out_f32, out_bf16, nullptr, 1.0f, rows, d, st);
+}
+
+as_status embed_ln_ex(const int32_t* tok_ids, const int32_t* row_tok, const int32_t* row_pos, const float* tok_emb,
+                      const float* pos_emb, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                      uint8_t* out_e4m3, float e4m3_scale, int64_t rows, int32_t d, cudaStream_t st) {
   if (rows == 0) return AS_OK;
   const unsigned grid = (unsigned)((rows + 7) / 8);
+  const Out2 o2{out_bf16, out_e4m3, 1.0f / e4m3_scale};
   AS_CH_DISPATCH(d, embed_ln_kernel<CH><<<grid, 256, 0, st>>>(tok_ids, row_tok, row_pos, tok_emb, pos_emb, g, b,
-                                                              out_f32, out_bf16, rows, d));
+                                                              out_f32, o2, rows, d));
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
@@ -565,6 +629,44 @@ as_status layernorm_classify(const float* in, const float* g, const float* b, co
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
+}
+
+// Largest |x| over a buffer, folded into *amax_bits with atomicMax on the
+// IEEE bit pattern (non-negative floats order like unsigned integers).
+template <typename T>
+__global__ void amax_kernel(const T* __restrict__ x, uint64_t n, unsigned int* amax_bits) {
+  float m = 0.f;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, __float_as_uint(m));
+}
+
+void amax_f32(const float* x, uint64_t n, unsigned int* amax_bits, cudaStream_t st) {
+  if (n == 0) return;
+  amax_kernel<float><<<grid_1d(n, 256, 148 * 16), 256, 0, st>>>(x, n, amax_bits);
+  count_launch();
+}
+
+void amax_bf16(const __nv_bfloat16* x, uint64_t n, unsigned int* amax_bits, cudaStream_t st) {
+  if (n == 0) return;
+  amax_kernel<__nv_bfloat16><<<grid_1d(n, 256, 148 * 16), 256, 0, st>>>(x, n, amax_bits);
+  count_launch();
+}
+
+// y = E4M3(x / scale), round to nearest even with saturation.
+__global__ void quantize_e4m3_kernel(const float* __restrict__ x, uint8_t* __restrict__ y, uint64_t n2, float inv) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n2; i += (uint64_t)gridDim.x * blockDim.x) {
+    const float2 v = reinterpret_cast<const float2*>(x)[i];
+    reinterpret_cast<uint16_t*>(y)[i] = pack_e4m3(v.x * inv, v.y * inv);
+  }
+}
+
+void quantize_e4m3(const float* x, uint8_t* y, uint64_t n, float scale, cudaStream_t st) {
+  if (n == 0) return;
+  quantize_e4m3_kernel<<<grid_1d(n / 2, 256, 148 * 64), 256, 0, st>>>(x, y, n / 2, 1.0f / scale);
+  count_launch();
 }
 
 __global__ void f32_to_bf16_kernel(const float* in, __nv_bfloat16* out, uint64_t n) {

@@ -9,6 +9,12 @@ namespace as {
 // C = epi(A . B^T) on tcgen05 (BF16 in, FP32 accumulate). See gemm_tc.cu.
 as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
                        const float* resid, void* out, DevError* err, cudaStream_t st);
+// General form: A and B in BF16 or E4M3 (in_e4m3), output BF16 / FP32 (by
+// epilogue) or E4M3 (out_e4m3, GELU epilogue only, value / out_scale with
+// saturation); out = epi(alpha * (A . B^T)).
+as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
+                          const void* B, const float* bias, const float* resid, void* out, float alpha,
+                          float out_scale, DevError* err, cudaStream_t st);
 // Same contract in FP32 on CUDA cores.
 as_status gemm_simt_f32(int epi, int64_t M, int64_t N, int64_t K, const float* A, const float* B, const float* bias,
                         const float* resid, float* out, cudaStream_t st);
@@ -42,6 +48,22 @@ as_status embed_ln(const int32_t* tok_ids, const int32_t* row_tok, const int32_t
 as_status layernorm_classify(const float* in, const float* g, const float* b, const float* cls_w, const float* cls_b,
                              int32_t C, const int32_t* row_tok, const uint8_t* row_own, float* logits,
                              uint8_t* labels, int64_t rows, int32_t d, cudaStream_t st);
+
+// Same with the second copy in E4M3 (value / e4m3_scale, saturating) when
+// out_e4m3 is not NULL.
+as_status layernorm_rows_ex(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                            uint8_t* out_e4m3, float e4m3_scale, int64_t rows, int32_t d, cudaStream_t st);
+as_status embed_ln_ex(const int32_t* tok_ids, const int32_t* row_tok, const int32_t* row_pos, const float* tok_emb,
+                      const float* pos_emb, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,
+                      uint8_t* out_e4m3, float e4m3_scale, int64_t rows, int32_t d, cudaStream_t st);
+// BF16 attention writing E4M3 (value / out_scale, saturating).
+as_status attention_bf16_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* seq_start,
+                              const int32_t* seq_len, int32_t n_seq, int32_t max_len, int32_t d_model,
+                              int32_t n_heads, cudaStream_t st);
+// amax (as float bits, atomicMax) and E4M3 quantization (n even).
+void amax_f32(const float* x, uint64_t n, unsigned int* amax_bits, cudaStream_t st);
+void amax_bf16(const __nv_bfloat16* x, uint64_t n, unsigned int* amax_bits, cudaStream_t st);
+void quantize_e4m3(const float* x, uint8_t* y, uint64_t n, float scale, cudaStream_t st);
 
 // FP32 -> BF16 copy (round to nearest even).
 void convert_f32_bf16(const float* in, __nv_bfloat16* out, uint64_t n, cudaStream_t st);

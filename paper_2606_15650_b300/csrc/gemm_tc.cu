@@ -30,7 +30,12 @@ namespace as {
 namespace tc {
 
 constexpr int kBM = 128;
-constexpr int kBK = 64;             // one 128-byte swizzle atom of BF16
+constexpr int kBK = 64;             // BF16 elements per k-block: one 128-byte swizzle atom
+// Operand / output element types of one instantiation
+constexpr int kInBF16 = 0, kInE4M3 = 1;
+constexpr int kOutBF16 = 0, kOutF32 = 1, kOutE4M3 = 2;
+// elements per k-block: a 128-byte swizzled row holds 64 BF16 or 128 E4M3
+__host__ __device__ constexpr int bk_elems(int in) { return in == kInE4M3 ? 128 : 64; }
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer + MMA + epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -43,6 +48,8 @@ struct Params {
   const float* resid;
   void* out;
   DevError* err;
+  float alpha;          // accumulator scale (product of the FP8 operand scales; 1 for BF16)
+  float out_scale_inv;  // 1 / scale of an FP8 output
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -130,12 +137,25 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f8f6f4 with A and B in E4M3 (format code 0), D in FP32.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
@@ -203,22 +223,24 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // Epilogue staging: each epilogue warp owns two 32x32 chunk buffers. BF16
 // chunks have 64-byte rows stored with the 64-byte TMA swizzle (16-byte
 // piece j of row r at j ^ ((r >> 1) & 3)); FP32 chunks have 128-byte rows
-// with the 128-byte swizzle (piece j at j ^ (r & 7)). The warp writes (and,
-// for the residual, reads) one row per lane without bank conflicts, and the
-// TMA engine moves whole lines to and from global memory.
-template <int EPI>
+// with the 128-byte swizzle (piece j at j ^ (r & 7)); E4M3 chunks have
+// 32-byte rows with the 32-byte swizzle (piece j at j ^ ((r >> 2) & 1)). The
+// warp writes (and, for the residual, reads) one row per lane without bank
+// conflicts, and the TMA engine moves whole lines to and from global memory.
+template <int OUT>
 struct EpiTraits {
-  static constexpr bool kF32 = EPI == AS_EPI_BIAS_RESID;
-  static constexpr int kChunkBytes = 32 * 32 * (kF32 ? 4 : 2);
+  static constexpr bool kF32 = OUT == kOutF32;
+  static constexpr int kEsize = OUT == kOutF32 ? 4 : (OUT == kOutBF16 ? 2 : 1);
+  static constexpr int kChunkBytes = 32 * 32 * kEsize;
 };
 
-template <int BN, int STAGES, int EPI>
+template <int BN, int STAGES, int OUT>
 struct Smem {
-  static constexpr int kABytes = kBM * kBK * 2;   // 16 KB
-  static constexpr int kBBytes = BN * kBK * 2;    // 16 or 32 KB
+  static constexpr int kABytes = kBM * 128;       // 16 KB: 128 rows x 128 bytes
+  static constexpr int kBBytes = BN * 128;        // 16 or 32 KB
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStgOff = STAGES * kStageBytes;                       // 1024-aligned
-  static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<EPI>::kChunkBytes;
+  static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<OUT>::kChunkBytes;
   static constexpr int kBarOff = kStgOff + kStgBytes;
   // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][2]; tmem slot + abort flag
   static constexpr int kNumBars = 2 * STAGES + 4 + 2 * kEpiWarps;
@@ -226,14 +248,16 @@ struct Smem {
   static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
 };
 
-template <int BN, int STAGES, int EPI>
+template <int BN, int STAGES, int EPI, int IN, int OUT>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR, Params p) {
-  using L = Smem<BN, STAGES, EPI>;
-  using E = EpiTraits<EPI>;
+  using L = Smem<BN, STAGES, OUT>;
+  using E = EpiTraits<OUT>;
+  static_assert((EPI == AS_EPI_BIAS_RESID) == (OUT == kOutF32), "the residual epilogue writes FP32");
   constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
-  constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+  constexpr uint32_t kIdesc = IN == kInE4M3 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
+  constexpr int kBKe = bk_elems(IN);
   constexpr int CH = BN / 64;              // 32-column chunks per epilogue warp and tile
   static_assert(CH % 2 == 0, "chunks alternate between two staging buffers");
   extern __shared__ uint8_t smem_raw[];
@@ -250,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int KB = p.K / kBK;
+  const int KB = p.K / kBKe;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -295,8 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.err, 10)) goto done;
           mbar_expect_tx(full_bar(s), L::kStageBytes);
           const uint32_t a_dst = sbase + s * L::kStageBytes;
-          tma_load_2d(a_dst, &tmA, full_bar(s), kb * kBK, m0);
-          tma_load_2d(a_dst + L::kABytes, &tmB, full_bar(s), kb * kBK, n0);
+          tma_load_2d(a_dst, &tmA, full_bar(s), kb * kBKe, m0);
+          tma_load_2d(a_dst + L::kABytes, &tmB, full_bar(s), kb * kBKe, n0);
         }
       }
     }
@@ -316,9 +340,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after();
           const uint32_t a_addr = sbase + s * L::kStageBytes;
           const uint64_t adesc = sw128_desc(a_addr), bdesc = sw128_desc(a_addr + L::kABytes);
+          // four MMAs per 128-byte k-block (K = 16 BF16 or 32 E4M3 each): 32 bytes apart
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k) {
+            if (IN == kInE4M3)
+              mma_e4m3(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+            else
+              mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+          }
           mma_commit(empty_bar(s));
         }
         mma_commit(tfull_bar(acc));
@@ -363,10 +392,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
-          v[j + 0] = __uint_as_float(rr[j + 0]) + b.x;
-          v[j + 1] = __uint_as_float(rr[j + 1]) + b.y;
-          v[j + 2] = __uint_as_float(rr[j + 2]) + b.z;
-          v[j + 3] = __uint_as_float(rr[j + 3]) + b.w;
+          v[j + 0] = fmaf(__uint_as_float(rr[j + 0]), p.alpha, b.x);
+          v[j + 1] = fmaf(__uint_as_float(rr[j + 1]), p.alpha, b.y);
+          v[j + 2] = fmaf(__uint_as_float(rr[j + 2]), p.alpha, b.z);
+          v[j + 3] = fmaf(__uint_as_float(rr[j + 3]), p.alpha, b.w);
         }
         uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
         if (E::kF32) {
@@ -386,18 +415,36 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (lane == 0) bulk_wait_read<1>();  // the store two chunks back has read this buffer
           __syncwarp();
+          if (OUT == kOutE4M3) {
+            // E4M3 with saturation, round to nearest even: 32 bytes = 2 pieces
+            uint32_t q[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint4 w;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * j + 0], v[8 * j + 1]);
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * j + 2], v[8 * j + 3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 4], v[8 * j + 5]);
-            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * j + 6], v[8 * j + 7]);
-            w.x = *reinterpret_cast<uint32_t*>(&h0);
-            w.y = *reinterpret_cast<uint32_t*>(&h1);
-            w.z = *reinterpret_cast<uint32_t*>(&h2);
-            w.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4)) = w;
+            for (int j = 0; j < 8; ++j) {
+              uint16_t lo, hi;
+              asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(v[4 * j + 1] * p.out_scale_inv),
+                  "f"(v[4 * j] * p.out_scale_inv));
+              asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(v[4 * j + 3] * p.out_scale_inv),
+                  "f"(v[4 * j + 2] * p.out_scale_inv));
+              q[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+              *reinterpret_cast<uint4*>(cb + r * 32 + ((j ^ ((r >> 2) & 1)) << 4)) =
+                  make_uint4(q[4 * j], q[4 * j + 1], q[4 * j + 2], q[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              uint4 w;
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * j + 0], v[8 * j + 1]);
+              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * j + 2], v[8 * j + 3]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 4], v[8 * j + 5]);
+              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * j + 6], v[8 * j + 7]);
+              w.x = *reinterpret_cast<uint32_t*>(&h0);
+              w.y = *reinterpret_cast<uint32_t*>(&h1);
+              w.z = *reinterpret_cast<uint32_t*>(&h2);
+              w.w = *reinterpret_cast<uint32_t*>(&h3);
+              *reinterpret_cast<uint4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4)) = w;
+            }
           }
         }
         fence_proxy_async();
@@ -467,28 +514,34 @@ as_status make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dtype, 
   return AS_OK;
 }
 
-template <int BN, int STAGES, int EPI>
+template <int BN, int STAGES, int EPI, int IN, int OUT>
 as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStream_t st) {
-  using L = tc::Smem<BN, STAGES, EPI>;
+  using L = tc::Smem<BN, STAGES, OUT>;
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
-    AS_CUDA_OK(
-        cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
+    AS_CUDA_OK(cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, EPI, IN, OUT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
     attr_set[dev & 63] = true;
   }
   CUtensorMap tmA, tmB, tmC, tmR;
   const auto bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  as_status s = make_map(&tmA, A, bf, 2, (uint64_t)p0.M, (uint64_t)p0.K, tc::kBK, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
-  if (s == AS_OK) s = make_map(&tmB, B, bf, 2, (uint64_t)p0.N, (uint64_t)p0.K, tc::kBK, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  const auto u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const auto ein = IN == tc::kInE4M3 ? u8 : bf;
+  const uint32_t isz = IN == tc::kInE4M3 ? 1 : 2, bke = tc::bk_elems(IN);
+  as_status s = make_map(&tmA, A, ein, isz, (uint64_t)p0.M, (uint64_t)p0.K, bke, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK) s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN, CU_TENSOR_MAP_SWIZZLE_128B);
   if (s == AS_OK) {
-    if (tc::EpiTraits<EPI>::kF32) {
+    if (OUT == tc::kOutF32) {
       s = make_map(&tmC, p0.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
                    CU_TENSOR_MAP_SWIZZLE_128B);
       if (s == AS_OK)
         s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
                      CU_TENSOR_MAP_SWIZZLE_128B);
+    } else if (OUT == tc::kOutE4M3) {
+      s = make_map(&tmC, p0.out, u8, 1, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32, CU_TENSOR_MAP_SWIZZLE_32B);
+      tmR = tmC;  // unused
     } else {
       s = make_map(&tmC, p0.out, bf, 2, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B);
       tmR = tmC;  // unused
@@ -499,16 +552,42 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   p.n_tiles_n = p.N / BN;
   p.n_tiles = p.n_tiles_n * ((p.M + tc::kBM - 1) / tc::kBM);
   int grid = p.n_tiles < g_num_sms ? p.n_tiles : g_num_sms;
-  tc::gemm_kernel<BN, STAGES, EPI><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
+  tc::gemm_kernel<BN, STAGES, EPI, IN, OUT><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
 }
 
+template <int IN>
+as_status dispatch(const tc::Params& p, int epi, bool out_e4m3, const void* A, const void* B, cudaStream_t st) {
+  const bool wide = p.N % 256 == 0;
+  switch (epi) {
+    case AS_EPI_BIAS:
+      if (out_e4m3) break;
+      return wide ? launch_bn<256, 4, AS_EPI_BIAS, IN, tc::kOutBF16>(p, A, B, st)
+                  : launch_bn<128, 6, AS_EPI_BIAS, IN, tc::kOutBF16>(p, A, B, st);
+    case AS_EPI_BIAS_GELU:
+      if (out_e4m3)
+        return wide ? launch_bn<256, 4, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3>(p, A, B, st)
+                    : launch_bn<128, 6, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3>(p, A, B, st);
+      return wide ? launch_bn<256, 4, AS_EPI_BIAS_GELU, IN, tc::kOutBF16>(p, A, B, st)
+                  : launch_bn<128, 6, AS_EPI_BIAS_GELU, IN, tc::kOutBF16>(p, A, B, st);
+    case AS_EPI_BIAS_RESID:
+      if (out_e4m3) break;
+      return wide ? launch_bn<256, 3, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st)
+                  : launch_bn<128, 4, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st);
+    default:
+      break;
+  }
+  set_k_error("gemm_tcgen05: unsupported epilogue / output combination");
+  return AS_ERR_ARG;
+}
+
 }  // namespace
 
-as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
-                       const float* resid, void* out, DevError* err, cudaStream_t st) {
+as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
+                          const void* B, const float* bias, const float* resid, void* out, float alpha,
+                          float out_scale, DevError* err, cudaStream_t st) {
   as_status s = ensure_driver();
   if (s != AS_OK) return s;
   if (g_num_sms == 0) {
@@ -517,11 +596,12 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = kDefaultSMs;
   }
-  if (M < 1 || N % 128 != 0 || K % tc::kBK != 0 || K < tc::kBK || M > (1ll << 31) - 1 ||
+  const int bke = tc::bk_elems(in_e4m3 ? tc::kInE4M3 : tc::kInBF16);
+  if (M < 1 || N % 128 != 0 || K % bke != 0 || K < bke || M > (1ll << 31) - 1 ||
       (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
       (reinterpret_cast<uintptr_t>(out) & 15) || (epi == AS_EPI_BIAS_RESID && (reinterpret_cast<uintptr_t>(resid) & 15)) ||
-      (bias && (reinterpret_cast<uintptr_t>(bias) & 15))) {
-    set_k_error("gemm_tcgen05: unsupported shape or alignment");
+      (bias && (reinterpret_cast<uintptr_t>(bias) & 15)) || (out_e4m3 && !(out_scale > 0.f))) {
+    set_k_error("gemm_tcgen05: unsupported shape, alignment or scale");
     return AS_ERR_ARG;
   }
   tc::Params p{};
@@ -533,19 +613,14 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
   p.resid = resid;
   p.out = out;
   p.err = err;
-  switch (epi) {
-    case AS_EPI_BIAS:
-      return N % 256 == 0 ? launch_bn<256, 4, AS_EPI_BIAS>(p, A, B, st) : launch_bn<128, 6, AS_EPI_BIAS>(p, A, B, st);
-    case AS_EPI_BIAS_GELU:
-      return N % 256 == 0 ? launch_bn<256, 4, AS_EPI_BIAS_GELU>(p, A, B, st)
-                          : launch_bn<128, 6, AS_EPI_BIAS_GELU>(p, A, B, st);
-    case AS_EPI_BIAS_RESID:
-      return N % 256 == 0 ? launch_bn<256, 3, AS_EPI_BIAS_RESID>(p, A, B, st)
-                          : launch_bn<128, 4, AS_EPI_BIAS_RESID>(p, A, B, st);
-    default:
-      set_k_error("gemm_tcgen05: bad epilogue");
-      return AS_ERR_ARG;
-  }
+  p.alpha = alpha;
+  p.out_scale_inv = out_e4m3 ? 1.0f / out_scale : 1.0f;
+  return in_e4m3 ? dispatch<tc::kInE4M3>(p, epi, out_e4m3, A, B, st) : dispatch<tc::kInBF16>(p, epi, out_e4m3, A, B, st);
+}
+
+as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
+                       const float* resid, void* out, DevError* err, cudaStream_t st) {
+  return gemm_tcgen05_ex(epi, false, false, M, N, K, A, B, bias, resid, out, 1.0f, 1.0f, err, st);
 }
 
 }  // namespace as

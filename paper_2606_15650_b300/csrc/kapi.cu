@@ -40,6 +40,16 @@ as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t 
   return AS_ERR_ARG;
 }
 
+as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_t K, const void* A8, const void* B8,
+                        float alpha, float out_scale, const float* bias, const float* resid, void* out, void* stream) {
+  if (epilogue == AS_EPI_BIAS_RESID && !resid) {
+    set_k_error("as_k_gemm_fp8: residual epilogue needs resid");
+    return AS_ERR_ARG;
+  }
+  return gemm_tcgen05_ex(epilogue, true, out_e4m3 != 0, M, N, K, A8, B8, bias, resid, out, alpha, out_scale, nullptr,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
 as_status as_k_attention(int precision, const void* qkv, void* out, const int32_t* seq_start, const int32_t* seq_len,
                          int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads, void* stream) {
   (void)rows;

@@ -8,6 +8,7 @@
 // Device buffers are owned by the ctx and only grow, so a steady stream of
 // calls allocates nothing after warm-up.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -61,7 +62,15 @@ void release(DBuf& b) {
 struct LayerW {
   const float *w_qkv, *b_qkv, *w_o, *b_o, *ln1_g, *ln1_b, *w_1, *b_1, *w_2, *b_2, *ln2_g, *ln2_b;
   __nv_bfloat16 *w_qkv16, *w_o16, *w_1_16, *w_2_16;
+  uint8_t *w_qkv8, *w_o8, *w_1_8, *w_2_8;   // E4M3 copies (FP8 precision)
+  float s_qkv, s_o, s_1, s_2;                // their per-tensor scales: amax / 448
 };
+
+// Encoder arithmetic of one call.
+enum EncMode { kEncF32 = 0, kEncBF16 = 1, kEncFP8 = 2, kEncCalib = 3 };
+// Activation scales of the FP8 path, four per layer: inputs of the QKV, output,
+// FFN-in and FFN-out projections.
+constexpr int kActPerLayer = 4;
 
 struct NonZeroU16 {
   const uint16_t* p;
@@ -116,7 +125,9 @@ struct as_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   // weights
-  DBuf w32, w16;
+  DBuf w32, w16, w8, amax_dev;
+  std::vector<float> act_scale;   // kActPerLayer per layer (FP8); empty until calibrated
+  bool calibrating = false;
   const float *tok_emb = nullptr, *pos_emb = nullptr, *emb_g = nullptr, *emb_b = nullptr;
   const float *cls_w = nullptr, *cls_b = nullptr;
   std::vector<LayerW> layers;
@@ -143,7 +154,7 @@ struct as_ctx {
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
   DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len;
-  DBuf X32, X16, QKV, ATT, Y32, H, VT;
+  DBuf X32, X16, QKV, ATT, Y32, H, VT, X8, ATT8, H8;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
   bool last_logits = false;
@@ -301,7 +312,7 @@ as_status load_weights(as_ctx* c) {
   }
   c->cls_w = take((uint64_t)g.n_labels * d);
   c->cls_b = take(g.n_labels);
-  if (g.precision == AS_BF16) {
+  if (g.precision == AS_BF16 || g.precision == AS_FP8) {
     uint64_t per = 3 * d * d + d * d + f * d + d * f;
     CKS(grow(c->w16, per * g.n_layers * 2));
     __nv_bfloat16* q = c->w16.as<__nv_bfloat16>();
@@ -310,6 +321,42 @@ as_status load_weights(as_ctx* c) {
       L.w_o16 = q; convert_f32_bf16(L.w_o, q, d * d, c->stream); q += d * d;
       L.w_1_16 = q; convert_f32_bf16(L.w_1, q, f * d, c->stream); q += f * d;
       L.w_2_16 = q; convert_f32_bf16(L.w_2, q, d * f, c->stream); q += d * f;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (g.precision == AS_FP8) {
+    // per-tensor weight scales s = amax / 448, then E4M3 copies
+    uint64_t per = 3 * d * d + d * d + f * d + d * f;
+    CKS(grow(c->w8, per * g.n_layers));
+    CKS(grow(c->amax_dev, 4 * g.n_layers * 4));
+    CK(cudaMemsetAsync(c->amax_dev.p, 0, 4 * g.n_layers * 4, c->stream));
+    unsigned int* am = c->amax_dev.as<unsigned int>();
+    for (uint32_t l = 0; l < g.n_layers; ++l) {
+      const LayerW& L = c->layers[l];
+      amax_f32(L.w_qkv, 3 * d * d, am + 4 * l + 0, c->stream);
+      amax_f32(L.w_o, d * d, am + 4 * l + 1, c->stream);
+      amax_f32(L.w_1, f * d, am + 4 * l + 2, c->stream);
+      amax_f32(L.w_2, d * f, am + 4 * l + 3, c->stream);
+    }
+    std::vector<unsigned int> bits(4 * g.n_layers);
+    CK(cudaMemcpyAsync(bits.data(), am, bits.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    auto scale_of = [](unsigned int b) {
+      float a;
+      memcpy(&a, &b, 4);
+      return a > 0.f ? a / 448.0f : 1.0f;
+    };
+    uint8_t* q = c->w8.as<uint8_t>();
+    for (uint32_t l = 0; l < g.n_layers; ++l) {
+      LayerW& L = c->layers[l];
+      L.s_qkv = scale_of(bits[4 * l + 0]);
+      L.s_o = scale_of(bits[4 * l + 1]);
+      L.s_1 = scale_of(bits[4 * l + 2]);
+      L.s_2 = scale_of(bits[4 * l + 3]);
+      L.w_qkv8 = q; quantize_e4m3(L.w_qkv, q, 3 * d * d, L.s_qkv, c->stream); q += 3 * d * d;
+      L.w_o8 = q; quantize_e4m3(L.w_o, q, d * d, L.s_o, c->stream); q += d * d;
+      L.w_1_8 = q; quantize_e4m3(L.w_1, q, f * d, L.s_1, c->stream); q += f * d;
+      L.w_2_8 = q; quantize_e4m3(L.w_2, q, d * f, L.s_2, c->stream); q += d * f;
     }
     CK(cudaStreamSynchronize(c->stream));
   }
@@ -376,15 +423,45 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
   count_launch();
   float* X32 = c->X32.as<float>();
   float* Y32 = c->Y32.as<float>();
-  const bool bf = g.precision == AS_BF16;
+  const int mode = g.precision == AS_FP32 ? kEncF32
+                   : g.precision == AS_BF16 ? kEncBF16
+                                            : (c->calibrating ? kEncCalib : kEncFP8);
+  const bool bf = mode == kEncBF16 || mode == kEncCalib;
+  const bool f8 = mode == kEncFP8;
   __nv_bfloat16* X16 = bf ? c->X16.as<__nv_bfloat16>() : nullptr;
-  CKS(embed_ln(c->tok_ids.as<int32_t>(), c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(), c->tok_emb, c->pos_emb,
-               c->emb_g, c->emb_b, X32, X16, R, d, st));
+  uint8_t* X8 = f8 ? c->X8.as<uint8_t>() : nullptr;
+  unsigned int* amax = c->amax_dev.as<unsigned int>();
+  const float* as8 = f8 ? c->act_scale.data() : nullptr;
+  const uint64_t Rd = (uint64_t)R * d;
+  CKS(embed_ln_ex(c->tok_ids.as<int32_t>(), c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(), c->tok_emb,
+                  c->pos_emb, c->emb_g, c->emb_b, X32, X16, X8, f8 ? as8[0] : 1.0f, R, d, st));
+  if (mode == kEncCalib) amax_bf16(X16, Rd, amax + 0, st);
   DevError* err = c->dev_err.as<DevError>();
   for (uint32_t l = 0; l < g.n_layers; ++l) {
     const LayerW& L = c->layers[l];
     const bool last = l + 1 == g.n_layers;
-    if (bf) {
+    if (f8) {
+      const float* sc = as8 + kActPerLayer * l;
+      __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
+      uint8_t* ATT8 = c->ATT8.as<uint8_t>();
+      uint8_t* H8 = c->H8.as<uint8_t>();
+      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d);
+        CKS(gemm_tcgen05_ex(AS_EPI_BIAS, true, false, R, 3 * d, d, X8, L.w_qkv8, L.b_qkv, nullptr, QKV,
+                            sc[0] * L.s_qkv, 1.0f, err, st)); }
+      { ProfScope ps(c, 1, attn_flops);
+        CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns,
+                                (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * d);
+        CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
+                            1.0f, err, st)); }
+      CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
+      { ProfScope ps(c, 0, 2.0 * R * f * d);
+        CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, true, true, R, f, d, X8, L.w_1_8, L.b_1, nullptr, H8, sc[2] * L.s_1,
+                            sc[3], err, st)); }
+      { ProfScope ps(c, 0, 2.0 * R * d * f);
+        CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, f, H8, L.w_2_8, L.b_2, X32, Y32, sc[3] * L.s_2,
+                            1.0f, err, st)); }
+    } else if (bf) {
       __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
       __nv_bfloat16* ATT = c->ATT.as<__nv_bfloat16>();
       __nv_bfloat16* H = c->H.as<__nv_bfloat16>();
@@ -398,9 +475,12 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
         CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
                            (int32_t)g.n_heads, st));
       }
+      if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
       { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
+      if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * l + 2, st);
       { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
+      if (mode == kEncCalib) amax_bf16(H, (uint64_t)R * f, amax + kActPerLayer * l + 3, st);
       { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st)); }
     } else {
       float* QKV = c->QKV.as<float>();
@@ -416,7 +496,8 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
       { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
     }
     if (!last) {
-      CKS(layernorm_rows(Y32, L.ln2_g, L.ln2_b, X32, X16, R, d, st));
+      CKS(layernorm_rows_ex(Y32, L.ln2_g, L.ln2_b, X32, X16, X8, f8 ? as8[kActPerLayer * (l + 1)] : 1.0f, R, d, st));
+      if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * (l + 1), st);
     } else {
       CKS(layernorm_classify(Y32, L.ln2_g, L.ln2_b, c->cls_w, c->cls_b, (int32_t)g.n_labels, c->row_tok.as<int32_t>(),
                              c->row_own.as<uint8_t>(), want_logits ? c->logits.as<float>() : nullptr,
@@ -429,7 +510,8 @@ as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, 
 as_status ensure_encoder_buffers(as_ctx* c, uint64_t rows, uint64_t n_seq) {
   const as_config& g = c->cfg;
   const uint64_t d = g.d_model, f = g.d_ffn;
-  const bool bf = g.precision == AS_BF16;
+  const bool bf = g.precision != AS_FP32;   // FP8 keeps BF16 buffers for calibration and QKV
+  const bool f8 = g.precision == AS_FP8;
   const size_t act = bf ? 2 : 4;
   CKS(grow(c->row_tok, rows * 4));
   CKS(grow(c->row_pos, rows * 4));
@@ -446,6 +528,13 @@ as_status ensure_encoder_buffers(as_ctx* c, uint64_t rows, uint64_t n_seq) {
   if (c->ATT.p != att_before) CK(cudaMemsetAsync(c->ATT.p, 0, c->ATT.cap, c->stream));
   if (bf && g.attention == AS_ATTN_TCGEN05) CKS(grow(c->VT, attention_vt_elems((int64_t)rows, (int32_t)d) * 2));
   CKS(grow(c->H, rows * f * act));
+  if (f8) {
+    CKS(grow(c->X8, rows * d));
+    const void* before = c->ATT8.p;
+    CKS(grow(c->ATT8, rows * d));
+    if (c->ATT8.p != before) CK(cudaMemsetAsync(c->ATT8.p, 0, c->ATT8.cap, c->stream));
+    CKS(grow(c->H8, rows * f));
+  }
   return AS_OK;
 }
 
@@ -494,14 +583,19 @@ as_status d2h_vec(as_ctx* c, std::vector<T>& v, const void* src, uint64_t n) {
   return AS_OK;
 }
 
+// calibrate = true: run the tokenizer and the BF16 encoder only, recording
+// the amax of every FP8 GEMM input, and set the static activation scales.
 as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch, const uint8_t* key, size_t key_len,
-                         as_output** out) {
+                         as_output** out, bool calibrate = false) {
   const as_config& g = c->cfg;
   cudaStream_t st = c->stream;
-  if (!rec || !out) return fail(c, AS_ERR_ARG, "records / out is NULL");
-  *out = nullptr;
+  if (!rec || (!out && !calibrate)) return fail(c, AS_ERR_ARG, "records / out is NULL");
+  if (out) *out = nullptr;
   CKI(validate_schema(c, sch));
-  CKI(set_key(c, key, key_len));
+  if (calibrate && g.precision != AS_FP8) return fail(c, AS_ERR_STATE, "calibration is for AS_FP8 contexts");
+  if (!calibrate && g.precision == AS_FP8 && c->act_scale.empty())
+    return fail(c, AS_ERR_STATE, "FP8 context without activation scales: call as_calibrate or as_set_scales first");
+  if (!calibrate) CKI(set_key(c, key, key_len));
   c->slug_len = sch->slug_hex_len;
   const uint64_t n = rec->n_records;
   if (n > 0 && (!rec->offsets)) return fail(c, AS_ERR_ARG, "offsets is NULL");
@@ -662,14 +756,37 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   CKS(grow(c->labels, T + 16));
   if (want_logits) CKS(grow(c->logits, (T + 1) * g.n_labels * 4));
   CK(cudaMemsetAsync(c->labels.p, 0, T + 16, st));
+  if (calibrate) {
+    c->calibrating = true;
+    CK(cudaMemsetAsync(c->amax_dev.p, 0, (size_t)kActPerLayer * g.n_layers * 4, st));
+  }
   for (const Chunk& ch : chunks) {
     double af = 0;  // attention FLOPs of the batch: QK^T and PV, 2 * 2 * L^2 * d per sequence
     for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
-    CKI(run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), af, want_logits));
+    as_status es = run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), af, want_logits);
+    if (es != AS_OK) {
+      c->calibrating = false;
+      return es;
+    }
     if (c->prof && c->ev_used > 4096) {  // bound the event pool
       CK(cudaStreamSynchronize(st));
       prof_collect(c);
     }
+  }
+  if (calibrate) {
+    // static per-tensor activation scales: amax over the calibration set / 448
+    c->calibrating = false;
+    std::vector<unsigned int> bits((size_t)kActPerLayer * g.n_layers);
+    CK(cudaMemcpyAsync(bits.data(), c->amax_dev.p, bits.size() * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CKI(check_dev_error(c));
+    c->act_scale.resize(bits.size());
+    for (size_t i = 0; i < bits.size(); ++i) {
+      float a;
+      memcpy(&a, &bits[i], 4);
+      c->act_scale[i] = a > 0.f ? a / 448.0f : 1.0f;
+    }
+    return AS_OK;
   }
   // ---- BIO decode
   CKS(grow(c->tok_flags, T + 16));
@@ -965,8 +1082,8 @@ as_status as_create(const as_config* cfg, as_ctx** out) {
     c->err = "unsupported dimensions (d_model multiple of 128 up to 1024, d_ffn multiple of 128, 9..32 labels)";
     return bail(AS_ERR_UNSUPPORTED);
   }
-  if (g.precision != AS_FP32 && g.precision != AS_BF16) {
-    c->err = "precision must be AS_FP32 or AS_BF16";
+  if (g.precision != AS_FP32 && g.precision != AS_BF16 && g.precision != AS_FP8) {
+    c->err = "precision must be AS_FP32, AS_BF16 or AS_FP8";
     return bail(AS_ERR_UNSUPPORTED);
   }
   if (g.attention != AS_ATTN_MMA_SYNC && g.attention != AS_ATTN_TCGEN05) {
@@ -1026,7 +1143,7 @@ void as_destroy(as_ctx* c) {
                  &c->nk_s, &c->nk_l, &c->nk_t, &c->rk_s, &c->rk_l, &c->rk_t, &c->fin_s, &c->fin_l, &c->fin_t,
                  &c->digests, &c->delta, &c->shift, &c->names, &c->name_off, &c->name_len, &c->seqs, &c->row_tok,
                  &c->row_pos, &c->row_own, &c->seq_start, &c->seq_len, &c->X32, &c->X16, &c->QKV, &c->ATT, &c->Y32,
-                 &c->H, &c->VT};
+                 &c->H, &c->VT, &c->X8, &c->ATT8, &c->H8, &c->w8, &c->amax_dev};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -1175,6 +1292,34 @@ as_status as_map_clear(as_ctx* c) {
   c->key_set = false;
   c->key.clear();
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, AS_ERR_CUDA, "map clear");
+  return AS_OK;
+}
+
+as_status as_calibrate(as_ctx* c, const as_records* records, const as_schema* schema) {
+  if (!c) return AS_ERR_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  as_status s = anonymize_impl(c, records, schema, nullptr, 0, nullptr, true);
+  if (s == AS_ERR_CUDA) cudaGetLastError();
+  return s;
+}
+
+as_status as_get_scales(as_ctx* c, float* scales, uint64_t n) {
+  if (!c || !scales) return AS_ERR_ARG;
+  const uint64_t need = (uint64_t)kActPerLayer * c->cfg.n_layers;
+  if (c->act_scale.size() != need) return fail(c, AS_ERR_STATE, "no activation scales yet");
+  if (n < need) return fail(c, AS_ERR_ARG, "need room for 4 scales per layer");
+  memcpy(scales, c->act_scale.data(), need * 4);
+  return AS_OK;
+}
+
+as_status as_set_scales(as_ctx* c, const float* scales, uint64_t n) {
+  if (!c || !scales) return AS_ERR_ARG;
+  if (c->cfg.precision != AS_FP8) return fail(c, AS_ERR_STATE, "scales are for AS_FP8 contexts");
+  const uint64_t need = (uint64_t)kActPerLayer * c->cfg.n_layers;
+  if (n != need) return fail(c, AS_ERR_ARG, "expected 4 scales per layer");
+  for (uint64_t i = 0; i < n; ++i)
+    if (!(scales[i] > 0.f) || !std::isfinite(scales[i])) return fail(c, AS_ERR_ARG, "scales must be finite and > 0");
+  c->act_scale.assign(scales, scales + n);
   return AS_OK;
 }
 

@@ -5,7 +5,7 @@ import numpy as np
 
 from oracle import pipeline as P
 
-TOL = {"fp32": 1e-4, "bf16": 2e-2}
+TOL = {"fp32": 1e-4, "bf16": 2e-2, "fp8": 1e-1}
 MARGIN = 0.05
 
 

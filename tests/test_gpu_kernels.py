@@ -46,6 +46,44 @@ def test_gemm_tcgen05_bf16(M, N, K, epi):
     assert bool((err <= tol + 1e-4).all()), f"max err {err.max().item()} at {divmod(int(err.argmax()), N)}"
 
 
+def _e4m3(x, scale):
+    return (x / scale).clamp(-448, 448).to(torch.float8_e4m3fn)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 128, 128), (128, 256, 128), (200, 384, 256), (1000, 768, 768),
+                                   (4096, 2304, 768), (777, 768, 3072), (300, 3072, 768)])
+@pytest.mark.parametrize("epi,out8", [("bias", False), ("bias_gelu", False), ("bias_gelu", True), ("bias_resid", False)])
+def test_gemm_tcgen05_fp8(M, N, K, epi, out8):
+    """E4M3 GEMM against FP32 matmul of the dequantized operands."""
+    g = torch.Generator(device=DEV).manual_seed(M + 3 * N + K)
+    A = torch.randn(M, K, device=DEV, generator=g)
+    B = 0.05 * torch.randn(N, K, device=DEV, generator=g)
+    sa, sb = A.abs().max().item() / 448, B.abs().max().item() / 448
+    A8, B8 = _e4m3(A, sa), _e4m3(B, sb)
+    bias = torch.randn(N, device=DEV, generator=g)
+    resid = torch.randn(M, N, device=DEV, generator=g) if epi == "bias_resid" else None
+    if out8:
+        out = torch.empty(M, N, device=DEV, dtype=torch.float8_e4m3fn)
+    else:
+        out = torch.empty(M, N, device=DEV, dtype=torch.float32 if epi == "bias_resid" else torch.bfloat16)
+    ref = _ref_gemm(A8.float() * sa, B8.float() * sb, bias, resid, epi)
+    so = ref.abs().max().item() / 448 if out8 else 0.0
+    api.gemm_fp8(epi, A8, B8, sa * sb, bias, resid, out, out_scale=so)
+    torch.cuda.synchronize()
+    if out8:
+        got = out.float() * so
+        exp = (ref / so).clamp(-448, 448).to(torch.float8_e4m3fn).float() * so
+        # accumulation order (and the GELU approximation, |err| <= 1.5e-7) may move a value across an
+        # E4M3 rounding boundary: at most one step, 2^-3 of the larger magnitude (or one subnormal step)
+        step = torch.maximum(exp.abs(), got.abs()) * 0.125 + 2e-3 * so
+        assert ((got - exp).abs() <= step).all()
+        assert (got == exp).float().mean().item() > 0.99
+    else:
+        tol = 2e-3 * math.sqrt(K) * 0.05 * 4 + (8e-3 * ref.abs() if out.dtype == torch.bfloat16 else 0)
+        err = (out.float() - ref).abs()
+        assert bool((err <= tol + 1e-4).all()), f"max err {err.max().item()}"
+
+
 @pytest.mark.parametrize("M,N,K", [(1, 128, 8), (130, 256, 64), (300, 384, 128), (517, 768, 768)])
 @pytest.mark.parametrize("epi", ["bias", "bias_gelu", "bias_resid"])
 def test_gemm_simt_fp32(M, N, K, epi):

@@ -71,6 +71,46 @@ def test_c1_parity(c1, vocab_words, vocab_index, prec, mode, attention):
     ctx.close()
 
 
+@pytest.fixture(scope="module")
+def fp8_ctx(c1, vocab_words):
+    recs, w, key, ref = c1
+    ctx = api.Context(DIMS, synth.pack_blob(DIMS, w), vocab_words, precision="fp8", keep_trace=True)
+    cal = synth.make_records(synth.scaled(synth.C1, 64).records, vocab_words, seed=synth.SEED_CALIB)
+    ctx.calibrate(cal.data, cal.offsets, SCHEMA)
+    return ctx
+
+
+def test_c1_parity_fp8(c1, fp8_ctx, vocab_index):
+    """FP8 e4m3 GEMMs with static per-tensor scales: logits within 1e-1 of FP64."""
+    recs, w, key, ref = c1
+    scales = fp8_ctx.scales()
+    assert scales.shape == (4 * DIMS.n_layers,) and (scales > 0).all()
+    out = fp8_ctx.anonymize(recs.data, recs.offsets, SCHEMA, key)
+    tr = fp8_ctx.trace()
+    records = recs.records()
+    U.check_tokens(tr, records, recs.offsets, ref.traces)
+    U.check_regex(tr, recs.offsets, ref.traces)
+    err, agree, flips = U.check_logits(tr, ref.traces, "fp8")
+    U.check_stage_isolated(out.records(), tr, records, SCHEMA, key, vocab_index)
+    print(f"fp8: max|dlogit| {err:.3e}, agreement {agree:.5f}, flips {flips}")
+    out.free()
+
+
+def test_fp8_result_independent_of_batch(c1, fp8_ctx):
+    """Static scales: a record's logits are the same alone and inside a batch."""
+    recs, w, key, ref = c1
+    fp8_ctx.map_clear()
+    sub = synth.records_from_list(recs.records()[:24])
+    fp8_ctx.anonymize(sub.data, sub.offsets, SCHEMA, key).free()
+    batch = fp8_ctx.trace()
+    sl = U.split_tokens(batch, sub.n)
+    for i in (0, 7, 23):
+        one = synth.records_from_list([recs.record(i)])
+        fp8_ctx.anonymize(one.data, one.offsets, SCHEMA, key).free()
+        alone = fp8_ctx.trace()
+        assert np.array_equal(alone["logits"], batch["logits"][sl[i]])
+
+
 def test_per_record_equals_packed_fp32(c1, vocab_words):
     """The FP32 path gives the same logits whether records are packed or run one per launch."""
     _, _, a = _run(c1, vocab_words, "fp32", "packed")
