@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--records", type=int, default=0, help="override the record count (testing only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP32 / CPU baselines (profiling runs)")
     ap.add_argument("--chunk", type=int, default=0, help="encoder rows per packed batch (0 = library default)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="measured seconds per offered rate of the serving leg (0 = skip it)")
+    ap.add_argument("--serve-rates", default="1000,5000,20000,50000", help="offered records/s of the serving leg")
     return ap.parse_args()
 
 
@@ -362,7 +365,62 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
                                             "sample": f"first {sample.n} records, FP32 margin > 0.05"}}
     out["fp8"] = fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32)
     out["cpu_baseline"] = cpu_baseline(w, words, recs, weights, key)
+    if args.serve_seconds > 0:
+        out["serving"] = serving_leg(args, words, blob, key, local)
     return out
+
+
+def serving_leg(args, words, blob, key, local) -> dict:
+    """Serving loop under Poisson arrivals: one record per request, continuous batching.
+
+    Records follow the serving workload (lognormal(300, 0.6) clipped 32..4096
+    tokens, windows 512/384); arrivals are exponential gaps at each offered
+    rate (seed 4004). Requests are submitted with results discarded, so the
+    latency is submit -> output bytes on the host. The admission queue holds at
+    most 16,384 requests; beyond that submissions are rejected and counted.
+    """
+    import paper_2606_15650_b300.api as api
+    w4 = synth.scaled(synth.C4, 20000)
+    pool = synth.make_records(w4.records, words, seed=synth.SEED_RECORDS + 4).records()
+    schema = api.Schema(synth.TYPE_NAMES_4, window=w4.window, stride=w4.stride)
+    rng = np.random.default_rng(synth.SEED_ARRIVALS)
+    rates = [int(r) for r in args.serve_rates.split(",") if r]
+    ctx = api.Context(w4.dims, blob, words, precision="bf16", mode="packed", device=local)
+    res = []
+    for rate in rates:
+        ctx.serve_start(schema, key, lanes=2, max_batch_bytes=1 << 20, max_pending=16384)
+        warm, meas = 1.0, args.serve_seconds
+        n_total = int(rate * (warm + meas) * 1.05) + 16
+        gaps = rng.exponential(1.0 / rate, n_total)
+        t_arr = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        i, submitted, rejected, measuring = 0, 0, 0, False
+        t_meas0 = None
+        while True:
+            now = time.perf_counter() - t0
+            if not measuring and now >= warm:
+                ctx.serve_stats(reset=True)
+                measuring, t_meas0, submitted, rejected = True, now, 0, 0
+            if now >= warm + meas:
+                break
+            if t_arr[i % n_total] > now:
+                continue
+            rid = ctx.submit(pool[i % len(pool)], discard=True)
+            submitted += 1
+            rejected += rid is None
+            i += 1
+        st = ctx.serve_stats()
+        elapsed = time.perf_counter() - t0 - t_meas0
+        ctx.serve_stop()  # drains what was admitted
+        res.append({"offered_rps": rate, "submitted_rps": submitted / elapsed, "rejected": rejected,
+                    "completed_rps": st["completed"] / st["seconds"], "tokens_per_s": st["tokens"] / st["seconds"],
+                    "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                    "batches": int(st["batches"]), "queue_at_end": int(st["pending"])})
+    ctx.close()
+    return {"workload": f"{synth.C4.name}: lognormal(300, 0.6) clipped 32..4096 tokens, windows 512/384, "
+                        f"pool of {len(pool)} records, Poisson arrivals (seed {synth.SEED_ARRIVALS})",
+            "lanes": 2, "max_batch_bytes": 1 << 20, "max_pending": 16384,
+            "seconds_per_rate": args.serve_seconds, "warmup_s": 1.0, "rates": res}
 
 
 def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32) -> dict:

@@ -47,6 +47,7 @@ typedef int32_t as_status;
 #define AS_ERR_STATE       -6  /* key changed on a non-empty map, etc.      */
 #define AS_ERR_UNSUPPORTED -7  /* configuration not built                   */
 #define AS_ERR_CAPACITY    -8  /* entity map or arena full                  */
+#define AS_ERR_AGAIN       -9  /* serving admission queue full: retry       */
 
 /* Encoder arithmetic. FP32: FP32 everywhere (SIMT GEMM). BF16: GEMM inputs
  * rounded to BF16, FP32 accumulate; bias, residual, LayerNorm, softmax and
@@ -202,6 +203,42 @@ typedef struct {
   const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+/* Serving loop (continuous batching). After as_serve_start the ctx accepts
+ * single records with as_submit from any thread; worker threads (one per
+ * lane, each with its own CUDA stream and buffers) take the oldest admitted
+ * requests up to max_batch_bytes, run the whole path on them and post the
+ * results; with two or more lanes a batch starts while others are still on
+ * the GPU. A request's record index (first_seen / last_seen) is its request
+ * id, and every step computes a record from that record's data alone, so the
+ * result of a request is the same alone and in any mix. The entity map stays
+ * on the device; as_map_export gives a snapshot. as_anonymize and
+ * as_calibrate return AS_ERR_STATE while serving. */
+typedef struct {
+  uint32_t lanes;              /* concurrent batches on the GPU; 0 = 2        */
+  uint64_t max_batch_bytes;    /* admission budget per batch; 0 = 3/4 of max_chunk_tokens */
+  uint32_t max_batch_records;  /* 0 = 65536                                    */
+  uint64_t max_pending;        /* queue bound (AS_ERR_AGAIN beyond); 0 = 2^20 */
+} as_serve_config;
+typedef struct {
+  uint64_t completed, rejected, failed, batches, tokens, pending;
+  double seconds;              /* since start or the last reset               */
+  double p50_ms, p99_ms, max_ms; /* submit -> result ready, completed requests */
+} as_serve_stats_t;
+#define AS_SUBMIT_DISCARD 1u   /* drop the result (load tests): latency only  */
+as_status as_serve_start(as_ctx* ctx, const as_schema* schema, const uint8_t* key, size_t key_len,
+                         const as_serve_config* cfg);
+/* Copy one record and queue it; *request_id identifies it for as_poll.
+ * AS_ERR_AGAIN when max_pending requests are already waiting. */
+as_status as_submit(as_ctx* ctx, const uint8_t* record, uint64_t len, uint32_t flags, uint64_t* request_id);
+/* Wait up to timeout_us for a request; on success *out holds its one output
+ * record (host memory; free with as_output_free). AS_ERR_TIMEOUT leaves the
+ * request queued; a finished request can be polled once. */
+as_status as_poll(as_ctx* ctx, uint64_t request_id, as_output** out, int64_t timeout_us);
+/* Counters and latency percentiles; reset = 1 starts a new window. */
+as_status as_serve_stats(as_ctx* ctx, as_serve_stats_t* stats, uint32_t reset);
+/* Finish every admitted request, then stop the workers. */
+as_status as_serve_stop(as_ctx* ctx);
 
 /* FP8 contexts: set the static activation scales from a calibration set.
  * Runs the tokenizer and the BF16 encoder over `records` (same layout rules

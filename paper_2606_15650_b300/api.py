@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libanonshield.so")
 
 AS_OK = 0
 STATUS = {0: "AS_OK", -1: "AS_ERR_ARG", -2: "AS_ERR_OOM", -3: "AS_ERR_CUDA", -4: "AS_ERR_TOO_LONG",
-          -5: "AS_ERR_TIMEOUT", -6: "AS_ERR_STATE", -7: "AS_ERR_UNSUPPORTED", -8: "AS_ERR_CAPACITY"}
+          -5: "AS_ERR_TIMEOUT", -6: "AS_ERR_STATE", -7: "AS_ERR_UNSUPPORTED", -8: "AS_ERR_CAPACITY",
+          -9: "AS_ERR_AGAIN"}
 PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 MODE = {"packed": 0, "per_record": 1}
 EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
@@ -74,6 +75,16 @@ class _Trace(C.Structure):
                 ("final_len", C.POINTER(C.c_uint32)), ("final_type", C.POINTER(C.c_uint8))]
 
 
+class _ServeConfig(C.Structure):
+    _fields_ = [("lanes", C.c_uint32), ("max_batch_bytes", C.c_uint64), ("max_batch_records", C.c_uint32),
+                ("max_pending", C.c_uint64)]
+
+
+class _ServeStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("completed", "rejected", "failed", "batches", "tokens", "pending")] + \
+               [(n, C.c_double) for n in ("seconds", "p50_ms", "p99_ms", "max_ms")]
+
+
 class _Profile(C.Structure):
     _fields_ = [("gemm_launches", C.c_uint64), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
                 ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double)]
@@ -82,7 +93,8 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
+            "as_get_scales", "as_set_scales", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -120,6 +132,11 @@ def load() -> C.CDLL:
     lib.as_calibrate.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema)]
     lib.as_get_scales.argtypes = [P, P, C.c_uint64]
     lib.as_set_scales.argtypes = [P, P, C.c_uint64]
+    lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
+    lib.as_submit.argtypes = [P, P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]
+    lib.as_poll.argtypes = [P, C.c_uint64, C.POINTER(P), C.c_int64]
+    lib.as_serve_stats.argtypes = [P, C.POINTER(_ServeStats), C.c_uint32]
+    lib.as_serve_stop.argtypes = [P]
     lib.as_profile.argtypes = [P, C.c_uint32]
     lib.as_profile_read.argtypes = [P, C.POINTER(_Profile)]
     lib.as_tokenize_static.argtypes = [P, P, P, C.c_uint64, C.c_uint64, P, P, P, P, P, P]
@@ -412,6 +429,42 @@ class Context:
             arr[i].last_seen = e.last_seen
             arr[i].count = e.count
         self._check(load().as_map_import(self._h, key, len(key), arr, len(entries)))
+
+    # ---- serving loop (continuous batching)
+    def serve_start(self, schema: Schema, key: bytes, lanes: int = 2, max_batch_bytes: int = 0,
+                    max_batch_records: int = 0, max_pending: int = 0):
+        sc, names = self._schema(schema)
+        cfg = _ServeConfig(lanes=lanes, max_batch_bytes=max_batch_bytes, max_batch_records=max_batch_records,
+                           max_pending=max_pending)
+        self._check(load().as_serve_start(self._h, C.byref(sc), key, len(key), C.byref(cfg)))
+        del names
+
+    def submit(self, record: bytes, discard: bool = False) -> int | None:
+        """Queue one record; returns its request id, or None when the queue is full."""
+        rid = C.c_uint64()
+        st = load().as_submit(self._h, bytes(record) if record else None, len(record), 1 if discard else 0,
+                              C.byref(rid))
+        if st == -9:
+            return None
+        self._check(st)
+        return rid.value
+
+    def poll(self, request_id: int, timeout_s: float = 10.0) -> bytes | None:
+        """The anonymized record, or None if it is not ready within the timeout."""
+        out = C.c_void_p()
+        st = load().as_poll(self._h, request_id, C.byref(out), int(timeout_s * 1e6))
+        if st == -5:
+            return None
+        self._check(st)
+        return Output(self, out.value).records()[0]
+
+    def serve_stats(self, reset: bool = False) -> dict:
+        s = _ServeStats()
+        self._check(load().as_serve_stats(self._h, C.byref(s), 1 if reset else 0))
+        return {k: getattr(s, k) for k, _ in _ServeStats._fields_}
+
+    def serve_stop(self):
+        self._check(load().as_serve_stop(self._h))
 
     def stream(self) -> int:
         """The ctx's cudaStream_t (as an int), for torch.cuda.ExternalStream."""

@@ -15,6 +15,7 @@
 // that is a multiple of 8 (the batch packer inserts padding rows).
 // Keys past the sequence end are masked to -inf; query rows past it are not
 // stored. Every mbarrier wait is bounded (see gemm_tc.cu).
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -389,8 +390,9 @@ __global__ void vt_transpose_kernel(const __nv_bfloat16* __restrict__ qkv, __nv_
 }  // namespace atc
 
 namespace {
-PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
-int g_attn_attr_dev = -1;
+// Set once per process / device; concurrent callers write the same values.
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_enc{nullptr};
+std::atomic<bool> g_attn_attr_set[64] = {};
 
 as_status make_map_bf16(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld_elems,
                         uint32_t box_cols, uint32_t box_rows) {
@@ -398,7 +400,7 @@ as_status make_map_bf16(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_
   cuuint64_t strides[1] = {(cuuint64_t)(ld_elems * 2)};
   cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+  CUresult r = g_enc.load()(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -420,7 +422,7 @@ as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* vt, __nv_bf
     set_k_error("attention_tcgen05: head dim 64, sequences <= 4096 tokens, 16-byte aligned buffers");
     return AS_ERR_ARG;
   }
-  if (!g_enc) {
+  if (!g_enc.load()) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     AS_CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
@@ -428,13 +430,13 @@ as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* vt, __nv_bf
       set_k_error("cuTensorMapEncodeTiled not available from the driver");
       return AS_ERR_CUDA;
     }
-    g_enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    g_enc.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  if (g_attn_attr_dev != dev) {
+  if (!g_attn_attr_set[dev & 63].load()) {
     AS_CUDA_OK(cudaFuncSetAttribute(atc::attn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, atc::kSmemAlloc));
-    g_attn_attr_dev = dev;
+    g_attn_attr_set[dev & 63].store(true);
   }
   const int ldt = (int)((rows + 7) & ~7ll);
   dim3 tg((unsigned)((ldt + 31) / 32), (unsigned)(d_model / 32));

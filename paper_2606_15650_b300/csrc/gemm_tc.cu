@@ -20,6 +20,7 @@
 // the main loop of tile i+1. Every mbarrier wait is bounded (globaltimer):
 // on timeout the kernel records the failure, every role leaves its loop,
 // TMEM is freed and the kernel returns.
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -482,11 +483,13 @@ done:
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-int g_num_sms = 0;
+// Set once; several host threads (serving lanes) may race to set them, each
+// writing the same value.
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
+std::atomic<int> g_num_sms{0};
 
 as_status ensure_driver() {
-  if (g_encode) return AS_OK;
+  if (g_encode.load()) return AS_OK;
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
   AS_CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
@@ -494,7 +497,7 @@ as_status ensure_driver() {
     set_k_error("cuTensorMapEncodeTiled not available from the driver");
     return AS_ERR_CUDA;
   }
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));
   return AS_OK;
 }
 
@@ -505,7 +508,7 @@ as_status make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dtype, 
   cuuint64_t strides[1] = {(cuuint64_t)(cols * esize)};
   cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(tm, dtype, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult r = g_encode.load()(tm, dtype, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_k_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
@@ -517,7 +520,7 @@ as_status make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dtype, 
 template <int BN, int STAGES, int EPI, int IN, int OUT>
 as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStream_t st) {
   using L = tc::Smem<BN, STAGES, OUT>;
-  static bool attr_set[64] = {};
+  static std::atomic<bool> attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
@@ -551,7 +554,8 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   tc::Params p = p0;
   p.n_tiles_n = p.N / BN;
   p.n_tiles = p.n_tiles_n * ((p.M + tc::kBM - 1) / tc::kBM);
-  int grid = p.n_tiles < g_num_sms ? p.n_tiles : g_num_sms;
+  const int n_sms = g_num_sms.load();
+  int grid = p.n_tiles < n_sms ? p.n_tiles : n_sms;
   tc::gemm_kernel<BN, STAGES, EPI, IN, OUT><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
@@ -590,11 +594,11 @@ as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64
                           float out_scale, DevError* err, cudaStream_t st) {
   as_status s = ensure_driver();
   if (s != AS_OK) return s;
-  if (g_num_sms == 0) {
-    int dev = 0;
+  if (g_num_sms.load() == 0) {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = kDefaultSMs;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms.store(n > 0 ? n : kDefaultSMs);
   }
   const int bke = tc::bk_elems(in_e4m3 ? tc::kInE4M3 : tc::kInBF16);
   if (M < 1 || N % 128 != 0 || K % bke != 0 || K < bke || M > (1ll << 31) - 1 ||

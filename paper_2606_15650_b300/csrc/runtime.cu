@@ -8,7 +8,13 @@
 // Device buffers are owned by the ctx and only grow, so a steady stream of
 // calls allocates nothing after warm-up.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -119,33 +125,13 @@ __global__ void expand_rows_kernel(const SeqDesc* __restrict__ seqs, int32_t* ro
 
 }  // namespace
 
-struct as_ctx {
-  as_config cfg{};
-  int device = 0;
+// Everything one in-flight call owns: its stream, device error flag, the
+// per-call buffers (grown, never shrunk), the trace of its last call and its
+// launch timing. as_anonymize uses the ctx's main lane; each serving worker
+// has a lane of its own, so batches overlap on the device.
+struct Lane {
   cudaStream_t stream = nullptr;
-  std::string err;
-  // weights
-  DBuf w32, w16, w8, amax_dev;
-  std::vector<float> act_scale;   // kActPerLayer per layer (FP8); empty until calibrated
-  bool calibrating = false;
-  const float *tok_emb = nullptr, *pos_emb = nullptr, *emb_g = nullptr, *emb_b = nullptr;
-  const float *cls_w = nullptr, *cls_b = nullptr;
-  std::vector<LayerW> layers;
-  // vocab
-  DBuf vocab_slots;
-  uint32_t vocab_mask = 0;
-  // map
-  DBuf map_slots, map_arena, map_ctr;  // map_ctr: arena_used, n_entries
-  uint64_t map_mask = 0;
-  std::vector<uint8_t> key;
-  bool key_set = false;
-  DBuf key_dev, key_state;
-  uint32_t call_id = 0;
-  uint64_t records_done = 0;
-  uint32_t slug_len = 10;
-  uint64_t n_entries_seen = 0;  // map size after the previous call
   DBuf dev_err;
-  // per-call buffers
   DBuf in_bytes, in_off, rs_bits, tok_at, pos_b, scan_tiles, counters, delta_total;
   DBuf tok_ids, tok_off, tok_len, rec_tok;
   DBuf rx_len_b, rx_type_b, rx_s, rx_l, rx_t;
@@ -169,6 +155,37 @@ struct as_ctx {
   size_t ev_used = 0;
   std::vector<std::pair<int, double>> ev_pending;  // (kind, flops) per event pair
   as_profile_stats prof_acc{};
+
+  void release_all();
+};
+
+struct Server;
+
+struct as_ctx {
+  as_config cfg{};
+  int device = 0;
+  Lane main;
+  // weights
+  DBuf w32, w16, w8, amax_dev;
+  std::vector<float> act_scale;   // kActPerLayer per layer (FP8); empty until calibrated
+  bool calibrating = false;
+  const float *tok_emb = nullptr, *pos_emb = nullptr, *emb_g = nullptr, *emb_b = nullptr;
+  const float *cls_w = nullptr, *cls_b = nullptr;
+  std::vector<LayerW> layers;
+  // vocab
+  DBuf vocab_slots;
+  uint32_t vocab_mask = 0;
+  // map
+  DBuf map_slots, map_arena, map_ctr;  // map_ctr: arena_used, n_entries
+  uint64_t map_mask = 0;
+  std::vector<uint8_t> key;
+  bool key_set = false;
+  DBuf key_dev, key_state;
+  std::atomic<uint32_t> call_id{0};
+  uint64_t records_done = 0;
+  uint32_t slug_len = 10;
+  std::atomic<uint64_t> n_entries_seen{0};  // map size after the previous call
+  Server* server = nullptr;                 // serving loop (as_serve_start)
 };
 
 struct as_output {
@@ -186,10 +203,26 @@ struct as_output {
   std::vector<uint8_t> map_orig;
 };
 
+void Lane::release_all() {
+  DBuf* all[] = {&dev_err, &in_bytes, &in_off, &rs_bits, &tok_at, &pos_b, &scan_tiles, &counters, &delta_total,
+                 &tok_ids, &tok_off, &tok_len, &rec_tok, &rx_len_b, &rx_type_b, &rx_s, &rx_l, &rx_t, &labels, &logits,
+                 &tok_flags, &rx_pos, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
+                 &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
+                 &name_off, &name_len, &seqs, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
+                 &ATT, &Y32, &H, &VT, &X8, &ATT8, &H8};
+  for (DBuf* b : all) release(*b);
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  ev_pool.clear();
+}
+
 namespace {
 
-as_status fail(as_ctx* c, as_status s, const std::string& msg) {
-  if (c) c->err = msg;
+// Message of the last failure on the calling thread (one ctx per thread is
+// the ABI convention; serving workers are threads of their own).
+thread_local std::string t_err;
+
+as_status fail(as_ctx*, as_status s, const std::string& msg) {
+  t_err = msg;
   return s;
 }
 
@@ -227,12 +260,12 @@ MapView map_view(as_ctx* c) {
   return m;
 }
 
-as_status check_dev_error(as_ctx* c) {
+as_status check_dev_error(as_ctx* c, Lane* ln) {
   DevError e{};
-  CK(cudaMemcpyAsync(&e, c->dev_err.p, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(&e, ln->dev_err.p, sizeof(e), cudaMemcpyDeviceToHost, ln->stream));
+  CK(cudaStreamSynchronize(ln->stream));
   if (e.code == 0) return AS_OK;
-  cudaMemsetAsync(c->dev_err.p, 0, sizeof(DevError), c->stream);
+  cudaMemsetAsync(ln->dev_err.p, 0, sizeof(DevError), ln->stream);
   if (e.code == kErrTimeout)
     return fail(c, AS_ERR_TIMEOUT, "a bounded device wait ran out (site " + std::to_string(e.where) + ")");
   if (e.code == kErrCapacity)
@@ -317,30 +350,30 @@ as_status load_weights(as_ctx* c) {
     CKS(grow(c->w16, per * g.n_layers * 2));
     __nv_bfloat16* q = c->w16.as<__nv_bfloat16>();
     for (auto& L : c->layers) {
-      L.w_qkv16 = q; convert_f32_bf16(L.w_qkv, q, 3 * d * d, c->stream); q += 3 * d * d;
-      L.w_o16 = q; convert_f32_bf16(L.w_o, q, d * d, c->stream); q += d * d;
-      L.w_1_16 = q; convert_f32_bf16(L.w_1, q, f * d, c->stream); q += f * d;
-      L.w_2_16 = q; convert_f32_bf16(L.w_2, q, d * f, c->stream); q += d * f;
+      L.w_qkv16 = q; convert_f32_bf16(L.w_qkv, q, 3 * d * d, c->main.stream); q += 3 * d * d;
+      L.w_o16 = q; convert_f32_bf16(L.w_o, q, d * d, c->main.stream); q += d * d;
+      L.w_1_16 = q; convert_f32_bf16(L.w_1, q, f * d, c->main.stream); q += f * d;
+      L.w_2_16 = q; convert_f32_bf16(L.w_2, q, d * f, c->main.stream); q += d * f;
     }
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(c->main.stream));
   }
   if (g.precision == AS_FP8) {
     // per-tensor weight scales s = amax / 448, then E4M3 copies
     uint64_t per = 3 * d * d + d * d + f * d + d * f;
     CKS(grow(c->w8, per * g.n_layers));
     CKS(grow(c->amax_dev, 4 * g.n_layers * 4));
-    CK(cudaMemsetAsync(c->amax_dev.p, 0, 4 * g.n_layers * 4, c->stream));
+    CK(cudaMemsetAsync(c->amax_dev.p, 0, 4 * g.n_layers * 4, c->main.stream));
     unsigned int* am = c->amax_dev.as<unsigned int>();
     for (uint32_t l = 0; l < g.n_layers; ++l) {
       const LayerW& L = c->layers[l];
-      amax_f32(L.w_qkv, 3 * d * d, am + 4 * l + 0, c->stream);
-      amax_f32(L.w_o, d * d, am + 4 * l + 1, c->stream);
-      amax_f32(L.w_1, f * d, am + 4 * l + 2, c->stream);
-      amax_f32(L.w_2, d * f, am + 4 * l + 3, c->stream);
+      amax_f32(L.w_qkv, 3 * d * d, am + 4 * l + 0, c->main.stream);
+      amax_f32(L.w_o, d * d, am + 4 * l + 1, c->main.stream);
+      amax_f32(L.w_1, f * d, am + 4 * l + 2, c->main.stream);
+      amax_f32(L.w_2, d * f, am + 4 * l + 3, c->main.stream);
     }
     std::vector<unsigned int> bits(4 * g.n_layers);
-    CK(cudaMemcpyAsync(bits.data(), am, bits.size() * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(bits.data(), am, bits.size() * 4, cudaMemcpyDeviceToHost, c->main.stream));
+    CK(cudaStreamSynchronize(c->main.stream));
     auto scale_of = [](unsigned int b) {
       float a;
       memcpy(&a, &b, 4);
@@ -353,12 +386,12 @@ as_status load_weights(as_ctx* c) {
       L.s_o = scale_of(bits[4 * l + 1]);
       L.s_1 = scale_of(bits[4 * l + 2]);
       L.s_2 = scale_of(bits[4 * l + 3]);
-      L.w_qkv8 = q; quantize_e4m3(L.w_qkv, q, 3 * d * d, L.s_qkv, c->stream); q += 3 * d * d;
-      L.w_o8 = q; quantize_e4m3(L.w_o, q, d * d, L.s_o, c->stream); q += d * d;
-      L.w_1_8 = q; quantize_e4m3(L.w_1, q, f * d, L.s_1, c->stream); q += f * d;
-      L.w_2_8 = q; quantize_e4m3(L.w_2, q, d * f, L.s_2, c->stream); q += d * f;
+      L.w_qkv8 = q; quantize_e4m3(L.w_qkv, q, 3 * d * d, L.s_qkv, c->main.stream); q += 3 * d * d;
+      L.w_o8 = q; quantize_e4m3(L.w_o, q, d * d, L.s_o, c->main.stream); q += d * d;
+      L.w_1_8 = q; quantize_e4m3(L.w_1, q, f * d, L.s_1, c->main.stream); q += f * d;
+      L.w_2_8 = q; quantize_e4m3(L.w_2, q, d * f, L.s_2, c->main.stream); q += d * f;
     }
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(c->main.stream));
   }
   return AS_OK;
 }
@@ -367,173 +400,173 @@ as_status load_weights(as_ctx* c) {
 
 // Event pair around one launch when profiling is on (kind 0 GEMM, 1 attention).
 struct ProfScope {
-  as_ctx* c;
+  Lane* ln;
   bool on;
-  ProfScope(as_ctx* c_, int kind, double flops) : c(c_), on(c_->prof) {
+  ProfScope(Lane* ln_, int kind, double flops) : ln(ln_), on(ln_->prof) {
     if (!on) return;
-    if (c->ev_used + 2 > c->ev_pool.size()) {
+    if (ln->ev_used + 2 > ln->ev_pool.size()) {
       for (int i = 0; i < 64; ++i) {
         cudaEvent_t e;
         cudaEventCreate(&e);
-        c->ev_pool.push_back(e);
+        ln->ev_pool.push_back(e);
       }
     }
-    cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
-    c->ev_pending.push_back({kind, flops});
+    cudaEventRecord(ln->ev_pool[ln->ev_used], ln->stream);
+    ln->ev_pending.push_back({kind, flops});
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
-    c->ev_used += 2;
+    cudaEventRecord(ln->ev_pool[ln->ev_used + 1], ln->stream);
+    ln->ev_used += 2;
   }
 };
 
 // After a stream sync: fold the recorded event pairs into the totals.
-void prof_collect(as_ctx* c) {
-  for (size_t i = 0; i < c->ev_pending.size(); ++i) {
+void prof_collect(Lane* ln) {
+  for (size_t i = 0; i < ln->ev_pending.size(); ++i) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]);
-    if (c->ev_pending[i].first == 0) {
-      c->prof_acc.gemm_launches++;
-      c->prof_acc.gemm_ms += ms;
-      c->prof_acc.gemm_flops += c->ev_pending[i].second;
+    cudaEventElapsedTime(&ms, ln->ev_pool[2 * i], ln->ev_pool[2 * i + 1]);
+    if (ln->ev_pending[i].first == 0) {
+      ln->prof_acc.gemm_launches++;
+      ln->prof_acc.gemm_ms += ms;
+      ln->prof_acc.gemm_flops += ln->ev_pending[i].second;
     } else {
-      c->prof_acc.attn_launches++;
-      c->prof_acc.attn_ms += ms;
-      c->prof_acc.attn_flops += c->ev_pending[i].second;
+      ln->prof_acc.attn_launches++;
+      ln->prof_acc.attn_ms += ms;
+      ln->prof_acc.attn_flops += ln->ev_pending[i].second;
     }
   }
-  c->ev_pending.clear();
-  c->ev_used = 0;
+  ln->ev_pending.clear();
+  ln->ev_used = 0;
 }
 
-as_status run_encoder_chunk(as_ctx* c, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
+as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
                             bool want_logits) {
   const as_config& g = c->cfg;
   const int64_t R = (int64_t)ch.rows;
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
   const int32_t ns = (int32_t)(ch.s1 - ch.s0);
-  cudaStream_t st = c->stream;
+  cudaStream_t st = ln->stream;
   // padding rows between sequences: token 0, position 0, owned by nobody
-  CK(cudaMemsetAsync(c->row_tok.p, 0, R * 4, st));
-  CK(cudaMemsetAsync(c->row_pos.p, 0, R * 4, st));
-  CK(cudaMemsetAsync(c->row_own.p, 0, R, st));
-  expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(),
-                                         c->row_own.as<uint8_t>(), c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>());
+  CK(cudaMemsetAsync(ln->row_tok.p, 0, R * 4, st));
+  CK(cudaMemsetAsync(ln->row_pos.p, 0, R * 4, st));
+  CK(cudaMemsetAsync(ln->row_own.p, 0, R, st));
+  expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, ln->row_tok.as<int32_t>(), ln->row_pos.as<int32_t>(),
+                                         ln->row_own.as<uint8_t>(), ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>());
   count_launch();
-  float* X32 = c->X32.as<float>();
-  float* Y32 = c->Y32.as<float>();
+  float* X32 = ln->X32.as<float>();
+  float* Y32 = ln->Y32.as<float>();
   const int mode = g.precision == AS_FP32 ? kEncF32
                    : g.precision == AS_BF16 ? kEncBF16
                                             : (c->calibrating ? kEncCalib : kEncFP8);
   const bool bf = mode == kEncBF16 || mode == kEncCalib;
   const bool f8 = mode == kEncFP8;
-  __nv_bfloat16* X16 = bf ? c->X16.as<__nv_bfloat16>() : nullptr;
-  uint8_t* X8 = f8 ? c->X8.as<uint8_t>() : nullptr;
+  __nv_bfloat16* X16 = bf ? ln->X16.as<__nv_bfloat16>() : nullptr;
+  uint8_t* X8 = f8 ? ln->X8.as<uint8_t>() : nullptr;
   unsigned int* amax = c->amax_dev.as<unsigned int>();
   const float* as8 = f8 ? c->act_scale.data() : nullptr;
   const uint64_t Rd = (uint64_t)R * d;
-  CKS(embed_ln_ex(c->tok_ids.as<int32_t>(), c->row_tok.as<int32_t>(), c->row_pos.as<int32_t>(), c->tok_emb,
+  CKS(embed_ln_ex(ln->tok_ids.as<int32_t>(), ln->row_tok.as<int32_t>(), ln->row_pos.as<int32_t>(), c->tok_emb,
                   c->pos_emb, c->emb_g, c->emb_b, X32, X16, X8, f8 ? as8[0] : 1.0f, R, d, st));
   if (mode == kEncCalib) amax_bf16(X16, Rd, amax + 0, st);
-  DevError* err = c->dev_err.as<DevError>();
+  DevError* err = ln->dev_err.as<DevError>();
   for (uint32_t l = 0; l < g.n_layers; ++l) {
     const LayerW& L = c->layers[l];
     const bool last = l + 1 == g.n_layers;
     if (f8) {
       const float* sc = as8 + kActPerLayer * l;
-      __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
-      uint8_t* ATT8 = c->ATT8.as<uint8_t>();
-      uint8_t* H8 = c->H8.as<uint8_t>();
-      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d);
+      __nv_bfloat16* QKV = ln->QKV.as<__nv_bfloat16>();
+      uint8_t* ATT8 = ln->ATT8.as<uint8_t>();
+      uint8_t* H8 = ln->H8.as<uint8_t>();
+      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS, true, false, R, 3 * d, d, X8, L.w_qkv8, L.b_qkv, nullptr, QKV,
                             sc[0] * L.s_qkv, 1.0f, err, st)); }
-      { ProfScope ps(c, 1, attn_flops);
-        CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns,
+      { ProfScope ps(ln, 1, attn_flops);
+        CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
                                 (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
-      { ProfScope ps(c, 0, 2.0 * R * d * d);
+      { ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
                             1.0f, err, st)); }
       CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
-      { ProfScope ps(c, 0, 2.0 * R * f * d);
+      { ProfScope ps(ln, 0, 2.0 * R * f * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, true, true, R, f, d, X8, L.w_1_8, L.b_1, nullptr, H8, sc[2] * L.s_1,
                             sc[3], err, st)); }
-      { ProfScope ps(c, 0, 2.0 * R * d * f);
+      { ProfScope ps(ln, 0, 2.0 * R * d * f);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, f, H8, L.w_2_8, L.b_2, X32, Y32, sc[3] * L.s_2,
                             1.0f, err, st)); }
     } else if (bf) {
-      __nv_bfloat16* QKV = c->QKV.as<__nv_bfloat16>();
-      __nv_bfloat16* ATT = c->ATT.as<__nv_bfloat16>();
-      __nv_bfloat16* H = c->H.as<__nv_bfloat16>();
-      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
+      __nv_bfloat16* QKV = ln->QKV.as<__nv_bfloat16>();
+      __nv_bfloat16* ATT = ln->ATT.as<__nv_bfloat16>();
+      __nv_bfloat16* H = ln->H.as<__nv_bfloat16>();
+      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
       if (g.attention == AS_ATTN_TCGEN05) {
-        ProfScope ps(c, 1, attn_flops);
-        CKS(attention_tcgen05(QKV, c->VT.as<__nv_bfloat16>(), ATT, c->seq_start.as<int32_t>(),
-                              c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+        ProfScope ps(ln, 1, attn_flops);
+        CKS(attention_tcgen05(QKV, ln->VT.as<__nv_bfloat16>(), ATT, ln->seq_start.as<int32_t>(),
+                              ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
       } else {
-        ProfScope ps(c, 1, attn_flops);
-        CKS(attention_bf16(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+        ProfScope ps(ln, 1, attn_flops);
+        CKS(attention_bf16(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
                            (int32_t)g.n_heads, st));
       }
       if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
-      { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
       if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * l + 2, st);
-      { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
       if (mode == kEncCalib) amax_bf16(H, (uint64_t)R * f, amax + kActPerLayer * l + 3, st);
-      { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st)); }
     } else {
-      float* QKV = c->QKV.as<float>();
-      float* ATT = c->ATT.as<float>();
-      float* H = c->H.as<float>();
-      { ProfScope ps(c, 0, 2.0 * R * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
-      { ProfScope ps(c, 1, attn_flops);
-        CKS(attention_f32(QKV, ATT, c->seq_start.as<int32_t>(), c->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+      float* QKV = ln->QKV.as<float>();
+      float* ATT = ln->ATT.as<float>();
+      float* H = ln->H.as<float>();
+      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
+      { ProfScope ps(ln, 1, attn_flops);
+        CKS(attention_f32(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
                           (int32_t)g.n_heads, st)); }
-      { ProfScope ps(c, 0, 2.0 * R * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, nullptr, R, d, st));
-      { ProfScope ps(c, 0, 2.0 * R * f * d); CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st)); }
-      { ProfScope ps(c, 0, 2.0 * R * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
     }
     if (!last) {
       CKS(layernorm_rows_ex(Y32, L.ln2_g, L.ln2_b, X32, X16, X8, f8 ? as8[kActPerLayer * (l + 1)] : 1.0f, R, d, st));
       if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * (l + 1), st);
     } else {
-      CKS(layernorm_classify(Y32, L.ln2_g, L.ln2_b, c->cls_w, c->cls_b, (int32_t)g.n_labels, c->row_tok.as<int32_t>(),
-                             c->row_own.as<uint8_t>(), want_logits ? c->logits.as<float>() : nullptr,
-                             c->labels.as<uint8_t>(), R, d, st));
+      CKS(layernorm_classify(Y32, L.ln2_g, L.ln2_b, c->cls_w, c->cls_b, (int32_t)g.n_labels, ln->row_tok.as<int32_t>(),
+                             ln->row_own.as<uint8_t>(), want_logits ? ln->logits.as<float>() : nullptr,
+                             ln->labels.as<uint8_t>(), R, d, st));
     }
   }
   return AS_OK;
 }
 
-as_status ensure_encoder_buffers(as_ctx* c, uint64_t rows, uint64_t n_seq) {
+as_status ensure_encoder_buffers(as_ctx* c, Lane* ln, uint64_t rows, uint64_t n_seq) {
   const as_config& g = c->cfg;
   const uint64_t d = g.d_model, f = g.d_ffn;
   const bool bf = g.precision != AS_FP32;   // FP8 keeps BF16 buffers for calibration and QKV
   const bool f8 = g.precision == AS_FP8;
   const size_t act = bf ? 2 : 4;
-  CKS(grow(c->row_tok, rows * 4));
-  CKS(grow(c->row_pos, rows * 4));
-  CKS(grow(c->row_own, rows));
-  CKS(grow(c->seq_start, n_seq * 4));
-  CKS(grow(c->seq_len, n_seq * 4));
-  CKS(grow(c->X32, rows * d * 4));
-  CKS(grow(c->Y32, rows * d * 4));
-  if (bf) CKS(grow(c->X16, rows * d * 2));
-  CKS(grow(c->QKV, rows * 3 * d * act));
-  const void* att_before = c->ATT.p;
-  CKS(grow(c->ATT, rows * d * act));
+  CKS(grow(ln->row_tok, rows * 4));
+  CKS(grow(ln->row_pos, rows * 4));
+  CKS(grow(ln->row_own, rows));
+  CKS(grow(ln->seq_start, n_seq * 4));
+  CKS(grow(ln->seq_len, n_seq * 4));
+  CKS(grow(ln->X32, rows * d * 4));
+  CKS(grow(ln->Y32, rows * d * 4));
+  if (bf) CKS(grow(ln->X16, rows * d * 2));
+  CKS(grow(ln->QKV, rows * 3 * d * act));
+  const void* att_before = ln->ATT.p;
+  CKS(grow(ln->ATT, rows * d * act));
   // rows no sequence covers are never written by attention: keep them finite
-  if (c->ATT.p != att_before) CK(cudaMemsetAsync(c->ATT.p, 0, c->ATT.cap, c->stream));
-  if (bf && g.attention == AS_ATTN_TCGEN05) CKS(grow(c->VT, attention_vt_elems((int64_t)rows, (int32_t)d) * 2));
-  CKS(grow(c->H, rows * f * act));
+  if (ln->ATT.p != att_before) CK(cudaMemsetAsync(ln->ATT.p, 0, ln->ATT.cap, ln->stream));
+  if (bf && g.attention == AS_ATTN_TCGEN05) CKS(grow(ln->VT, attention_vt_elems((int64_t)rows, (int32_t)d) * 2));
+  CKS(grow(ln->H, rows * f * act));
   if (f8) {
-    CKS(grow(c->X8, rows * d));
-    const void* before = c->ATT8.p;
-    CKS(grow(c->ATT8, rows * d));
-    if (c->ATT8.p != before) CK(cudaMemsetAsync(c->ATT8.p, 0, c->ATT8.cap, c->stream));
-    CKS(grow(c->H8, rows * f));
+    CKS(grow(ln->X8, rows * d));
+    const void* before = ln->ATT8.p;
+    CKS(grow(ln->ATT8, rows * d));
+    if (ln->ATT8.p != before) CK(cudaMemsetAsync(ln->ATT8.p, 0, ln->ATT8.cap, ln->stream));
+    CKS(grow(ln->H8, rows * f));
   }
   return AS_OK;
 }
@@ -562,40 +595,40 @@ as_status set_key(as_ctx* c, const uint8_t* key, size_t key_len) {
   std::vector<uint8_t> k(key, key + key_len);
   if (c->key_set && k == c->key) return AS_OK;
   uint64_t n_entries = 0;
-  CK(cudaMemcpyAsync(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost, c->main.stream));
+  CK(cudaStreamSynchronize(c->main.stream));
   if (c->key_set && n_entries > 0)
     return fail(c, AS_ERR_STATE, "key differs from the key of the non-empty entity map (clear the map first)");
   c->key = k;
   c->key_set = true;
   CKS(grow(c->key_dev, key_len + 1));
-  if (key_len) CK(cudaMemcpyAsync(c->key_dev.p, key, key_len, cudaMemcpyHostToDevice, c->stream));
+  if (key_len) CK(cudaMemcpyAsync(c->key_dev.p, key, key_len, cudaMemcpyHostToDevice, c->main.stream));
   CKS(grow(c->key_state, 16 * 4));
-  launch_hmac_key_setup(c->key_dev.as<uint8_t>(), (uint32_t)key_len, c->key_state.as<uint32_t>(), c->stream);
-  CK(cudaStreamSynchronize(c->stream));
+  launch_hmac_key_setup(c->key_dev.as<uint8_t>(), (uint32_t)key_len, c->key_state.as<uint32_t>(), c->main.stream);
+  CK(cudaStreamSynchronize(c->main.stream));
   return AS_OK;
 }
 
 template <typename T>
-as_status d2h_vec(as_ctx* c, std::vector<T>& v, const void* src, uint64_t n) {
+as_status d2h_vec(as_ctx* c, Lane* ln, std::vector<T>& v, const void* src, uint64_t n) {
   v.resize(n);
-  if (n) CK(cudaMemcpyAsync(v.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  if (n) CK(cudaMemcpyAsync(v.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ln->stream));
   return AS_OK;
 }
 
 // calibrate = true: run the tokenizer and the BF16 encoder only, recording
 // the amax of every FP8 GEMM input, and set the static activation scales.
-as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch, const uint8_t* key, size_t key_len,
-                         as_output** out, bool calibrate = false) {
+as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_schema* sch, const uint8_t* key,
+                         size_t key_len, as_output** out, bool calibrate = false, int64_t rec_base = -1) {
   const as_config& g = c->cfg;
-  cudaStream_t st = c->stream;
+  cudaStream_t st = ln->stream;
   if (!rec || (!out && !calibrate)) return fail(c, AS_ERR_ARG, "records / out is NULL");
   if (out) *out = nullptr;
   CKI(validate_schema(c, sch));
   if (calibrate && g.precision != AS_FP8) return fail(c, AS_ERR_STATE, "calibration is for AS_FP8 contexts");
   if (!calibrate && g.precision == AS_FP8 && c->act_scale.empty())
     return fail(c, AS_ERR_STATE, "FP8 context without activation scales: call as_calibrate or as_set_scales first");
-  if (!calibrate) CKI(set_key(c, key, key_len));
+  if (!calibrate && rec_base < 0) CKI(set_key(c, key, key_len));  // serving sets the key once at start
   c->slug_len = sch->slug_hex_len;
   const uint64_t n = rec->n_records;
   if (n > 0 && (!rec->offsets)) return fail(c, AS_ERR_ARG, "offsets is NULL");
@@ -617,70 +650,69 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
   const uint8_t* d_bytes;
   const uint64_t* d_off;
-  CKS(grow(c->in_off, (n + 1) * 8));
+  CKS(grow(ln->in_off, (n + 1) * 8));
   if (rec->on_device) {
     d_bytes = rec->bytes;
     d_off = rec->offsets;
   } else {
-    CKS(grow(c->in_bytes, N + 16));
-    if (N) CK(cudaMemcpyAsync(c->in_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+    CKS(grow(ln->in_bytes, N + 16));
+    if (N) CK(cudaMemcpyAsync(ln->in_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
     uint64_t zero = 0;
-    if (n) CK(cudaMemcpyAsync(c->in_off.p, rec->offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
-    else CK(cudaMemcpyAsync(c->in_off.p, &zero, 8, cudaMemcpyHostToDevice, st));
-    d_bytes = c->in_bytes.as<uint8_t>();
-    d_off = c->in_off.as<uint64_t>();
+    if (n) CK(cudaMemcpyAsync(ln->in_off.p, rec->offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemcpyAsync(ln->in_off.p, &zero, 8, cudaMemcpyHostToDevice, st));
+    d_bytes = ln->in_bytes.as<uint8_t>();
+    d_off = ln->in_off.as<uint64_t>();
   }
   if (n == 0) {
     static const uint64_t zero_off = 0;
-    CK(cudaMemcpyAsync(c->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
-    d_off = c->in_off.as<uint64_t>();
+    CK(cudaMemcpyAsync(ln->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
+    d_off = ln->in_off.as<uint64_t>();
   }
   const uint32_t N32 = (uint32_t)N;
   const uint64_t launches0 = g_launches.load();
-  ++c->call_id;
-  const uint32_t call_id = c->call_id;
+  const uint32_t call_id = ++c->call_id;
   // ---- tokenizer + recognizers
-  CKS(grow(c->counters, 64));
-  uint32_t* cnt = c->counters.as<uint32_t>();  // 0 T, 1 n_rx, 2 n_ner, 3 n_nerk, 4 n_rxk, 5 n_fin
+  CKS(grow(ln->counters, 64));
+  uint32_t* cnt = ln->counters.as<uint32_t>();  // 0 T, 1 n_rx, 2 n_ner, 3 n_nerk, 4 n_rxk, 5 n_fin
   CK(cudaMemsetAsync(cnt, 0, 64, st));
-  CKS(grow(c->rs_bits, ((size_t)N / 32 + 1) * 4));
-  CKS(grow(c->tok_at, N * 2));
-  CKS(grow(c->pos_b, (N + 1) * 4));
-  CKS(grow(c->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(N + 1, 1) * 2) + 16) * 8));
-  CKS(grow(c->tok_ids, N * 4));
-  CKS(grow(c->tok_off, N * 4));
-  CKS(grow(c->tok_len, N * 4));
-  CKS(grow(c->rec_tok, (n + 1) * 8));
+  CKS(grow(ln->rs_bits, ((size_t)N / 32 + 1) * 4));
+  CKS(grow(ln->tok_at, N * 2));
+  CKS(grow(ln->pos_b, (N + 1) * 4));
+  CKS(grow(ln->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(N + 1, 1) * 2) + 16) * 8));
+  CKS(grow(ln->tok_ids, N * 4));
+  CKS(grow(ln->tok_off, N * 4));
+  CKS(grow(ln->tok_len, N * 4));
+  CKS(grow(ln->rec_tok, (n + 1) * 8));
   VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask};
-  launch_mark_record_starts(d_off, n, N32, c->rs_bits.as<uint32_t>(), st);
-  launch_tokenize_mark(d_bytes, N32, c->rs_bits.as<uint32_t>(), vt, c->tok_at.as<uint16_t>(), st);
-  exclusive_scan<uint32_t>(NonZeroU16{c->tok_at.as<uint16_t>()}, N, c->pos_b.as<uint32_t>(), cnt + 0,
-                           c->scan_tiles.as<uint32_t>(), st);
-  launch_tokenize_emit(c->tok_at.as<uint16_t>(), c->pos_b.as<uint32_t>(), N32, c->tok_ids.as<int32_t>(),
-                       c->tok_off.as<uint32_t>(), st);
-  launch_record_token_offsets(d_off, n, c->pos_b.as<uint32_t>(), N32, cnt + 0, c->rec_tok.as<uint64_t>(), st);
+  launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
+  launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU16{ln->tok_at.as<uint16_t>()}, N, ln->pos_b.as<uint32_t>(), cnt + 0,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  launch_tokenize_emit(ln->tok_at.as<uint16_t>(), ln->pos_b.as<uint32_t>(), N32, ln->tok_ids.as<int32_t>(),
+                       ln->tok_off.as<uint32_t>(), st);
+  launch_record_token_offsets(d_off, n, ln->pos_b.as<uint32_t>(), N32, cnt + 0, ln->rec_tok.as<uint64_t>(), st);
   // recognizers (pos_b reused after the token emit above)
-  CKS(grow(c->rx_len_b, N * 4));
-  CKS(grow(c->rx_type_b, N + 16));
-  launch_recognize_mark(d_bytes, N32, c->rs_bits.as<uint32_t>(), c->rx_len_b.as<uint32_t>(), c->rx_type_b.as<uint8_t>(),
+  CKS(grow(ln->rx_len_b, N * 4));
+  CKS(grow(ln->rx_type_b, N + 16));
+  launch_recognize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(),
                         st);
-  CKS(grow(c->rx_pos, (N + 1) * 4));
-  exclusive_scan<uint32_t>(NonZeroU8{c->rx_type_b.as<uint8_t>()}, N, c->rx_pos.as<uint32_t>(), cnt + 1,
-                           c->scan_tiles.as<uint32_t>(), st);
-  CKS(grow(c->rx_s, (N / 2 + 2) * 4));
-  CKS(grow(c->rx_l, (N / 2 + 2) * 4));
-  CKS(grow(c->rx_t, N / 2 + 2));
-  launch_recognize_emit(c->rx_len_b.as<uint32_t>(), c->rx_type_b.as<uint8_t>(), c->rx_pos.as<uint32_t>(), N32,
-                        c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), c->rx_t.as<uint8_t>(), st);
+  CKS(grow(ln->rx_pos, (N + 1) * 4));
+  exclusive_scan<uint32_t>(NonZeroU8{ln->rx_type_b.as<uint8_t>()}, N, ln->rx_pos.as<uint32_t>(), cnt + 1,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(ln->rx_s, (N / 2 + 2) * 4));
+  CKS(grow(ln->rx_l, (N / 2 + 2) * 4));
+  CKS(grow(ln->rx_t, N / 2 + 2));
+  launch_recognize_emit(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), ln->rx_pos.as<uint32_t>(), N32,
+                        ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), st);
   // ---- sync 1: token counts
   uint32_t h_cnt[2] = {0, 0};
   CK(cudaMemcpyAsync(h_cnt, cnt, 8, cudaMemcpyDeviceToHost, st));
-  std::vector<uint64_t>& rt = c->h_rec_tok;
+  std::vector<uint64_t>& rt = ln->h_rec_tok;
   rt.resize(n + 1);
-  CK(cudaMemcpyAsync(rt.data(), c->rec_tok.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rt.data(), ln->rec_tok.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint64_t T = h_cnt[0], n_rx = h_cnt[1];
-  launch_token_lengths(c->tok_off.as<uint32_t>(), (uint32_t)T, N32, c->tok_len.as<uint32_t>(), st);
+  launch_token_lengths(ln->tok_off.as<uint32_t>(), (uint32_t)T, N32, ln->tok_len.as<uint32_t>(), st);
   // ---- sequences (windows) and encoder batches
   const uint32_t W = sch->window, S = sch->stride;
   std::vector<SeqDesc> seqs;
@@ -749,13 +781,13 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     max_rows = std::max(max_rows, ch.rows);
     max_seqs = std::max<uint64_t>(max_seqs, ch.s1 - ch.s0);
   }
-  CKS(grow(c->seqs, std::max<size_t>(1, seqs.size()) * sizeof(SeqDesc)));
-  if (!seqs.empty()) CK(cudaMemcpyAsync(c->seqs.p, seqs.data(), seqs.size() * sizeof(SeqDesc), cudaMemcpyHostToDevice, st));
-  CKI(ensure_encoder_buffers(c, std::max<uint64_t>(max_rows, 1), std::max<uint64_t>(max_seqs, 1)));
+  CKS(grow(ln->seqs, std::max<size_t>(1, seqs.size()) * sizeof(SeqDesc)));
+  if (!seqs.empty()) CK(cudaMemcpyAsync(ln->seqs.p, seqs.data(), seqs.size() * sizeof(SeqDesc), cudaMemcpyHostToDevice, st));
+  CKI(ensure_encoder_buffers(c, ln, std::max<uint64_t>(max_rows, 1), std::max<uint64_t>(max_seqs, 1)));
   const bool want_logits = g.keep_trace != 0;
-  CKS(grow(c->labels, T + 16));
-  if (want_logits) CKS(grow(c->logits, (T + 1) * g.n_labels * 4));
-  CK(cudaMemsetAsync(c->labels.p, 0, T + 16, st));
+  CKS(grow(ln->labels, T + 16));
+  if (want_logits) CKS(grow(ln->logits, (T + 1) * g.n_labels * 4));
+  CK(cudaMemsetAsync(ln->labels.p, 0, T + 16, st));
   if (calibrate) {
     c->calibrating = true;
     CK(cudaMemsetAsync(c->amax_dev.p, 0, (size_t)kActPerLayer * g.n_layers * 4, st));
@@ -763,14 +795,14 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   for (const Chunk& ch : chunks) {
     double af = 0;  // attention FLOPs of the batch: QK^T and PV, 2 * 2 * L^2 * d per sequence
     for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
-    as_status es = run_encoder_chunk(c, ch, c->seqs.as<SeqDesc>(), af, want_logits);
+    as_status es = run_encoder_chunk(c, ln, ch, ln->seqs.as<SeqDesc>(), af, want_logits);
     if (es != AS_OK) {
       c->calibrating = false;
       return es;
     }
-    if (c->prof && c->ev_used > 4096) {  // bound the event pool
+    if (ln->prof && ln->ev_used > 4096) {  // bound the event pool
       CK(cudaStreamSynchronize(st));
-      prof_collect(c);
+      prof_collect(ln);
     }
   }
   if (calibrate) {
@@ -779,7 +811,7 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     std::vector<unsigned int> bits((size_t)kActPerLayer * g.n_layers);
     CK(cudaMemcpyAsync(bits.data(), c->amax_dev.p, bits.size() * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    CKI(check_dev_error(c));
+    CKI(check_dev_error(c, ln));
     c->act_scale.resize(bits.size());
     for (size_t i = 0; i < bits.size(); ++i) {
       float a;
@@ -789,65 +821,66 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     return AS_OK;
   }
   // ---- BIO decode
-  CKS(grow(c->tok_flags, T + 16));
-  CK(cudaMemsetAsync(c->tok_flags.p, 0, T + 1, st));
-  launch_token_flags(c->rec_tok.as<uint64_t>(), n, c->tok_flags.as<uint8_t>(), st);
-  CKS(grow(c->bio_start, T + 16));
-  CKS(grow(c->bio_end, T + 16));
-  CKS(grow(c->pos_t, (T + 1) * 4));
-  launch_bio_mark(c->labels.as<uint8_t>(), c->tok_flags.as<uint8_t>(), (uint32_t)T, c->bio_start.as<uint8_t>(),
-                  c->bio_end.as<uint8_t>(), st);
-  exclusive_scan<uint32_t>(NonZeroU8{c->bio_start.as<uint8_t>()}, T, c->pos_t.as<uint32_t>(), cnt + 2,
-                           c->scan_tiles.as<uint32_t>(), st);
-  CKS(grow(c->ner_s, (T + 1) * 4));
-  CKS(grow(c->ner_l, (T + 1) * 4));
-  CKS(grow(c->ner_t, T + 16));
-  launch_bio_emit(c->labels.as<uint8_t>(), c->bio_start.as<uint8_t>(), c->bio_end.as<uint8_t>(), c->pos_t.as<uint32_t>(),
-                  (uint32_t)T, c->tok_off.as<uint32_t>(), c->tok_len.as<uint32_t>(), d_bytes, c->ner_s.as<uint32_t>(),
-                  c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), st);
-  launch_bio_to_bytes(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), cnt + 2, (uint32_t)T, c->tok_off.as<uint32_t>(),
-                      c->tok_len.as<uint32_t>(), d_bytes, st);
+  CKS(grow(ln->tok_flags, T + 16));
+  CK(cudaMemsetAsync(ln->tok_flags.p, 0, T + 1, st));
+  launch_token_flags(ln->rec_tok.as<uint64_t>(), n, ln->tok_flags.as<uint8_t>(), st);
+  CKS(grow(ln->bio_start, T + 16));
+  CKS(grow(ln->bio_end, T + 16));
+  CKS(grow(ln->pos_t, (T + 1) * 4));
+  launch_bio_mark(ln->labels.as<uint8_t>(), ln->tok_flags.as<uint8_t>(), (uint32_t)T, ln->bio_start.as<uint8_t>(),
+                  ln->bio_end.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{ln->bio_start.as<uint8_t>()}, T, ln->pos_t.as<uint32_t>(), cnt + 2,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(ln->ner_s, (T + 1) * 4));
+  CKS(grow(ln->ner_l, (T + 1) * 4));
+  CKS(grow(ln->ner_t, T + 16));
+  launch_bio_emit(ln->labels.as<uint8_t>(), ln->bio_start.as<uint8_t>(), ln->bio_end.as<uint8_t>(), ln->pos_t.as<uint32_t>(),
+                  (uint32_t)T, ln->tok_off.as<uint32_t>(), ln->tok_len.as<uint32_t>(), d_bytes, ln->ner_s.as<uint32_t>(),
+                  ln->ner_l.as<uint32_t>(), ln->ner_t.as<uint8_t>(), st);
+  launch_bio_to_bytes(ln->ner_s.as<uint32_t>(), ln->ner_l.as<uint32_t>(), cnt + 2, (uint32_t)T, ln->tok_off.as<uint32_t>(),
+                      ln->tok_len.as<uint32_t>(), d_bytes, st);
   // ---- overlap rule + preserve
   const uint32_t ner_cap = (uint32_t)T, rx_cap = (uint32_t)n_rx;
-  CKS(grow(c->pos_k, (T + n_rx + 2) * 4));
-  DBuf& keep = c->keep;
+  CKS(grow(ln->pos_k, (T + n_rx + 2) * 4));
+  DBuf& keep = ln->keep;
   CKS(grow(keep, T + n_rx + 16));
-  launch_ner_keep(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), cnt + 2, ner_cap,
-                  c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), cnt + 1, sch->preserve_mask, keep.as<uint8_t>(), st);
-  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, ner_cap, c->pos_k.as<uint32_t>(), cnt + 3,
-                           c->scan_tiles.as<uint32_t>(), st);
-  CKS(grow(c->nk_s, (T + 1) * 4));
-  CKS(grow(c->nk_l, (T + 1) * 4));
-  CKS(grow(c->nk_t, T + 16));
-  launch_compact_spans(c->ner_s.as<uint32_t>(), c->ner_l.as<uint32_t>(), c->ner_t.as<uint8_t>(), keep.as<uint8_t>(),
-                       c->pos_k.as<uint32_t>(), cnt + 2, ner_cap, c->nk_s.as<uint32_t>(), c->nk_l.as<uint32_t>(),
-                       c->nk_t.as<uint8_t>(), st);
-  launch_rx_keep(c->rx_t.as<uint8_t>(), cnt + 1, rx_cap, sch->preserve_mask, keep.as<uint8_t>(), st);
-  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, rx_cap, c->pos_k.as<uint32_t>(), cnt + 4,
-                           c->scan_tiles.as<uint32_t>(), st);
-  CKS(grow(c->rk_s, (n_rx + 1) * 4));
-  CKS(grow(c->rk_l, (n_rx + 1) * 4));
-  CKS(grow(c->rk_t, n_rx + 16));
-  launch_compact_spans(c->rx_s.as<uint32_t>(), c->rx_l.as<uint32_t>(), c->rx_t.as<uint8_t>(), keep.as<uint8_t>(),
-                       c->pos_k.as<uint32_t>(), cnt + 1, rx_cap, c->rk_s.as<uint32_t>(), c->rk_l.as<uint32_t>(),
-                       c->rk_t.as<uint8_t>(), st);
+  launch_ner_keep(ln->ner_s.as<uint32_t>(), ln->ner_l.as<uint32_t>(), ln->ner_t.as<uint8_t>(), cnt + 2, ner_cap,
+                  ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), cnt + 1, sch->preserve_mask, keep.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, ner_cap, ln->pos_k.as<uint32_t>(), cnt + 3,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(ln->nk_s, (T + 1) * 4));
+  CKS(grow(ln->nk_l, (T + 1) * 4));
+  CKS(grow(ln->nk_t, T + 16));
+  launch_compact_spans(ln->ner_s.as<uint32_t>(), ln->ner_l.as<uint32_t>(), ln->ner_t.as<uint8_t>(), keep.as<uint8_t>(),
+                       ln->pos_k.as<uint32_t>(), cnt + 2, ner_cap, ln->nk_s.as<uint32_t>(), ln->nk_l.as<uint32_t>(),
+                       ln->nk_t.as<uint8_t>(), st);
+  launch_rx_keep(ln->rx_t.as<uint8_t>(), cnt + 1, rx_cap, sch->preserve_mask, keep.as<uint8_t>(), st);
+  exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, rx_cap, ln->pos_k.as<uint32_t>(), cnt + 4,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  CKS(grow(ln->rk_s, (n_rx + 1) * 4));
+  CKS(grow(ln->rk_l, (n_rx + 1) * 4));
+  CKS(grow(ln->rk_t, n_rx + 16));
+  launch_compact_spans(ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), keep.as<uint8_t>(),
+                       ln->pos_k.as<uint32_t>(), cnt + 1, rx_cap, ln->rk_s.as<uint32_t>(), ln->rk_l.as<uint32_t>(),
+                       ln->rk_t.as<uint8_t>(), st);
   const uint32_t fin_cap = ner_cap + rx_cap;
-  CKS(grow(c->fin_s, (fin_cap + 1) * 4));
-  CKS(grow(c->fin_l, (fin_cap + 1) * 4));
-  CKS(grow(c->fin_t, fin_cap + 16));
-  launch_merge_spans(c->rk_s.as<uint32_t>(), c->rk_l.as<uint32_t>(), c->rk_t.as<uint8_t>(), cnt + 4, rx_cap,
-                     c->nk_s.as<uint32_t>(), c->nk_l.as<uint32_t>(), c->nk_t.as<uint8_t>(), cnt + 3, ner_cap,
-                     c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), c->fin_t.as<uint8_t>(), st);
+  CKS(grow(ln->fin_s, (fin_cap + 1) * 4));
+  CKS(grow(ln->fin_l, (fin_cap + 1) * 4));
+  CKS(grow(ln->fin_t, fin_cap + 16));
+  launch_merge_spans(ln->rk_s.as<uint32_t>(), ln->rk_l.as<uint32_t>(), ln->rk_t.as<uint8_t>(), cnt + 4, rx_cap,
+                     ln->nk_s.as<uint32_t>(), ln->nk_l.as<uint32_t>(), ln->nk_t.as<uint8_t>(), cnt + 3, ner_cap,
+                     ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), st);
   // the HMAC / map / substitution kernels read the final span count from cnt[5]
   sum_kept_kernel<<<1, 32, 0, st>>>(cnt);
   count_launch();
   // ---- HMAC + map
-  CKS(grow(c->digests, (size_t)(fin_cap + 1) * 32));
-  launch_hmac_spans(d_bytes, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), cnt + 5, fin_cap,
-                    c->key_state.as<uint32_t>(), c->digests.as<uint32_t>(), st);
-  launch_map_insert_spans(map_view(c), d_bytes, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(),
-                          c->fin_t.as<uint8_t>(), c->digests.as<uint32_t>(), cnt + 5, fin_cap, d_off, n,
-                          c->records_done, call_id, c->dev_err.as<DevError>(), st);
+  CKS(grow(ln->digests, (size_t)(fin_cap + 1) * 32));
+  launch_hmac_spans(d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, fin_cap,
+                    c->key_state.as<uint32_t>(), ln->digests.as<uint32_t>(), st);
+  launch_map_insert_spans(map_view(c), d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(),
+                          ln->fin_t.as<uint8_t>(), ln->digests.as<uint32_t>(), cnt + 5, fin_cap, d_off, n,
+                          rec_base >= 0 ? (uint64_t)rec_base : c->records_done, call_id, ln->dev_err.as<DevError>(),
+                          st);
   // ---- substitution
   {
     std::vector<uint32_t> noff(sch->n_types + 2, 0), nlen(sch->n_types + 1, 0);
@@ -858,25 +891,25 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
       noff[t + 1] = (uint32_t)all.size();
       nlen[t] = noff[t + 1] - noff[t];
     }
-    CKS(grow(c->names, all.size() + 16));
-    CKS(grow(c->name_off, noff.size() * 4));
-    CKS(grow(c->name_len, nlen.size() * 4));
-    CK(cudaMemcpyAsync(c->names.p, all.data(), all.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->name_off.p, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
+    CKS(grow(ln->names, all.size() + 16));
+    CKS(grow(ln->name_off, noff.size() * 4));
+    CKS(grow(ln->name_len, nlen.size() * 4));
+    CK(cudaMemcpyAsync(ln->names.p, all.data(), all.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->name_off.p, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));  // the host vectors above go out of scope
   }
-  CKS(grow(c->delta, (size_t)(fin_cap + 1) * 8));
-  CKS(grow(c->shift, (size_t)(fin_cap + 1) * 8));
-  CKS(grow(c->delta_total, 16));
-  launch_sub_delta(c->fin_l.as<uint32_t>(), c->fin_t.as<uint8_t>(), cnt + 5, fin_cap + 1, c->name_len.as<uint32_t>(),
-                   sch->slug_hex_len, c->delta.as<int64_t>(), st);
-  exclusive_scan<int64_t>(LoadI64{c->delta.as<int64_t>()}, fin_cap + 1, c->shift.as<int64_t>(),
-                          c->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(c->scan_tiles.p), st);
+  CKS(grow(ln->delta, (size_t)(fin_cap + 1) * 8));
+  CKS(grow(ln->shift, (size_t)(fin_cap + 1) * 8));
+  CKS(grow(ln->delta_total, 16));
+  launch_sub_delta(ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_cap + 1, ln->name_len.as<uint32_t>(),
+                   sch->slug_hex_len, ln->delta.as<int64_t>(), st);
+  exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, fin_cap + 1, ln->shift.as<int64_t>(),
+                          ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st);
   // ---- sync 2: output size and counts
   int64_t total_delta = 0;
   uint32_t h_cnt2[6];
-  CK(cudaMemcpyAsync(&total_delta, c->delta_total.p, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&total_delta, ln->delta_total.p, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h_cnt2, cnt, 24, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint64_t out_size = (uint64_t)((int64_t)N + total_delta);
@@ -894,12 +927,12 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     delete o;
     return fail(c, AS_ERR_OOM, "output allocation failed");
   }
-  launch_sub_copy(d_bytes, N32, c->fin_s.as<uint32_t>(), c->fin_l.as<uint32_t>(), cnt + 5, c->shift.as<int64_t>(),
+  launch_sub_copy(d_bytes, N32, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(),
                   reinterpret_cast<uint8_t*>(d_out), st);
-  launch_sub_replace(c->fin_s.as<uint32_t>(), c->fin_t.as<uint8_t>(), cnt + 5, fin_cap, c->shift.as<int64_t>(),
-                     c->digests.as<uint32_t>(), c->names.as<char>(), c->name_off.as<uint32_t>(), sch->slug_hex_len,
+  launch_sub_replace(ln->fin_s.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_cap, ln->shift.as<int64_t>(),
+                     ln->digests.as<uint32_t>(), ln->names.as<char>(), ln->name_off.as<uint32_t>(), sch->slug_hex_len,
                      reinterpret_cast<uint8_t*>(d_out), st);
-  launch_sub_offsets(d_off, n, c->fin_s.as<uint32_t>(), cnt + 5, c->shift.as<int64_t>(), d_out_off, st);
+  launch_sub_offsets(d_off, n, ln->fin_s.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(), d_out_off, st);
   if (rec->on_device) {
     o->d_bytes = d_out;
     o->d_off = d_out_off;
@@ -912,37 +945,42 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
     cudaFreeAsync(d_out_off, st);
   }
   // ---- trace for as_debug_trace
-  c->last_n = n;
-  c->last_T = T;
-  c->last_nrx = n_rx;
-  c->last_nfin = h_cnt2[5];
-  c->last_logits = want_logits;
+  ln->last_n = n;
+  ln->last_T = T;
+  ln->last_nrx = n_rx;
+  ln->last_nfin = h_cnt2[5];
+  ln->last_logits = want_logits;
   if (g.keep_trace) {
-    CKS(d2h_vec(c, c->h_tok_ids, c->tok_ids.p, T));
-    CKS(d2h_vec(c, c->h_tok_off, c->tok_off.p, T));
-    CKS(d2h_vec(c, c->h_tok_len, c->tok_len.p, T));
-    CKS(d2h_vec(c, c->h_rx_s, c->rx_s.p, n_rx));
-    CKS(d2h_vec(c, c->h_rx_l, c->rx_l.p, n_rx));
-    CKS(d2h_vec(c, c->h_rx_t, c->rx_t.p, n_rx));
-    CKS(d2h_vec(c, c->h_labels, c->labels.p, T));
-    CKS(d2h_vec(c, c->h_logits, c->logits.p, T * g.n_labels));
-    CKS(d2h_vec(c, c->h_fin_s, c->fin_s.p, h_cnt2[5]));
-    CKS(d2h_vec(c, c->h_fin_l, c->fin_l.p, h_cnt2[5]));
-    CKS(d2h_vec(c, c->h_fin_t, c->fin_t.p, h_cnt2[5]));
+    CKS(d2h_vec(c, ln, ln->h_tok_ids, ln->tok_ids.p, T));
+    CKS(d2h_vec(c, ln, ln->h_tok_off, ln->tok_off.p, T));
+    CKS(d2h_vec(c, ln, ln->h_tok_len, ln->tok_len.p, T));
+    CKS(d2h_vec(c, ln, ln->h_rx_s, ln->rx_s.p, n_rx));
+    CKS(d2h_vec(c, ln, ln->h_rx_l, ln->rx_l.p, n_rx));
+    CKS(d2h_vec(c, ln, ln->h_rx_t, ln->rx_t.p, n_rx));
+    CKS(d2h_vec(c, ln, ln->h_labels, ln->labels.p, T));
+    CKS(d2h_vec(c, ln, ln->h_logits, ln->logits.p, T * g.n_labels));
+    CKS(d2h_vec(c, ln, ln->h_fin_s, ln->fin_s.p, h_cnt2[5]));
+    CKS(d2h_vec(c, ln, ln->h_fin_l, ln->fin_l.p, h_cnt2[5]));
+    CKS(d2h_vec(c, ln, ln->h_fin_t, ln->fin_t.p, h_cnt2[5]));
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     as_output_free(o);
     return fail(c, AS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
   }
-  if (c->prof) prof_collect(c);
-  as_status ds = check_dev_error(c);
+  if (ln->prof) prof_collect(ln);
+  as_status ds = check_dev_error(c, ln);
   if (ds != AS_OK) {
     as_output_free(o);
     return ds;
   }
   uint64_t n_entries = 0;
-  cudaMemcpy(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost);
+  if (cudaMemcpyAsync(&n_entries, c->map_ctr.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    as_output_free(o);
+    return fail(c, AS_ERR_CUDA, "map counter read failed");
+  }
   as_stats& s = o->stats;
   s.n_records = n;
   s.n_bytes = N;
@@ -954,16 +992,16 @@ as_status anonymize_impl(as_ctx* c, const as_records* rec, const as_schema* sch,
   s.n_final_spans = h_cnt2[5];
   s.n_out_bytes = out_size;
   s.n_map_entries = n_entries;
-  s.n_new_entries = n_entries >= c->n_entries_seen ? n_entries - c->n_entries_seen : 0;
-  c->n_entries_seen = n_entries;
+  const uint64_t seen = c->n_entries_seen.exchange(n_entries);
+  s.n_new_entries = n_entries >= seen ? n_entries - seen : 0;
   s.kernel_launches = g_launches.load() - launches0;
-  c->records_done += n;
+  if (rec_base < 0) c->records_done += n;
   *out = o;
   return AS_OK;
 }
 
 as_status map_collect(as_ctx* c, uint32_t call_id, std::vector<as_entity>& ents, std::vector<uint8_t>& orig) {
-  cudaStream_t st = c->stream;
+  cudaStream_t st = c->main.stream;
   const uint64_t slots = c->map_mask + 1;
   DBuf keep, pos, idx, tiles, total;
   auto cleanup = [&]() { release(keep); release(pos); release(idx); release(tiles); release(total); };
@@ -1045,6 +1083,118 @@ bool ctx_vocab(const as_ctx* ctx, VocabTable* vt, int* device) {
 }
 }  // namespace as
 
+// ------------------------------------------------------------------ serving
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct ServeRequest {
+  uint64_t id = 0;
+  std::vector<uint8_t> bytes;
+  int64_t t_submit = 0, t_done = 0;
+  bool discard = false, done = false;
+  as_status status = AS_OK;
+  std::vector<uint8_t> out;
+  uint64_t tokens = 0;
+};
+
+}  // namespace
+
+// Continuous batching: admitted requests wait in FIFO order; every worker
+// owns a lane (stream + buffers) and, whenever it is free, takes the oldest
+// requests up to the batch byte budget and runs the whole path on them. With
+// two or more lanes a batch is admitted while others are still on the GPU and
+// their kernels overlap. Record index of a request = its id, so results and
+// map sightings do not depend on which batch a request joined.
+struct Server {
+  as_ctx* c = nullptr;
+  std::vector<std::string> names;
+  std::vector<const char*> name_ptrs;
+  as_schema schema{};
+  uint64_t batch_bytes = 0;
+  uint32_t max_batch = 0;
+  uint64_t max_pending = 0;
+  std::vector<std::unique_ptr<Lane>> lanes;
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ServeRequest*> queue;
+  std::unordered_map<uint64_t, ServeRequest*> live;
+  uint64_t next_id = 0;
+  bool stop = false;
+  // statistics since start or the last reset
+  std::vector<double> lat_ms;
+  uint64_t completed = 0, rejected = 0, batches = 0, tokens = 0, failed = 0;
+  int64_t t_stats0 = 0;
+
+  void worker(Lane* ln);
+};
+
+void Server::worker(Lane* ln) {
+  cudaSetDevice(c->device);
+  std::vector<ServeRequest*> batch;
+  std::vector<uint8_t> arena;
+  std::vector<uint64_t> offs;
+  while (true) {
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+      if (queue.empty()) break;  // stop requested and nothing left
+      uint64_t bytes = 0;
+      while (!queue.empty() && batch.size() < max_batch &&
+             (batch.empty() || bytes + queue.front()->bytes.size() <= batch_bytes)) {
+        bytes += queue.front()->bytes.size();
+        batch.push_back(queue.front());
+        queue.pop_front();
+      }
+    }
+    arena.clear();
+    offs.assign(1, 0);
+    for (ServeRequest* r : batch) {
+      arena.insert(arena.end(), r->bytes.begin(), r->bytes.end());
+      offs.push_back(arena.size());
+    }
+    as_records rec{arena.empty() ? nullptr : arena.data(), offs.data(), (uint64_t)batch.size(), 0};
+    as_output* o = nullptr;
+    // ids of one batch are consecutive (FIFO admission), so the first is the base
+    const as_status st = anonymize_impl(c, ln, &rec, &schema, nullptr, 0, &o, false, (int64_t)batch[0]->id);
+    const int64_t t = now_ns();
+    std::vector<uint64_t> rec_tokens(batch.size(), 0);
+    if (st == AS_OK && !ln->h_rec_tok.empty() && ln->h_rec_tok.size() == batch.size() + 1)
+      for (size_t i = 0; i < batch.size(); ++i) rec_tokens[i] = ln->h_rec_tok[i + 1] - ln->h_rec_tok[i];
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ++batches;
+      if (st == AS_OK) tokens += o->stats.n_encoded_tokens;
+      for (size_t i = 0; i < batch.size(); ++i) {
+        ServeRequest* r = batch[i];
+        r->status = st;
+        r->t_done = t;
+        r->tokens = rec_tokens[i];
+        if (st == AS_OK) {
+          r->out.assign(o->h_bytes.begin() + o->h_off[i], o->h_bytes.begin() + o->h_off[i + 1]);
+          ++completed;
+          lat_ms.push_back((t - r->t_submit) * 1e-6);
+        } else {
+          ++failed;
+        }
+        r->done = true;
+        if (r->discard) {
+          live.erase(r->id);
+          delete r;
+        }
+      }
+    }
+    cv_done.notify_all();
+    if (o) as_output_free(o);
+  }
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -1053,7 +1203,7 @@ const char* as_k_last_error(void) { return as::t_k_error.c_str(); }
 
 const char* as_version(void) { return "anonshield-b300 0.1 (sm_103a)"; }
 
-const char* as_last_error(const as_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+const char* as_last_error(const as_ctx*) { return t_err.c_str(); }
 
 void as_free(void* p) { free(p); }
 
@@ -1064,48 +1214,48 @@ as_status as_create(const as_config* cfg, as_ctx** out) {
   c->cfg = *cfg;
   const as_config& g = c->cfg;
   auto bail = [&](as_status s) {
-    std::string m = c->err;
+    std::string m = t_err;
     as_destroy(c);
     set_k_error(m);
     return s;
   };
   if (g.vocab < 258 || g.n_vocab_words != g.vocab - 257 || !g.vocab_bytes || !g.vocab_offsets) {
-    c->err = "vocab must be > 257 with vocab - 257 strings";
+    t_err = "vocab must be > 257 with vocab - 257 strings";
     return bail(AS_ERR_ARG);
   }
   if (g.d_model == 0 || g.n_heads == 0 || g.d_model != g.n_heads * 64) {
-    c->err = "head dim must be 64 (d_model = 64 * n_heads)";
+    t_err = "head dim must be 64 (d_model = 64 * n_heads)";
     return bail(AS_ERR_UNSUPPORTED);
   }
   if (g.d_model % 128 || g.d_model > 1024 || g.d_ffn % 128 || g.d_ffn == 0 || g.n_layers == 0 || g.n_labels < 9 ||
       g.n_labels > 32 || g.max_pos == 0 || g.max_pos > 4096) {
-    c->err = "unsupported dimensions (d_model multiple of 128 up to 1024, d_ffn multiple of 128, 9..32 labels)";
+    t_err = "unsupported dimensions (d_model multiple of 128 up to 1024, d_ffn multiple of 128, 9..32 labels)";
     return bail(AS_ERR_UNSUPPORTED);
   }
   if (g.precision != AS_FP32 && g.precision != AS_BF16 && g.precision != AS_FP8) {
-    c->err = "precision must be AS_FP32, AS_BF16 or AS_FP8";
+    t_err = "precision must be AS_FP32, AS_BF16 or AS_FP8";
     return bail(AS_ERR_UNSUPPORTED);
   }
   if (g.attention != AS_ATTN_MMA_SYNC && g.attention != AS_ATTN_TCGEN05) {
-    c->err = "attention must be AS_ATTN_MMA_SYNC or AS_ATTN_TCGEN05";
+    t_err = "attention must be AS_ATTN_MMA_SYNC or AS_ATTN_TCGEN05";
     return bail(AS_ERR_ARG);
   }
   if (g.mode != AS_MODE_PACKED && g.mode != AS_MODE_PER_RECORD) {
-    c->err = "mode must be AS_MODE_PACKED or AS_MODE_PER_RECORD";
+    t_err = "mode must be AS_MODE_PACKED or AS_MODE_PER_RECORD";
     return bail(AS_ERR_ARG);
   }
   if (!g.weights || g.weights_len != expected_weights(g)) {
-    c->err = "weights_len " + std::to_string(g.weights_len) + " != expected " + std::to_string(expected_weights(g));
+    t_err = "weights_len " + std::to_string(g.weights_len) + " != expected " + std::to_string(expected_weights(g));
     return bail(AS_ERR_ARG);
   }
   c->device = g.device;
   if (cudaSetDevice(g.device) != cudaSuccess) {
     cudaGetLastError();
-    c->err = "cudaSetDevice failed";
+    t_err = "cudaSetDevice failed";
     return bail(AS_ERR_CUDA);
   }
-  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-    c->err = "stream creation failed";
+  if (cudaStreamCreateWithFlags(&c->main.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    t_err = "stream creation failed";
     return bail(AS_ERR_CUDA);
   }
   sha256_init_constants();
@@ -1115,16 +1265,16 @@ as_status as_create(const as_config* cfg, as_ctx** out) {
   uint64_t cap = g.map_capacity ? pow2_at_least(g.map_capacity) : (1ull << 22);
   uint64_t arena = g.map_arena_bytes ? g.map_arena_bytes : (256ull << 20);
   if (grow(c->map_slots, cap * sizeof(MapSlot)) || grow(c->map_arena, arena) || grow(c->map_ctr, 16) ||
-      grow(c->dev_err, sizeof(DevError))) {
-    c->err = "map allocation failed";
+      grow(c->main.dev_err, sizeof(DevError))) {
+    t_err = "map allocation failed";
     return bail(AS_ERR_OOM);
   }
   c->map_arena.cap = arena;
   c->map_mask = cap - 1;
-  cudaMemsetAsync(c->dev_err.p, 0, sizeof(DevError), c->stream);
-  launch_map_init(map_view(c), c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    c->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
+  cudaMemsetAsync(c->main.dev_err.p, 0, sizeof(DevError), c->main.stream);
+  launch_map_init(map_view(c), c->main.stream);
+  if (cudaStreamSynchronize(c->main.stream) != cudaSuccess) {
+    t_err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
     return bail(AS_ERR_CUDA);
   }
   *out = c;
@@ -1134,19 +1284,13 @@ as_status as_create(const as_config* cfg, as_ctx** out) {
 void as_destroy(as_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  DBuf* all[] = {&c->w32, &c->w16, &c->vocab_slots, &c->map_slots, &c->map_arena, &c->map_ctr, &c->key_dev,
-                 &c->key_state, &c->dev_err, &c->in_bytes, &c->in_off, &c->rs_bits, &c->tok_at, &c->pos_b,
-                 &c->scan_tiles, &c->counters, &c->delta_total, &c->tok_ids, &c->tok_off, &c->tok_len, &c->rec_tok,
-                 &c->rx_len_b, &c->rx_type_b, &c->rx_s, &c->rx_l, &c->rx_t, &c->labels, &c->logits, &c->tok_flags,
-                 &c->rx_pos, &c->bio_start, &c->bio_end, &c->pos_t, &c->ner_s, &c->ner_l, &c->ner_t, &c->keep, &c->pos_k,
-                 &c->nk_s, &c->nk_l, &c->nk_t, &c->rk_s, &c->rk_l, &c->rk_t, &c->fin_s, &c->fin_l, &c->fin_t,
-                 &c->digests, &c->delta, &c->shift, &c->names, &c->name_off, &c->name_len, &c->seqs, &c->row_tok,
-                 &c->row_pos, &c->row_own, &c->seq_start, &c->seq_len, &c->X32, &c->X16, &c->QKV, &c->ATT, &c->Y32,
-                 &c->H, &c->VT, &c->X8, &c->ATT8, &c->H8, &c->w8, &c->amax_dev};
+  as_serve_stop(c);
+  if (c->main.stream) cudaStreamSynchronize(c->main.stream);
+  DBuf* all[] = {&c->w32, &c->w16, &c->w8, &c->amax_dev, &c->vocab_slots, &c->map_slots, &c->map_arena, &c->map_ctr,
+                 &c->key_dev, &c->key_state};
   for (DBuf* b : all) release(*b);
-  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  if (c->stream) cudaStreamDestroy(c->stream);
+  c->main.release_all();
+  if (c->main.stream) cudaStreamDestroy(c->main.stream);
   delete c;
 }
 
@@ -1154,7 +1298,8 @@ as_status as_anonymize(as_ctx* ctx, const as_records* records, const as_schema* 
                        size_t key_len, as_output** out) {
   if (!ctx) return AS_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, AS_ERR_CUDA, "cudaSetDevice failed");
-  as_status s = anonymize_impl(ctx, records, schema, key, key_len, out);
+  if (ctx->server) return fail(ctx, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
+  as_status s = anonymize_impl(ctx, &ctx->main, records, schema, key, key_len, out);
   if (s == AS_ERR_CUDA) cudaGetLastError();
   return s;
 }
@@ -1199,7 +1344,7 @@ void as_output_free(as_output* o) {
   if (!o) return;
   if (o->d_bytes || o->d_off) {
     cudaSetDevice(o->ctx->device);
-    cudaStreamSynchronize(o->ctx->stream);
+    cudaStreamSynchronize(o->ctx->main.stream);
     if (o->d_bytes) cudaFree(o->d_bytes);
     if (o->d_off) cudaFree(o->d_off);
   }
@@ -1265,7 +1410,7 @@ as_status as_map_import(as_ctx* c, const uint8_t* key, size_t key_len, const as_
     cleanup();
     return fail(c, AS_ERR_OOM, "import staging");
   }
-  cudaStream_t st = c->stream;
+  cudaStream_t st = c->main.stream;
   if (!orig.empty()) cudaMemcpyAsync(b_orig.p, orig.data(), orig.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b_off.p, off.data(), n * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b_len.p, len.data(), n * 4, cudaMemcpyHostToDevice, st);
@@ -1274,31 +1419,32 @@ as_status as_map_import(as_ctx* c, const uint8_t* key, size_t key_len, const as_
   cudaMemcpyAsync(b_first.p, first.data(), n * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b_last.p, last.data(), n * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b_count.p, count.data(), n * 8, cudaMemcpyHostToDevice, st);
-  ++c->call_id;
+  const uint32_t import_id = ++c->call_id;
   launch_map_import(map_view(c), b_orig.as<uint8_t>(), b_off.as<uint64_t>(), b_len.as<uint32_t>(),
                     b_type.as<uint32_t>(), b_dig.as<uint32_t>(), b_first.as<uint64_t>(), b_last.as<uint64_t>(),
-                    b_count.as<uint64_t>(), n, c->call_id, c->dev_err.as<DevError>(), st);
+                    b_count.as<uint64_t>(), n, import_id, c->main.dev_err.as<DevError>(), st);
   cudaError_t e = cudaStreamSynchronize(st);
   cleanup();
   if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
-  return check_dev_error(c);
+  return check_dev_error(c, &c->main);
 }
 
 as_status as_map_clear(as_ctx* c) {
   if (!c) return AS_ERR_ARG;
   cudaSetDevice(c->device);
-  launch_map_init(map_view(c), c->stream);
+  launch_map_init(map_view(c), c->main.stream);
   c->n_entries_seen = 0;
   c->key_set = false;
   c->key.clear();
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, AS_ERR_CUDA, "map clear");
+  if (cudaStreamSynchronize(c->main.stream) != cudaSuccess) return fail(c, AS_ERR_CUDA, "map clear");
   return AS_OK;
 }
 
 as_status as_calibrate(as_ctx* c, const as_records* records, const as_schema* schema) {
   if (!c) return AS_ERR_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
-  as_status s = anonymize_impl(c, records, schema, nullptr, 0, nullptr, true);
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving");
+  as_status s = anonymize_impl(c, &c->main, records, schema, nullptr, 0, nullptr, true);
   if (s == AS_ERR_CUDA) cudaGetLastError();
   return s;
 }
@@ -1323,48 +1469,206 @@ as_status as_set_scales(as_ctx* c, const float* scales, uint64_t n) {
   return AS_OK;
 }
 
+as_status as_serve_start(as_ctx* c, const as_schema* schema, const uint8_t* key, size_t key_len,
+                         const as_serve_config* cfg) {
+  if (!c || !cfg) return AS_ERR_ARG;
+  if (c->server) return fail(c, AS_ERR_STATE, "already serving");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  CKI(validate_schema(c, schema));
+  if (c->cfg.precision == AS_FP8 && c->act_scale.empty())
+    return fail(c, AS_ERR_STATE, "FP8 context without activation scales");
+  CKI(set_key(c, key, key_len));
+  Server* sv = new Server();
+  sv->c = c;
+  for (uint32_t t = 0; t < schema->n_types; ++t) sv->names.emplace_back(schema->type_names[t]);
+  for (auto& n : sv->names) sv->name_ptrs.push_back(n.c_str());
+  sv->schema = *schema;
+  sv->schema.type_names = sv->name_ptrs.data();
+  const uint64_t chunk = c->cfg.max_chunk_tokens ? c->cfg.max_chunk_tokens : (1ull << 19);
+  sv->batch_bytes = cfg->max_batch_bytes ? cfg->max_batch_bytes : chunk * 3 / 4;
+  sv->max_batch = cfg->max_batch_records ? cfg->max_batch_records : 65536;
+  sv->max_pending = cfg->max_pending ? cfg->max_pending : (1ull << 20);
+  sv->next_id = c->records_done;
+  sv->t_stats0 = now_ns();
+  const uint32_t n_lanes = cfg->lanes ? std::min<uint32_t>(cfg->lanes, 8) : 2;
+  for (uint32_t i = 0; i < n_lanes; ++i) {
+    auto ln = std::make_unique<Lane>();
+    if (cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        grow(ln->dev_err, sizeof(DevError)) != AS_OK ||
+        cudaMemsetAsync(ln->dev_err.p, 0, sizeof(DevError), ln->stream) != cudaSuccess) {
+      for (auto& l : sv->lanes) {
+        l->release_all();
+        cudaStreamDestroy(l->stream);
+      }
+      if (ln->stream) cudaStreamDestroy(ln->stream);
+      delete sv;
+      return fail(c, AS_ERR_CUDA, "serving lane set-up failed");
+    }
+    sv->lanes.push_back(std::move(ln));
+  }
+  c->server = sv;
+  for (auto& ln : sv->lanes) sv->workers.emplace_back(&Server::worker, sv, ln.get());
+  return AS_OK;
+}
+
+as_status as_submit(as_ctx* c, const uint8_t* rec, uint64_t len, uint32_t flags, uint64_t* request_id) {
+  if (!c || (!rec && len) || !request_id) return AS_ERR_ARG;
+  Server* sv = c->server;
+  if (!sv) return fail(c, AS_ERR_STATE, "not serving: call as_serve_start");
+  auto* r = new ServeRequest();
+  r->bytes.assign(rec, rec + len);
+  r->discard = (flags & AS_SUBMIT_DISCARD) != 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) {
+      delete r;
+      return fail(c, AS_ERR_STATE, "serving is stopping");
+    }
+    if (sv->queue.size() >= sv->max_pending) {
+      ++sv->rejected;
+      delete r;
+      return fail(c, AS_ERR_AGAIN, "admission queue full");
+    }
+    r->id = sv->next_id++;
+    r->t_submit = now_ns();
+    sv->queue.push_back(r);
+    sv->live[r->id] = r;
+    *request_id = r->id;
+  }
+  sv->cv_work.notify_one();
+  return AS_OK;
+}
+
+as_status as_poll(as_ctx* c, uint64_t request_id, as_output** out, int64_t timeout_us) {
+  if (!c || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  Server* sv = c->server;
+  if (!sv) return fail(c, AS_ERR_STATE, "not serving");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->live.find(request_id);
+  if (it == sv->live.end()) return fail(c, AS_ERR_ARG, "unknown request id (or submitted with AS_SUBMIT_DISCARD)");
+  ServeRequest* r = it->second;
+  if (r->discard) return fail(c, AS_ERR_ARG, "request was submitted with AS_SUBMIT_DISCARD");
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+  if (!sv->cv_done.wait_until(lk, deadline, [&] { return r->done; }))
+    return fail(c, AS_ERR_TIMEOUT, "request not finished within the timeout");
+  sv->live.erase(it);
+  lk.unlock();
+  const as_status st = r->status;
+  if (st == AS_OK) {
+    as_output* o = new as_output();
+    o->ctx = c;
+    o->on_device = 0;
+    o->n = 1;
+    o->h_bytes = std::move(r->out);
+    o->h_off = {0, (uint64_t)o->h_bytes.size()};
+    o->stats.n_records = 1;
+    o->stats.n_bytes = r->bytes.size();
+    o->stats.n_tokens = r->tokens;
+    o->stats.n_out_bytes = o->h_bytes.size();
+    o->map_loaded = true;  // per-request map views are not kept; use as_map_export
+    *out = o;
+  }
+  delete r;
+  return st == AS_OK ? AS_OK : fail(c, st, "the batch of this request failed");
+}
+
+as_status as_serve_stats(as_ctx* c, as_serve_stats_t* s, uint32_t reset) {
+  if (!c || !s) return AS_ERR_ARG;
+  Server* sv = c->server;
+  if (!sv) return fail(c, AS_ERR_STATE, "not serving");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  memset(s, 0, sizeof(*s));
+  s->completed = sv->completed;
+  s->rejected = sv->rejected;
+  s->failed = sv->failed;
+  s->batches = sv->batches;
+  s->tokens = sv->tokens;
+  s->pending = sv->queue.size();
+  s->seconds = (now_ns() - sv->t_stats0) * 1e-9;
+  if (!sv->lat_ms.empty()) {
+    std::vector<double> v = sv->lat_ms;
+    auto pct = [&](double q) {
+      size_t k = std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5));
+      std::nth_element(v.begin(), v.begin() + k, v.end());
+      return v[k];
+    };
+    s->p50_ms = pct(0.50);
+    s->p99_ms = pct(0.99);
+    s->max_ms = *std::max_element(v.begin(), v.end());
+  }
+  if (reset) {
+    sv->lat_ms.clear();
+    sv->completed = sv->rejected = sv->batches = sv->tokens = sv->failed = 0;
+    sv->t_stats0 = now_ns();
+  }
+  return AS_OK;
+}
+
+as_status as_serve_stop(as_ctx* c) {
+  if (!c) return AS_ERR_ARG;
+  Server* sv = c->server;
+  if (!sv) return AS_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  for (auto& t : sv->workers) t.join();  // workers drain the queue first
+  for (auto& kv : sv->live) delete kv.second;
+  for (auto& ln : sv->lanes) {
+    cudaStreamSynchronize(ln->stream);
+    ln->release_all();
+    cudaStreamDestroy(ln->stream);
+  }
+  c->records_done = std::max(c->records_done, sv->next_id);
+  delete sv;
+  c->server = nullptr;
+  return AS_OK;
+}
+
 as_status as_get_stream(as_ctx* c, void** stream) {
   if (!c || !stream) return AS_ERR_ARG;
-  *stream = reinterpret_cast<void*>(c->stream);
+  *stream = reinterpret_cast<void*>(c->main.stream);
   return AS_OK;
 }
 
 as_status as_profile(as_ctx* c, uint32_t enable) {
   if (!c) return AS_ERR_ARG;
   cudaSetDevice(c->device);
-  cudaStreamSynchronize(c->stream);
-  c->ev_pending.clear();
-  c->ev_used = 0;
-  c->prof_acc = as_profile_stats{};
-  c->prof = enable != 0;
+  cudaStreamSynchronize(c->main.stream);
+  c->main.ev_pending.clear();
+  c->main.ev_used = 0;
+  c->main.prof_acc = as_profile_stats{};
+  c->main.prof = enable != 0;
   return AS_OK;
 }
 
 as_status as_profile_read(as_ctx* c, as_profile_stats* s) {
   if (!c || !s) return AS_ERR_ARG;
-  *s = c->prof_acc;
+  *s = c->main.prof_acc;
   return AS_OK;
 }
 
 as_status as_debug_trace(as_ctx* c, as_trace* t) {
   if (!c || !t) return AS_ERR_ARG;
   if (!c->cfg.keep_trace) return fail(c, AS_ERR_STATE, "create the context with keep_trace = 1");
-  t->n_records = c->last_n;
-  t->n_tokens = c->last_T;
-  t->n_regex = c->last_nrx;
-  t->n_final = c->last_nfin;
-  t->rec_tok = c->h_rec_tok.data();
-  t->tok_ids = c->h_tok_ids.data();
-  t->tok_off = c->h_tok_off.data();
-  t->tok_len = c->h_tok_len.data();
-  t->regex_start = c->h_rx_s.data();
-  t->regex_len = c->h_rx_l.data();
-  t->regex_type = c->h_rx_t.data();
-  t->logits = c->last_logits ? c->h_logits.data() : nullptr;
-  t->labels = c->h_labels.data();
-  t->final_start = c->h_fin_s.data();
-  t->final_len = c->h_fin_l.data();
-  t->final_type = c->h_fin_t.data();
+  t->n_records = c->main.last_n;
+  t->n_tokens = c->main.last_T;
+  t->n_regex = c->main.last_nrx;
+  t->n_final = c->main.last_nfin;
+  t->rec_tok = c->main.h_rec_tok.data();
+  t->tok_ids = c->main.h_tok_ids.data();
+  t->tok_off = c->main.h_tok_off.data();
+  t->tok_len = c->main.h_tok_len.data();
+  t->regex_start = c->main.h_rx_s.data();
+  t->regex_len = c->main.h_rx_l.data();
+  t->regex_type = c->main.h_rx_t.data();
+  t->logits = c->main.last_logits ? c->main.h_logits.data() : nullptr;
+  t->labels = c->main.h_labels.data();
+  t->final_start = c->main.h_fin_s.data();
+  t->final_len = c->main.h_fin_l.data();
+  t->final_type = c->main.h_fin_t.data();
   return AS_OK;
 }
 
