@@ -284,6 +284,16 @@ def run_ours(args):
         out.free()
     e2e_value = tokens_per_step / (np.mean(e2e_ms) / 1e3)
 
+    # ---- the one exchange of a replica run: union of the entity maps on rank 0
+    merge = None
+    if world > 1:
+        from paper_2606_15650_b300 import replicas
+        t0 = time.perf_counter()
+        merged = replicas.gather_merge(ctx.map_export(), rank * recs.n)
+        if rank == 0:
+            merge = {"entries": len(merged), "ms": 1e3 * (time.perf_counter() - t0),
+                     "how": "export per rank, gather_object to rank 0, as_map_merge (host); outside the timed region"}
+
     result = {}
     if rank == 0 and not args.no_baselines:
         result = baselines(args, w, words, recs, weights, blob, key, schema, local)
@@ -322,6 +332,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": int(len(recs.data) + recs.offsets.nbytes),
                 "d2h_bytes_per_step": int(out_bytes + recs.offsets.nbytes)},
         "gpu_launches": int(launches),
+        "map_merge": merge,
         "clocks": clk,
     }
     line.update(result)

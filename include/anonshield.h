@@ -182,6 +182,19 @@ as_status as_map_export(as_ctx* ctx, as_entity** entries, uint64_t* n);
  * already present keeps min first_seen, max last_seen, summed count. The
  * entries' full_hash must be the HMAC under this ctx's key. */
 as_status as_map_import(as_ctx* ctx, const uint8_t* key, size_t key_len, const as_entity* entries, uint64_t n);
+/* Union of the maps of replicas that processed disjoint record ranges of one
+ * job (the one exchange of a multi-GPU run, done on the host; needs no GPU
+ * and no ctx). shards[s] holds n[s] entries, e.g. that replica's export;
+ * record_offset[s] (NULL = all 0) is the global index of that replica's
+ * first record and is added to its first_seen / last_seen. Entries with the
+ * same (type, original) keep min first_seen, max last_seen and the summed
+ * count; their full_hash must agree (AS_ERR_STATE otherwise: the replicas
+ * used different keys). The pseudonym being a function of key and bytes
+ * alone (AnonShield §2 stage (4)), replicas never exchange anything else.
+ * *out is sorted as in as_map_export, one allocation (free with as_free);
+ * messages via as_last_error(NULL). */
+as_status as_map_merge(const as_entity* const* shards, const uint64_t* n, const uint64_t* record_offset,
+                       uint32_t n_shards, as_entity** out, uint64_t* n_out);
 /* Empty the map and forget the key. */
 as_status as_map_clear(as_ctx* ctx);
 

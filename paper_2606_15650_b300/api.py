@@ -91,7 +91,7 @@ class _Profile(C.Structure):
 
 
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
-            "as_output_free", "as_map_export", "as_map_import", "as_map_clear", "as_debug_trace", "as_last_error",
+            "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
             "as_get_scales", "as_set_scales", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
@@ -121,6 +121,8 @@ def load() -> C.CDLL:
     lib.as_output_free.restype = None
     lib.as_map_export.argtypes = [P, C.POINTER(C.POINTER(_Entity)), C.POINTER(C.c_uint64)]
     lib.as_map_import.argtypes = [P, C.c_char_p, C.c_size_t, C.POINTER(_Entity), C.c_uint64]
+    lib.as_map_merge.argtypes = [C.POINTER(C.POINTER(_Entity)), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                 C.c_uint32, C.POINTER(C.POINTER(_Entity)), C.POINTER(C.c_uint64)]
     lib.as_map_clear.argtypes = [P]
     lib.as_debug_trace.argtypes = [P, C.POINTER(_Trace)]
     lib.as_last_error.argtypes = [P]
@@ -254,6 +256,41 @@ def _entities(ptr, n) -> list[Entity]:
         out.append(Entity(int(e.type), C.string_at(e.original, e.original_len) if e.original_len else b"",
                           e.full_hash.decode(), e.slug.decode(), int(e.first_seen), int(e.last_seen), int(e.count)))
     return out
+
+
+def _entity_array(entries: list[Entity]):
+    """ctypes array of as_entity for `entries` (plus the buffers it points into)."""
+    arr = (_Entity * max(len(entries), 1))()
+    bufs = []
+    for i, e in enumerate(entries):
+        b = (C.c_uint8 * max(len(e.original), 1)).from_buffer_copy(e.original + b"\0")
+        bufs.append(b)
+        arr[i].type = e.type
+        arr[i].original_len = len(e.original)
+        arr[i].original = C.cast(b, C.POINTER(C.c_uint8))
+        arr[i].full_hash = e.full_hash.encode()
+        arr[i].slug = e.slug.encode()
+        arr[i].first_seen = e.first_seen
+        arr[i].last_seen = e.last_seen
+        arr[i].count = e.count
+    return arr, bufs
+
+
+def map_merge(shards: list[list[Entity]], record_offsets: list[int] | None = None) -> list[Entity]:
+    """Host-side union of replica maps (as_map_merge); runs without a GPU."""
+    lib = load()
+    arrs = [_entity_array(s) for s in shards]
+    ptrs = (C.POINTER(_Entity) * max(len(shards), 1))(*[C.cast(a, C.POINTER(_Entity)) for a, _ in arrs])
+    ns = (C.c_uint64 * max(len(shards), 1))(*[len(s) for s in shards])
+    offs = (C.c_uint64 * max(len(shards), 1))(*(record_offsets or [0] * len(shards)))
+    p, n = C.POINTER(_Entity)(), C.c_uint64()
+    st = lib.as_map_merge(ptrs, ns, offs, len(shards), C.byref(p), C.byref(n))
+    if st != AS_OK:
+        raise AnonShieldError(st, (lib.as_last_error(None) or b"").decode())
+    try:
+        return _entities(p, n.value)
+    finally:
+        lib.as_free(C.cast(p, C.c_void_p))
 
 
 class Output:
@@ -415,19 +452,7 @@ class Context:
             load().as_free(C.cast(p, C.c_void_p))
 
     def map_import(self, key: bytes, entries: list[Entity]):
-        arr = (_Entity * max(len(entries), 1))()
-        bufs = []
-        for i, e in enumerate(entries):
-            b = (C.c_uint8 * max(len(e.original), 1)).from_buffer_copy(e.original + b"\0")
-            bufs.append(b)
-            arr[i].type = e.type
-            arr[i].original_len = len(e.original)
-            arr[i].original = C.cast(b, C.POINTER(C.c_uint8))
-            arr[i].full_hash = e.full_hash.encode()
-            arr[i].slug = e.slug.encode()
-            arr[i].first_seen = e.first_seen
-            arr[i].last_seen = e.last_seen
-            arr[i].count = e.count
+        arr, bufs = _entity_array(entries)
         self._check(load().as_map_import(self._h, key, len(key), arr, len(entries)))
 
     # ---- serving loop (continuous batching)

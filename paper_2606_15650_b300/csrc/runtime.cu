@@ -12,6 +12,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <thread>
 #include <unordered_map>
@@ -1370,6 +1371,61 @@ as_status as_map_export(as_ctx* c, as_entity** entries, uint64_t* n) {
   }
   *entries = e;
   *n = ents.size();
+  return AS_OK;
+}
+
+as_status as_map_merge(const as_entity* const* shards, const uint64_t* n, const uint64_t* record_offset,
+                       uint32_t n_shards, as_entity** out, uint64_t* n_out) {
+  if (!out || !n_out || (n_shards && (!shards || !n))) return AS_ERR_ARG;
+  struct Acc {
+    const as_entity* first;  // type, bytes, hash and slug come from here
+    uint64_t first_seen, last_seen, count;
+  };
+  // key: type byte then the original bytes; std::string orders bytes as
+  // unsigned char with a prefix first, the order of as_map_export
+  std::map<std::string, Acc> acc;
+  uint64_t total_len = 0;
+  for (uint32_t s = 0; s < n_shards; ++s) {
+    if (n[s] && !shards[s]) return fail(nullptr, AS_ERR_ARG, "shard " + std::to_string(s) + " is NULL");
+    const uint64_t off = record_offset ? record_offset[s] : 0;
+    for (uint64_t i = 0; i < n[s]; ++i) {
+      const as_entity& e = shards[s][i];
+      if (e.type > 255 || (e.original_len && !e.original)) return fail(nullptr, AS_ERR_ARG, "malformed entry");
+      std::string k(1, (char)e.type);
+      k.append(reinterpret_cast<const char*>(e.original), e.original_len);
+      auto it = acc.find(k);
+      if (it == acc.end()) {
+        acc.emplace(std::move(k), Acc{&e, e.first_seen + off, e.last_seen + off, e.count});
+        total_len += e.original_len;
+        continue;
+      }
+      Acc& a = it->second;
+      if (memcmp(a.first->full_hash, e.full_hash, 64) != 0)
+        return fail(nullptr, AS_ERR_STATE, "shards disagree on an entity's HMAC: maps made under different keys");
+      a.first_seen = std::min(a.first_seen, e.first_seen + off);
+      a.last_seen = std::max(a.last_seen, e.last_seen + off);
+      a.count += e.count;
+    }
+  }
+  const size_t bytes = acc.size() * sizeof(as_entity) + total_len + 1;
+  uint8_t* blob = static_cast<uint8_t*>(malloc(bytes));
+  if (!blob) return fail(nullptr, AS_ERR_OOM, "host allocation");
+  as_entity* e = reinterpret_cast<as_entity*>(blob);
+  uint8_t* o = blob + acc.size() * sizeof(as_entity);
+  size_t i = 0;
+  for (auto& kv : acc) {
+    const Acc& a = kv.second;
+    e[i] = *a.first;
+    e[i].original = o;
+    if (a.first->original_len) memcpy(o, a.first->original, a.first->original_len);
+    o += a.first->original_len;
+    e[i].first_seen = a.first_seen;
+    e[i].last_seen = a.last_seen;
+    e[i].count = a.count;
+    ++i;
+  }
+  *out = e;
+  *n_out = acc.size();
   return AS_OK;
 }
 

@@ -135,3 +135,20 @@ def test_stop_drains_and_batch_api_resumes(blob, vocab_words, batch_ref):
     assert out == got[50:60]
     # record indices continue after the served requests
     assert max(e.last_seen for e in ctx.map_export()) >= 50
+
+
+def test_replica_maps_merge_to_single_run(blob, vocab_words, batch_ref):
+    """Two contexts (replicas) on disjoint halves, merged on the host == one context over all."""
+    from paper_2606_15650_b300 import replicas
+    recs, got, emap = batch_ref
+    ranges = replicas.shard_ranges(np.array([len(r) for r in recs]), 2)
+    shards, outs = [], []
+    for a, b in ranges:
+        ctx = _ctx(blob, vocab_words)
+        rs = synth.records_from_list(recs[a:b])
+        outs += ctx.anonymize(rs.data, rs.offsets, SCHEMA, KEY).records()
+        shards.append(ctx.map_export())
+        ctx.close()
+    assert outs == got
+    merged = api.map_merge(shards, [a for a, _ in ranges])
+    assert sorted(U.map_tuples(merged)) == emap
