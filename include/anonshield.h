@@ -217,6 +217,24 @@ typedef struct {
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
 
+/* Streaming (AnonShield §2 stage (1) reads large inputs as a stream): the
+ * same result as one as_anonymize call over `records` (host memory only),
+ * computed in consecutive batches of at most batch_bytes (a longer record
+ * goes alone). `lanes` worker threads each own a CUDA stream, device buffers
+ * and a pinned staging buffer: a worker copies its batch into pinned memory,
+ * the H2D copy, kernels and D2H of one batch overlap those of the others.
+ * Record indices are positions in `records` (plus earlier calls), so the
+ * output bytes and the map equal those of a single call. The output is on
+ * the host; as_output_map gives the entries touched by this call. Errors as
+ * as_anonymize (the message names the failing batch); on error, batches
+ * that completed have updated the map. */
+typedef struct {
+  uint64_t batch_bytes;  /* 0 = 16 MiB */
+  uint32_t lanes;        /* concurrent batches, 0 = 2 (max 8) */
+} as_stream_config;
+as_status as_anonymize_stream(as_ctx* ctx, const as_records* records, const as_schema* schema, const uint8_t* key,
+                              size_t key_len, const as_stream_config* cfg, as_output** out);
+
 /* Serving loop (continuous batching). After as_serve_start the ctx accepts
  * single records with as_submit from any thread; worker threads (one per
  * lane, each with its own CUDA stream and buffers) take the oldest admitted

@@ -85,6 +85,10 @@ class _ServeStats(C.Structure):
                [(n, C.c_double) for n in ("seconds", "p50_ms", "p99_ms", "max_ms")]
 
 
+class _StreamConfig(C.Structure):
+    _fields_ = [("batch_bytes", C.c_uint64), ("lanes", C.c_uint32)]
+
+
 class _Profile(C.Structure):
     _fields_ = [("gemm_launches", C.c_uint64), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
                 ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double)]
@@ -93,7 +97,7 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
@@ -134,6 +138,8 @@ def load() -> C.CDLL:
     lib.as_calibrate.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema)]
     lib.as_get_scales.argtypes = [P, P, C.c_uint64]
     lib.as_set_scales.argtypes = [P, P, C.c_uint64]
+    lib.as_anonymize_stream.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t,
+                                        C.POINTER(_StreamConfig), C.POINTER(P)]
     lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
     lib.as_submit.argtypes = [P, P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]
     lib.as_poll.argtypes = [P, C.c_uint64, C.POINTER(P), C.c_int64]
@@ -421,6 +427,22 @@ class Context:
         out = C.c_void_p()
         st = load().as_anonymize(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(out))
         del keep, names
+        self._check(st)
+        return Output(self, out.value)
+
+    def anonymize_stream(self, data, offsets, schema: Schema, key: bytes, batch_bytes: int = 0,
+                         lanes: int = 0) -> Output:
+        """Host records in overlapping batches (as_anonymize_stream); output on the host."""
+        d = np.ascontiguousarray(data, dtype=np.uint8)
+        o = np.ascontiguousarray(offsets, dtype=np.uint64)
+        rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
+                       on_device=0)
+        sc, names = self._schema(schema)
+        cfg = _StreamConfig(batch_bytes=batch_bytes, lanes=lanes)
+        out = C.c_void_p()
+        st = load().as_anonymize_stream(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(cfg),
+                                        C.byref(out))
+        del names
         self._check(st)
         return Output(self, out.value)
 

@@ -136,15 +136,15 @@ void launch_map_import(MapView m, const uint8_t* orig, const uint64_t* orig_off,
   count_launch();
 }
 
-__global__ void map_select_kernel(MapView m, uint32_t call_id, uint8_t* keep) {
+__global__ void map_select_kernel(MapView m, uint32_t call_lo, uint32_t call_hi, uint8_t* keep) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= m.mask; i += (uint64_t)gridDim.x * blockDim.x) {
     const MapSlot& s = m.slots[i];
-    keep[i] = s.key != 0 && (call_id == 0 || s.last_call == call_id);
+    keep[i] = s.key != 0 && (call_lo == 0 || (s.last_call >= call_lo && s.last_call <= call_hi));
   }
 }
 
-void launch_map_select(MapView m, uint32_t call_id, uint8_t* keep, cudaStream_t st) {
-  map_select_kernel<<<grid_1d(m.mask + 1, 256, 148 * 64), 256, 0, st>>>(m, call_id, keep);
+void launch_map_select(MapView m, uint32_t call_lo, uint32_t call_hi, uint8_t* keep, cudaStream_t st) {
+  map_select_kernel<<<grid_1d(m.mask + 1, 256, 148 * 64), 256, 0, st>>>(m, call_lo, call_hi, keep);
   count_launch();
 }
 

@@ -156,6 +156,11 @@ struct Lane {
   size_t ev_used = 0;
   std::vector<std::pair<int, double>> ev_pending;  // (kind, flops) per event pair
   as_profile_stats prof_acc{};
+  // pinned host staging (streaming): one batch's bytes and rebased offsets
+  uint8_t* h_in = nullptr;
+  size_t h_in_cap = 0;
+  uint64_t* h_in_off = nullptr;
+  size_t h_in_off_cap = 0;
 
   void release_all();
 };
@@ -187,11 +192,13 @@ struct as_ctx {
   uint32_t slug_len = 10;
   std::atomic<uint64_t> n_entries_seen{0};  // map size after the previous call
   Server* server = nullptr;                 // serving loop (as_serve_start)
+  std::vector<std::unique_ptr<Lane>> stream_lanes;  // as_anonymize_stream workers, kept between calls
 };
 
 struct as_output {
   as_ctx* ctx = nullptr;
   uint32_t call_id = 0;
+  uint32_t call_lo = 0;  // streaming outputs span the calls call_lo..call_id
   uint32_t on_device = 0;
   std::vector<uint8_t> h_bytes;
   std::vector<uint64_t> h_off;
@@ -214,6 +221,11 @@ void Lane::release_all() {
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
+  if (h_in) cudaFreeHost(h_in);
+  if (h_in_off) cudaFreeHost(h_in_off);
+  h_in = nullptr;
+  h_in_off = nullptr;
+  h_in_cap = h_in_off_cap = 0;
 }
 
 namespace {
@@ -1001,7 +1013,8 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   return AS_OK;
 }
 
-as_status map_collect(as_ctx* c, uint32_t call_id, std::vector<as_entity>& ents, std::vector<uint8_t>& orig) {
+as_status map_collect(as_ctx* c, uint32_t call_lo, uint32_t call_hi, std::vector<as_entity>& ents,
+                      std::vector<uint8_t>& orig) {
   cudaStream_t st = c->main.stream;
   const uint64_t slots = c->map_mask + 1;
   DBuf keep, pos, idx, tiles, total;
@@ -1012,7 +1025,7 @@ as_status map_collect(as_ctx* c, uint32_t call_id, std::vector<as_entity>& ents,
     return fail(c, AS_ERR_OOM, "map export scratch");
   }
   MapView m = map_view(c);
-  launch_map_select(m, call_id, keep.as<uint8_t>(), st);
+  launch_map_select(m, call_lo, call_hi, keep.as<uint8_t>(), st);
   exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, slots, pos.as<uint32_t>(), total.as<uint32_t>(),
                            tiles.as<uint32_t>(), st);
   uint32_t cnt = 0;
@@ -1292,6 +1305,11 @@ void as_destroy(as_ctx* c) {
   for (DBuf* b : all) release(*b);
   c->main.release_all();
   if (c->main.stream) cudaStreamDestroy(c->main.stream);
+  for (auto& ln : c->stream_lanes) {
+    cudaStreamSynchronize(ln->stream);
+    ln->release_all();
+    cudaStreamDestroy(ln->stream);
+  }
   delete c;
 }
 
@@ -1303,6 +1321,149 @@ as_status as_anonymize(as_ctx* ctx, const as_records* records, const as_schema* 
   as_status s = anonymize_impl(ctx, &ctx->main, records, schema, key, key_len, out);
   if (s == AS_ERR_CUDA) cudaGetLastError();
   return s;
+}
+
+namespace {
+
+as_status grow_pinned(void** p, size_t* cap, size_t need) {
+  if (*cap >= need) return AS_OK;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  need = std::max<size_t>(need, 4096);
+  if (cudaHostAlloc(p, need, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return AS_ERR_OOM;
+  }
+  *cap = need;
+  return AS_OK;
+}
+
+}  // namespace
+
+as_status as_anonymize_stream(as_ctx* c, const as_records* rec, const as_schema* sch, const uint8_t* key,
+                              size_t key_len, const as_stream_config* scfg, as_output** out) {
+  if (!c || !rec || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
+  if (rec->on_device) return fail(c, AS_ERR_ARG, "streaming takes host records (on_device = 0)");
+  const uint64_t n = rec->n_records;
+  if (!rec->offsets) return fail(c, AS_ERR_ARG, "offsets is NULL");
+  if (rec->offsets[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
+  for (uint64_t r = 0; r < n; ++r)
+    if (rec->offsets[r + 1] < rec->offsets[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
+  if (rec->offsets[n] && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
+  CKI(validate_schema(c, sch));
+  if (c->cfg.precision == AS_FP8 && c->act_scale.empty())
+    return fail(c, AS_ERR_STATE, "FP8 context without activation scales");
+  CKI(set_key(c, key, key_len));
+  const uint64_t budget = scfg && scfg->batch_bytes ? scfg->batch_bytes : (16ull << 20);
+  if (budget >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "batch_bytes must be below 4 GiB");
+  const uint32_t n_lanes = scfg && scfg->lanes ? std::min<uint32_t>(scfg->lanes, 8) : 2;
+  // batches: consecutive records, at most `budget` bytes each (a longer record alone)
+  std::vector<uint64_t> cut{0};
+  for (uint64_t r = 0; r < n; ++r)
+    if (r > cut.back() && rec->offsets[r + 1] - rec->offsets[cut.back()] > budget) cut.push_back(r);
+  if (n) cut.push_back(n);
+  const size_t n_batches = cut.size() - 1;
+  while (c->stream_lanes.size() < n_lanes) {
+    auto ln = std::make_unique<Lane>();
+    if (cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        grow(ln->dev_err, sizeof(DevError)) != AS_OK ||
+        cudaMemsetAsync(ln->dev_err.p, 0, sizeof(DevError), ln->stream) != cudaSuccess) {
+      if (ln->stream) cudaStreamDestroy(ln->stream);
+      ln->release_all();
+      return fail(c, AS_ERR_CUDA, "streaming lane set-up failed");
+    }
+    c->stream_lanes.push_back(std::move(ln));
+  }
+  const uint64_t base = c->records_done;
+  const uint32_t call_lo = c->call_id.load() + 1;
+  std::vector<as_output*> part(n_batches, nullptr);
+  std::atomic<size_t> next{0};
+  std::atomic<bool> failed{false};
+  std::mutex err_mu;
+  as_status first_err = AS_OK;
+  std::string first_msg;
+  auto worker = [&](Lane* ln) {
+    cudaSetDevice(c->device);
+    while (!failed.load()) {
+      const size_t b = next.fetch_add(1);
+      if (b >= n_batches) break;
+      const uint64_t r0 = cut[b], r1 = cut[b + 1], m = r1 - r0;
+      const uint64_t o0 = rec->offsets[r0], nb = rec->offsets[r1] - o0;
+      as_status s = AS_OK;
+      // the previous batch's H2D from this staging buffer has completed:
+      // anonymize_impl synchronizes its stream before returning
+      if (grow_pinned(reinterpret_cast<void**>(&ln->h_in), &ln->h_in_cap, nb + 16) != AS_OK ||
+          grow_pinned(reinterpret_cast<void**>(&ln->h_in_off), &ln->h_in_off_cap, (m + 1) * 8) != AS_OK) {
+        s = AS_ERR_OOM;
+        t_err = "pinned staging allocation failed";
+      } else {
+        if (nb) memcpy(ln->h_in, rec->bytes + o0, nb);
+        for (uint64_t i = 0; i <= m; ++i) ln->h_in_off[i] = rec->offsets[r0 + i] - o0;
+        as_records part_rec{ln->h_in, ln->h_in_off, m, 0};
+        s = anonymize_impl(c, ln, &part_rec, sch, nullptr, 0, &part[b], false, (int64_t)(base + r0));
+        if (s == AS_ERR_CUDA) cudaGetLastError();
+      }
+      if (s != AS_OK) {
+        std::lock_guard<std::mutex> lk(err_mu);
+        if (first_err == AS_OK) {
+          first_err = s;
+          first_msg = "batch " + std::to_string(b) + " (records " + std::to_string(r0) + ".." +
+                      std::to_string(r1 - 1) + "): " + t_err;
+        }
+        failed.store(true);
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  const uint32_t used = (uint32_t)std::min<size_t>(n_lanes, std::max<size_t>(n_batches, 1));
+  for (uint32_t i = 0; i < used; ++i) th.emplace_back(worker, c->stream_lanes[i].get());
+  for (auto& t : th) t.join();
+  if (first_err != AS_OK) {
+    for (as_output* p : part) as_output_free(p);
+    return fail(c, first_err, first_msg);
+  }
+  // one host output in record order
+  as_output* o = new as_output();
+  o->ctx = c;
+  o->on_device = 0;
+  o->n = n;
+  o->call_lo = call_lo;
+  o->call_id = c->call_id.load();
+  uint64_t total = 0;
+  for (as_output* p : part) total += p->h_bytes.size();
+  o->h_bytes.resize(total);
+  o->h_off.resize(n + 1);
+  o->h_off[0] = 0;
+  uint64_t pos = 0, r = 0;
+  for (as_output* p : part) {
+    if (!p->h_bytes.empty()) memcpy(o->h_bytes.data() + pos, p->h_bytes.data(), p->h_bytes.size());
+    for (uint64_t i = 1; i <= p->n; ++i) o->h_off[r + i] = pos + p->h_off[i];
+    pos += p->h_bytes.size();
+    r += p->n;
+    const as_stats& ps = p->stats;
+    as_stats& s = o->stats;
+    s.n_records += ps.n_records;
+    s.n_bytes += ps.n_bytes;
+    s.n_tokens += ps.n_tokens;
+    s.n_encoded_tokens += ps.n_encoded_tokens;
+    s.n_sequences += ps.n_sequences;
+    s.n_regex_spans += ps.n_regex_spans;
+    s.n_ner_spans += ps.n_ner_spans;
+    s.n_final_spans += ps.n_final_spans;
+    s.n_out_bytes += ps.n_out_bytes;
+    s.n_new_entries += ps.n_new_entries;
+    s.n_map_entries = std::max(s.n_map_entries, ps.n_map_entries);
+    s.kernel_launches += ps.kernel_launches;
+    as_output_free(p);
+  }
+  c->records_done += n;
+  *out = o;
+  return AS_OK;
 }
 
 as_status as_output_records(const as_output* o, const uint8_t** bytes, const uint64_t** offsets, uint64_t* n,
@@ -1331,7 +1492,7 @@ as_status as_output_map(as_output* o, const as_entity** entries, uint64_t* n) {
   if (!o->map_loaded) {
     as_ctx* c = o->ctx;
     cudaSetDevice(c->device);
-    as_status s = map_collect(c, o->call_id, o->map, o->map_orig);
+    as_status s = map_collect(c, o->call_lo ? o->call_lo : o->call_id, o->call_id, o->map, o->map_orig);
     if (s != AS_OK) return s;
     for (auto& e : o->map) e.original = o->map_orig.data() + reinterpret_cast<uint64_t&>(e.original);
     o->map_loaded = true;
@@ -1357,7 +1518,7 @@ as_status as_map_export(as_ctx* c, as_entity** entries, uint64_t* n) {
   cudaSetDevice(c->device);
   std::vector<as_entity> ents;
   std::vector<uint8_t> orig;
-  as_status s = map_collect(c, 0, ents, orig);
+  as_status s = map_collect(c, 0, 0, ents, orig);
   if (s != AS_OK) return s;
   size_t bytes = ents.size() * sizeof(as_entity) + orig.size() + 1;
   uint8_t* blob = static_cast<uint8_t*>(malloc(bytes));

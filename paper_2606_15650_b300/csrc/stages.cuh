@@ -112,7 +112,9 @@ void launch_map_import(MapView m, const uint8_t* orig, const uint64_t* orig_off,
                        const uint32_t* type, const uint32_t* digests, const uint64_t* first, const uint64_t* last,
                        const uint64_t* count, uint64_t n, uint32_t call_id, DevError* err, cudaStream_t st);
 // keep[i] = slot i occupied and (call_id == 0 or touched by call_id).
-void launch_map_select(MapView m, uint32_t call_id, uint8_t* keep, cudaStream_t st);
+// keep[i] = slot i holds an entry last touched by a call in [call_lo, call_hi]
+// (call_lo = 0: every entry).
+void launch_map_select(MapView m, uint32_t call_lo, uint32_t call_hi, uint8_t* keep, cudaStream_t st);
 void launch_map_gather(MapView m, const uint8_t* keep, const uint32_t* pos, uint32_t* idx, cudaStream_t st);
 void launch_map_gather_slots(MapView m, const uint32_t* idx, uint32_t n, MapSlot* out, cudaStream_t st);
 

@@ -1,0 +1,91 @@
+"""Streaming (as_anonymize_stream) through the C ABI on the GPU.
+
+Host records processed in overlapping batches must give the bytes, stats and
+entity map of one as_anonymize call over the same records: several batch
+budgets (one record per batch up to one batch), lane counts, sliding
+windows, FP8 with static scales, record indices continuing across calls.
+"""
+import numpy as np
+import pytest
+
+import synth
+import paper_2606_15650_b300.api as api
+
+import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+DIMS = synth.C1.dims
+KEY = synth.make_key()
+SCHEMA = api.Schema(synth.TYPE_NAMES_4)
+WIN = api.Schema(synth.TYPE_NAMES_4, window=128, stride=96)
+STAT_KEYS = ("n_records", "n_bytes", "n_tokens", "n_encoded_tokens", "n_sequences", "n_regex_spans",
+             "n_ner_spans", "n_final_spans", "n_out_bytes", "n_map_entries", "n_new_entries")
+
+
+@pytest.fixture(scope="module")
+def blob():
+    return synth.pack_blob(DIMS, synth.make_weights(DIMS, seed=31, random_affine=True))
+
+
+def _one_call(blob, words, recs, schema, prec="bf16", cal=None):
+    ctx = api.Context(DIMS, blob, words, precision=prec)
+    if cal is not None:
+        ctx.set_scales(cal)
+    rs = synth.records_from_list(recs)
+    out = ctx.anonymize(rs.data, rs.offsets, schema, KEY)
+    res = out.records(), out.stats(), sorted(U.map_tuples(ctx.map_export()))
+    ctx.close()
+    return res
+
+
+@pytest.mark.parametrize("schema", [SCHEMA, WIN], ids=["nowin", "win128"])
+@pytest.mark.parametrize("batch_bytes,lanes", [(1, 2), (3000, 1), (3000, 3), (40000, 2), (0, 2)])
+def test_stream_equals_one_call(blob, vocab_words, c1_records, schema, batch_bytes, lanes):
+    recs = c1_records.records()[:160]
+    ref_out, ref_stats, ref_map = _one_call(blob, vocab_words, recs, schema)
+    ctx = api.Context(DIMS, blob, vocab_words, precision="bf16")
+    rs = synth.records_from_list(recs)
+    out = ctx.anonymize_stream(rs.data, rs.offsets, schema, KEY, batch_bytes=batch_bytes, lanes=lanes)
+    assert out.records() == ref_out
+    st = out.stats()
+    for k in STAT_KEYS:
+        assert st[k] == ref_stats[k], k
+    assert sorted(U.map_tuples(ctx.map_export())) == ref_map
+    assert sorted(U.map_tuples(out.map())) == ref_map  # every entry was touched by this call
+    ctx.close()
+
+
+def test_stream_fp8_static_scales(blob, vocab_words, c1_records):
+    recs = c1_records.records()[:120]
+    ctx = api.Context(DIMS, blob, vocab_words, precision="fp8")
+    cal = synth.make_records(synth.scaled(synth.C1, 16).records, vocab_words, seed=synth.SEED_CALIB)
+    ctx.calibrate(cal.data, cal.offsets, SCHEMA)
+    scales = ctx.scales()
+    ref_out, _, ref_map = _one_call(blob, vocab_words, recs, SCHEMA, prec="fp8", cal=scales)
+    rs = synth.records_from_list(recs)
+    out = ctx.anonymize_stream(rs.data, rs.offsets, SCHEMA, KEY, batch_bytes=5000, lanes=3)
+    assert out.records() == ref_out
+    assert sorted(U.map_tuples(ctx.map_export())) == ref_map
+    ctx.close()
+
+
+def test_stream_indices_continue_and_edges(blob, vocab_words, c1_records):
+    recs = c1_records.records()[:100]
+    _, _, ref_map = _one_call(blob, vocab_words, recs, SCHEMA)
+    ctx = api.Context(DIMS, blob, vocab_words, precision="bf16")
+    a = synth.records_from_list(recs[:37])
+    ctx.anonymize(a.data, a.offsets, SCHEMA, KEY).free()
+    b = synth.records_from_list(recs[37:])
+    ctx.anonymize_stream(b.data, b.offsets, SCHEMA, KEY, batch_bytes=2000).free()
+    assert sorted(U.map_tuples(ctx.map_export())) == ref_map
+    # empty input and empty records
+    out = ctx.anonymize_stream(np.zeros(0, np.uint8), np.zeros(1, np.uint64), SCHEMA, KEY)
+    assert out.records() == []
+    e = synth.records_from_list([b"", b"", b"10.1.2.3", b""])
+    got = ctx.anonymize_stream(e.data, e.offsets, SCHEMA, KEY, batch_bytes=1).records()
+    assert got[0] == b"" and got[1] == b"" and got[3] == b"" and got[2].startswith(b"[IP_ADDRESS_")
+    # a different key on the non-empty map is refused, as for as_anonymize
+    with pytest.raises(api.AnonShieldError):
+        ctx.anonymize_stream(e.data, e.offsets, SCHEMA, b"other key")
+    ctx.close()
