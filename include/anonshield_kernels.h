@@ -57,10 +57,10 @@ as_status as_k_attention(int precision, const void* qkv, void* out, const int32_
                          int32_t n_heads, void* stream);
 
 /* The same attention (BF16) on the tcgen05 tensor cores: S = Q K^T and
- * O = P V in TMEM, softmax in four warps. Every seq_start must be a multiple
- * of 8 (AS_ERR_ARG otherwise); vt_scratch must hold d_model * round8(rows)
- * BF16 elements (the kernel writes V transposed there first). */
-as_status as_k_attention_tc(const void* qkv, void* vt_scratch, void* out, const int32_t* seq_start,
+ * O = P V in TMEM, softmax in four warps, Q, K and V read by TMA straight
+ * from the qkv rows. Every sequence must lie inside [0, rows) (AS_ERR_ARG
+ * otherwise; checked on the host, which reads seq_start / seq_len back). */
+as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start,
                             const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
                             void* stream);
 

@@ -152,7 +152,7 @@ def load() -> C.CDLL:
     lib.as_k_gemm_fp8.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, C.c_float, C.c_float,
                                   P, P, P, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
-    lib.as_k_attention_tc.argtypes = [P, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
+    lib.as_k_attention_tc.argtypes = [P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
     lib.as_k_launch_count.restype = C.c_uint64
     lib.as_k_last_error.restype = C.c_char_p
@@ -216,9 +216,9 @@ def attention(precision: str, qkv, out, seq_start, seq_len, d_model: int, n_head
     return out
 
 
-def attention_tc(qkv, vt_scratch, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
-    """tcgen05 attention (BF16); sequence starts must be multiples of 8."""
-    _check_k(load().as_k_attention_tc(_ptr(qkv), _ptr(vt_scratch), _ptr(out), _ptr(seq_start), _ptr(seq_len),
+def attention_tc(qkv, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
+    """tcgen05 attention (BF16) over packed sequences."""
+    _check_k(load().as_k_attention_tc(_ptr(qkv), _ptr(out), _ptr(seq_start), _ptr(seq_len),
                                       int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
     return out
 

@@ -1,21 +1,31 @@
 // Self-attention on the 5th-generation tensor cores (sm_103a), BF16 in,
 // FP32 softmax statistics and accumulation (encoder of AnonShield §2 stage (2)).
 //
-// One CTA computes one (sequence, head, 128-query tile):
-//   S_j = Q K_j^T           tcgen05.mma M=128 N=128 K=64, S in TMEM
-//   P_j = exp2(S_j*c - m)   four softmax warps, one query row per thread,
-//                           online max / sum in FP32, P rounded to BF16 and
-//                           written to shared memory (128-byte swizzle)
-//   O  += P_j V_j           tcgen05.mma M=128 N=64 K=128, O in TMEM, O
-//                           rescaled in TMEM when the row maximum grows
-// Both MMAs read K-major operands: Q and K rows come straight from the packed
-// QKV buffer; V is read from a transposed copy (feature-major, tokens
-// contiguous), written by vt_transpose_kernel. TMA loads need the token
-// coordinate of V^T on a 16-byte boundary, so every sequence starts on a row
-// that is a multiple of 8 (the batch packer inserts padding rows).
+// One CTA computes one (sequence, head, 128-query tile), keys in tiles of 64:
+//   S_j = Q K_j^T           tcgen05.mma M=128 N=64 K=64, S in TMEM
+//   P_j = exp2(S_j*c - m)   four softmax warps, one query row per thread; the
+//                           whole 64-key row of S is read into registers in one
+//                           pass and S is released at once, so the MMA of
+//                           S_{j+1} overlaps the exp2 work on S_j; P rounded to
+//                           BF16 into shared memory (128-byte swizzle)
+//   O  += P_j V_j           tcgen05.mma M=128 N=64 K=64, O in TMEM
+// The maximum m that P is taken against is raised only when a row's true
+// maximum exceeds it by more than 2^8 (P stays <= 256), so O is rescaled in
+// TMEM only on those raises instead of on every growth of the maximum.
+// Q, K and V tiles come straight from the packed QKV rows by TMA: Q and K as
+// K-major operands, V as an MN-major B operand (keys along K, features
+// contiguous), so no transposed copy of V is made.
+// One thread issues both the TMA loads and the MMAs, polling its barriers
+// without blocking. P is double-buffered, so the softmax warps start on
+// tile j+1 while O += P_j V_j runs; K and V go through a 3-stage ring. A CTA is
+// five warps, 96 KB of shared memory and 128 TMEM columns: two CTAs per SM.
 // Keys past the sequence end are masked to -inf; query rows past it are not
-// stored. Every mbarrier wait is bounded (see gemm_tc.cu).
+// stored. Every mbarrier wait is bounded (see gemm_tc.cu); on a timeout the
+// issuing thread waits (bounded) for its copies and MMAs in flight before the
+// CTA frees its TMEM.
+#include <algorithm>
 #include <atomic>
+#include <vector>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -25,15 +35,19 @@ namespace as {
 namespace atc {
 
 constexpr int kQ = 128;        // query rows per CTA
-constexpr int kKT = 128;       // keys per tile
-constexpr int kThreads = 192;  // loader, MMA, 4 softmax warps
+constexpr int kKT = 64;        // keys per tile
+constexpr int kThreads = 160;  // control (TMA + MMA), 4 softmax warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
+// Work item = one 128-query tile of one sequence: (sequence << 6) | q-tile.
+// A work unit is an (item, head) pair; CTA b takes units b, b + grid, ...
 struct Params {
   const int32_t* seq_start;
   const int32_t* seq_len;
+  const int32_t* items;
+  int n_items;
   __nv_bfloat16* out;
-  int d, n_heads, q_tiles;
+  int d, n_heads;
   DevError* err;
 };
 
@@ -57,6 +71,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
@@ -106,6 +131,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
+// The same 128-byte-swizzle descriptor for an MN-major operand whose swizzle
+// atoms (8 K-rows of 128 bytes) follow each other along K: both strides are
+// 1024 bytes (the MN stride is unused with N = 64, one atom wide).
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(1024 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+constexpr uint32_t kIdescTransposeB = 1u << 16;  // B operand MN-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -150,64 +188,96 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Shared memory (offsets from a 1024-aligned base)
-constexpr int kQBytes = kQ * 64 * 2;                 // 16 KB, one swizzle panel
-constexpr int kKBytes = kKT * 64 * 2;                // 16 KB per stage
-constexpr int kVBytes = 64 * kKT * 2;                // 16 KB per stage: two 64x64 panels
-constexpr int kPBytes = kQ * kKT * 2;                // 32 KB: two 128x64 panels
-constexpr int kOffQ = 0;
-constexpr int kOffK = kOffQ + kQBytes;               // 2 stages
-constexpr int kOffV = kOffK + 2 * kKBytes;           // 2 stages
-constexpr int kOffP = kOffV + 2 * kVBytes;
-constexpr int kOffBar = kOffP + kPBytes;
-// bars: q_full, kv_full[2], kv_empty[2], s_full, s_empty, p_full, o_done
-constexpr int kNumBars = 9;
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared memory (offsets from a 1024-aligned base): 96 KB, two CTAs per SM.
+constexpr int kQBytes = kQ * 64 * 2;                 // 16 KB per buffer: Q tile, one 128-byte-swizzle panel
+constexpr int kKBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
+constexpr int kVBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
+constexpr int kPBytes = kQ * kKT * 2;                // 16 KB per buffer: P tile, 128 rows x 64 keys
+constexpr int kKVStages = 2;
+constexpr int kOffQ = 0;                             // 2 buffers (consecutive work units)
+constexpr int kOffK = kOffQ + 2 * kQBytes;
+constexpr int kOffV = kOffK + kKVStages * kKBytes;
+constexpr int kOffP = kOffV + kKVStages * kVBytes;   // 2 buffers (consecutive key tiles)
+constexpr int kOffBar = kOffP + 2 * kPBytes;
+// mbarriers (8 bytes each)
+enum {
+  kBarQFull = 0,     // [2] Q of a unit landed
+  kBarQEmpty = 2,    // [2] the S MMAs of a unit are done with its Q
+  kBarKVFull = 4,    // [kKVStages]
+  kBarKVEmpty = 6,   // [kKVStages]
+  kBarSFull = 8,     // S_g in TMEM
+  kBarSEmpty = 9,    // softmax holds S_g in registers (128 arrivals)
+  kBarPFull = 10,    // [2] P_g in shared memory (128 arrivals)
+  kBarODone = 12,    // [2] O += P_g V_g done (by P buffer)
+  kBarOFree = 14,    // [2] epilogue has read an O buffer (128 arrivals)
+  kBarDrain = 16,
+  kNumBars = 17
+};
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
-constexpr int kSmemAlloc = kSmemBytes;             // two CTAs fit on one SM
-constexpr uint32_t kTmemCols = 256;                  // S: cols 0..127, O: cols 128..191
-constexpr uint32_t kColO = 128;
+constexpr int kSmemAlloc = kSmemBytes + 1024;        // room to align the base to 1024 bytes
+constexpr uint32_t kTmemCols = 256;                  // S: cols 0..63, O buffers: 64..127 and 128..191
+constexpr uint32_t kColO = 64;
+// P is exp2(t - m) against a row maximum m that is raised only when the true
+// maximum exceeds it by more than this (log2 units): P <= 2^8, and O and the
+// row sum are rescaled only on those rare raises.
+constexpr float kRescaleSlack = 8.0f;
 
-__global__ void __launch_bounds__(kThreads, 1)
-    attn_tc_kernel(const __grid_constant__ CUtensorMap tmQK, const __grid_constant__ CUtensorMap tmVt, Params p) {
-  const int qt = blockIdx.x % p.q_tiles;
-  const int rest = blockIdx.x / p.q_tiles;
-  const int h = rest % p.n_heads, s = rest / p.n_heads;
-  const int L = p.seq_len[s], q0 = qt * kQ;
-  if (q0 >= L) return;  // whole CTA leaves before any barrier or TMEM use
-  const int row0 = p.seq_start[s];
-  const int n_tiles = (L + kKT - 1) / kKT;
+struct Work {
+  int L, row0, q0, h, n_t;
+};
+__device__ __forceinline__ Work work_of(const Params& p, int u) {
+  const int it = p.items[u / p.n_heads];
+  const int s = it >> 6;
+  Work w;
+  w.h = u % p.n_heads;
+  w.L = p.seq_len[s];
+  w.row0 = p.seq_start[s];
+  w.q0 = (it & 63) * kQ;
+  w.n_t = (w.L + kKT - 1) / kKT;
+  return w;
+}
 
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = smem_raw;
-  // A V^T tile load starts at token row0 + 128 j: TMA needs that coordinate on a
-  // 16-byte boundary (8 tokens), and the swizzled panels need a 1024-byte
-  // aligned base. Record and skip instead of issuing a misaligned copy.
-  if ((row0 & 7) || (smem_u32(smem) & 1023)) {
-    if (threadIdx.x == 0) report_error(p.err, kErrBounds, 70, (uint32_t)row0, smem_u32(smem));
-    return;
-  }
+// Persistent: a CTA loops over its work units; tiles are numbered globally
+// across units (g), which fixes every buffer index and barrier phase.
+__global__ void __launch_bounds__(kThreads, 2)
+    attn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmKV, Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sb = smem_u32(smem);
   const uint32_t bar0 = sb + kOffBar;
-  const uint32_t q_full = bar0, kv_full0 = bar0 + 8, kv_empty0 = bar0 + 24, s_full = bar0 + 40, s_empty = bar0 + 48,
-                 p_full = bar0 + 56, o_done = bar0 + 64;
+  auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + kNumBars * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_units = p.n_items * p.n_heads;
 
   if (threadIdx.x == 0) {
-    mbar_init(q_full, 1);
-    mbar_init(kv_full0, 1);
-    mbar_init(kv_full0 + 8, 1);
-    mbar_init(kv_empty0, 1);
-    mbar_init(kv_empty0 + 8, 1);
-    mbar_init(s_full, 1);
-    mbar_init(s_empty, 128);
-    mbar_init(p_full, 128);
-    mbar_init(o_done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(kBarQFull + i), 1);
+      mbar_init(bar(kBarQEmpty + i), 1);
+      mbar_init(bar(kBarPFull + i), 128);
+      mbar_init(bar(kBarODone + i), 1);
+      mbar_init(bar(kBarOFree + i), 128);
+    }
+    for (int i = 0; i < kKVStages; ++i) {
+      mbar_init(bar(kBarKVFull + i), 1);
+      mbar_init(bar(kBarKVEmpty + i), 1);
+    }
+    mbar_init(bar(kBarSFull), 1);
+    mbar_init(bar(kBarSEmpty), 128);
+    mbar_init(bar(kBarDrain), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
@@ -221,169 +291,242 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- loader
-      mbar_expect_tx(q_full, kQBytes);
-      tma_load_2d(sb + kOffQ, &tmQK, q_full, h * 64, row0 + q0);
-      for (int j = 0; j < n_tiles; ++j) {
-        const int st = j & 1;
-        if (!mbar_wait(kv_empty0 + 8 * st, ((j >> 1) & 1) ^ 1u, abort_flag, p.err, 40)) goto done;
-        mbar_expect_tx(kv_full0 + 8 * st, kKBytes + kVBytes);
-        const int k0 = row0 + j * kKT;
-        tma_load_2d(sb + kOffK + st * kKBytes, &tmQK, kv_full0 + 8 * st, d + h * 64, k0);
-        tma_load_2d(sb + kOffV + st * kVBytes, &tmVt, kv_full0 + 8 * st, k0, h * 64);
-        tma_load_2d(sb + kOffV + st * kVBytes + kVBytes / 2, &tmVt, kv_full0 + 8 * st, k0 + 64, h * 64);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
-      constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64);
-      if (!mbar_wait(q_full, 0, abort_flag, p.err, 50)) goto done;
-      const uint64_t qdesc = sw128_desc(sb + kOffQ);
-      for (int j = 0; j < n_tiles; ++j) {
-        const int st = j & 1;
-        if (!mbar_wait(kv_full0 + 8 * st, (j >> 1) & 1, abort_flag, p.err, 51)) goto done;
-        if (j > 0 && !mbar_wait(s_empty, (j - 1) & 1, abort_flag, p.err, 52)) goto done;
-        fence_after();
-        const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) mma_bf16(tmem, qdesc + 2 * k, kdesc + 2 * k, idS, k > 0 ? 1u : 0u);
-        mma_commit(s_full);
-        if (!mbar_wait(p_full, j & 1, abort_flag, p.err, 53)) goto done;
-        fence_after();
-        const uint32_t vb = sb + kOffV + st * kVBytes;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const uint64_t pdesc = sw128_desc(sb + kOffP + (k >> 2) * (kPBytes / 2)) + 2 * (k & 3);
-          const uint64_t vdesc = sw128_desc(vb + (k >> 2) * (kVBytes / 2)) + 2 * (k & 3);
-          mma_bf16(tmem + kColO, pdesc, vdesc, idO, (j > 0 || k > 0) ? 1u : 0u);
+      // ---------------- control: TMA loads and MMAs for three cursors over the
+      // same unit sequence, by polling: loads (Q of a unit, then its K_t, V_t),
+      // S_g = Q K_g^T (issued as soon as the softmax warps hold S_{g-1}, so it
+      // overlaps their exp2 work) and O += P_g V_g (once P_g is in shared memory).
+      constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
+      const int step = gridDim.x;
+      int ul = blockIdx.x, il = 0, tl = 0, gl = 0;  // loads
+      int us = blockIdx.x, is = 0, ts = 0, gs = 0;  // S
+      int uo = blockIdx.x, io = 0, to = 0, go = 0;  // O
+      bool ql = false, qs = false, of = false, issued_mma = false;
+      Work wl = work_of(p, ul), ws = wl, wo = wl;
+      uint64_t t_idle = 0;
+      uint32_t idle = 0;
+      while (uo < n_units) {
+        bool prog = false;
+        if (ul < n_units) {
+          if (!ql) {
+            const int b = il & 1;
+            if (il < 2 || mbar_test(bar(kBarQEmpty + b), ((il >> 1) - 1) & 1)) {
+              mbar_expect_tx(bar(kBarQFull + b), kQBytes);
+              tma_load_2d(sb + kOffQ + b * kQBytes, &tmQ, bar(kBarQFull + b), wl.h * 64, wl.row0 + wl.q0);
+              ql = true;
+              prog = true;
+            }
+          } else {
+            const int st = gl % kKVStages;
+            if (mbar_test(bar(kBarKVEmpty + st), ((gl / kKVStages) & 1) ^ 1u)) {
+              const int k0 = wl.row0 + tl * kKT;
+              mbar_expect_tx(bar(kBarKVFull + st), kKBytes + kVBytes);
+              tma_load_2d(sb + kOffK + st * kKBytes, &tmKV, bar(kBarKVFull + st), d + wl.h * 64, k0);
+              tma_load_2d(sb + kOffV + st * kVBytes, &tmKV, bar(kBarKVFull + st), 2 * d + wl.h * 64, k0);
+              ++gl;
+              prog = true;
+              if (++tl == wl.n_t) {
+                ul += step;
+                ++il;
+                tl = 0;
+                ql = false;
+                if (ul < n_units) wl = work_of(p, ul);
+              }
+            }
+          }
         }
-        mma_commit(o_done);
-        mma_commit(kv_empty0 + 8 * st);
-      }
-    }
-  } else {
-    // ---------------- softmax: warp w owns TMEM lanes (query rows) 32*(w%4)..
-    const int sub = warp & 3;
-    const int r = sub * 32 + lane;               // query row in the tile
-    const uint32_t trow = tmem + ((uint32_t)(sub * 32) << 16);
-    const float c = 0.125f * 1.4426950408889634f;  // 1/sqrt(64) * log2(e)
-    float m = -INFINITY, l = 0.f;
-    bool ok = true;
-    for (int j = 0; j < n_tiles && ok; ++j) {
-      const int valid = min(kKT, L - j * kKT);   // keys of this tile inside the sequence
-      if (!warp_wait(s_full, j & 1, abort_flag, p.err, 60)) { ok = false; break; }
-      fence_after();
-      // pass 1: row maximum of the scaled scores
-      float mx = -INFINITY;
-#pragma unroll 1
-      for (int cc = 0; cc < kKT / 32; ++cc) {
-        uint32_t v[32];
-        tmem_ld32(trow + cc * 32, v);
+        if (us < n_units && gs < gl) {
+          if (!qs) qs = mbar_test(bar(kBarQFull + (is & 1)), (is >> 1) & 1);
+          const int st = gs % kKVStages;
+          if (qs && mbar_test(bar(kBarKVFull + st), (gs / kKVStages) & 1) &&
+              (gs == 0 || mbar_test(bar(kBarSEmpty), (gs - 1) & 1))) {
+            fence_after();
+            const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
+            const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (cc * 32 + i < valid) mx = fmaxf(mx, __uint_as_float(v[i]) * c);
-      }
-      const float mn = fmaxf(m, mx);
-      const float corr = ex2_approx(m - mn);     // 0 on the first tile (m = -inf)
-      // pass 2: P = exp2(s*c - mn), row sum, BF16 into the swizzled P panels.
-      // P is written only after the previous P.V has finished reading it.
-      if (j > 0 && !warp_wait(o_done, (j - 1) & 1, abort_flag, p.err, 61)) { ok = false; break; }
-      float sum = 0.f;
-#pragma unroll 1
-      for (int cc = 0; cc < kKT / 32; ++cc) {
-        uint32_t v[32];
-        tmem_ld32(trow + cc * 32, v);
-        uint32_t pk[16];
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          const float p0 = (cc * 32 + i < valid) ? ex2_approx(__uint_as_float(v[i]) * c - mn) : 0.f;
-          const float p1 = (cc * 32 + i + 1 < valid) ? ex2_approx(__uint_as_float(v[i + 1]) * c - mn) : 0.f;
-          sum += p0 + p1;
-          __nv_bfloat162 b = __floats2bfloat162_rn(p0, p1);
-          pk[i >> 1] = *reinterpret_cast<uint32_t*>(&b);
+            for (int k = 0; k < 4; ++k) mma_bf16(tmem, qdesc + 2 * k, kdesc + 2 * k, idS, k > 0 ? 1u : 0u);
+            mma_commit(bar(kBarSFull));
+            issued_mma = true;
+            ++gs;
+            prog = true;
+            if (++ts == ws.n_t) {
+              mma_commit(bar(kBarQEmpty + (is & 1)));
+              us += step;
+              ++is;
+              ts = 0;
+              qs = false;
+              if (us < n_units) ws = work_of(p, us);
+            }
+          }
         }
-        // 32 keys = 64 bytes = four 16-byte pieces of row r in panel cc/2
-        uint8_t* panel = smem + kOffP + (cc >> 1) * (kPBytes / 2);
+        if (go < gs) {
+          if (to == 0 && !of) of = io < 2 || mbar_test(bar(kBarOFree + (io & 1)), ((io >> 1) - 1) & 1);
+          if ((to > 0 || of) && mbar_test(bar(kBarPFull + (go & 1)), (go >> 1) & 1)) {
+            fence_after();
+            const uint64_t pdesc = sw128_desc(sb + kOffP + (go & 1) * kPBytes);
+            const uint64_t vdesc = sw128_desc_mn(sb + kOffV + (go % kKVStages) * kVBytes);
+            const uint32_t ocol = tmem + kColO + 64u * (uint32_t)(io & 1);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int piece = (cc & 1) * 4 + q;
-          *reinterpret_cast<uint4*>(panel + r * 128 + ((piece ^ (r & 7)) << 4)) =
-              make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(ocol, pdesc + 2 * k, vdesc + 128 * k, idO, (to > 0 || k > 0) ? 1u : 0u);
+            mma_commit(bar(kBarODone + (go & 1)));
+            mma_commit(bar(kBarKVEmpty + (go % kKVStages)));
+            ++go;
+            prog = true;
+            if (++to == wo.n_t) {
+              uo += step;
+              ++io;
+              to = 0;
+              of = false;
+              if (uo < n_units) wo = work_of(p, uo);
+            }
+          }
         }
-      }
-      fence_before();
-      mbar_arrive(s_empty);                      // S may be overwritten by S_{j+1}
-      l = l * corr + sum;
-      // tcgen05.ld / st are warp-collective: the whole warp rescales when any
-      // of its rows needs it (rows whose maximum did not grow multiply by 1)
-      if (j > 0 && __any_sync(0xffffffffu, corr < 1.f)) {
-        // rescale the running output O (its last update, P_{j-1} V_{j-1}, is done)
-#pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-          uint32_t v[32];
-          tmem_ld32(trow + kColO + cc * 32, v);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) * corr);
-          tmem_st32(trow + kColO + cc * 32, v);
+        if (prog) {
+          idle = 0;
+        } else if ((++idle & 255u) == 0) {
+          if (*abort_flag) break;
+          const uint64_t now = globaltimer();
+          if (idle == 256) {
+            t_idle = now;
+          } else if (now - t_idle > kTimeoutNs) {
+            report_error(p.err, kErrTimeout, 41, blockIdx.x, (uint32_t)(gl | (gs << 16)));
+            *abort_flag = 1;
+            break;
+          }
         }
       }
-      m = mn;
-      fence_proxy_async();
-      fence_before();
-      mbar_arrive(p_full);
-    }
-    if (ok && warp_wait(o_done, (n_tiles - 1) & 1, abort_flag, p.err, 62)) {
-      fence_after();
-      const float inv = 1.f / l;
-      const bool row_ok = q0 + r < L;
-      __nv_bfloat16* o = p.out + (size_t)(row0 + q0 + r) * d + h * 64;
-#pragma unroll 1
-      for (int cc = 0; cc < 2; ++cc) {
-        uint32_t v[32];
-        tmem_ld32(trow + kColO + cc * 32, v);
-        if (row_ok) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 8) {
-            uint4 w;
-            __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[i]) * inv, __uint_as_float(v[i + 1]) * inv);
-            __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[i + 2]) * inv, __uint_as_float(v[i + 3]) * inv);
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[i + 4]) * inv, __uint_as_float(v[i + 5]) * inv);
-            __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[i + 6]) * inv, __uint_as_float(v[i + 7]) * inv);
-            w.x = *reinterpret_cast<uint32_t*>(&a0);
-            w.y = *reinterpret_cast<uint32_t*>(&a1);
-            w.z = *reinterpret_cast<uint32_t*>(&a2);
-            w.w = *reinterpret_cast<uint32_t*>(&a3);
-            *reinterpret_cast<uint4*>(o + cc * 32 + i) = w;
+      if (uo < n_units) {
+        // aborted: wait (bounded) for the copies and MMAs this thread started
+        const uint64_t t0 = globaltimer();
+        const int q_issued = il + (ql ? 1 : 0);
+        for (int j = is; j < q_issued; ++j)
+          while (!mbar_test(bar(kBarQFull + (j & 1)), (j >> 1) & 1) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        for (int j = gs; j < gl; ++j)
+          while (!mbar_test(bar(kBarKVFull + j % kKVStages), (j / kKVStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        if (issued_mma) {
+          mma_commit(bar(kBarDrain));
+          while (!mbar_test(bar(kBarDrain), 0) && globaltimer() - t0 < kTimeoutNs) {
           }
         }
       }
     }
+  } else {
+    // ---------------- softmax + epilogue: warp w owns TMEM lanes (query rows) 32*(w%4)..
+    const int sub = warp & 3;
+    const int r = sub * 32 + lane;               // query row in the tile
+    const uint32_t trow = tmem + ((uint32_t)(sub * 32) << 16);
+    const float c = 0.125f * 1.4426950408889634f;  // 1/sqrt(64) * log2(e)
+    // O += P_k V_k completes phase k/2 of o_done[k&1]
+    auto wait_o = [&](int k, uint32_t where) {
+      return warp_wait(bar(kBarODone + (k & 1)), (k >> 1) & 1, abort_flag, p.err, where);
+    };
+    int g = 0, i = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
+      const Work w = work_of(p, u);
+      const uint32_t ocol = kColO + 64u * (uint32_t)(i & 1);
+      float m = -INFINITY, l = 0.f;              // m: the maximum P is taken against
+      for (int t = 0; t < w.n_t; ++t, ++g) {
+        const int valid = min(kKT, w.L - t * kKT);  // keys of this tile inside the sequence
+        if (!warp_wait(bar(kBarSFull), g & 1, abort_flag, p.err, 60)) { ok = false; break; }
+        fence_after();
+        uint32_t v[64];
+        tmem_ld64(trow, v);
+        fence_before();
+        mbar_arrive(bar(kBarSEmpty));            // S_g is in registers: S_{g+1} may overwrite it
+        // row maximum of the raw scores (keys past the end masked to -inf); the
+        // scale c > 0 is applied in the exp2 argument: t = s * c - m
+        float mxr = -INFINITY;
+        if (valid == kKT) {
+#pragma unroll
+          for (int q = 0; q < 64; ++q) mxr = fmaxf(mxr, __uint_as_float(v[q]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 64; ++q) {
+            if (q >= valid) v[q] = __float_as_uint(-INFINITY);
+            mxr = fmaxf(mxr, __uint_as_float(v[q]));
+          }
+        }
+        const float mx = mxr * c;
+        // tcgen05.ld / st are warp-collective: the warp raises together when any
+        // of its rows needs it (a row that does not multiplies by <= 1, exactly)
+        if (__any_sync(0xffffffffu, mx > m + kRescaleSlack)) {
+          const float mn = fmaxf(m, mx);
+          const float corr = ex2_approx(m - mn);  // 0 on the first tile of a unit (m = -inf)
+          l *= corr;
+          if (t > 0) {
+            // rescale the running output once its last update O_{g-1} is done
+            if (!wait_o(g - 1, 61)) { ok = false; break; }
+            fence_after();
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+              uint32_t ov[32];
+              tmem_ld32(trow + ocol + 32 * half, ov);
+#pragma unroll
+              for (int q = 0; q < 32; ++q) ov[q] = __float_as_uint(__uint_as_float(ov[q]) * corr);
+              tmem_st32(trow + ocol + 32 * half, ov);
+            }
+          }
+          m = mn;
+        }
+        // P packed in place: the pair (2q, 2q+1) goes to v[q], already read
+        float sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < 64; q += 2) {
+          const float p0 = ex2_approx(fmaf(__uint_as_float(v[q]), c, -m));
+          const float p1 = ex2_approx(fmaf(__uint_as_float(v[q + 1]), c, -m));
+          sum += p0 + p1;
+          __nv_bfloat162 b = __floats2bfloat162_rn(p0, p1);
+          v[q >> 1] = *reinterpret_cast<uint32_t*>(&b);
+        }
+        l += sum;
+        // P_g goes to buffer g&1 once O += P_{g-2} V_{g-2} has read it
+        if (g >= 2 && !wait_o(g - 2, 62)) { ok = false; break; }
+        uint8_t* prow = smem + kOffP + (g & 1) * kPBytes + r * 128;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<uint4*>(prow + ((q ^ (r & 7)) << 4)) =
+              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        fence_proxy_async();
+        fence_before();
+        mbar_arrive(bar(kBarPFull + (g & 1)));
+      }
+      if (!ok) break;
+      // epilogue: O_{g-1} is this unit's last update; its buffer is released
+      // for unit i+2 as soon as it is in registers
+      if (!wait_o(g - 1, 63)) { ok = false; break; }
+      fence_after();
+      uint32_t v[64];
+      tmem_ld64(trow + ocol, v);
+      fence_before();
+      mbar_arrive(bar(kBarOFree + (i & 1)));
+      if (w.q0 + r < w.L) {
+        const float inv = 1.f / l;
+        __nv_bfloat16* o = p.out + (size_t)(w.row0 + w.q0 + r) * d + w.h * 64;
+#pragma unroll
+        for (int q = 0; q < 64; q += 8) {
+          uint4 x;
+          __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
+          __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
+          __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
+          x.x = *reinterpret_cast<uint32_t*>(&a0);
+          x.y = *reinterpret_cast<uint32_t*>(&a1);
+          x.z = *reinterpret_cast<uint32_t*>(&a2);
+          x.w = *reinterpret_cast<uint32_t*>(&a3);
+          *reinterpret_cast<uint4*>(o + q) = x;
+        }
+      }
+    }
   }
-done:
   fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 0) {
     __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  }
-}
-
-// Vt[c][r] = V[r][c] = qkv[r][2d + c] for c < d, r < rows (32x32 smem tiles).
-__global__ void vt_transpose_kernel(const __nv_bfloat16* __restrict__ qkv, __nv_bfloat16* __restrict__ vt, int rows,
-                                    int d, int ldt) {
-  __shared__ __nv_bfloat16 t[32][33];
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + i;
-    t[i][tx] = r < rows ? qkv[(size_t)r * 3 * d + 2 * d + c0 + tx] : __float2bfloat16(0.f);
-  }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + tx;
-    if (r < ldt) vt[(size_t)(c0 + i) * ldt + r] = t[tx][i];
   }
 }
 
@@ -393,6 +536,7 @@ namespace {
 // Set once per process / device; concurrent callers write the same values.
 std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_enc{nullptr};
 std::atomic<bool> g_attn_attr_set[64] = {};
+std::atomic<int> g_attn_sms[64] = {};
 
 as_status make_map_bf16(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld_elems,
                         uint32_t box_cols, uint32_t box_rows) {
@@ -411,15 +555,22 @@ as_status make_map_bf16(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_
 }
 }  // namespace
 
-uint64_t attention_vt_elems(int64_t rows, int32_t d_model) { return (uint64_t)d_model * (uint64_t)((rows + 7) & ~7ll); }
+void attention_items(const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items) {
+  for (int32_t s = 0; s < n_seq; ++s)
+    for (int32_t qt = 0; qt * atc::kQ < seq_len[s]; ++qt) items.push_back((s << 6) | qt);
+}
 
-as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* vt, __nv_bfloat16* out, const int32_t* seq_start,
-                            const int32_t* seq_len, int32_t n_seq, int32_t max_len, int64_t rows, int32_t d_model,
-                            int32_t n_heads, DevError* err, cudaStream_t st) {
-  if (n_seq == 0 || max_len == 0 || rows == 0) return AS_OK;
+as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
+                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
+  if (n_items == 0 || max_len == 0 || rows == 0) return AS_OK;
   if (d_model != n_heads * 64 || d_model % 64 || max_len > 4096 || rows > (1ll << 31) - 8 ||
-      (reinterpret_cast<uintptr_t>(qkv) & 15) || (reinterpret_cast<uintptr_t>(vt) & 15)) {
+      (reinterpret_cast<uintptr_t>(qkv) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) {
     set_k_error("attention_tcgen05: head dim 64, sequences <= 4096 tokens, 16-byte aligned buffers");
+    return AS_ERR_ARG;
+  }
+  if ((int64_t)n_items * n_heads > 0x7FFFFFFFll) {
+    set_k_error("attention_tcgen05: too many work items in one batch");
     return AS_ERR_ARG;
   }
   if (!g_enc.load()) {
@@ -436,30 +587,27 @@ as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* vt, __nv_bf
   cudaGetDevice(&dev);
   if (!g_attn_attr_set[dev & 63].load()) {
     AS_CUDA_OK(cudaFuncSetAttribute(atc::attn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, atc::kSmemAlloc));
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_attn_sms[dev & 63].store(n > 0 ? n : 148);
     g_attn_attr_set[dev & 63].store(true);
   }
-  const int ldt = (int)((rows + 7) & ~7ll);
-  dim3 tg((unsigned)((ldt + 31) / 32), (unsigned)(d_model / 32));
-  atc::vt_transpose_kernel<<<tg, 256, 0, st>>>(qkv, vt, (int)rows, d_model, ldt);
-  count_launch();
-  CUtensorMap tmQK, tmVt;
-  as_status s = make_map_bf16(&tmQK, qkv, (uint64_t)rows, 3ull * d_model, 3ull * d_model, 64, atc::kQ);
-  if (s == AS_OK) s = make_map_bf16(&tmVt, vt, (uint64_t)d_model, (uint64_t)ldt, (uint64_t)ldt, 64, 64);
+  CUtensorMap tmQ, tmKV;
+  as_status s = make_map_bf16(&tmQ, qkv, (uint64_t)rows, 3ull * d_model, 3ull * d_model, 64, atc::kQ);
+  if (s == AS_OK) s = make_map_bf16(&tmKV, qkv, (uint64_t)rows, 3ull * d_model, 3ull * d_model, 64, atc::kKT);
   if (s != AS_OK) return s;
   atc::Params p;
   p.seq_start = seq_start;
   p.seq_len = seq_len;
+  p.items = items;
+  p.n_items = n_items;
   p.out = out;
   p.d = d_model;
   p.n_heads = n_heads;
-  p.q_tiles = (max_len + atc::kQ - 1) / atc::kQ;
   p.err = err;
-  const uint64_t blocks = (uint64_t)n_seq * n_heads * p.q_tiles;
-  if (blocks > 0x7FFFFFFFull) {
-    set_k_error("attention_tcgen05: too many sequences in one batch");
-    return AS_ERR_ARG;
-  }
-  atc::attn_tc_kernel<<<(unsigned)blocks, atc::kThreads, atc::kSmemAlloc, st>>>(tmQK, tmVt, p);
+  const int64_t units = (int64_t)n_items * n_heads;
+  const int grid = (int)std::min<int64_t>(units, 2ll * g_attn_sms[dev & 63].load());  // two CTAs per SM, persistent
+  atc::attn_tc_kernel<<<grid, atc::kThreads, atc::kSmemAlloc, st>>>(tmQ, tmKV, p);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;

@@ -1,6 +1,8 @@
 // Encoder kernels of the token classifier (AnonShield §2 stage (2)).
 #pragma once
 
+#include <vector>
+
 #include "../../include/anonshield_kernels.h"
 #include "common.cuh"
 
@@ -26,12 +28,13 @@ as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int
                          const int32_t* seq_len, int32_t n_seq, int32_t max_len, int32_t d_model, int32_t n_heads,
                          cudaStream_t st);
 
-// Self-attention on tcgen05 (see attn_tc.cu). Every seq_start must be a
-// multiple of 8; vt is scratch of attention_vt_elems(rows, d_model) BF16.
-uint64_t attention_vt_elems(int64_t rows, int32_t d_model);
-as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* vt, __nv_bfloat16* out, const int32_t* seq_start,
-                            const int32_t* seq_len, int32_t n_seq, int32_t max_len, int64_t rows, int32_t d_model,
-                            int32_t n_heads, DevError* err, cudaStream_t st);
+// Self-attention on tcgen05 (see attn_tc.cu), persistent over work items:
+// attention_items appends one item per 128-query tile of each sequence
+// ((s << 6) | tile); rows of each sequence inside [0, rows).
+void attention_items(const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items);
+as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
+                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st);
 
 // Row LayerNorm; writes FP32 and (optionally) BF16 copies.
 as_status layernorm_rows(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,

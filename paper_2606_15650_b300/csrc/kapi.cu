@@ -72,7 +72,7 @@ as_status as_k_attention(int precision, const void* qkv, void* out, const int32_
   return AS_ERR_ARG;
 }
 
-as_status as_k_attention_tc(const void* qkv, void* vt_scratch, void* out, const int32_t* seq_start,
+as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start,
                             const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
                             void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -84,15 +84,25 @@ as_status as_k_attention_tc(const void* qkv, void* vt_scratch, void* out, const 
   }
   int32_t mx = 0;
   for (int32_t i = 0; i < n_seq; ++i) {
-    if (starts[i] % 8 != 0 || starts[i] < 0 || (int64_t)starts[i] + lens[i] > rows) {
-      set_k_error("as_k_attention_tc: sequence starts must be multiples of 8 inside the rows");
+    if (starts[i] < 0 || lens[i] < 0 || (int64_t)starts[i] + lens[i] > rows) {
+      set_k_error("as_k_attention_tc: every sequence must lie inside the rows");
       return AS_ERR_ARG;
     }
     mx = lens[i] > mx ? lens[i] : mx;
   }
-  return attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(vt_scratch),
-                           static_cast<__nv_bfloat16*>(out), seq_start, seq_len, n_seq, mx, rows, d_model, n_heads,
-                           nullptr, st);
+  std::vector<int32_t> items;
+  attention_items(lens.data(), n_seq, items);
+  if (items.empty()) return AS_OK;
+  int32_t* d_items = nullptr;
+  AS_CUDA_OK(cudaMallocAsync(reinterpret_cast<void**>(&d_items), items.size() * 4, st));
+  cudaError_t e = cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st);
+  as_status s = e == cudaSuccess ? AS_OK : AS_ERR_CUDA;
+  if (s == AS_OK)
+    s = attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(out), seq_start, seq_len,
+                          d_items, (int32_t)items.size(), mx, rows, d_model, n_heads, nullptr, st);
+  cudaFreeAsync(d_items, st);
+  if (e != cudaSuccess) set_k_error(std::string("as_k_attention_tc: ") + cudaGetErrorString(e));
+  return s;
 }
 
 as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16, int64_t rows,

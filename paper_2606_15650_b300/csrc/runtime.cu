@@ -140,8 +140,8 @@ struct Lane {
   DBuf ner_s, ner_l, ner_t, keep, pos_k, nk_s, nk_l, nk_t, rk_s, rk_l, rk_t;
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
-  DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len;
-  DBuf X32, X16, QKV, ATT, Y32, H, VT, X8, ATT8, H8;
+  DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len, attn_items;
+  DBuf X32, X16, QKV, ATT, Y32, H, X8, ATT8, H8;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
   bool last_logits = false;
@@ -216,8 +216,8 @@ void Lane::release_all() {
                  &tok_ids, &tok_off, &tok_len, &rec_tok, &rx_len_b, &rx_type_b, &rx_s, &rx_l, &rx_t, &labels, &logits,
                  &tok_flags, &rx_pos, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
                  &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
-                 &name_off, &name_len, &seqs, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
-                 &ATT, &Y32, &H, &VT, &X8, &ATT8, &H8};
+                 &name_off, &name_len, &seqs, &attn_items, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
+                 &ATT, &Y32, &H, &X8, &ATT8, &H8};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
@@ -454,7 +454,7 @@ void prof_collect(Lane* ln) {
 }
 
 as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
-                            bool want_logits) {
+                            bool want_logits, const int32_t* attn_items, int32_t n_items) {
   const as_config& g = c->cfg;
   const int64_t R = (int64_t)ch.rows;
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
@@ -514,8 +514,8 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
       if (g.attention == AS_ATTN_TCGEN05) {
         ProfScope ps(ln, 1, attn_flops);
-        CKS(attention_tcgen05(QKV, ln->VT.as<__nv_bfloat16>(), ATT, ln->seq_start.as<int32_t>(),
-                              ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+        CKS(attention_tcgen05(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), attn_items, n_items,
+                              (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
       } else {
         ProfScope ps(ln, 1, attn_flops);
         CKS(attention_bf16(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
@@ -572,7 +572,6 @@ as_status ensure_encoder_buffers(as_ctx* c, Lane* ln, uint64_t rows, uint64_t n_
   CKS(grow(ln->ATT, rows * d * act));
   // rows no sequence covers are never written by attention: keep them finite
   if (ln->ATT.p != att_before) CK(cudaMemsetAsync(ln->ATT.p, 0, ln->ATT.cap, ln->stream));
-  if (bf && g.attention == AS_ATTN_TCGEN05) CKS(grow(ln->VT, attention_vt_elems((int64_t)rows, (int32_t)d) * 2));
   CKS(grow(ln->H, rows * f * act));
   if (f8) {
     CKS(grow(ln->X8, rows * d));
@@ -805,10 +804,29 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     c->calibrating = true;
     CK(cudaMemsetAsync(c->amax_dev.p, 0, (size_t)kActPerLayer * g.n_layers * 4, st));
   }
-  for (const Chunk& ch : chunks) {
+  // tcgen05 attention work items (one per 128-query tile), all chunks in one upload
+  std::vector<int32_t> items;
+  std::vector<size_t> item_off{0};
+  const bool tc_attn = g.attention == AS_ATTN_TCGEN05 && g.precision == AS_BF16;
+  if (tc_attn) {
+    std::vector<int32_t> lens;
+    for (const Chunk& ch : chunks) {
+      lens.clear();
+      for (uint64_t i = ch.s0; i < ch.s1; ++i) lens.push_back((int32_t)seqs[i].len);
+      attention_items(lens.data(), (int32_t)lens.size(), items);
+      item_off.push_back(items.size());
+    }
+    CKS(grow(ln->attn_items, std::max<size_t>(items.size(), 1) * 4));
+    if (!items.empty())
+      CK(cudaMemcpyAsync(ln->attn_items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
+  }
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    const Chunk& ch = chunks[ci];
     double af = 0;  // attention FLOPs of the batch: QK^T and PV, 2 * 2 * L^2 * d per sequence
     for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
-    as_status es = run_encoder_chunk(c, ln, ch, ln->seqs.as<SeqDesc>(), af, want_logits);
+    as_status es = run_encoder_chunk(c, ln, ch, ln->seqs.as<SeqDesc>(), af, want_logits,
+                                     tc_attn ? ln->attn_items.as<int32_t>() + item_off[ci] : nullptr,
+                                     tc_attn ? (int32_t)(item_off[ci + 1] - item_off[ci]) : 0);
     if (es != AS_OK) {
       c->calibrating = false;
       return es;

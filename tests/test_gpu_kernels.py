@@ -131,33 +131,56 @@ def test_attention(prec, d, h):
 
 
 @pytest.mark.parametrize("d,h", [(128, 2), (768, 12), (1024, 16)])
-@pytest.mark.parametrize("lens", [[1, 5, 64, 65, 300, 512, 17, 128], [127, 128, 129, 255, 256, 257, 1000, 8, 2048]])
-def test_attention_tcgen05(d, h, lens):
-    """tcgen05 attention against the per-sequence softmax reference; starts on multiples of 8."""
-    g = torch.Generator(device="cpu").manual_seed(d + len(lens))
+@pytest.mark.parametrize("lens", [[1, 5, 64, 65, 300, 512, 17, 128], [127, 128, 129, 255, 256, 257, 1000, 8, 2048],
+                                  [63, 64, 65, 191, 192, 193, 33, 4096]])
+@pytest.mark.parametrize("gap", [0, 3])
+def test_attention_tcgen05(d, h, lens, gap):
+    """tcgen05 attention against the per-sequence softmax reference; packed (gap 0) and
+    with unused rows between sequences (gap 3: starts on any row)."""
+    g = torch.Generator(device="cpu").manual_seed(d + len(lens) + gap)
     lens = torch.tensor(lens, dtype=torch.int32)
     starts = torch.zeros_like(lens)
     for i in range(1, len(lens)):
-        starts[i] = ((int(starts[i - 1]) + int(lens[i - 1]) + 7) // 8) * 8 + 8 * (i % 3)
+        starts[i] = int(starts[i - 1]) + int(lens[i - 1]) + gap * (i % 3)
     rows = int(starts[-1] + lens[-1]) + 5
     qkv = torch.randn(rows, 3 * d, generator=g).to(DEV).to(torch.bfloat16)
     out = torch.full((rows, d), float("nan"), device=DEV, dtype=torch.bfloat16)
-    vt = torch.empty(d * ((rows + 7) // 8) * 8, device=DEV, dtype=torch.bfloat16)
-    api.attention_tc(qkv, vt, out, starts.to(DEV), lens.to(DEV), d, h)
+    api.attention_tc(qkv, out, starts.to(DEV), lens.to(DEV), d, h)
     torch.cuda.synchronize()
     ref = _ref_attention(qkv, starts, lens, d, h)
     for s0, L in zip(starts.tolist(), lens.tolist()):
         got = out[s0:s0 + L].float()
         assert torch.isfinite(got).all()
         assert (got - ref[s0:s0 + L]).abs().max().item() < 2.5e-2
+    # rows outside every sequence are not written
+    written = torch.zeros(rows, dtype=torch.bool)
+    for s0, L in zip(starts.tolist(), lens.tolist()):
+        written[s0:s0 + L] = True
+    assert torch.isnan(out[~written.to(DEV)].float()).all()
 
 
-def test_attention_tcgen05_rejects_unaligned():
+def test_attention_tcgen05_large_logits():
+    """Scores far apart (raises of the running maximum by more than 2^8) stay exact."""
+    d, h, L = 128, 2, 700
+    g = torch.Generator(device="cpu").manual_seed(5)
+    qkv = torch.randn(L, 3 * d, generator=g)
+    qkv[:, :d] *= 6.0          # |S| up to several hundred: exp2 range far beyond 2^8
+    qkv[:, d:2 * d] *= 6.0
+    qkv = qkv.to(DEV).to(torch.bfloat16)
+    out = torch.empty(L, d, device=DEV, dtype=torch.bfloat16)
+    st = torch.tensor([0], dtype=torch.int32)
+    ln = torch.tensor([L], dtype=torch.int32)
+    api.attention_tc(qkv, out, st.to(DEV), ln.to(DEV), d, h)
+    torch.cuda.synchronize()
+    ref = _ref_attention(qkv, st, ln, d, h)
+    assert (out.float() - ref).abs().max().item() < 5e-2
+
+
+def test_attention_tcgen05_rejects_out_of_range():
     qkv = torch.zeros(64, 3 * 128, device=DEV, dtype=torch.bfloat16)
     out = torch.zeros(64, 128, device=DEV, dtype=torch.bfloat16)
-    vt = torch.zeros(128 * 64, device=DEV, dtype=torch.bfloat16)
     with pytest.raises(api.AnonShieldError):
-        api.attention_tc(qkv, vt, out, torch.tensor([0, 13], dtype=torch.int32, device=DEV),
+        api.attention_tc(qkv, out, torch.tensor([0, 50], dtype=torch.int32, device=DEV),
                          torch.tensor([10, 20], dtype=torch.int32, device=DEV), 128, 2)
 
 
