@@ -94,14 +94,15 @@ typedef struct {
   uint64_t map_arena_bytes;      /* bytes for map originals; 0 = 256 MiB       */
   int32_t device;                /* CUDA device ordinal                        */
   uint32_t keep_trace;           /* 1: keep per-stage results for as_debug_*   */
-  uint32_t attention;            /* BF16 attention engine: AS_ATTN_MMA_SYNC or
-                                    AS_ATTN_TCGEN05 (0 = AS_ATTN_MMA_SYNC)      */
+  uint32_t attention;            /* BF16/FP8 attention engine: AS_ATTN_TCGEN05
+                                    (0, default) or AS_ATTN_MMA_SYNC           */
 } as_config;
 
-/* BF16 attention engines: flash-style on mma.sync m16n8k16 tensor cores, or
- * on tcgen05 with S and O in TMEM (see include/anonshield_kernels.h). */
-#define AS_ATTN_MMA_SYNC 0
-#define AS_ATTN_TCGEN05  1
+/* Attention engines of BF16 and FP8 contexts: persistent tcgen05 kernel with
+ * S, P and O in TMEM (default), or flash-style on mma.sync m16n8k16 tensor
+ * cores (see include/anonshield_kernels.h). Results agree to BF16 rounding. */
+#define AS_ATTN_TCGEN05  0
+#define AS_ATTN_MMA_SYNC 1
 
 /* Input records: one byte arena plus n_records + 1 offsets (offsets[0] = 0,
  * non-decreasing, offsets[n] = total bytes < 2^32). on_device = 0: host

@@ -24,7 +24,7 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 MODE = {"packed": 0, "per_record": 1}
 EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
 ENGINE = {"auto": 0, "tcgen05": 1, "simt": 2}
-ATTENTION = {"mma_sync": 0, "tcgen05": 1}
+ATTENTION = {"tcgen05": 0, "mma_sync": 1}
 
 
 class AnonShieldError(RuntimeError):
@@ -373,7 +373,7 @@ class Context:
 
     def __init__(self, dims, weights_blob: np.ndarray, vocab_words: list[bytes], precision: str = "bf16",
                  mode: str = "packed", max_chunk_tokens: int = 0, map_capacity: int = 0, map_arena_bytes: int = 0,
-                 keep_trace: bool = False, device: int = 0, attention: str = "mma_sync"):
+                 keep_trace: bool = False, device: int = 0, attention: str = "tcgen05"):
         lib = load()
         self.dims = dims
         self.device = device

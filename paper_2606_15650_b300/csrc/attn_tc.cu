@@ -1,26 +1,29 @@
 // Self-attention on the 5th-generation tensor cores (sm_103a), BF16 in,
 // FP32 softmax statistics and accumulation (encoder of AnonShield §2 stage (2)).
 //
-// One CTA computes one (sequence, head, 128-query tile), keys in tiles of 64:
-//   S_j = Q K_j^T           tcgen05.mma M=128 N=64 K=64, S in TMEM
-//   P_j = exp2(S_j*c - m)   four softmax warps, one query row per thread; the
-//                           whole 64-key row of S is read into registers in one
-//                           pass and S is released at once, so the MMA of
-//                           S_{j+1} overlaps the exp2 work on S_j; P rounded to
-//                           BF16 into shared memory (128-byte swizzle)
-//   O  += P_j V_j           tcgen05.mma M=128 N=64 K=64, O in TMEM
+// Persistent: two CTAs per SM, each looping over work units (one 128-query
+// tile of one sequence, one head); keys in tiles of 64, numbered globally
+// across a CTA's units (g), which fixes every buffer index and barrier phase.
+//   S_g = Q K_g^T           tcgen05.mma M=128 N=64 K=64 into one of two S
+//                           buffers in TMEM, issued two tiles ahead
+//   P_g = exp2(S_g*c - m)   four softmax warps, one query row per thread: the
+//                           64-key row of S is read in one pass and released,
+//                           P rounded to BF16 and stored back into one of two
+//                           P buffers in TMEM
+//   O  += P_g V_g           tcgen05.mma with A (P) from TMEM and B (V) from
+//                           shared memory; O in TMEM, read by the same warps
+//                           at the end of the unit (epilogue)
 // The maximum m that P is taken against is raised only when a row's true
 // maximum exceeds it by more than 2^8 (P stays <= 256), so O is rescaled in
 // TMEM only on those raises instead of on every growth of the maximum.
 // Q, K and V tiles come straight from the packed QKV rows by TMA: Q and K as
 // K-major operands, V as an MN-major B operand (keys along K, features
-// contiguous), so no transposed copy of V is made.
-// One thread issues both the TMA loads and the MMAs, polling its barriers
-// without blocking. P is double-buffered, so the softmax warps start on
-// tile j+1 while O += P_j V_j runs; K and V go through a 3-stage ring. A CTA is
-// five warps, 96 KB of shared memory and 128 TMEM columns: two CTAs per SM.
+// contiguous), so no transposed copy of V is made. K (4 stages) and V (4
+// stages) have rings of their own; Q is double-buffered across units.
+// Warps: Q/K loader, V loader, MMA issuer (one thread each, blocking on their
+// own barriers), four softmax warps. 96 KB shared memory, 256 TMEM columns.
 // Keys past the sequence end are masked to -inf; query rows past it are not
-// stored. Every mbarrier wait is bounded (see gemm_tc.cu); on a timeout the
+// stored. Every mbarrier wait is bounded (see gemm_tc.cu); on a timeout each
 // issuing thread waits (bounded) for its copies and MMAs in flight before the
 // CTA frees its TMEM.
 #include <algorithm>
@@ -36,7 +39,7 @@ namespace atc {
 
 constexpr int kQ = 128;        // query rows per CTA
 constexpr int kKT = 64;        // keys per tile
-constexpr int kThreads = 160;  // control (TMA + MMA), 4 softmax warps
+constexpr int kThreads = 224;  // Q/K loader, V loader, MMA issuer, 4 softmax warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 // Work item = one 128-query tile of one sequence: (sequence << 6) | q-tile.
@@ -46,7 +49,8 @@ struct Params {
   const int32_t* seq_len;
   const int32_t* items;
   int n_items;
-  __nv_bfloat16* out;
+  void* out;            // BF16, or E4M3 of value * out_inv_scale
+  float out_inv_scale;
   int d, n_heads;
   DevError* err;
 };
@@ -155,6 +159,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// A operand from TMEM (M lanes x K/2 columns, two 16-bit values per column,
+// the lower K index in the low half), B from shared memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -200,31 +214,37 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
 constexpr int kQBytes = kQ * 64 * 2;                 // 16 KB per buffer: Q tile, one 128-byte-swizzle panel
 constexpr int kKBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
 constexpr int kVBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
-constexpr int kPBytes = kQ * kKT * 2;                // 16 KB per buffer: P tile, 128 rows x 64 keys
-constexpr int kKVStages = 2;
+// K and V have rings of their own: a K stage is free as soon as S_g = Q K_g^T
+// is done, a V stage only after O += P_g V_g, which comes a softmax later.
+constexpr int kKStages = 4;
+constexpr int kVStages = 4;
 constexpr int kOffQ = 0;                             // 2 buffers (consecutive work units)
 constexpr int kOffK = kOffQ + 2 * kQBytes;
-constexpr int kOffV = kOffK + kKVStages * kKBytes;
-constexpr int kOffP = kOffV + kKVStages * kVBytes;   // 2 buffers (consecutive key tiles)
-constexpr int kOffBar = kOffP + 2 * kPBytes;
+constexpr int kOffV = kOffK + kKStages * kKBytes;
+constexpr int kOffBar = kOffV + kVStages * kVBytes;
 // mbarriers (8 bytes each)
 enum {
   kBarQFull = 0,     // [2] Q of a unit landed
   kBarQEmpty = 2,    // [2] the S MMAs of a unit are done with its Q
-  kBarKVFull = 4,    // [kKVStages]
-  kBarKVEmpty = 6,   // [kKVStages]
-  kBarSFull = 8,     // S_g in TMEM
-  kBarSEmpty = 9,    // softmax holds S_g in registers (128 arrivals)
-  kBarPFull = 10,    // [2] P_g in shared memory (128 arrivals)
-  kBarODone = 12,    // [2] O += P_g V_g done (by P buffer)
-  kBarOFree = 14,    // [2] epilogue has read an O buffer (128 arrivals)
-  kBarDrain = 16,
-  kNumBars = 17
+  kBarKFull = 4,     // [kKStages]
+  kBarKEmpty = 8,    // [kKStages]
+  kBarVFull = 12,    // [kVStages]
+  kBarVEmpty = 16,   // [kVStages]
+  kBarSFull = 20,    // [2] S_g in TMEM (by S buffer)
+  kBarSEmpty = 22,   // [2] softmax holds S_g in registers (128 arrivals)
+  kBarPFull = 24,    // [2] P_g in TMEM (128 arrivals)
+  kBarODone = 26,    // [2] O += P_g V_g done (by P buffer)
+  kBarDrain = 28,
+  kNumBars = 29
 };
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
 constexpr int kSmemAlloc = kSmemBytes + 1024;        // room to align the base to 1024 bytes
-constexpr uint32_t kTmemCols = 256;                  // S: cols 0..63, O buffers: 64..127 and 128..191
-constexpr uint32_t kColO = 64;
+// TMEM: S buffers at columns 0 and 64, O at 128, P buffers at 192 and 224.
+// One O suffices: the softmax warps read a unit's O (epilogue) before they
+// produce the next unit's first P, which the next O MMA waits for.
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kColO = 128;
+constexpr uint32_t kColP = 192;                      // P_g: 64 BF16 keys per row = 32 columns
 // P is exp2(t - m) against a row maximum m that is raised only when the true
 // maximum exceeds it by more than this (log2 units): P <= 2^8, and O and the
 // row sum are rescaled only on those rare raises.
@@ -245,8 +265,15 @@ __device__ __forceinline__ Work work_of(const Params& p, int u) {
   return w;
 }
 
+__device__ __forceinline__ uint16_t e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // Persistent: a CTA loops over its work units; tiles are numbered globally
 // across units (g), which fixes every buffer index and barrier phase.
+template <bool OUT8>
 __global__ void __launch_bounds__(kThreads, 2)
     attn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmKV, Params p) {
   extern __shared__ uint8_t smem_raw[];
@@ -265,19 +292,22 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_init(bar(kBarQEmpty + i), 1);
       mbar_init(bar(kBarPFull + i), 128);
       mbar_init(bar(kBarODone + i), 1);
-      mbar_init(bar(kBarOFree + i), 128);
+      mbar_init(bar(kBarSFull + i), 1);
+      mbar_init(bar(kBarSEmpty + i), 128);
     }
-    for (int i = 0; i < kKVStages; ++i) {
-      mbar_init(bar(kBarKVFull + i), 1);
-      mbar_init(bar(kBarKVEmpty + i), 1);
+    for (int i = 0; i < kKStages; ++i) {
+      mbar_init(bar(kBarKFull + i), 1);
+      mbar_init(bar(kBarKEmpty + i), 1);
     }
-    mbar_init(bar(kBarSFull), 1);
-    mbar_init(bar(kBarSEmpty), 128);
+    for (int i = 0; i < kVStages; ++i) {
+      mbar_init(bar(kBarVFull + i), 1);
+      mbar_init(bar(kBarVEmpty + i), 1);
+    }
     mbar_init(bar(kBarDrain), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
@@ -289,126 +319,125 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t tmem = *tmem_slot;
   const int d = p.d;
 
+  const int step = gridDim.x;
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- control: TMA loads and MMAs for three cursors over the
-      // same unit sequence, by polling: loads (Q of a unit, then its K_t, V_t),
-      // S_g = Q K_g^T (issued as soon as the softmax warps hold S_{g-1}, so it
-      // overlaps their exp2 work) and O += P_g V_g (once P_g is in shared memory).
-      constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
-      const int step = gridDim.x;
-      int ul = blockIdx.x, il = 0, tl = 0, gl = 0;  // loads
-      int us = blockIdx.x, is = 0, ts = 0, gs = 0;  // S
-      int uo = blockIdx.x, io = 0, to = 0, go = 0;  // O
-      bool ql = false, qs = false, of = false, issued_mma = false;
-      Work wl = work_of(p, ul), ws = wl, wo = wl;
-      uint64_t t_idle = 0;
-      uint32_t idle = 0;
-      while (uo < n_units) {
-        bool prog = false;
-        if (ul < n_units) {
-          if (!ql) {
-            const int b = il & 1;
-            if (il < 2 || mbar_test(bar(kBarQEmpty + b), ((il >> 1) - 1) & 1)) {
-              mbar_expect_tx(bar(kBarQFull + b), kQBytes);
-              tma_load_2d(sb + kOffQ + b * kQBytes, &tmQ, bar(kBarQFull + b), wl.h * 64, wl.row0 + wl.q0);
-              ql = true;
-              prog = true;
-            }
-          } else {
-            const int st = gl % kKVStages;
-            if (mbar_test(bar(kBarKVEmpty + st), ((gl / kKVStages) & 1) ^ 1u)) {
-              const int k0 = wl.row0 + tl * kKT;
-              mbar_expect_tx(bar(kBarKVFull + st), kKBytes + kVBytes);
-              tma_load_2d(sb + kOffK + st * kKBytes, &tmKV, bar(kBarKVFull + st), d + wl.h * 64, k0);
-              tma_load_2d(sb + kOffV + st * kVBytes, &tmKV, bar(kBarKVFull + st), 2 * d + wl.h * 64, k0);
-              ++gl;
-              prog = true;
-              if (++tl == wl.n_t) {
-                ul += step;
-                ++il;
-                tl = 0;
-                ql = false;
-                if (ul < n_units) wl = work_of(p, ul);
-              }
-            }
-          }
-        }
-        if (us < n_units && gs < gl) {
-          if (!qs) qs = mbar_test(bar(kBarQFull + (is & 1)), (is >> 1) & 1);
-          const int st = gs % kKVStages;
-          if (qs && mbar_test(bar(kBarKVFull + st), (gs / kKVStages) & 1) &&
-              (gs == 0 || mbar_test(bar(kBarSEmpty), (gs - 1) & 1))) {
-            fence_after();
-            const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
-            const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) mma_bf16(tmem, qdesc + 2 * k, kdesc + 2 * k, idS, k > 0 ? 1u : 0u);
-            mma_commit(bar(kBarSFull));
-            issued_mma = true;
-            ++gs;
-            prog = true;
-            if (++ts == ws.n_t) {
-              mma_commit(bar(kBarQEmpty + (is & 1)));
-              us += step;
-              ++is;
-              ts = 0;
-              qs = false;
-              if (us < n_units) ws = work_of(p, us);
-            }
-          }
-        }
-        if (go < gs) {
-          if (to == 0 && !of) of = io < 2 || mbar_test(bar(kBarOFree + (io & 1)), ((io >> 1) - 1) & 1);
-          if ((to > 0 || of) && mbar_test(bar(kBarPFull + (go & 1)), (go >> 1) & 1)) {
-            fence_after();
-            const uint64_t pdesc = sw128_desc(sb + kOffP + (go & 1) * kPBytes);
-            const uint64_t vdesc = sw128_desc_mn(sb + kOffV + (go % kKVStages) * kVBytes);
-            const uint32_t ocol = tmem + kColO + 64u * (uint32_t)(io & 1);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              mma_bf16(ocol, pdesc + 2 * k, vdesc + 128 * k, idO, (to > 0 || k > 0) ? 1u : 0u);
-            mma_commit(bar(kBarODone + (go & 1)));
-            mma_commit(bar(kBarKVEmpty + (go % kKVStages)));
-            ++go;
-            prog = true;
-            if (++to == wo.n_t) {
-              uo += step;
-              ++io;
-              to = 0;
-              of = false;
-              if (uo < n_units) wo = work_of(p, uo);
-            }
-          }
-        }
-        if (prog) {
-          idle = 0;
-        } else if ((++idle & 255u) == 0) {
-          if (*abort_flag) break;
-          const uint64_t now = globaltimer();
-          if (idle == 256) {
-            t_idle = now;
-          } else if (now - t_idle > kTimeoutNs) {
-            report_error(p.err, kErrTimeout, 41, blockIdx.x, (uint32_t)(gl | (gs << 16)));
-            *abort_flag = 1;
-            break;
-          }
+      // ---------------- Q and K loads, in unit order
+      int i = 0, g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += step, ++i) {
+        const Work w = work_of(p, u);
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(bar(kBarQEmpty + b), ((i >> 1) - 1) & 1, abort_flag, p.err, 40)) { ok = false; break; }
+        mbar_expect_tx(bar(kBarQFull + b), kQBytes);
+        tma_load_2d(sb + kOffQ + b * kQBytes, &tmQ, bar(kBarQFull + b), w.h * 64, w.row0 + w.q0);
+        for (int t = 0; t < w.n_t; ++t, ++g) {
+          const int st = g % kKStages;
+          if (!mbar_wait(bar(kBarKEmpty + st), ((g / kKStages) & 1) ^ 1u, abort_flag, p.err, 41)) { ok = false; break; }
+          mbar_expect_tx(bar(kBarKFull + st), kKBytes);
+          tma_load_2d(sb + kOffK + st * kKBytes, &tmKV, bar(kBarKFull + st), d + w.h * 64, w.row0 + t * kKT);
         }
       }
-      if (uo < n_units) {
-        // aborted: wait (bounded) for the copies and MMAs this thread started
+      if (!ok) {
+        // wait (bounded) for the loads still in flight: the last ones of each ring
         const uint64_t t0 = globaltimer();
-        const int q_issued = il + (ql ? 1 : 0);
-        for (int j = is; j < q_issued; ++j)
+        for (int j = max(0, g - kKStages); j < g; ++j)
+          while (!mbar_test(bar(kBarKFull + j % kKStages), (j / kKStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        for (int j = max(0, i - 1); j <= i; ++j)
           while (!mbar_test(bar(kBarQFull + (j & 1)), (j >> 1) & 1) && globaltimer() - t0 < kTimeoutNs) {
           }
-        for (int j = gs; j < gl; ++j)
-          while (!mbar_test(bar(kBarKVFull + j % kKVStages), (j / kKVStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- V loads, in unit order (a ring of their own: a V stage
+      // frees only after O += P V, later than the K stage of the same tile)
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += step) {
+        const Work w = work_of(p, u);
+        for (int t = 0; t < w.n_t; ++t, ++g) {
+          const int st = g % kVStages;
+          if (!mbar_wait(bar(kBarVEmpty + st), ((g / kVStages) & 1) ^ 1u, abort_flag, p.err, 42)) { ok = false; break; }
+          mbar_expect_tx(bar(kBarVFull + st), kVBytes);
+          tma_load_2d(sb + kOffV + st * kVBytes, &tmKV, bar(kBarVFull + st), 2 * d + w.h * 64, w.row0 + t * kKT);
+        }
+      }
+      if (!ok) {
+        const uint64_t t0 = globaltimer();
+        for (int j = max(0, g - kVStages); j < g; ++j)
+          while (!mbar_test(bar(kBarVFull + j % kVStages), (j / kVStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
           }
-        if (issued_mma) {
-          mma_commit(bar(kBarDrain));
-          while (!mbar_test(bar(kBarDrain), 0) && globaltimer() - t0 < kTimeoutNs) {
-          }
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: S_0, S_1, then S_{g+2} before O_g for every g:
+      // S runs two tiles ahead of the softmax warps (two S buffers in TMEM)
+      constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
+      int us = blockIdx.x, is = 0, ts = 0, gs = 0;  // S cursor
+      int uo = blockIdx.x, io = 0, to = 0, go = 0;  // O cursor
+      Work ws = work_of(p, us), wo = ws;
+      bool ok = true, issued = false;
+      auto issue_s = [&]() -> bool {
+        const int st = gs % kKStages;
+        if (ts == 0 && !mbar_wait(bar(kBarQFull + (is & 1)), (is >> 1) & 1, abort_flag, p.err, 50)) return false;
+        if (!mbar_wait(bar(kBarKFull + st), (gs / kKStages) & 1, abort_flag, p.err, 51)) return false;
+        const int sbuf = gs & 1;
+        if (gs >= 2 && !mbar_wait(bar(kBarSEmpty + sbuf), ((gs >> 1) - 1) & 1, abort_flag, p.err, 52)) return false;
+        fence_after();
+        const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
+        const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16(tmem + 64u * (uint32_t)sbuf, qdesc + 2 * k, kdesc + 2 * k, idS, k > 0 ? 1u : 0u);
+        mma_commit(bar(kBarSFull + sbuf));
+        mma_commit(bar(kBarKEmpty + st));
+        issued = true;
+        ++gs;
+        if (++ts == ws.n_t) {
+          mma_commit(bar(kBarQEmpty + (is & 1)));
+          us += step;
+          ++is;
+          ts = 0;
+          if (us < n_units) ws = work_of(p, us);
+        }
+        return true;
+      };
+      auto issue_o = [&]() -> bool {
+        const int st = go % kVStages;
+        if (!mbar_wait(bar(kBarPFull + (go & 1)), (go >> 1) & 1, abort_flag, p.err, 54)) return false;
+        if (!mbar_wait(bar(kBarVFull + st), (go / kVStages) & 1, abort_flag, p.err, 55)) return false;
+        fence_after();
+        const uint32_t pcol = tmem + kColP + 32u * (uint32_t)(go & 1);
+        const uint64_t vdesc = sw128_desc_mn(sb + kOffV + st * kVBytes);
+        const uint32_t ocol = tmem + kColO;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16_ta(ocol, pcol + 8 * k, vdesc + 128 * k, idO, (to > 0 || k > 0) ? 1u : 0u);
+        mma_commit(bar(kBarODone + (go & 1)));
+        mma_commit(bar(kBarVEmpty + st));
+        ++go;
+        if (++to == wo.n_t) {
+          uo += step;
+          ++io;
+          to = 0;
+          if (uo < n_units) wo = work_of(p, uo);
+        }
+        return true;
+      };
+      ok = issue_s();
+      if (ok && us < n_units) ok = issue_s();
+      while (ok && uo < n_units) {
+        if (us < n_units) ok = issue_s();
+        if (ok) ok = issue_o();
+      }
+      if (!ok && issued) {
+        // wait (bounded) for the MMAs in flight before the TMEM is freed
+        mma_commit(bar(kBarDrain));
+        const uint64_t t0 = globaltimer();
+        while (!mbar_test(bar(kBarDrain), 0) && globaltimer() - t0 < kTimeoutNs) {
         }
       }
     }
@@ -426,30 +455,31 @@ __global__ void __launch_bounds__(kThreads, 2)
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
       const Work w = work_of(p, u);
-      const uint32_t ocol = kColO + 64u * (uint32_t)(i & 1);
+      const uint32_t ocol = kColO;
       float m = -INFINITY, l = 0.f;              // m: the maximum P is taken against
       for (int t = 0; t < w.n_t; ++t, ++g) {
         const int valid = min(kKT, w.L - t * kKT);  // keys of this tile inside the sequence
-        if (!warp_wait(bar(kBarSFull), g & 1, abort_flag, p.err, 60)) { ok = false; break; }
+        if (!warp_wait(bar(kBarSFull + (g & 1)), (g >> 1) & 1, abort_flag, p.err, 60)) { ok = false; break; }
         fence_after();
         uint32_t v[64];
-        tmem_ld64(trow, v);
+        tmem_ld64(trow + 64u * (uint32_t)(g & 1), v);
         fence_before();
-        mbar_arrive(bar(kBarSEmpty));            // S_g is in registers: S_{g+1} may overwrite it
+        mbar_arrive(bar(kBarSEmpty + (g & 1)));  // S_g is in registers: S_{g+2} may overwrite it
         // row maximum of the raw scores (keys past the end masked to -inf); the
         // scale c > 0 is applied in the exp2 argument: t = s * c - m
-        float mxr = -INFINITY;
-        if (valid == kKT) {
+        if (valid < kKT) {
 #pragma unroll
-          for (int q = 0; q < 64; ++q) mxr = fmaxf(mxr, __uint_as_float(v[q]));
-        } else {
-#pragma unroll
-          for (int q = 0; q < 64; ++q) {
+          for (int q = 0; q < 64; ++q)
             if (q >= valid) v[q] = __float_as_uint(-INFINITY);
-            mxr = fmaxf(mxr, __uint_as_float(v[q]));
-          }
         }
-        const float mx = mxr * c;
+        // eight independent running maxima, then a tree: short dependency chains
+        float m8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) m8[q] = __uint_as_float(v[q]);
+#pragma unroll
+        for (int q = 8; q < 64; ++q) m8[q & 7] = fmaxf(m8[q & 7], __uint_as_float(v[q]));
+        const float mx =
+            fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7]))) * c;
         // tcgen05.ld / st are warp-collective: the warp raises together when any
         // of its rows needs it (a row that does not multiplies by <= 1, exactly)
         if (__any_sync(0xffffffffu, mx > m + kRescaleSlack)) {
@@ -472,58 +502,70 @@ __global__ void __launch_bounds__(kThreads, 2)
           m = mn;
         }
         // P packed in place: the pair (2q, 2q+1) goes to v[q], already read
-        float sum = 0.f;
+        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 64; q += 2) {
           const float p0 = ex2_approx(fmaf(__uint_as_float(v[q]), c, -m));
           const float p1 = ex2_approx(fmaf(__uint_as_float(v[q + 1]), c, -m));
-          sum += p0 + p1;
+          s8[(q >> 1) & 7] += p0 + p1;
           __nv_bfloat162 b = __floats2bfloat162_rn(p0, p1);
           v[q >> 1] = *reinterpret_cast<uint32_t*>(&b);
         }
-        l += sum;
-        // P_g goes to buffer g&1 once O += P_{g-2} V_{g-2} has read it
+        l += ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+        // P_g goes to TMEM buffer g&1 once O += P_{g-2} V_{g-2} has read it
         if (g >= 2 && !wait_o(g - 2, 62)) { ok = false; break; }
-        uint8_t* prow = smem + kOffP + (g & 1) * kPBytes + r * 128;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<uint4*>(prow + ((q ^ (r & 7)) << 4)) =
-              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        fence_proxy_async();
+        fence_after();
+        tmem_st32(trow + kColP + 32u * (uint32_t)(g & 1), *reinterpret_cast<uint32_t(*)[32]>(&v[0]));
         fence_before();
         mbar_arrive(bar(kBarPFull + (g & 1)));
       }
       if (!ok) break;
-      // epilogue: O_{g-1} is this unit's last update; its buffer is released
-      // for unit i+2 as soon as it is in registers
+      // epilogue: O_{g-1} is this unit's last update (the next unit's first
+      // O MMA waits for P, which these warps write only after this read)
       if (!wait_o(g - 1, 63)) { ok = false; break; }
       fence_after();
       uint32_t v[64];
       tmem_ld64(trow + ocol, v);
-      fence_before();
-      mbar_arrive(bar(kBarOFree + (i & 1)));
       if (w.q0 + r < w.L) {
-        const float inv = 1.f / l;
-        __nv_bfloat16* o = p.out + (size_t)(w.row0 + w.q0 + r) * d + w.h * 64;
+        const size_t off = (size_t)(w.row0 + w.q0 + r) * d + w.h * 64;
+        if (OUT8) {
+          const float inv = p.out_inv_scale / l;
+          uint8_t* o = static_cast<uint8_t*>(p.out) + off;
 #pragma unroll
-        for (int q = 0; q < 64; q += 8) {
-          uint4 x;
-          __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
-          __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
-          __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
-          x.x = *reinterpret_cast<uint32_t*>(&a0);
-          x.y = *reinterpret_cast<uint32_t*>(&a1);
-          x.z = *reinterpret_cast<uint32_t*>(&a2);
-          x.w = *reinterpret_cast<uint32_t*>(&a3);
-          *reinterpret_cast<uint4*>(o + q) = x;
+          for (int q = 0; q < 64; q += 16) {
+            uint4 x;
+            uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              xw[k] = (uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k]) * inv, __uint_as_float(v[q + 4 * k + 1]) * inv) |
+                      ((uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k + 2]) * inv,
+                                        __uint_as_float(v[q + 4 * k + 3]) * inv)
+                       << 16);
+            *reinterpret_cast<uint4*>(o + q) = x;
+          }
+        } else {
+          const float inv = 1.f / l;
+          __nv_bfloat16* o = static_cast<__nv_bfloat16*>(p.out) + off;
+#pragma unroll
+          for (int q = 0; q < 64; q += 8) {
+            uint4 x;
+            __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
+            __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
+            __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
+            x.x = *reinterpret_cast<uint32_t*>(&a0);
+            x.y = *reinterpret_cast<uint32_t*>(&a1);
+            x.z = *reinterpret_cast<uint32_t*>(&a2);
+            x.w = *reinterpret_cast<uint32_t*>(&a3);
+            *reinterpret_cast<uint4*>(o + q) = x;
+          }
         }
       }
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 2) {
     __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -560,9 +602,10 @@ void attention_items(const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>
     for (int32_t qt = 0; qt * atc::kQ < seq_len[s]; ++qt) items.push_back((s << 6) | qt);
 }
 
-as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
-                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
-                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
+namespace {
+as_status attention_tc_launch(bool out8, const __nv_bfloat16* qkv, void* out, float out_scale, const int32_t* seq_start,
+                              const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+                              int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
   if (n_items == 0 || max_len == 0 || rows == 0) return AS_OK;
   if (d_model != n_heads * 64 || d_model % 64 || max_len > 4096 || rows > (1ll << 31) - 8 ||
       (reinterpret_cast<uintptr_t>(qkv) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) {
@@ -586,7 +629,10 @@ as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const 
   int dev = 0;
   cudaGetDevice(&dev);
   if (!g_attn_attr_set[dev & 63].load()) {
-    AS_CUDA_OK(cudaFuncSetAttribute(atc::attn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, atc::kSmemAlloc));
+    AS_CUDA_OK(cudaFuncSetAttribute(atc::attn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    atc::kSmemAlloc));
+    AS_CUDA_OK(cudaFuncSetAttribute(atc::attn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    atc::kSmemAlloc));
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     g_attn_sms[dev & 63].store(n > 0 ? n : 148);
@@ -602,15 +648,39 @@ as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const 
   p.items = items;
   p.n_items = n_items;
   p.out = out;
+  p.out_inv_scale = out8 ? 1.0f / out_scale : 1.0f;
   p.d = d_model;
   p.n_heads = n_heads;
   p.err = err;
   const int64_t units = (int64_t)n_items * n_heads;
   const int grid = (int)std::min<int64_t>(units, 2ll * g_attn_sms[dev & 63].load());  // two CTAs per SM, persistent
-  atc::attn_tc_kernel<<<grid, atc::kThreads, atc::kSmemAlloc, st>>>(tmQ, tmKV, p);
+  if (out8)
+    atc::attn_tc_kernel<true><<<grid, atc::kThreads, atc::kSmemAlloc, st>>>(tmQ, tmKV, p);
+  else
+    atc::attn_tc_kernel<false><<<grid, atc::kThreads, atc::kSmemAlloc, st>>>(tmQ, tmKV, p);
   count_launch();
   AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
+}
+
+}  // namespace
+
+as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
+                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
+  return attention_tc_launch(false, qkv, out, 1.0f, seq_start, seq_len, items, n_items, max_len, rows, d_model,
+                             n_heads, err, st);
+}
+
+as_status attention_tcgen05_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* seq_start,
+                                 const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+                                 int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
+  if (!(out_scale > 0.f)) {
+    set_k_error("attention_tcgen05_e4m3: out_scale must be positive");
+    return AS_ERR_ARG;
+  }
+  return attention_tc_launch(true, qkv, out, out_scale, seq_start, seq_len, items, n_items, max_len, rows, d_model,
+                             n_heads, err, st);
 }
 
 }  // namespace as

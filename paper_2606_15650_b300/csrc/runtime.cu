@@ -495,8 +495,12 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS, true, false, R, 3 * d, d, X8, L.w_qkv8, L.b_qkv, nullptr, QKV,
                             sc[0] * L.s_qkv, 1.0f, err, st)); }
       { ProfScope ps(ln, 1, attn_flops);
-        CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
-                                (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
+        if (g.attention == AS_ATTN_TCGEN05)
+          CKS(attention_tcgen05_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(),
+                                     attn_items, n_items, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+        else
+          CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
+                                  (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
       { ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
                             1.0f, err, st)); }
@@ -807,7 +811,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   // tcgen05 attention work items (one per 128-query tile), all chunks in one upload
   std::vector<int32_t> items;
   std::vector<size_t> item_off{0};
-  const bool tc_attn = g.attention == AS_ATTN_TCGEN05 && g.precision == AS_BF16;
+  const bool tc_attn = g.attention == AS_ATTN_TCGEN05 && g.precision != AS_FP32;
   if (tc_attn) {
     std::vector<int32_t> lens;
     for (const Chunk& ch : chunks) {

@@ -71,10 +71,12 @@ def test_c1_parity(c1, vocab_words, vocab_index, prec, mode, attention):
     ctx.close()
 
 
-@pytest.fixture(scope="module")
-def fp8_ctx(c1, vocab_words):
+@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
+def fp8_ctx(c1, vocab_words, request):
+    """FP8 context (attention writing E4M3) on each attention engine."""
     recs, w, key, ref = c1
-    ctx = api.Context(DIMS, synth.pack_blob(DIMS, w), vocab_words, precision="fp8", keep_trace=True)
+    ctx = api.Context(DIMS, synth.pack_blob(DIMS, w), vocab_words, precision="fp8", keep_trace=True,
+                      attention=request.param)
     cal = synth.make_records(synth.scaled(synth.C1, 64).records, vocab_words, seed=synth.SEED_CALIB)
     ctx.calibrate(cal.data, cal.offsets, SCHEMA)
     return ctx
