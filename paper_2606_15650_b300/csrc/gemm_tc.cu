@@ -178,6 +178,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // GELU 0.5 x (1 + erf(x / sqrt 2)) for the BF16 epilogue. erf uses the
 // rational approximation of Abramowitz & Stegun, Handbook of Mathematical
 // Functions, eq. 7.1.26 (|error| <= 1.5e-7): erf(z) = 1 - t (a1 + t (a2 + t (a3
@@ -221,18 +231,20 @@ template <int N>
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Epilogue staging: each epilogue warp owns two 32x32 chunk buffers. BF16
-// chunks have 64-byte rows stored with the 64-byte TMA swizzle (16-byte
-// piece j of row r at j ^ ((r >> 1) & 3)); FP32 chunks have 128-byte rows
-// with the 128-byte swizzle (piece j at j ^ (r & 7)); E4M3 chunks have
-// 32-byte rows with the 32-byte swizzle (piece j at j ^ ((r >> 2) & 1)). The
-// warp writes (and, for the residual, reads) one row per lane without bank
-// conflicts, and the TMA engine moves whole lines to and from global memory.
+// Epilogue staging: each epilogue warp owns two chunk buffers of 32 rows.
+// BF16 chunks are 32 columns with 64-byte rows stored with the 64-byte TMA
+// swizzle (16-byte piece j of row r at j ^ ((r >> 1) & 3)); FP32 chunks are
+// 16 columns, also 64-byte rows with the 64-byte swizzle (2 KB per buffer, so
+// the residual GEMMs keep room for four pipeline stages); E4M3 chunks are 32
+// columns, 32-byte rows with the 32-byte swizzle (piece j at j ^ ((r >> 2) &
+// 1)). The warp writes (and, for the residual, reads) one row per lane without
+// bank conflicts, and the TMA engine moves whole lines to and from global memory.
 template <int OUT>
 struct EpiTraits {
   static constexpr bool kF32 = OUT == kOutF32;
   static constexpr int kEsize = OUT == kOutF32 ? 4 : (OUT == kOutBF16 ? 2 : 1);
-  static constexpr int kChunkBytes = 32 * 32 * kEsize;
+  static constexpr int kCols = OUT == kOutF32 ? 16 : 32;   // columns per chunk
+  static constexpr int kChunkBytes = 32 * kCols * kEsize;
 };
 
 template <int BN, int STAGES, int OUT>
@@ -259,7 +271,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
   constexpr uint32_t kIdesc = IN == kInE4M3 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
   constexpr int kBKe = bk_elems(IN);
-  constexpr int CH = BN / 64;              // 32-column chunks per epilogue warp and tile
+  constexpr int CW = E::kCols;             // columns per chunk
+  constexpr int CH = BN / 2 / CW;          // chunks per epilogue warp and tile (a warp owns half the columns)
   static_assert(CH % 2 == 0, "chunks alternate between two staging buffers");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -375,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
             mbar_expect_tx(resid_bar(ew, i), E::kChunkBytes);
-            tma_load_2d(stg + i * E::kChunkBytes, &tmR, resid_bar(ew, i), n0 + (half * CH + i) * 32, row0);
+            tma_load_2d(stg + i * E::kChunkBytes, &tmR, resid_bar(ew, i), n0 + (half * CH + i) * CW, row0);
           }
         }
         __syncwarp();
@@ -386,12 +399,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < CH; ++i) {
         const int c = half * CH + i;
         const int buf = i & 1;
-        uint32_t rr[32];
-        tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN + c * 32, rr);
-        const int n = n0 + c * 32;
-        float v[32];
+        uint32_t rr[CW];
+        {
+          const uint32_t ta = tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN + c * CW;
+          if constexpr (CW == 32) tmem_ld32(ta, rr); else tmem_ld16(ta, rr);
+        }
+        const int n = n0 + c * CW;
+        float v[CW];
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
+        for (int j = 0; j < CW; j += 4) {
           float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
           v[j + 0] = fmaf(__uint_as_float(rr[j + 0]), p.alpha, b.x);
           v[j + 1] = fmaf(__uint_as_float(rr[j + 1]), p.alpha, b.y);
@@ -404,15 +420,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t par = (lt * (CH / 2) + (i >> 1)) & 1u;
           if (!warp_wait(resid_bar(ew, buf), par, abort_flag, p.err, 31)) break;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float4* q = reinterpret_cast<float4*>(cb + r * 128 + ((j ^ (r & 7)) << 4));
+          for (int j = 0; j < CW / 4; ++j) {
+            float4* q = reinterpret_cast<float4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
             float4 x = *q;
             *q = make_float4(v[4 * j] + x.x, v[4 * j + 1] + x.y, v[4 * j + 2] + x.z, v[4 * j + 3] + x.w);
           }
         } else {
           if (EPI == AS_EPI_BIAS_GELU) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = gelu_erf(v[j]);
+            for (int j = 0; j < CW; ++j) v[j] = gelu_erf(v[j]);
           }
           if (lane == 0) bulk_wait_read<1>();  // the store two chunks back has read this buffer
           __syncwarp();
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // store has read it
             bulk_wait_read<0>();
             mbar_expect_tx(resid_bar(ew, buf), E::kChunkBytes);
-            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + 64, row0);
+            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + 2 * CW, row0);
           }
         }
       }
@@ -537,11 +553,11 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   if (s == AS_OK) s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN, CU_TENSOR_MAP_SWIZZLE_128B);
   if (s == AS_OK) {
     if (OUT == tc::kOutF32) {
-      s = make_map(&tmC, p0.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
-                   CU_TENSOR_MAP_SWIZZLE_128B);
+      s = make_map(&tmC, p0.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32,
+                   CU_TENSOR_MAP_SWIZZLE_64B);
       if (s == AS_OK)
-        s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32,
-                     CU_TENSOR_MAP_SWIZZLE_128B);
+        s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32,
+                     CU_TENSOR_MAP_SWIZZLE_64B);
     } else if (OUT == tc::kOutE4M3) {
       s = make_map(&tmC, p0.out, u8, 1, (uint64_t)p0.M, (uint64_t)p0.N, 32, 32, CU_TENSOR_MAP_SWIZZLE_32B);
       tmR = tmC;  // unused
@@ -578,8 +594,8 @@ as_status dispatch(const tc::Params& p, int epi, bool out_e4m3, const void* A, c
                   : launch_bn<128, 6, AS_EPI_BIAS_GELU, IN, tc::kOutBF16>(p, A, B, st);
     case AS_EPI_BIAS_RESID:
       if (out_e4m3) break;
-      return wide ? launch_bn<256, 3, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st)
-                  : launch_bn<128, 4, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st);
+      return wide ? launch_bn<256, 4, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st)
+                  : launch_bn<128, 6, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st);
     default:
       break;
   }
