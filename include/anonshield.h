@@ -272,6 +272,30 @@ as_status as_serve_stats(as_ctx* ctx, as_serve_stats_t* stats, uint32_t reset);
 /* Finish every admitted request, then stop the workers. */
 as_status as_serve_stop(as_ctx* ctx);
 
+/* Tile autotuner for the encoder's four tcgen05 projection GEMMs (per
+ * layer: QKV, attention output + residual, FFN1 + GELU, FFN2 + residual).
+ * Configurations: bit 0 = tile order (0: along N within a 128-row block,
+ * 1: along M within a column block), bit 1 = 128-column tiles with 6
+ * pipeline stages instead of 256-column tiles with 4 (cfg 0 and 1 need
+ * N % 256 == 0); -1 = the built-in default (cfg 0 when valid, else 2).
+ * as_autotune times every valid configuration of each projection at `rows`
+ * rows (0 = the ctx's batch size, max_chunk_tokens) on the ctx's stream with
+ * the ctx's weights and scratch activations, keeps the fastest for later
+ * calls and reports all timings (ms < 0: not valid). Results do not depend on
+ * the configuration (the tile only changes which CTA computes an output).
+ * AS_ERR_UNSUPPORTED for FP32 contexts (CUDA-core GEMM). as_set_tiles /
+ * as_get_tiles store or read the choices, e.g. to reuse a saved tuning. */
+#define AS_TUNE_ROLES 4
+typedef struct {
+  uint32_t role;       /* 0 QKV, 1 attention output, 2 FFN1, 3 FFN2        */
+  uint64_t m, n, k;
+  int32_t chosen;
+  float ms[4];         /* per configuration; negative = not valid           */
+} as_tune_entry;
+as_status as_autotune(as_ctx* ctx, uint64_t rows, as_tune_entry entries[AS_TUNE_ROLES]);
+as_status as_set_tiles(as_ctx* ctx, const int32_t cfg[AS_TUNE_ROLES]);
+as_status as_get_tiles(as_ctx* ctx, int32_t cfg[AS_TUNE_ROLES]);
+
 /* FP8 contexts: set the static activation scales from a calibration set.
  * Runs the tokenizer and the BF16 encoder over `records` (same layout rules
  * as as_anonymize) and records, for each FP8 GEMM input (per layer: the QKV,

@@ -89,6 +89,14 @@ class _StreamConfig(C.Structure):
     _fields_ = [("batch_bytes", C.c_uint64), ("lanes", C.c_uint32)]
 
 
+class _TuneEntry(C.Structure):
+    _fields_ = [("role", C.c_uint32), ("m", C.c_uint64), ("n", C.c_uint64), ("k", C.c_uint64),
+                ("chosen", C.c_int32), ("ms", C.c_float * 4)]
+
+
+TUNE_ROLES = ("qkv", "attn_out", "ffn1", "ffn2")
+
+
 class _Profile(C.Structure):
     _fields_ = [("gemm_launches", C.c_uint64), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
                 ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double)]
@@ -97,7 +105,7 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
@@ -138,6 +146,9 @@ def load() -> C.CDLL:
     lib.as_calibrate.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema)]
     lib.as_get_scales.argtypes = [P, P, C.c_uint64]
     lib.as_set_scales.argtypes = [P, P, C.c_uint64]
+    lib.as_autotune.argtypes = [P, C.c_uint64, C.POINTER(_TuneEntry)]
+    lib.as_set_tiles.argtypes = [P, C.POINTER(C.c_int32)]
+    lib.as_get_tiles.argtypes = [P, C.POINTER(C.c_int32)]
     lib.as_anonymize_stream.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t,
                                         C.POINTER(_StreamConfig), C.POINTER(P)]
     lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
@@ -445,6 +456,22 @@ class Context:
         del names
         self._check(st)
         return Output(self, out.value)
+
+    def autotune(self, rows: int = 0) -> list[dict]:
+        """Time every tile configuration of the four projection GEMMs; keep the fastest."""
+        ent = (_TuneEntry * 4)()
+        self._check(load().as_autotune(self._h, rows, ent))
+        return [{"role": TUNE_ROLES[e.role], "m": e.m, "n": e.n, "k": e.k, "chosen": e.chosen,
+                 "ms": [float(x) for x in e.ms]} for e in ent]
+
+    def set_tiles(self, cfg: list[int]):
+        arr = (C.c_int32 * 4)(*cfg)
+        self._check(load().as_set_tiles(self._h, arr))
+
+    def tiles(self) -> list[int]:
+        arr = (C.c_int32 * 4)()
+        self._check(load().as_get_tiles(self._h, arr))
+        return list(arr)
 
     def calibrate(self, data, offsets, schema: Schema):
         """FP8: set static activation scales from calibration records (host arrays)."""

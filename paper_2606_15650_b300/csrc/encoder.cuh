@@ -13,10 +13,15 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
                        const float* resid, void* out, DevError* err, cudaStream_t st);
 // General form: A and B in BF16 or E4M3 (in_e4m3), output BF16 / FP32 (by
 // epilogue) or E4M3 (out_e4m3, GELU epilogue only, value / out_scale with
-// saturation); out = epi(alpha * (A . B^T)).
+// saturation); out = epi(alpha * (A . B^T)). cfg: tile configuration
+// 0..kGemmCfgs-1 (bit 0: tile order along M instead of N; bit 1: 128-column
+// tiles, 6 stages, instead of 256-column tiles, 4 stages), -1 = the default
+// (256-column tiles when N allows, order along N).
+constexpr int kGemmCfgs = 4;
+bool gemm_tcgen05_cfg_valid(int cfg, int64_t N);
 as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
                           const void* B, const float* bias, const float* resid, void* out, float alpha,
-                          float out_scale, DevError* err, cudaStream_t st);
+                          float out_scale, DevError* err, cudaStream_t st, int cfg = -1);
 // Same contract in FP32 on CUDA cores.
 as_status gemm_simt_f32(int epi, int64_t M, int64_t N, int64_t K, const float* A, const float* B, const float* bias,
                         const float* resid, float* out, cudaStream_t st);

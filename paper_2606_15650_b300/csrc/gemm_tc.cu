@@ -44,6 +44,7 @@ constexpr uint64_t kTimeoutNs = 2000000000ull;
 struct Params {
   int M, N, K;
   int n_tiles_n, n_tiles;
+  int raster;           // tile order: 0 = along N within a row block, 1 = along M within a column block
   int epi;
   const float* bias;
   const float* resid;
@@ -54,6 +55,18 @@ struct Params {
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Output tile t -> (first row, first column).
+__device__ __forceinline__ void tile_origin(const Params& p, int t, int bn, int& m0, int& n0) {
+  if (p.raster == 0) {
+    m0 = (t / p.n_tiles_n) * 128;
+    n0 = (t % p.n_tiles_n) * bn;
+  } else {
+    const int n_tiles_m = p.n_tiles / p.n_tiles_n;
+    m0 = (t % n_tiles_m) * 128;
+    n0 = (t / n_tiles_m) * bn;
+  }
+}
 
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -326,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- TMA producer
       uint32_t it = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
-        const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
+        int m0, n0;
+        tile_origin(p, tile, BN, m0, n0);
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -379,7 +393,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t lt = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
-      const int m0 = (tile / p.n_tiles_n) * kBM, n0 = (tile % p.n_tiles_n) * BN;
+      int m0, n0;
+      tile_origin(p, tile, BN, m0, n0);
       const int row0 = m0 + sub * 32;
       if (E::kF32) {
         // residual chunks of this tile: fetched before the accumulator is ready
@@ -578,9 +593,17 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   return AS_OK;
 }
 
+// Tile configurations (the autotuner's choices): cfg & 1 = raster order,
+// cfg & 2 = 128-column tiles (6 stages) instead of 256-column tiles (4 stages).
 template <int IN>
-as_status dispatch(const tc::Params& p, int epi, bool out_e4m3, const void* A, const void* B, cudaStream_t st) {
-  const bool wide = p.N % 256 == 0;
+as_status dispatch(const tc::Params& p0, int epi, bool out_e4m3, const void* A, const void* B, cudaStream_t st,
+                   int cfg) {
+  tc::Params p = p0;
+  bool wide = p.N % 256 == 0;
+  if (cfg >= 0) {
+    p.raster = cfg & 1;
+    if (cfg & 2) wide = false;
+  }
   switch (epi) {
     case AS_EPI_BIAS:
       if (out_e4m3) break;
@@ -605,9 +628,11 @@ as_status dispatch(const tc::Params& p, int epi, bool out_e4m3, const void* A, c
 
 }  // namespace
 
+bool gemm_tcgen05_cfg_valid(int cfg, int64_t N) { return cfg >= 0 && cfg < kGemmCfgs && ((cfg & 2) || N % 256 == 0); }
+
 as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
                           const void* B, const float* bias, const float* resid, void* out, float alpha,
-                          float out_scale, DevError* err, cudaStream_t st) {
+                          float out_scale, DevError* err, cudaStream_t st, int cfg) {
   as_status s = ensure_driver();
   if (s != AS_OK) return s;
   if (g_num_sms.load() == 0) {
@@ -635,12 +660,17 @@ as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64
   p.err = err;
   p.alpha = alpha;
   p.out_scale_inv = out_e4m3 ? 1.0f / out_scale : 1.0f;
-  return in_e4m3 ? dispatch<tc::kInE4M3>(p, epi, out_e4m3, A, B, st) : dispatch<tc::kInBF16>(p, epi, out_e4m3, A, B, st);
+  if (cfg >= 0 && !gemm_tcgen05_cfg_valid(cfg, N)) {
+    set_k_error("gemm_tcgen05: tile configuration not valid for this shape");
+    return AS_ERR_ARG;
+  }
+  return in_e4m3 ? dispatch<tc::kInE4M3>(p, epi, out_e4m3, A, B, st, cfg)
+                 : dispatch<tc::kInBF16>(p, epi, out_e4m3, A, B, st, cfg);
 }
 
 as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
                        const float* resid, void* out, DevError* err, cudaStream_t st) {
-  return gemm_tcgen05_ex(epi, false, false, M, N, K, A, B, bias, resid, out, 1.0f, 1.0f, err, st);
+  return gemm_tcgen05_ex(epi, false, false, M, N, K, A, B, bias, resid, out, 1.0f, 1.0f, err, st, -1);
 }
 
 }  // namespace as

@@ -192,6 +192,7 @@ struct as_ctx {
   uint32_t slug_len = 10;
   std::atomic<uint64_t> n_entries_seen{0};  // map size after the previous call
   Server* server = nullptr;                 // serving loop (as_serve_start)
+  int gemm_cfg[AS_TUNE_ROLES] = {-1, -1, -1, -1};  // tile configuration per projection (as_autotune)
   std::vector<std::unique_ptr<Lane>> stream_lanes;  // as_anonymize_stream workers, kept between calls
 };
 
@@ -493,7 +494,7 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       uint8_t* H8 = ln->H8.as<uint8_t>();
       { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS, true, false, R, 3 * d, d, X8, L.w_qkv8, L.b_qkv, nullptr, QKV,
-                            sc[0] * L.s_qkv, 1.0f, err, st)); }
+                            sc[0] * L.s_qkv, 1.0f, err, st, c->gemm_cfg[0])); }
       { ProfScope ps(ln, 1, attn_flops);
         if (g.attention == AS_ATTN_TCGEN05)
           CKS(attention_tcgen05_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(),
@@ -503,19 +504,19 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
                                   (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
       { ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
-                            1.0f, err, st)); }
+                            1.0f, err, st, c->gemm_cfg[1])); }
       CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
       { ProfScope ps(ln, 0, 2.0 * R * f * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, true, true, R, f, d, X8, L.w_1_8, L.b_1, nullptr, H8, sc[2] * L.s_1,
-                            sc[3], err, st)); }
+                            sc[3], err, st, c->gemm_cfg[2])); }
       { ProfScope ps(ln, 0, 2.0 * R * d * f);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, f, H8, L.w_2_8, L.b_2, X32, Y32, sc[3] * L.s_2,
-                            1.0f, err, st)); }
+                            1.0f, err, st, c->gemm_cfg[3])); }
     } else if (bf) {
       __nv_bfloat16* QKV = ln->QKV.as<__nv_bfloat16>();
       __nv_bfloat16* ATT = ln->ATT.as<__nv_bfloat16>();
       __nv_bfloat16* H = ln->H.as<__nv_bfloat16>();
-      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS, false, false, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, 1.0f, 1.0f, err, st, c->gemm_cfg[0])); }
       if (g.attention == AS_ATTN_TCGEN05) {
         ProfScope ps(ln, 1, attn_flops);
         CKS(attention_tcgen05(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), attn_items, n_items,
@@ -526,12 +527,12 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
                            (int32_t)g.n_heads, st));
       }
       if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
-      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
       if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * l + 2, st);
-      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_tcgen05(AS_EPI_BIAS_GELU, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, false, false, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, 1.0f, 1.0f, err, st, c->gemm_cfg[2])); }
       if (mode == kEncCalib) amax_bf16(H, (uint64_t)R * f, amax + kActPerLayer * l + 3, st);
-      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_tcgen05(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, err, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[3])); }
     } else {
       float* QKV = ln->QKV.as<float>();
       float* ATT = ln->ATT.as<float>();
@@ -1863,6 +1864,108 @@ as_status as_serve_stop(as_ctx* c) {
   c->records_done = std::max(c->records_done, sv->next_id);
   delete sv;
   c->server = nullptr;
+  return AS_OK;
+}
+
+as_status as_autotune(as_ctx* c, uint64_t rows, as_tune_entry* entries) {
+  if (!c || !entries) return AS_ERR_ARG;
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving");
+  const as_config& g = c->cfg;
+  if (g.precision == AS_FP32) return fail(c, AS_ERR_UNSUPPORTED, "FP32 contexts use the CUDA-core GEMM: nothing to tune");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (rows == 0) rows = g.max_chunk_tokens ? g.max_chunk_tokens : (1ull << 19);
+  if (rows > (1ull << 21)) return fail(c, AS_ERR_ARG, "rows above 2^21");
+  const bool f8 = g.precision == AS_FP8;
+  const uint64_t d = g.d_model, f = g.d_ffn, es = f8 ? 1 : 2;
+  const LayerW& L = c->layers[0];
+  struct Role {
+    int epi;
+    bool out8;
+    uint64_t n, k;
+    const void* w;
+    const float* b;
+  } roles[AS_TUNE_ROLES] = {
+      {AS_EPI_BIAS, false, 3 * d, d, f8 ? (const void*)L.w_qkv8 : (const void*)L.w_qkv16, L.b_qkv},
+      {AS_EPI_BIAS_RESID, false, d, d, f8 ? (const void*)L.w_o8 : (const void*)L.w_o16, L.b_o},
+      {AS_EPI_BIAS_GELU, f8, f, d, f8 ? (const void*)L.w_1_8 : (const void*)L.w_1_16, L.b_1},
+      {AS_EPI_BIAS_RESID, false, d, f, f8 ? (const void*)L.w_2_8 : (const void*)L.w_2_16, L.b_2}};
+  // scratch operands (values do not change the timing): A, output, residual
+  DBuf A, O, Rz;
+  auto cleanup = [&]() { release(A); release(O); release(Rz); };
+  cudaStream_t st = c->main.stream;
+  if (grow(A, rows * std::max(d, f) * es) || grow(O, rows * std::max(3 * d, f) * 4) || grow(Rz, rows * d * 4)) {
+    cleanup();
+    return fail(c, AS_ERR_OOM, "autotune scratch");
+  }
+  if (cudaMemsetAsync(A.p, 0x3C, rows * std::max(d, f) * es, st) != cudaSuccess ||
+      cudaMemsetAsync(Rz.p, 0, rows * d * 4, st) != cudaSuccess) {
+    cleanup();
+    return fail(c, AS_ERR_CUDA, "autotune scratch init");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  DevError* err = c->main.dev_err.as<DevError>();
+  as_status status = AS_OK;
+  for (int r = 0; r < AS_TUNE_ROLES && status == AS_OK; ++r) {
+    const Role& ro = roles[r];
+    as_tune_entry& en = entries[r];
+    en.role = (uint32_t)r;
+    en.m = rows;
+    en.n = ro.n;
+    en.k = ro.k;
+    float best = 0.f;
+    int best_cfg = -1;
+    for (int cfg = 0; cfg < kGemmCfgs && status == AS_OK; ++cfg) {
+      en.ms[cfg] = -1.f;
+      if (!gemm_tcgen05_cfg_valid(cfg, (int64_t)ro.n)) continue;
+      auto launch = [&]() {
+        return gemm_tcgen05_ex(ro.epi, f8, ro.out8, (int64_t)rows, (int64_t)ro.n, (int64_t)ro.k, A.p, ro.w, ro.b,
+                               ro.epi == AS_EPI_BIAS_RESID ? Rz.as<float>() : nullptr, O.p, 1.0f, 1.0f, err, st, cfg);
+      };
+      status = launch();  // warm-up (also sets the kernel's shared-memory attribute)
+      if (status != AS_OK) break;
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < 3 && status == AS_OK; ++i) status = launch();
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) status = AS_ERR_CUDA;
+      if (status != AS_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      en.ms[cfg] = ms / 3.f;
+      if (best_cfg < 0 || en.ms[cfg] < best) {
+        best = en.ms[cfg];
+        best_cfg = cfg;
+      }
+    }
+    en.chosen = best_cfg;
+    if (status == AS_OK) c->gemm_cfg[r] = best_cfg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (status != AS_OK) return fail(c, status, std::string("autotune: ") + as_k_last_error());
+  if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  return check_dev_error(c, &c->main);
+}
+
+as_status as_set_tiles(as_ctx* c, const int32_t* cfg) {
+  if (!c || !cfg) return AS_ERR_ARG;
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving");
+  const uint64_t d = c->cfg.d_model, f = c->cfg.d_ffn;
+  const uint64_t n[AS_TUNE_ROLES] = {3 * d, d, f, d};
+  for (int r = 0; r < AS_TUNE_ROLES; ++r)
+    if (cfg[r] != -1 && !gemm_tcgen05_cfg_valid(cfg[r], (int64_t)n[r]))
+      return fail(c, AS_ERR_ARG, "tile configuration " + std::to_string(cfg[r]) + " is not valid for projection " +
+                                     std::to_string(r));
+  for (int r = 0; r < AS_TUNE_ROLES; ++r) c->gemm_cfg[r] = cfg[r];
+  return AS_OK;
+}
+
+as_status as_get_tiles(as_ctx* c, int32_t* cfg) {
+  if (!c || !cfg) return AS_ERR_ARG;
+  for (int r = 0; r < AS_TUNE_ROLES; ++r) cfg[r] = c->gemm_cfg[r];
   return AS_OK;
 }
 
