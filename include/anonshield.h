@@ -94,6 +94,7 @@ typedef struct {
   uint64_t map_arena_bytes;      /* bytes for map originals; 0 = 256 MiB       */
   int32_t device;                /* CUDA device ordinal                        */
   uint32_t keep_trace;           /* 1: keep per-stage results for as_debug_*   */
+  uint32_t no_graphs;            /* 1: never replay CUDA graphs (see below)    */
   uint32_t attention;            /* BF16/FP8 attention engine: AS_ATTN_TCGEN05
                                     (0, default) or AS_ATTN_MMA_SYNC           */
 } as_config;
@@ -148,7 +149,17 @@ typedef struct {
   uint64_t n_regex_spans, n_ner_spans, n_final_spans, n_out_bytes;
   uint64_t n_map_entries, n_new_entries;
   uint64_t kernel_launches;
+  uint64_t graph_replays;        /* encoder batches run as one graph launch    */
 } as_stats;
+
+/* Encoder batches of at most AS_GRAPH_MAX_ROWS rows (BF16 / FP8 contexts,
+ * tcgen05 attention, profiling off) are padded to a power-of-two number of
+ * rows and of attention work items and run as one launch of a CUDA graph
+ * captured the first time that shape is seen (per lane; up to 16 shapes are
+ * kept). Padded rows belong to no record and padded work items to an empty
+ * sequence, so results are bit-identical to kernel-by-kernel launches. The
+ * first encoder batch of a lane always runs kernel by kernel. */
+#define AS_GRAPH_MAX_ROWS 16384
 
 /* Create a context: loads weights and vocabulary onto `device`, creates the
  * ctx's stream. Errors: AS_ERR_ARG (shape mismatch, weights_len wrong,

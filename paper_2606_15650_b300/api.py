@@ -41,7 +41,7 @@ class _Config(C.Structure):
                 ("vocab_bytes", C.POINTER(C.c_uint8)), ("vocab_offsets", C.POINTER(C.c_uint32)),
                 ("n_vocab_words", C.c_uint32), ("max_chunk_tokens", C.c_uint64), ("map_capacity", C.c_uint64),
                 ("map_arena_bytes", C.c_uint64), ("device", C.c_int32), ("keep_trace", C.c_uint32),
-                ("attention", C.c_uint32)]
+                ("no_graphs", C.c_uint32), ("attention", C.c_uint32)]
 
 
 class _Records(C.Structure):
@@ -62,7 +62,8 @@ class _Entity(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("n_records", "n_bytes", "n_tokens", "n_encoded_tokens", "n_sequences",
                                           "n_regex_spans", "n_ner_spans", "n_final_spans", "n_out_bytes",
-                                          "n_map_entries", "n_new_entries", "kernel_launches")]
+                                          "n_map_entries", "n_new_entries", "kernel_launches",
+                                          "graph_replays")]
 
 
 class _Trace(C.Structure):
@@ -384,7 +385,7 @@ class Context:
 
     def __init__(self, dims, weights_blob: np.ndarray, vocab_words: list[bytes], precision: str = "bf16",
                  mode: str = "packed", max_chunk_tokens: int = 0, map_capacity: int = 0, map_arena_bytes: int = 0,
-                 keep_trace: bool = False, device: int = 0, attention: str = "tcgen05"):
+                 keep_trace: bool = False, device: int = 0, attention: str = "tcgen05", graphs: bool = True):
         lib = load()
         self.dims = dims
         self.device = device
@@ -402,7 +403,8 @@ class Context:
                       vocab_offsets=self._vo.ctypes.data_as(C.POINTER(C.c_uint32)),
                       n_vocab_words=len(vocab_words), max_chunk_tokens=max_chunk_tokens,
                       map_capacity=map_capacity, map_arena_bytes=map_arena_bytes, device=device,
-                      keep_trace=1 if keep_trace else 0, attention=ATTENTION[attention])
+                      keep_trace=1 if keep_trace else 0, no_graphs=0 if graphs else 1,
+                      attention=ATTENTION[attention])
         h = C.c_void_p()
         st = lib.as_create(C.byref(cfg), C.byref(h))
         if st != AS_OK:

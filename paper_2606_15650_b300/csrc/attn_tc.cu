@@ -271,6 +271,15 @@ __device__ __forceinline__ uint16_t e4m3x2(float lo, float hi) {
   return r;
 }
 
+// The first unit at or after u (stepping by the grid) that has keys: items
+// that point at an empty sequence (padding of a fixed-size launch) are
+// skipped, in the same way by every role.
+__device__ __forceinline__ int next_unit(const Params& p, int u, int n_units) {
+  for (; u < n_units; u += gridDim.x)
+    if (p.seq_len[p.items[u / p.n_heads] >> 6] > 0) break;
+  return u;
+}
+
 // Persistent: a CTA loops over its work units; tiles are numbered globally
 // across units (g), which fixes every buffer index and barrier phase.
 template <bool OUT8>
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // ---------------- Q and K loads, in unit order
       int i = 0, g = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += step, ++i) {
+      for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + step, n_units), ++i) {
         const Work w = work_of(p, u);
         const int b = i & 1;
         if (i >= 2 && !mbar_wait(bar(kBarQEmpty + b), ((i >> 1) - 1) & 1, abort_flag, p.err, 40)) { ok = false; break; }
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // frees only after O += P V, later than the K stage of the same tile)
       int g = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += step) {
+      for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + step, n_units)) {
         const Work w = work_of(p, u);
         for (int t = 0; t < w.n_t; ++t, ++g) {
           const int st = g % kVStages;
@@ -376,9 +385,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       // ---------------- MMA issuer: S_0, S_1, then S_{g+2} before O_g for every g:
       // S runs two tiles ahead of the softmax warps (two S buffers in TMEM)
       constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
-      int us = blockIdx.x, is = 0, ts = 0, gs = 0;  // S cursor
-      int uo = blockIdx.x, io = 0, to = 0, go = 0;  // O cursor
-      Work ws = work_of(p, us), wo = ws;
+      int us = next_unit(p, blockIdx.x, n_units), is = 0, ts = 0, gs = 0;  // S cursor
+      int uo = us, io = 0, to = 0, go = 0;                                 // O cursor
+      Work ws{}, wo{};
+      if (us < n_units) ws = wo = work_of(p, us);
       bool ok = true, issued = false;
       auto issue_s = [&]() -> bool {
         const int st = gs % kKStages;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++gs;
         if (++ts == ws.n_t) {
           mma_commit(bar(kBarQEmpty + (is & 1)));
-          us += step;
+          us = next_unit(p, us + step, n_units);
           ++is;
           ts = 0;
           if (us < n_units) ws = work_of(p, us);
@@ -420,14 +430,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         mma_commit(bar(kBarVEmpty + st));
         ++go;
         if (++to == wo.n_t) {
-          uo += step;
+          uo = next_unit(p, uo + step, n_units);
           ++io;
           to = 0;
           if (uo < n_units) wo = work_of(p, uo);
         }
         return true;
       };
-      ok = issue_s();
+      if (us < n_units) ok = issue_s();
       if (ok && us < n_units) ok = issue_s();
       while (ok && uo < n_units) {
         if (us < n_units) ok = issue_s();
@@ -453,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     };
     int g = 0, i = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
+    for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + gridDim.x, n_units), ++i) {
       const Work w = work_of(p, u);
       const uint32_t ocol = kColO;
       float m = -INFINITY, l = 0.f;              // m: the maximum P is taken against
@@ -512,6 +522,18 @@ __global__ void __launch_bounds__(kThreads, 2)
           v[q >> 1] = *reinterpret_cast<uint32_t*>(&b);
         }
         l += ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+        if (valid < kKT) {
+          // keys past the sequence end have P = 0, but the MMA still multiplies
+          // their V rows: zero those rows of the landed V tile (a 128-byte row
+          // holds all its swizzled pieces), so that whatever lies past the
+          // sequence (another sequence's rows, padding, non-finite data)
+          // contributes exactly nothing
+          const int vst = g % kVStages;
+          if (!warp_wait(bar(kBarVFull + vst), (g / kVStages) & 1, abort_flag, p.err, 64)) { ok = false; break; }
+          uint4* vt = reinterpret_cast<uint4*>(smem + kOffV + vst * kVBytes);
+          for (int q = valid * 8 + (warp - 3) * 32 + lane; q < kKT * 8; q += 128) vt[q] = make_uint4(0u, 0u, 0u, 0u);
+          fence_proxy_async();
+        }
         // P_g goes to TMEM buffer g&1 once O += P_{g-2} V_{g-2} has read it
         if (g >= 2 && !wait_o(g - 2, 62)) { ok = false; break; }
         fence_after();

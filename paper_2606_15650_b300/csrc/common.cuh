@@ -16,10 +16,15 @@ namespace as {
 // count at start-up; this is only the fallback.
 constexpr int kDefaultSMs = 148;
 
-// Every kernel launch made by the library is counted here (host side).
+// Every kernel launch made by the library is counted here (host side), in
+// total and per host thread (a lane's own launches, with other lanes running).
 extern std::atomic<uint64_t> g_launches;
+extern thread_local uint64_t t_launches;
 
-inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+inline void count_launch(uint64_t n = 1) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 
 // Thread-local message of the last kernel-level failure.
 void set_k_error(const std::string& msg);

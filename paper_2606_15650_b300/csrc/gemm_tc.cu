@@ -31,7 +31,6 @@ namespace as {
 namespace tc {
 
 constexpr int kBM = 128;
-constexpr int kBK = 64;             // BF16 elements per k-block: one 128-byte swizzle atom
 // Operand / output element types of one instantiation
 constexpr int kInBF16 = 0, kInE4M3 = 1;
 constexpr int kOutBF16 = 0, kOutF32 = 1, kOutE4M3 = 2;

@@ -28,6 +28,7 @@
 namespace as {
 
 std::atomic<uint64_t> g_launches{0};
+thread_local uint64_t t_launches = 0;
 static thread_local std::string t_k_error;
 void set_k_error(const std::string& msg) { t_k_error = msg; }
 
@@ -156,6 +157,15 @@ struct Lane {
   size_t ev_used = 0;
   std::vector<std::pair<int, double>> ev_pending;  // (kind, flops) per event pair
   as_profile_stats prof_acc{};
+  // captured encoder graphs (small batches), keyed by shape, buffers and parameters
+  struct EncGraph {
+    std::vector<uint64_t> sig;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0, used = 0;
+  };
+  std::vector<EncGraph> graphs;
+  uint64_t graph_clock = 0, graph_replays = 0;
+  bool enc_warm = false;  // an encoder batch ran kernel by kernel on this lane
   // pinned host staging (streaming): one batch's bytes and rebased offsets
   uint8_t* h_in = nullptr;
   size_t h_in_cap = 0;
@@ -222,6 +232,10 @@ void Lane::release_all() {
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
+  for (EncGraph& gr : graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  graphs.clear();
+  enc_warm = false;
   if (h_in) cudaFreeHost(h_in);
   if (h_in_off) cudaFreeHost(h_in_off);
   h_in = nullptr;
@@ -454,20 +468,30 @@ void prof_collect(Lane* ln) {
   ln->ev_used = 0;
 }
 
-as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
-                            bool want_logits, const int32_t* attn_items, int32_t n_items) {
+constexpr uint64_t kGraphMaxRows = AS_GRAPH_MAX_ROWS;
+constexpr size_t kGraphCache = 16;
+
+uint64_t pow2_at_least(uint64_t x, uint64_t lo) {
+  uint64_t v = lo;
+  while (v < x) v <<= 1;
+  return v;
+}
+
+// Rows a batch occupies in the encoder buffers: graph-eligible batches are
+// padded to a power of two so that one captured graph serves every batch of
+// that size.
+bool graphable(const as_config& g, uint64_t rows) {
+  return !g.no_graphs && g.precision != AS_FP32 && g.attention == AS_ATTN_TCGEN05 && rows <= kGraphMaxRows;
+}
+uint64_t encoder_rows(const as_config& g, uint64_t rows) { return graphable(g, rows) ? pow2_at_least(rows, 128) : rows; }
+
+// Embedding, the layers and the classifier over R rows (everything of an
+// encoder batch whose launch shapes depend only on R and n_items).
+as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_len, double attn_flops,
+                       bool want_logits, const int32_t* attn_items, int32_t n_items) {
   const as_config& g = c->cfg;
-  const int64_t R = (int64_t)ch.rows;
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
-  const int32_t ns = (int32_t)(ch.s1 - ch.s0);
   cudaStream_t st = ln->stream;
-  // padding rows between sequences: token 0, position 0, owned by nobody
-  CK(cudaMemsetAsync(ln->row_tok.p, 0, R * 4, st));
-  CK(cudaMemsetAsync(ln->row_pos.p, 0, R * 4, st));
-  CK(cudaMemsetAsync(ln->row_own.p, 0, R, st));
-  expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, ln->row_tok.as<int32_t>(), ln->row_pos.as<int32_t>(),
-                                         ln->row_own.as<uint8_t>(), ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>());
-  count_launch();
   float* X32 = ln->X32.as<float>();
   float* Y32 = ln->Y32.as<float>();
   const int mode = g.precision == AS_FP32 ? kEncF32
@@ -498,10 +522,10 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       { ProfScope ps(ln, 1, attn_flops);
         if (g.attention == AS_ATTN_TCGEN05)
           CKS(attention_tcgen05_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(),
-                                     attn_items, n_items, (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+                                     attn_items, n_items, (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
         else
           CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
-                                  (int32_t)ch.max_len, d, (int32_t)g.n_heads, st)); }
+                                  (int32_t)max_len, d, (int32_t)g.n_heads, st)); }
       { ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
                             1.0f, err, st, c->gemm_cfg[1])); }
@@ -520,10 +544,10 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       if (g.attention == AS_ATTN_TCGEN05) {
         ProfScope ps(ln, 1, attn_flops);
         CKS(attention_tcgen05(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), attn_items, n_items,
-                              (int32_t)ch.max_len, R, d, (int32_t)g.n_heads, err, st));
+                              (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
       } else {
         ProfScope ps(ln, 1, attn_flops);
-        CKS(attention_bf16(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+        CKS(attention_bf16(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)max_len, d,
                            (int32_t)g.n_heads, st));
       }
       if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
@@ -539,7 +563,7 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       float* H = ln->H.as<float>();
       { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
       { ProfScope ps(ln, 1, attn_flops);
-        CKS(attention_f32(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)ch.max_len, d,
+        CKS(attention_f32(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)max_len, d,
                           (int32_t)g.n_heads, st)); }
       { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, nullptr, R, d, st));
@@ -555,6 +579,83 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
                              ln->labels.as<uint8_t>(), R, d, st));
     }
   }
+  return AS_OK;
+}
+
+as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc* seq_dev, double attn_flops,
+                            bool want_logits, const int32_t* attn_items, int32_t n_items) {
+  const as_config& g = c->cfg;
+  const int64_t R = (int64_t)ch.rows;
+  const int64_t Rb = (int64_t)encoder_rows(g, ch.rows);  // R, or its power-of-two bucket
+  const int32_t ns = (int32_t)(ch.s1 - ch.s0);
+  cudaStream_t st = ln->stream;
+  // padding rows between sequences (and up to the bucket): token 0, position 0, owned by nobody
+  CK(cudaMemsetAsync(ln->row_tok.p, 0, Rb * 4, st));
+  CK(cudaMemsetAsync(ln->row_pos.p, 0, Rb * 4, st));
+  CK(cudaMemsetAsync(ln->row_own.p, 0, Rb, st));
+  // sequence ns is empty: padded attention work items point at it
+  CK(cudaMemsetAsync(ln->seq_start.as<int32_t>() + ns, 0, 4, st));
+  CK(cudaMemsetAsync(ln->seq_len.as<int32_t>() + ns, 0, 4, st));
+  expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, ln->row_tok.as<int32_t>(), ln->row_pos.as<int32_t>(),
+                                         ln->row_own.as<uint8_t>(), ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>());
+  count_launch();
+  const bool graph = graphable(g, ch.rows);
+  if (!graph || !ln->enc_warm || ln->prof || c->calibrating) {
+    CKS(encoder_body(c, ln, graph ? Rb : R, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+    ln->enc_warm = true;
+    return AS_OK;
+  }
+  // one graph launch per batch: look up (or capture) the graph of this shape
+  std::vector<uint64_t> sig = {(uint64_t)Rb, (uint64_t)n_items, (uint64_t)want_logits, (uint64_t)g.precision};
+  for (const DBuf* b : {&ln->X32, &ln->Y32, &ln->X16, &ln->X8, &ln->QKV, &ln->ATT, &ln->ATT8, &ln->H, &ln->H8,
+                        &ln->row_tok, &ln->row_pos, &ln->row_own, &ln->seq_start, &ln->seq_len, &ln->tok_ids,
+                        &ln->logits, &ln->labels})
+    sig.push_back(reinterpret_cast<uint64_t>(b->p));
+  sig.push_back(reinterpret_cast<uint64_t>(attn_items));
+  for (int r = 0; r < AS_TUNE_ROLES; ++r) sig.push_back((uint64_t)(int64_t)c->gemm_cfg[r]);
+  for (float x : c->act_scale) {  // FP8 scales are kernel arguments
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    sig.push_back(u);
+  }
+  Lane::EncGraph* hit = nullptr;
+  for (Lane::EncGraph& gr : ln->graphs)
+    if (gr.sig == sig) hit = &gr;
+  if (!hit) {
+    if (ln->graphs.size() >= kGraphCache) {  // evict the least recently used
+      auto lru = std::min_element(ln->graphs.begin(), ln->graphs.end(),
+                                  [](const Lane::EncGraph& a, const Lane::EncGraph& b) { return a.used < b.used; });
+      cudaGraphExecDestroy(lru->exec);
+      ln->graphs.erase(lru);
+    }
+    cudaGraph_t gr = nullptr;
+    const uint64_t l0 = t_launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+      return AS_OK;
+    }
+    const as_status bs = encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items);
+    const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+    const uint64_t kernels = t_launches - l0;
+    g_launches.fetch_sub(kernels);  // captured, not run: counted when the graph is launched
+    t_launches -= kernels;
+    cudaGraphExec_t exec = nullptr;
+    if (bs != AS_OK || ce != cudaSuccess || !gr || cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      // capture refused: run this batch kernel by kernel
+      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+      return AS_OK;
+    }
+    cudaGraphDestroy(gr);
+    ln->graphs.push_back(Lane::EncGraph{std::move(sig), exec, kernels, 0});
+    hit = &ln->graphs.back();
+  }
+  hit->used = ++ln->graph_clock;
+  CK(cudaGraphLaunch(hit->exec, st));
+  count_launch(hit->kernels);
+  ++ln->graph_replays;
   return AS_OK;
 }
 
@@ -686,7 +787,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     d_off = ln->in_off.as<uint64_t>();
   }
   const uint32_t N32 = (uint32_t)N;
-  const uint64_t launches0 = g_launches.load();
+  const uint64_t launches0 = t_launches, replays0 = ln->graph_replays;
   const uint32_t call_id = ++c->call_id;
   // ---- tokenizer + recognizers
   CKS(grow(ln->counters, 64));
@@ -795,12 +896,12 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   }
   uint64_t max_rows = 0, max_seqs = 0;
   for (auto& ch : chunks) {
-    max_rows = std::max(max_rows, ch.rows);
+    max_rows = std::max(max_rows, encoder_rows(g, ch.rows));
     max_seqs = std::max<uint64_t>(max_seqs, ch.s1 - ch.s0);
   }
   CKS(grow(ln->seqs, std::max<size_t>(1, seqs.size()) * sizeof(SeqDesc)));
   if (!seqs.empty()) CK(cudaMemcpyAsync(ln->seqs.p, seqs.data(), seqs.size() * sizeof(SeqDesc), cudaMemcpyHostToDevice, st));
-  CKI(ensure_encoder_buffers(c, ln, std::max<uint64_t>(max_rows, 1), std::max<uint64_t>(max_seqs, 1)));
+  CKI(ensure_encoder_buffers(c, ln, std::max<uint64_t>(max_rows, 1), max_seqs + 1));  // + the empty sequence
   const bool want_logits = g.keep_trace != 0;
   CKS(grow(ln->labels, T + 16));
   if (want_logits) CKS(grow(ln->logits, (T + 1) * g.n_labels * 4));
@@ -819,6 +920,11 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
       lens.clear();
       for (uint64_t i = ch.s0; i < ch.s1; ++i) lens.push_back((int32_t)seqs[i].len);
       attention_items(lens.data(), (int32_t)lens.size(), items);
+      if (graphable(g, ch.rows)) {
+        // pad to a power of two with items of the empty sequence (index ns)
+        const size_t n = items.size() - item_off.back();
+        items.resize(item_off.back() + pow2_at_least(n, 16), (int32_t)((ch.s1 - ch.s0) << 6));
+      }
       item_off.push_back(items.size());
     }
     CKS(grow(ln->attn_items, std::max<size_t>(items.size(), 1) * 4));
@@ -1030,7 +1136,8 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   s.n_map_entries = n_entries;
   const uint64_t seen = c->n_entries_seen.exchange(n_entries);
   s.n_new_entries = n_entries >= seen ? n_entries - seen : 0;
-  s.kernel_launches = g_launches.load() - launches0;
+  s.kernel_launches = t_launches - launches0;
+  s.graph_replays = ln->graph_replays - replays0;
   if (rec_base < 0) c->records_done += n;
   *out = o;
   return AS_OK;
@@ -1482,6 +1589,7 @@ as_status as_anonymize_stream(as_ctx* c, const as_records* rec, const as_schema*
     s.n_new_entries += ps.n_new_entries;
     s.n_map_entries = std::max(s.n_map_entries, ps.n_map_entries);
     s.kernel_launches += ps.kernel_launches;
+    s.graph_replays += ps.graph_replays;
     as_output_free(p);
   }
   c->records_done += n;

@@ -159,6 +159,37 @@ def test_attention_tcgen05(d, h, lens, gap):
     assert torch.isnan(out[~written.to(DEV)].float()).all()
 
 
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("lens", [[300, 200, 57], [1, 2, 3, 130], [64, 65, 63]])
+def test_attention_ignores_rows_outside_sequences(engine, lens):
+    """Rows between and after the sequences hold NaN: keys past a sequence end (masked,
+    P = 0) must contribute exactly nothing, whatever their V rows contain."""
+    d, h, gap = 128, 2, 5
+    g = torch.Generator(device="cpu").manual_seed(len(lens))
+    starts, acc = [], 0
+    for L in lens:
+        starts.append(acc)
+        acc += L + gap
+    rows = acc - gap
+    qkv = torch.full((rows + 256, 3 * d), float("nan"), dtype=torch.bfloat16)
+    for s0, L in zip(starts, lens):
+        qkv[s0:s0 + L] = torch.randn(L, 3 * d, generator=g).to(torch.bfloat16)
+    qkv = qkv.to(DEV)
+    out = torch.zeros(rows, d, device=DEV, dtype=torch.bfloat16)
+    st = torch.tensor(starts, dtype=torch.int32)
+    ln = torch.tensor(lens, dtype=torch.int32)
+    if engine == "tcgen05":
+        api.attention_tc(qkv[:rows], out, st.to(DEV), ln.to(DEV), d, h)
+    else:
+        api.attention("bf16", qkv[:rows], out, st.to(DEV), ln.to(DEV), d, h)
+    torch.cuda.synchronize()
+    ref = _ref_attention(qkv[:rows], st, ln, d, h)
+    for s0, L in zip(starts, lens):
+        got = out[s0:s0 + L].float()
+        assert torch.isfinite(got).all()
+        assert (got - ref[s0:s0 + L]).abs().max().item() < 2.5e-2
+
+
 def test_attention_tcgen05_large_logits():
     """Scores far apart (raises of the running maximum by more than 2^8) stay exact."""
     d, h, L = 128, 2, 700
