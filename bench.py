@@ -42,9 +42,15 @@ import synth  # noqa: E402
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "tokens/s per B300, BF16/FP8 vs FP32 at >=99.9% label match; p50/p99 latency"
 
-# DRAM bytes per tcgen05 GEMM launch from an ncu capture of the kernel source
-# with this SHA-256 prefix; reported only while the source is unchanged.
-GEMM_TRAFFIC = {"source_sha256": None, "bytes_per_launch": None, "profile": None}
+# DRAM bytes (read + write) of the four projection GEMMs of one layer at
+# 65,536 rows, from one ncu capture of the GEMM source with this SHA-256
+# prefix (profiles/gemm_tc_c2_layer_65536rows.md); reported only while the
+# source is unchanged. A, C and the residual scale with the rows, so a launch
+# of R rows moves about mean(bytes) * R / 65,536.
+GEMM_TRAFFIC = {"source_sha256": "ec7789aaf220d122", "rows": 65536,
+                "bytes": {"qkv": 862670336 + 275248640, "attn_out": 502045440 + 167456000,
+                          "ffn1": 105011712 + 347317504, "ffn2": 632662528 + 176786688},
+                "profile": "profiles/gemm_tc_c2_layer_65536rows.md"}
 
 
 def parse():
@@ -57,6 +63,7 @@ def parse():
     ap.add_argument("--records", type=int, default=0, help="override the record count (testing only)")
     ap.add_argument("--no-baselines", action="store_true", help="skip FP32 / CPU baselines (profiling runs)")
     ap.add_argument("--chunk", type=int, default=0, help="encoder rows per packed batch (0 = library default)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMM tiles (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="measured seconds per offered rate of the serving leg (0 = skip it)")
     ap.add_argument("--stream-records", type=int, default=3000,
@@ -229,7 +236,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
 
     # ---- tile autotuner at the batch size (outside the timed region)
-    tune = ctx.autotune()
+    tune = [] if args.no_autotune else ctx.autotune()
 
     # ---- warm-up
     stats = None
@@ -310,7 +317,11 @@ def run_ours(args):
     achieved = gemm_flops_launch / (gemm_avg_ms / 1e3) / 1e12
     traffic = None
     if GEMM_TRAFFIC["source_sha256"] == gemm_source_sha():
-        traffic = GEMM_TRAFFIC["bytes_per_launch"]
+        # rows per launch from the FLOPs: 2 * R * mean(N * K) over the four projections
+        d, f = w.dims.d_model, w.dims.d_ffn
+        mean_nk = (3 * d * d + d * d + f * d + d * f) / 4.0
+        rows_avg = gemm_flops_launch / (2.0 * mean_nk)
+        traffic = float(np.mean(list(GEMM_TRAFFIC["bytes"].values()))) * rows_avg / GEMM_TRAFFIC["rows"]
     lat = np.array(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
