@@ -512,16 +512,23 @@ __global__ void __launch_bounds__(kThreads, 2)
           m = mn;
         }
         // P packed in place: the pair (2q, 2q+1) goes to v[q], already read
-        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // exp2 argument s*c - m and the row sum in two-lane FP32 (four packed
+        // partial sums = eight independent chains)
+        const uint64_t c2 = f2splat(c), nm2 = f2splat(-m);
+        uint64_t s2[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
         for (int q = 0; q < 64; q += 2) {
-          const float p0 = ex2_approx(fmaf(__uint_as_float(v[q]), c, -m));
-          const float p1 = ex2_approx(fmaf(__uint_as_float(v[q + 1]), c, -m));
-          s8[(q >> 1) & 7] += p0 + p1;
+          float a0, a1;
+          f2unpack(fma2(f2pack(__uint_as_float(v[q]), __uint_as_float(v[q + 1])), c2, nm2), a0, a1);
+          const float p0 = ex2_approx(a0), p1 = ex2_approx(a1);
+          s2[(q >> 1) & 3] = add2(s2[(q >> 1) & 3], f2pack(p0, p1));
           __nv_bfloat162 b = __floats2bfloat162_rn(p0, p1);
           v[q >> 1] = *reinterpret_cast<uint32_t*>(&b);
         }
-        l += ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+        float sl[8];
+        f2unpack(add2(s2[0], s2[1]), sl[0], sl[1]);
+        f2unpack(add2(s2[2], s2[3]), sl[2], sl[3]);
+        l += (sl[0] + sl[1]) + (sl[2] + sl[3]);
         if (valid < kKT) {
           // keys past the sequence end have P = 0, but the MMA still multiplies
           // their V rows: zero those rows of the landed V tile (a 128-byte row

@@ -229,34 +229,10 @@ __device__ __forceinline__ float gelu_erf(float x) {
   return 0.5f * x * (1.0f + erf_x);
 }
 
-// Two-lane FP32 arithmetic: one instruction computes both lanes, each rounded
-// exactly as the scalar instruction would, so gelu_erf2 returns bit for bit
-// what gelu_erf does, with about half the issue slots (the epilogue of the
-// GELU projection is issue-bound).
-__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2splat(float x) { return f2pack(x, x); }
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
+// gelu_erf2 (below) computes gelu_erf of two values with the two-lane FP32
+// instructions of common.cuh: each lane rounds exactly as the scalar
+// instruction would, so the result is bit for bit that of gelu_erf with about
+// half the issue slots (the epilogue of the GELU projection is issue-bound).
 // gelu_erf of two values, the same operations in the same order.
 __device__ __forceinline__ void gelu_erf2(float& x0, float& x1) {
   const uint64_t x = f2pack(x0, x1);
