@@ -68,6 +68,8 @@ def parse():
                     help="measured seconds per offered rate of the serving leg (0 = skip it)")
     ap.add_argument("--stream-records", type=int, default=3000,
                     help="records of the streaming leg (24-layer d1024 FP8 model; 0 = skip it)")
+    ap.add_argument("--field-records", type=int, default=20000,
+                    help="records of the per-field policy leg (0 = skip it)")
     ap.add_argument("--serve-rates", default="1000,5000,20000,50000", help="offered records/s of the serving leg")
     return ap.parse_args()
 
@@ -397,7 +399,56 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
         out["serving"] = serving_leg(args, words, blob, key, local)
     if args.stream_records > 0:
         out["streaming"] = streaming_leg(args, words, key, local)
+    if args.field_records > 0:
+        out["field_policy"] = field_policy_leg(args, w, words, blob, key, local)
     return out
+
+
+# The configuration of the per-field leg: the host columns are forced (address as
+# IP_ADDRESS, name as HOSTNAME), the boilerplate columns excluded, detection
+# runs on the plugin output only (columns of synth.COLUMNS).
+FIELD_POLICY = {0: ("force", 1), 1: ("force", 2), 2: "exclude", 3: "exclude", 4: "exclude", 5: "exclude",
+                6: "exclude", 7: "exclude", 8: "detect"}
+
+
+def field_policy_leg(args, w, words, blob, key, local) -> dict:
+    """CSV-like scan records: the whole record through detection vs the per-field policy."""
+    import torch
+    import paper_2606_15650_b300.api as api
+    fr = synth.make_fielded_records(synth.scaled(synth.C2, args.field_records).records, words,
+                                    seed=synth.SEED_RECORDS + 8)
+    schema = api.Schema(synth.TYPE_NAMES_4, window=512, stride=384)
+    data = torch.from_numpy(fr.records.data).to(f"cuda:{local}")
+    offs = torch.from_numpy(fr.records.offsets.astype(np.int64)).to(f"cuda:{local}")
+    nbytes = len(fr.records.data)
+    res = {}
+    for mode in ("whole_record", "field_policy"):
+        ctx = api.Context(w.dims, blob, words, precision="bf16", mode="packed", device=local)
+        stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{local}")
+
+        def call():
+            if mode == "whole_record":
+                return ctx.anonymize(data, offs, schema, key)
+            return ctx.anonymize_fields(data, offs, fr.start, fr.length, fr.field_id, FIELD_POLICY, schema, key)
+        call().free()
+        ms = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = call()
+            e1.record(stream)
+            e1.synchronize()
+            st = o.stats()
+            o.free()
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.mean(ms)) / 1e3
+        res[mode] = {"records_per_s": fr.records.n / t, "kb_per_s": nbytes / 1024 / t,
+                     "encoded_tokens": int(st["n_encoded_tokens"]), "ms": t * 1e3}
+        ctx.close()
+    res["speedup"] = res["field_policy"]["records_per_s"] / res["whole_record"]["records_per_s"]
+    res["workload"] = (f"{fr.records.n} CSV-like scan records ({nbytes} bytes, columns {', '.join(synth.COLUMNS)}); "
+                       "policy: host address and name forced, plugin output detected, the rest excluded")
+    return res
 
 
 def streaming_leg(args, words, key, local) -> dict:

@@ -182,7 +182,8 @@ as_status as_output_records(const as_output* out, const uint8_t** bytes, const u
                             uint64_t* n_records, uint32_t* on_device);
 as_status as_output_stats(const as_output* out, as_stats* stats);
 /* Map entries touched by this call (new or updated), sorted by (type, bytes).
- * Pointers valid until as_output_free. */
+ * Pointers valid until as_output_free; needs the ctx alive (as_output_records,
+ * as_output_stats and as_output_free do not: an output may outlive its ctx). */
 as_status as_output_map(as_output* out, const as_entity** entries, uint64_t* n);
 void as_output_free(as_output* out);
 
@@ -228,6 +229,46 @@ typedef struct {
   const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+/* Per-field policy: the schema-aware configuration of AnonShield §2
+ * (anonymization_config with force_anonymize, fields_to_anonymize,
+ * fields_to_exclude), which skips the detection steps for most of a record.
+ * Each record holds fields: byte spans (start into the arena, length, field
+ * id), sorted by start, disjoint, each inside one record. Per field id:
+ *   AS_FIELD_DETECT   the field's bytes are a record of their own for every
+ *                     detection step (tokenizer, recognizers, encoder with
+ *                     windows, BIO decode, overlap rule, preserve list); the
+ *                     spans found are shifted by the field start;
+ *   AS_FIELD_EXCLUDE  the field passes through unchanged (never scanned);
+ *   AS_FIELD_FORCE    the field's value, ASCII whitespace trimmed at both ends,
+ *                     is one entity of force_type (1..n_types), replaced
+ *                     whatever the preserve list says; nothing if empty.
+ * Bytes outside every field (separators, keys, layout) pass through
+ * unchanged. Ids >= n_ids take default_action (DETECT or EXCLUDE). Record
+ * indices, map and output are those of the records. Fields and policy are
+ * host arrays; records may be on the host or the device (as_anonymize). The
+ * debug trace's token arrays then describe the arena of detected fields (one
+ * sub-record per field, in field order). Errors as as_anonymize, plus
+ * AS_ERR_ARG for unsorted, overlapping or record-crossing fields and invalid
+ * actions or types. */
+#define AS_FIELD_DETECT  0
+#define AS_FIELD_EXCLUDE 1
+#define AS_FIELD_FORCE   2
+typedef struct {
+  const uint64_t* start;   /* byte offset of each field in the arena        */
+  const uint32_t* len;
+  const uint32_t* id;      /* field id (column or key index)                */
+  uint64_t n_fields;
+} as_fields;
+typedef struct {
+  uint32_t n_ids;
+  const uint8_t* action;      /* per field id: AS_FIELD_*                     */
+  const uint8_t* force_type;  /* per field id: entity type for AS_FIELD_FORCE */
+  uint8_t default_action;     /* for ids >= n_ids                             */
+} as_field_policy;
+as_status as_anonymize_fields(as_ctx* ctx, const as_records* records, const as_fields* fields,
+                              const as_field_policy* policy, const as_schema* schema, const uint8_t* key,
+                              size_t key_len, as_output** out);
 
 /* Streaming (AnonShield §2 stage (1) reads large inputs as a stream): the
  * same result as one as_anonymize call over `records` (host memory only),

@@ -86,6 +86,18 @@ class _ServeStats(C.Structure):
                [(n, C.c_double) for n in ("seconds", "p50_ms", "p99_ms", "max_ms")]
 
 
+class _Fields(C.Structure):
+    _fields_ = [("start", C.c_void_p), ("len", C.c_void_p), ("id", C.c_void_p), ("n_fields", C.c_uint64)]
+
+
+class _FieldPolicy(C.Structure):
+    _fields_ = [("n_ids", C.c_uint32), ("action", C.c_void_p), ("force_type", C.c_void_p),
+                ("default_action", C.c_uint8)]
+
+
+FIELD_ACTION = {"detect": 0, "exclude": 1, "force": 2}
+
+
 class _StreamConfig(C.Structure):
     _fields_ = [("batch_bytes", C.c_uint64), ("lanes", C.c_uint32)]
 
@@ -106,7 +118,7 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
@@ -150,6 +162,8 @@ def load() -> C.CDLL:
     lib.as_autotune.argtypes = [P, C.c_uint64, C.POINTER(_TuneEntry)]
     lib.as_set_tiles.argtypes = [P, C.POINTER(C.c_int32)]
     lib.as_get_tiles.argtypes = [P, C.POINTER(C.c_int32)]
+    lib.as_anonymize_fields.argtypes = [P, C.POINTER(_Records), C.POINTER(_Fields), C.POINTER(_FieldPolicy),
+                                        C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
     lib.as_anonymize_stream.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t,
                                         C.POINTER(_StreamConfig), C.POINTER(P)]
     lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
@@ -364,6 +378,8 @@ class Output:
         return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
 
     def map(self) -> list[Entity]:
+        if getattr(self._ctx, "_h", None) is None:
+            raise AnonShieldError(-6, "the output's context is closed: its map cannot be read")
         p, n = C.POINTER(_Entity)(), C.c_uint64()
         self._ctx._check(load().as_output_map(self._h, C.byref(p), C.byref(n)))
         return _entities(p, n.value)
@@ -439,6 +455,43 @@ class Context:
         sc, names = self._schema(schema)
         out = C.c_void_p()
         st = load().as_anonymize(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(out))
+        del keep, names
+        self._check(st)
+        return Output(self, out.value)
+
+    def anonymize_fields(self, data, offsets, field_start, field_len, field_id, policy: dict, schema: Schema,
+                         key: bytes, default: str = "detect") -> Output:
+        """Per-field policy (as_anonymize_fields). policy maps a field id to "detect", "exclude"
+        or ("force", entity_type); other ids take ``default`` ("detect" or "exclude")."""
+        on_dev = hasattr(data, "is_cuda") and data.is_cuda
+        if on_dev:
+            rec = _Records(bytes=data.data_ptr(), offsets=offsets.data_ptr(), n_records=offsets.numel() - 1,
+                           on_device=1)
+            keep = (data, offsets)
+        else:
+            d = np.ascontiguousarray(data, dtype=np.uint8)
+            o = np.ascontiguousarray(offsets, dtype=np.uint64)
+            rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
+                           on_device=0)
+            keep = (d, o)
+        fs = np.ascontiguousarray(field_start, dtype=np.uint64)
+        fl = np.ascontiguousarray(field_len, dtype=np.uint32)
+        fi = np.ascontiguousarray(field_id, dtype=np.uint32)
+        n_ids = (max(policy) + 1) if policy else 0
+        act = np.full(max(n_ids, 1), FIELD_ACTION[default], np.uint8)
+        ftype = np.zeros(max(n_ids, 1), np.uint8)
+        for fid, a in policy.items():
+            if isinstance(a, tuple):
+                act[fid], ftype[fid] = FIELD_ACTION[a[0]], a[1]
+            else:
+                act[fid] = FIELD_ACTION[a]
+        flds = _Fields(start=fs.ctypes.data, len=fl.ctypes.data, id=fi.ctypes.data, n_fields=fs.size)
+        pol = _FieldPolicy(n_ids=n_ids, action=act.ctypes.data, force_type=ftype.ctypes.data,
+                           default_action=FIELD_ACTION[default])
+        sc, names = self._schema(schema)
+        out = C.c_void_p()
+        st = load().as_anonymize_fields(self._h, C.byref(rec), C.byref(flds), C.byref(pol), C.byref(sc), key,
+                                        len(key), C.byref(out))
         del keep, names
         self._check(st)
         return Output(self, out.value)

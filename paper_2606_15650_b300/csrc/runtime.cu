@@ -93,6 +93,23 @@ struct LoadI64 {
   __device__ int64_t operator()(uint64_t i) const { return p[i]; }
 };
 
+// A call with a per-field policy: the detection steps run on `rec` (the
+// compact arena of fields, one sub-record per field); the rest of the path on
+// the original records described here.
+struct FieldJob {
+  const uint8_t* bytes;           // original records (device)
+  const uint64_t* offsets;        // n + 1
+  uint64_t n, N;
+  const uint32_t* field_start;    // nf (device)
+  const uint64_t* sub_off;        // nf + 1 sub-record offsets (device)
+  uint64_t nf;
+  const uint32_t *fs_s, *fs_l;    // forced spans, sorted (device)
+  const uint8_t* fs_t;
+  const uint32_t* n_force_dev;
+  uint32_t force_cap;
+  bool on_device;                 // the caller's records (and so the output) are on the device
+};
+
 struct SeqDesc {
   uint32_t src_tok;  // first token of the window (global token index)
   uint32_t len;
@@ -142,6 +159,8 @@ struct Lane {
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
   DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len, attn_items;
+  DBuf f_bytes, f_off, f_start, f_sub_off, f_sub, fs_s, fs_l, fs_t, fr_s, fr_l, fr_t, f_keep, f_pos, f_cnt, ff_s, ff_l,
+      ff_t;
   DBuf X32, X16, QKV, ATT, Y32, H, X8, ATT8, H8;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
@@ -207,7 +226,8 @@ struct as_ctx {
 };
 
 struct as_output {
-  as_ctx* ctx = nullptr;
+  as_ctx* ctx = nullptr;  // used only by as_output_map (the ctx must be alive then)
+  int device = 0;         // where d_bytes / d_off live: freeing needs no ctx
   uint32_t call_id = 0;
   uint32_t call_lo = 0;  // streaming outputs span the calls call_lo..call_id
   uint32_t on_device = 0;
@@ -227,7 +247,8 @@ void Lane::release_all() {
                  &tok_ids, &tok_off, &tok_len, &rec_tok, &rx_len_b, &rx_type_b, &rx_s, &rx_l, &rx_t, &labels, &logits,
                  &tok_flags, &rx_pos, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
                  &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
-                 &name_off, &name_len, &seqs, &attn_items, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
+                 &name_off, &name_len, &seqs, &attn_items, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
+                 &fs_l, &fs_t, &fr_s, &fr_l, &fr_t, &f_keep, &f_pos, &f_cnt, &ff_s, &ff_l, &ff_t, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
                  &ATT, &Y32, &H, &X8, &ATT8, &H8};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -737,7 +758,8 @@ as_status d2h_vec(as_ctx* c, Lane* ln, std::vector<T>& v, const void* src, uint6
 // calibrate = true: run the tokenizer and the BF16 encoder only, recording
 // the amax of every FP8 GEMM input, and set the static activation scales.
 as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_schema* sch, const uint8_t* key,
-                         size_t key_len, as_output** out, bool calibrate = false, int64_t rec_base = -1) {
+                         size_t key_len, as_output** out, bool calibrate = false, int64_t rec_base = -1,
+                         const FieldJob* fj = nullptr) {
   const as_config& g = c->cfg;
   cudaStream_t st = ln->stream;
   if (!rec || (!out && !calibrate)) return fail(c, AS_ERR_ARG, "records / out is NULL");
@@ -748,7 +770,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     return fail(c, AS_ERR_STATE, "FP8 context without activation scales: call as_calibrate or as_set_scales first");
   if (!calibrate && rec_base < 0) CKI(set_key(c, key, key_len));  // serving sets the key once at start
   c->slug_len = sch->slug_hex_len;
-  const uint64_t n = rec->n_records;
+  uint64_t n = rec->n_records;
   if (n > 0 && (!rec->offsets)) return fail(c, AS_ERR_ARG, "offsets is NULL");
   // ---- inputs
   uint64_t N = 0;
@@ -786,7 +808,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     CK(cudaMemcpyAsync(ln->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
     d_off = ln->in_off.as<uint64_t>();
   }
-  const uint32_t N32 = (uint32_t)N;
+  uint32_t N32 = (uint32_t)N;
   const uint64_t launches0 = t_launches, replays0 = ln->graph_replays;
   const uint32_t call_id = ++c->call_id;
   // ---- tokenizer + recognizers
@@ -1015,12 +1037,35 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   // the HMAC / map / substitution kernels read the final span count from cnt[5]
   sum_kept_kernel<<<1, 32, 0, st>>>(cnt);
   count_launch();
+  uint32_t fin_total = fin_cap;
+  const uint64_t n_detect = n;  // records the detection steps saw (sub-records with a field policy)
+  if (fj) {
+    // spans of the detected fields -> record coordinates, merged with the forced fields
+    launch_field_translate(ln->fin_s.as<uint32_t>(), cnt + 5, fin_cap, fj->sub_off, fj->nf, fj->field_start, st);
+    fin_total = fin_cap + fj->force_cap;
+    CKS(grow(ln->ff_s, ((size_t)fin_total + 1) * 4));
+    CKS(grow(ln->ff_l, ((size_t)fin_total + 1) * 4));
+    CKS(grow(ln->ff_t, (size_t)fin_total + 16));
+    launch_merge_spans(ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_cap,
+                       fj->fs_s, fj->fs_l, fj->fs_t, fj->n_force_dev, fj->force_cap, ln->ff_s.as<uint32_t>(),
+                       ln->ff_l.as<uint32_t>(), ln->ff_t.as<uint8_t>(), st);
+    launch_add_count(cnt + 5, fj->n_force_dev, st);
+    std::swap(ln->fin_s, ln->ff_s);
+    std::swap(ln->fin_l, ln->ff_l);
+    std::swap(ln->fin_t, ln->ff_t);
+    // the rest of the path works on the original records
+    d_bytes = fj->bytes;
+    d_off = fj->offsets;
+    n = fj->n;
+    N = fj->N;
+    N32 = (uint32_t)N;
+  }
   // ---- HMAC + map
-  CKS(grow(ln->digests, (size_t)(fin_cap + 1) * 32));
-  launch_hmac_spans(d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, fin_cap,
+  CKS(grow(ln->digests, (size_t)(fin_total + 1) * 32));
+  launch_hmac_spans(d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, fin_total,
                     c->key_state.as<uint32_t>(), ln->digests.as<uint32_t>(), st);
   launch_map_insert_spans(map_view(c), d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(),
-                          ln->fin_t.as<uint8_t>(), ln->digests.as<uint32_t>(), cnt + 5, fin_cap, d_off, n,
+                          ln->fin_t.as<uint8_t>(), ln->digests.as<uint32_t>(), cnt + 5, fin_total, d_off, n,
                           rec_base >= 0 ? (uint64_t)rec_base : c->records_done, call_id, ln->dev_err.as<DevError>(),
                           st);
   // ---- substitution
@@ -1041,12 +1086,12 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     CK(cudaMemcpyAsync(ln->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));  // the host vectors above go out of scope
   }
-  CKS(grow(ln->delta, (size_t)(fin_cap + 1) * 8));
-  CKS(grow(ln->shift, (size_t)(fin_cap + 1) * 8));
+  CKS(grow(ln->delta, (size_t)(fin_total + 1) * 8));
+  CKS(grow(ln->shift, (size_t)(fin_total + 1) * 8));
   CKS(grow(ln->delta_total, 16));
-  launch_sub_delta(ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_cap + 1, ln->name_len.as<uint32_t>(),
+  launch_sub_delta(ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_total + 1, ln->name_len.as<uint32_t>(),
                    sch->slug_hex_len, ln->delta.as<int64_t>(), st);
-  exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, fin_cap + 1, ln->shift.as<int64_t>(),
+  exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, fin_total + 1, ln->shift.as<int64_t>(),
                           ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st);
   // ---- sync 2: output size and counts
   int64_t total_delta = 0;
@@ -1057,8 +1102,10 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   const uint64_t out_size = (uint64_t)((int64_t)N + total_delta);
   as_output* o = new as_output();
   o->ctx = c;
+  o->device = c->device;
   o->call_id = call_id;
-  o->on_device = rec->on_device;
+  const bool out_dev = fj ? fj->on_device : rec->on_device != 0;
+  o->on_device = out_dev ? 1u : 0u;
   o->n = n;
   void* d_out = nullptr;
   uint64_t* d_out_off = nullptr;
@@ -1071,11 +1118,11 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   }
   launch_sub_copy(d_bytes, N32, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(),
                   reinterpret_cast<uint8_t*>(d_out), st);
-  launch_sub_replace(ln->fin_s.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_cap, ln->shift.as<int64_t>(),
+  launch_sub_replace(ln->fin_s.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_total, ln->shift.as<int64_t>(),
                      ln->digests.as<uint32_t>(), ln->names.as<char>(), ln->name_off.as<uint32_t>(), sch->slug_hex_len,
                      reinterpret_cast<uint8_t*>(d_out), st);
   launch_sub_offsets(d_off, n, ln->fin_s.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(), d_out_off, st);
-  if (rec->on_device) {
+  if (out_dev) {
     o->d_bytes = d_out;
     o->d_off = d_out_off;
   } else {
@@ -1087,7 +1134,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     cudaFreeAsync(d_out_off, st);
   }
   // ---- trace for as_debug_trace
-  ln->last_n = n;
+  ln->last_n = n_detect;
   ln->last_T = T;
   ln->last_nrx = n_rx;
   ln->last_nfin = h_cnt2[5];
@@ -1560,6 +1607,7 @@ as_status as_anonymize_stream(as_ctx* c, const as_records* rec, const as_schema*
   // one host output in record order
   as_output* o = new as_output();
   o->ctx = c;
+  o->device = c->device;
   o->on_device = 0;
   o->n = n;
   o->call_lo = call_lo;
@@ -1636,8 +1684,8 @@ as_status as_output_map(as_output* o, const as_entity** entries, uint64_t* n) {
 void as_output_free(as_output* o) {
   if (!o) return;
   if (o->d_bytes || o->d_off) {
-    cudaSetDevice(o->ctx->device);
-    cudaStreamSynchronize(o->ctx->main.stream);
+    // cudaFree waits for the work in flight: valid after the ctx is gone too
+    cudaSetDevice(o->device);
     if (o->d_bytes) cudaFree(o->d_bytes);
     if (o->d_off) cudaFree(o->d_off);
   }
@@ -1906,6 +1954,7 @@ as_status as_poll(as_ctx* c, uint64_t request_id, as_output** out, int64_t timeo
   if (st == AS_OK) {
     as_output* o = new as_output();
     o->ctx = c;
+    o->device = c->device;
     o->on_device = 0;
     o->n = 1;
     o->h_bytes = std::move(r->out);
@@ -2075,6 +2124,131 @@ as_status as_get_tiles(as_ctx* c, int32_t* cfg) {
   if (!c || !cfg) return AS_ERR_ARG;
   for (int r = 0; r < AS_TUNE_ROLES; ++r) cfg[r] = c->gemm_cfg[r];
   return AS_OK;
+}
+
+as_status as_anonymize_fields(as_ctx* c, const as_records* rec, const as_fields* fl, const as_field_policy* pol,
+                              const as_schema* sch, const uint8_t* key, size_t key_len, as_output** out) {
+  if (!c || !rec || !fl || !pol || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
+  CKI(validate_schema(c, sch));
+  Lane* ln = &c->main;
+  cudaStream_t st = ln->stream;
+  const uint64_t n = rec->n_records, nf = fl->n_fields;
+  if (n > 0 && !rec->offsets) return fail(c, AS_ERR_ARG, "offsets is NULL");
+  if (nf > 0 && (!fl->start || !fl->len || !fl->id)) return fail(c, AS_ERR_ARG, "field arrays are NULL");
+  if (pol->n_ids > 0 && (!pol->action || !pol->force_type)) return fail(c, AS_ERR_ARG, "policy arrays are NULL");
+  if (pol->default_action != AS_FIELD_DETECT && pol->default_action != AS_FIELD_EXCLUDE)
+    return fail(c, AS_ERR_ARG, "default_action must be AS_FIELD_DETECT or AS_FIELD_EXCLUDE");
+  // record offsets on the host (validation, field -> record)
+  std::vector<uint64_t> off(n + 1, 0);
+  if (n > 0) {
+    if (rec->on_device) {
+      CK(cudaMemcpyAsync(off.data(), rec->offsets, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      memcpy(off.data(), rec->offsets, (n + 1) * 8);
+    }
+    if (off[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
+    for (uint64_t r = 0; r < n; ++r)
+      if (off[r + 1] < off[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
+  }
+  const uint64_t N = off[n];
+  if (N >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "a call takes less than 4 GiB of text");
+  if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
+  // fields: sorted, disjoint, each inside one record; actions from the policy
+  std::vector<uint32_t> f_start(nf);
+  std::vector<uint64_t> sub_off(nf + 1, 0);
+  std::vector<uint32_t> fr_s, fr_l;
+  std::vector<uint8_t> fr_t;
+  uint64_t prev_end = 0, r = 0;
+  for (uint64_t k = 0; k < nf; ++k) {
+    const uint64_t a = fl->start[k], b = a + fl->len[k];
+    if (a < prev_end || b > N)
+      return fail(c, AS_ERR_ARG, "field " + std::to_string(k) + ": fields must be sorted, disjoint and inside the bytes");
+    while (r < n && off[r + 1] <= a) ++r;  // the record holding byte a (empty fields at a record end: the next one)
+    if (fl->len[k] > 0 && (r >= n || b > off[r + 1]))
+      return fail(c, AS_ERR_ARG, "field " + std::to_string(k) + " crosses a record boundary");
+    prev_end = b;
+    const uint32_t id = fl->id[k];
+    const uint8_t act = id < pol->n_ids ? pol->action[id] : pol->default_action;
+    f_start[k] = (uint32_t)a;
+    uint64_t detect_len = 0;
+    if (act == AS_FIELD_DETECT) {
+      detect_len = fl->len[k];
+    } else if (act == AS_FIELD_FORCE) {
+      const uint8_t t = pol->force_type[id];
+      if (t < 1 || t > sch->n_types)
+        return fail(c, AS_ERR_ARG, "field id " + std::to_string(id) + ": force_type must be 1..n_types");
+      if (fl->len[k] > 0) {
+        fr_s.push_back((uint32_t)a);
+        fr_l.push_back(fl->len[k]);
+        fr_t.push_back(t);
+      }
+    } else if (act != AS_FIELD_EXCLUDE) {
+      return fail(c, AS_ERR_ARG, "field id " + std::to_string(id) + ": unknown action");
+    }
+    sub_off[k + 1] = sub_off[k] + detect_len;
+  }
+  const uint64_t n_sub_bytes = sub_off[nf];
+  const uint32_t nforce = (uint32_t)fr_s.size();
+  // device inputs: the original records, the field starts, the sub-record offsets, the forced spans
+  const uint8_t* d_bytes;
+  const uint64_t* d_off;
+  if (rec->on_device) {
+    d_bytes = rec->bytes;
+    d_off = rec->offsets;
+  } else {
+    CKS(grow(ln->f_bytes, N + 16));
+    CKS(grow(ln->f_off, (n + 1) * 8));
+    if (N) CK(cudaMemcpyAsync(ln->f_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->f_off.p, off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    d_bytes = ln->f_bytes.as<uint8_t>();
+    d_off = ln->f_off.as<uint64_t>();
+  }
+  CKS(grow(ln->f_start, (nf + 1) * 4));
+  CKS(grow(ln->f_sub_off, (nf + 1) * 8));
+  CKS(grow(ln->f_sub, n_sub_bytes + 16));
+  CKS(grow(ln->fr_s, ((size_t)nforce + 1) * 4));
+  CKS(grow(ln->fr_l, ((size_t)nforce + 1) * 4));
+  CKS(grow(ln->fr_t, (size_t)nforce + 16));
+  CKS(grow(ln->fs_s, ((size_t)nforce + 1) * 4));
+  CKS(grow(ln->fs_l, ((size_t)nforce + 1) * 4));
+  CKS(grow(ln->fs_t, (size_t)nforce + 16));
+  CKS(grow(ln->f_keep, (size_t)nforce + 16));
+  CKS(grow(ln->f_pos, ((size_t)nforce + 1) * 4));
+  CKS(grow(ln->f_cnt, 16));
+  CKS(grow(ln->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(nforce + 1, 1) * 2) + 16) * 8));
+  if (nf) CK(cudaMemcpyAsync(ln->f_start.p, f_start.data(), nf * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ln->f_sub_off.p, sub_off.data(), (nf + 1) * 8, cudaMemcpyHostToDevice, st));
+  const uint32_t counts[2] = {0, nforce};  // [0]: forced spans kept, [1]: forced spans given
+  CK(cudaMemcpyAsync(ln->f_cnt.p, counts, 8, cudaMemcpyHostToDevice, st));
+  if (nforce) {
+    CK(cudaMemcpyAsync(ln->fr_s.p, fr_s.data(), nforce * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->fr_l.p, fr_l.data(), nforce * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->fr_t.p, fr_t.data(), nforce, cudaMemcpyHostToDevice, st));
+  }
+  launch_field_gather(d_bytes, ln->f_start.as<uint32_t>(), ln->f_sub_off.as<uint64_t>(), nf, ln->f_sub.as<uint8_t>(),
+                      st);
+  if (nforce) {
+    launch_field_force_trim(d_bytes, ln->fr_s.as<uint32_t>(), ln->fr_l.as<uint32_t>(), ln->f_keep.as<uint8_t>(), nforce,
+                            st);
+    exclusive_scan<uint32_t>(NonZeroU8{ln->f_keep.as<uint8_t>()}, nforce, ln->f_pos.as<uint32_t>(),
+                             ln->f_cnt.as<uint32_t>(), ln->scan_tiles.as<uint32_t>(), st);
+    launch_compact_spans(ln->fr_s.as<uint32_t>(), ln->fr_l.as<uint32_t>(), ln->fr_t.as<uint8_t>(),
+                         ln->f_keep.as<uint8_t>(), ln->f_pos.as<uint32_t>(), ln->f_cnt.as<uint32_t>() + 1, nforce,
+                         ln->fs_s.as<uint32_t>(), ln->fs_l.as<uint32_t>(), ln->fs_t.as<uint8_t>(), st);
+  }
+  // the host vectors above are read by the copies: finish them before they go out of scope
+  CK(cudaStreamSynchronize(st));
+  FieldJob fj{d_bytes, d_off, n, N, ln->f_start.as<uint32_t>(), ln->f_sub_off.as<uint64_t>(), nf,
+              ln->fs_s.as<uint32_t>(), ln->fs_l.as<uint32_t>(), ln->fs_t.as<uint8_t>(), ln->f_cnt.as<uint32_t>(),
+              nforce, rec->on_device != 0};
+  as_records sub{ln->f_sub.as<uint8_t>(), ln->f_sub_off.as<uint64_t>(), nf, 1};
+  as_status s = anonymize_impl(c, ln, &sub, sch, key, key_len, out, false, -1, &fj);
+  if (s == AS_ERR_CUDA) cudaGetLastError();
+  return s;
 }
 
 as_status as_get_stream(as_ctx* c, void** stream) {

@@ -72,6 +72,19 @@ void launch_merge_spans(const uint32_t* a_s, const uint32_t* a_l, const uint8_t*
                         const uint32_t* n_b_dev, uint32_t b_cap, uint32_t* o_s, uint32_t* o_l, uint8_t* o_t,
                         cudaStream_t st);
 
+// ---- per-field policy (fields.cu) ----
+// Copy detected fields to their sub-records (sub_off: nf + 1 offsets).
+void launch_field_gather(const uint8_t* bytes, const uint32_t* f_start, const uint64_t* sub_off, uint64_t nf,
+                         uint8_t* sub, cudaStream_t st);
+// Trim forced spans in place; keep[i] = non-empty.
+void launch_field_force_trim(const uint8_t* bytes, uint32_t* s, uint32_t* l, uint8_t* keep, uint32_t n,
+                             cudaStream_t st);
+// Sub-record span starts -> record coordinates.
+void launch_field_translate(uint32_t* sp_s, const uint32_t* n_dev, uint32_t cap, const uint64_t* sub_off, uint64_t nf,
+                            const uint32_t* f_start, cudaStream_t st);
+// *dst += *add (device counters).
+void launch_add_count(uint32_t* dst, const uint32_t* add, cudaStream_t st);
+
 // ---- HMAC-SHA256 ----
 void sha256_init_constants();  // uploads FIPS 180-4 constants (derived on the host)
 // key_state[0..7] = inner midstate, [8..15] = outer midstate.

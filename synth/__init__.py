@@ -10,9 +10,10 @@ from .workloads import (C1, C2, C3, C4, C5, WORKLOADS, ModelDims, RecordShape, W
                         SEED_ARRIVALS, SEED_CALIB, scaled)
 from .vocab import make_vocab, vocab_arrays, FIRST_WORD_ID
 from .records import RecordSet, make_records, records_from_list
+from .fielded import COLUMNS, FieldedRecords, make_fielded_records
 from .model import make_weights, pack_blob, blob_layout, blob_size, make_key
 
-__all__ = [
+__all__ = ["COLUMNS", "FieldedRecords", "make_fielded_records",
     "C1", "C2", "C3", "C4", "C5", "WORKLOADS", "ModelDims", "RecordShape", "Workload",
     "TYPE_NAMES_4", "TYPE_NAMES_8", "SEED_RECORDS", "SEED_WEIGHTS", "SEED_KEY",
     "SEED_ARRIVALS", "SEED_CALIB", "scaled", "make_vocab", "vocab_arrays", "FIRST_WORD_ID",
