@@ -456,14 +456,15 @@ def streaming_leg(args, words, key, local) -> dict:
 
     Model: 24 layers, d=1024, 16 heads, FFN 4096, 17 labels, FP8 e4m3 GEMMs with
     static scales (64 calibration records). Records: lognormal(1500, 0.8)
-    clipped 16..4096 tokens, windows 512/384, 8 entity types.
+    clipped 16..4096 tokens, windows 512/384, 8 entity types, URL, hash and CPE
+    recognizers on besides the address/CVE ones.
     """
     import torch
     import paper_2606_15650_b300.api as api
     w5 = synth.scaled(synth.C5, args.stream_records)
     recs = synth.make_records(w5.records, words, seed=synth.SEED_RECORDS + 5)
     blob = synth.pack_blob(w5.dims, synth.make_weights(w5.dims))
-    schema = api.Schema(synth.TYPE_NAMES_8, window=w5.window, stride=w5.stride)
+    schema = api.Schema(synth.TYPE_NAMES_8, window=w5.window, stride=w5.stride, recognizers=synth.RECOGNIZERS_8)
     ctx = api.Context(w5.dims, blob, words, precision="fp8", mode="packed", device=local)
     del blob
     cal = synth.make_records(synth.scaled(w5, 64).records, words, seed=synth.SEED_CALIB)

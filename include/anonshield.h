@@ -116,9 +116,37 @@ typedef struct {
   uint32_t on_device;
 } as_records;
 
+/* Pattern recognizers (AnonShield §2 stage (2) combines the NER model with
+ * custom patterns for addresses, URLs, host names, hashes, certificates and
+ * CVE/CPE identifiers; its entity types include UUIDs and OIDs). Index of a
+ * recognizer in as_schema.recognizer_types. Word recognizers test one word
+ * (a maximal run of [A-Za-z0-9.:-], trailing '.', '-', ':' stripped); the
+ * multi-word ones (URL, CPE, PEM) start at a word start and may cover
+ * several words. A candidate starting inside an accepted multi-word span is
+ * dropped, as in a left-to-right regex scan. */
+enum {
+  AS_RX_MAC = 0,       /* six hex pairs joined by one of ':' '-'                     */
+  AS_RX_IPV6 = 1,      /* 1..4-hex groups, eight, or at most seven with one '::'      */
+  AS_RX_IPV4 = 2,      /* four octets 0..255, no leading zeros; ':port' not in span   */
+  AS_RX_CVE = 3,       /* CVE-dddd-dddd+                                              */
+  AS_RX_HOSTNAME = 4,  /* >= 2 labels, last one alphabetic; ':port' not in span       */
+  AS_RX_URL = 5,       /* scheme://..., trailing .,:;!? stripped                      */
+  AS_RX_HASH = 6,      /* 32, 40, 64 or 128 hex digits                                */
+  AS_RX_UUID = 7,      /* 8-4-4-4-12 hex                                             */
+  AS_RX_CPE = 8,       /* cpe:2.3: with 11 components, or cpe:/ URI form              */
+  AS_RX_OID = 9,       /* >= 5 dotted decimal arcs, first 0..2                        */
+  AS_RX_CERT_FP = 10,  /* 16, 20 or 32 hex pairs joined by ':'                        */
+  AS_RX_PEM = 11,      /* -----BEGIN CERTIFICATE----- ... -----END CERTIFICATE-----   */
+  AS_RX_KINDS = 12
+};
+
 /* Replacement policy. type_names[t-1] is the name of entity type t
- * (t = 1..n_types; label 2t-1 = B-t, 2t = I-t, 0 = O). Pattern recognizers
- * emit types 1 IP_ADDRESS, 2 HOSTNAME, 3 CVE_ID, 4 MAC_ADDRESS.
+ * (t = 1..n_types; label 2t-1 = B-t, 2t = I-t, 0 = O).
+ * recognizer_types: NULL, or AS_RX_KINDS entries giving the entity type each
+ * recognizer emits (0 = recognizer off; every type <= n_types). NULL maps
+ * MAC to 4, IPv6 and IPv4 to 1, CVE to 3, host name to 2 (types 1
+ * IP_ADDRESS, 2 HOSTNAME, 3 CVE_ID, 4 MAC_ADDRESS; needs n_types >= 4) and
+ * switches the rest off. The table is copied by the call.
  * preserve_mask bit t set: type t is detected but passed through (the
  * paper's --entities-to-preserve, §2). slug_hex_len: 0..64 hex characters
  * (§2 stage (3)). window/stride: sliding windows for records longer than
@@ -130,6 +158,7 @@ typedef struct {
   uint64_t preserve_mask;
   uint32_t slug_hex_len;
   uint32_t window, stride;
+  const uint8_t* recognizer_types;
 } as_schema;
 
 /* One entity-map entry (§2 stage (4)): type, original bytes, full 64-hex

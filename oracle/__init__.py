@@ -9,7 +9,8 @@ the same seeded inputs from ``synth``.
 
 Modules, in pipeline order:
   tokenizer      byte pre-tokenization and greedy longest-match subwords
-  recognizers    pattern recognizers: IPv4 (+port), IPv6, CVE, host name (+port), MAC
+  recognizers    pattern recognizers: MAC, IPv6, IPv4 (+port), CVE, host name (+port), hash,
+                 UUID, certificate fingerprint, OID, PEM certificate, URL, CPE
   encoder        encoder-only token classifier, FP64, with sliding windows
   bio            BIO label decoding to token spans
   spans          token -> byte spans, overlap rule, preserve filter

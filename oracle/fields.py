@@ -50,7 +50,7 @@ def detect_spans(sub: bytes, schema: Schema, encoder: Encoder, vocab: dict[bytes
                  labels: list[int] | None = None) -> list[tuple[int, int, int]]:
     """Final spans of one detected field (its own record), relative to the field."""
     ids, offs, lens = tokenizer.tokenize(sub, vocab)
-    regex = recognizers.recognize(sub)
+    regex = recognizers.recognize(sub, schema.recognizers)
     if labels is None:
         logits = record_logits(encoder, ids, schema.window, schema.stride)
         labels = argmax_first(logits).tolist() if len(ids) else []

@@ -25,6 +25,7 @@ class Schema:
     slug_hex_len: int = 10
     window: int = 0
     stride: int = 0
+    recognizers: tuple[int, ...] | None = None   # kind -> entity type (None: the default five)
 
 
 @dataclass
@@ -66,7 +67,7 @@ def anonymize(records: list[bytes], schema: Schema, key: bytes, encoder: Encoder
     n_enc = 0
     for i, data in enumerate(records):
         ids, offs, lens = tokenizer.tokenize(data, vocab)
-        regex = recognizers.recognize(data)
+        regex = recognizers.recognize(data, schema.recognizers)
         logits = record_logits(encoder, ids, schema.window, schema.stride)
         labels = argmax_first(logits).tolist() if len(ids) else []
         n_enc += encoded_tokens(len(ids), schema.window, schema.stride)
@@ -87,7 +88,7 @@ def anonymize_from_labels(records: list[bytes], labels: list[list[int]], schema:
         ids, offs, lens = tokenizer.tokenize(data, vocab)
         if len(labels[i]) != len(ids):
             raise ValueError(f"record {i}: {len(labels[i])} labels for {len(ids)} tokens")
-        regex = recognizers.recognize(data)
+        regex = recognizers.recognize(data, schema.recognizers)
         tr = _finish(data, ids, offs, lens, regex, None, labels[i], schema, key, record_base + i, emap)
         outs.append(tr.output)
         traces.append(tr)

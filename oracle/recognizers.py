@@ -1,16 +1,20 @@
 """Pattern recognizers (oracle).
 
 The paper combines its NER model with 21 custom patterns covering, among
-others, IPv4/IPv6 addresses, host names and CVE identifiers (§2 stage (2)),
-and does not print them. This project implements five, as plain character
-checks (no regular-expression engine), under the following reading:
+others, IPv4/IPv6 addresses, URLs, host names, hashes, certificates and
+CVE/CPE identifiers, and lists UUIDs and OIDs among its entity types
+(§2 stages (2) and (5)); it does not print the patterns. This project
+implements twelve recognizers, as plain character checks (no
+regular-expression engine), under the following reading.
 
+Words and word recognizers
 * A word is a maximal run of bytes in ``[A-Za-z0-9.:-]``. Trailing ``.`` and
   ``-`` are stripped, and so is a trailing ``:`` unless it is the second
   colon of a final ``::`` (so ``fe80::`` stays an IPv6 address).
-* Each word yields at most one entity; the checks run in this order and the
+* A word yields at most one entity; the checks run in this order and the
   first that accepts the whole word wins (no matching inside a word):
-  MAC, IPv6, IPv4 (optionally ``:port``), CVE, host name (optionally ``:port``).
+  MAC, IPv6, IPv4 (optionally ``:port``), CVE, host name (optionally
+  ``:port``), hash, UUID, certificate fingerprint, OID.
   A port is ``:`` and 1..5 digits and is left out of the entity span.
 * MAC: six groups of two hex digits joined by one separator used throughout,
   ``:`` or ``-``.
@@ -22,13 +26,52 @@ checks (no regular-expression engine), under the following reading:
 * Host name: two or more labels of 1..63 bytes from ``[A-Za-z0-9-]`` that
   neither start nor end with ``-``, the last label all letters and at least
   two long, at most 253 bytes in all.
+* Hash: 32, 40, 64 or 128 hex digits (MD5, SHA-1, SHA-256, SHA-512).
+* UUID: hex groups of 8, 4, 4, 4 and 12 digits joined by ``-``.
+* Certificate fingerprint: 16, 20 or 32 groups of two hex digits joined by
+  ``:`` (MD5, SHA-1, SHA-256 fingerprints).
+* OID: five or more decimal arcs joined by ``.``, no leading zeros, the first
+  arc 0, 1 or 2, and the second at most 39 when the first is 0 or 1. (Four
+  arcs would collide with IPv4 and three with version numbers.)
 
-Entity type ids: 1 IP_ADDRESS (both IP families; the paper's example prefix,
-§2 stage (3)), 2 HOSTNAME, 3 CVE_ID, 4 MAC_ADDRESS.
+Recognizers that span several words. They are tried first, at the start of
+a word run; the first that matches there wins:
+* PEM certificate, only at the start of a line (record start or after
+  ``\\n``): ``-----BEGIN CERTIFICATE-----``, then only base64 bytes
+  ``[A-Za-z0-9+/=]`` and ASCII white space, then
+  ``-----END CERTIFICATE-----``, which ends the span.
+* URL: a scheme of 2..16 letters and digits beginning with a letter,
+  ``://``, then the longest run of URL bytes (letters, digits and
+  ``-._~:/?#[]@!$&*+,;=%``); trailing ``.,:;!?`` are stripped and at least
+  one byte must remain after ``://``.
+* CPE, formatted-string form: ``cpe:2.3:`` and eleven non-empty components
+  of ``[A-Za-z0-9._~%!*?-]`` joined by ``:``; the first (part) is ``a``,
+  ``o``, ``h``, ``*`` or ``-``; the span ends with the eleventh component,
+  less trailing ``.``. URI form: ``cpe:/``, a part letter ``a``, ``o`` or
+  ``h``, then up to six ``:``-prefixed components of ``[A-Za-z0-9._~%-]``
+  (possibly empty); trailing ``.`` and ``:`` are stripped.
+
+Resolution. Candidates are taken left to right, as a scanning regex engine
+does: a candidate whose start lies inside an already accepted span is
+dropped. Only the multi-word recognizers can cover another candidate.
+
+Recognizers map to entity types through a table of twelve entries indexed
+by kind (``KIND_*``; 0 switches a recognizer off). The default maps the
+five address/CVE recognizers to 1 IP_ADDRESS (both IP families; the
+paper's example prefix, §2 stage (3)), 2 HOSTNAME, 3 CVE_ID, 4 MAC_ADDRESS
+and switches the rest off.
 """
 from __future__ import annotations
 
 IP_ADDRESS, HOSTNAME, CVE_ID, MAC_ADDRESS = 1, 2, 3, 4
+
+# recognizer kinds (index into the kind -> entity type table)
+(KIND_MAC, KIND_IPV6, KIND_IPV4, KIND_CVE, KIND_HOSTNAME, KIND_URL, KIND_HASH, KIND_UUID,
+ KIND_CPE, KIND_OID, KIND_CERT_FP, KIND_PEM) = range(12)
+N_KINDS = 12
+KIND_NAMES = ("mac", "ipv6", "ipv4", "cve", "hostname", "url", "hash", "uuid", "cpe", "oid",
+              "cert_fp", "pem")
+DEFAULT_TYPES = (MAC_ADDRESS, IP_ADDRESS, IP_ADDRESS, CVE_ID, HOSTNAME, 0, 0, 0, 0, 0, 0, 0)
 
 _HEX = set(b"0123456789abcdefABCDEF")
 _DIG = set(b"0123456789")
@@ -165,19 +208,195 @@ def hostname_len(w: bytes) -> int:
     return len(core)
 
 
-def recognize(data: bytes) -> list[tuple[int, int, int]]:
-    """Entity spans (start, length, type) of one record, in order of start."""
+def is_hash(w: bytes) -> bool:
+    return len(w) in (32, 40, 64, 128) and all(c in _HEX for c in w)
+
+
+def is_uuid(w: bytes) -> bool:
+    groups = w.split(b"-")
+    if [len(g) for g in groups] != [8, 4, 4, 4, 12]:
+        return False
+    return all(c in _HEX for g in groups for c in g)
+
+
+def is_cert_fingerprint(w: bytes) -> bool:
+    groups = w.split(b":")
+    if len(groups) not in (16, 20, 32):
+        return False
+    return all(len(g) == 2 and g[0] in _HEX and g[1] in _HEX for g in groups)
+
+
+def is_oid(w: bytes) -> bool:
+    arcs = w.split(b".")
+    if len(arcs) < 5:
+        return False
+    for a in arcs:
+        if len(a) == 0 or any(c not in _DIG for c in a):
+            return False
+        if len(a) > 1 and a[0] == ord("0"):
+            return False
+    first = int(arcs[0])
+    if first > 2:
+        return False
+    return first == 2 or int(arcs[1]) <= 39
+
+
+_B64 = _DIG | _ALPHA | set(b"+/=")
+_SPACE = set(b"\t\n\v\f\r ")
+_PEM_BEGIN = b"-----BEGIN CERTIFICATE-----"
+_PEM_END = b"-----END CERTIFICATE-----"
+_URL = _DIG | _ALPHA | set(b"-._~:/?#[]@!$&*+,;=%")
+_URL_TRAIL = set(b".,:;!?")
+_CPE_FS = _DIG | _ALPHA | set(b"._~%!*?-")
+_CPE_URI = _DIG | _ALPHA | set(b"._~%-")
+
+
+def pem_end(data: bytes, i: int) -> int:
+    """End of a PEM certificate block starting at ``i``, else -1."""
+    if not (i == 0 or data[i - 1] == ord("\n")):
+        return -1
+    if data[i:i + len(_PEM_BEGIN)] != _PEM_BEGIN:
+        return -1
+    j = i + len(_PEM_BEGIN)
+    while j < len(data) and (data[j] in _B64 or data[j] in _SPACE):
+        j += 1
+    if data[j:j + len(_PEM_END)] != _PEM_END:
+        return -1
+    return j + len(_PEM_END)
+
+
+def url_end(data: bytes, i: int) -> int:
+    """End of a URL starting at ``i``, else -1."""
+    j = i
+    while j < len(data) and (data[j] in _ALPHA or data[j] in _DIG):
+        j += 1
+    if not (2 <= j - i <= 16) or data[i] not in _ALPHA or data[j:j + 3] != b"://":
+        return -1
+    body = j + 3
+    e = body
+    while e < len(data) and data[e] in _URL:
+        e += 1
+    while e > body and data[e - 1] in _URL_TRAIL:
+        e -= 1
+    return e if e > body else -1
+
+
+def _run(data: bytes, j: int, allowed: set) -> int:
+    while j < len(data) and data[j] in allowed:
+        j += 1
+    return j
+
+
+def cpe_end(data: bytes, i: int) -> int:
+    """End of a CPE name (formatted string or URI form) starting at ``i``, else -1."""
+    if data[i:i + 8] == b"cpe:2.3:":
+        j = i + 8
+        for comp in range(11):
+            if comp > 0:
+                if j >= len(data) or data[j] != ord(":"):
+                    return -1
+                j += 1
+            e = _run(data, j, _CPE_FS)
+            if e == j:
+                return -1
+            if comp == 0 and data[j:e] not in (b"a", b"o", b"h", b"*", b"-"):
+                return -1
+            start_last, j = j, e
+        while j > start_last + 1 and data[j - 1] == ord("."):
+            j -= 1
+        return j if data[j - 1] != ord(".") else -1
+    if data[i:i + 5] == b"cpe:/" and i + 5 < len(data) and data[i + 5] in b"aoh":
+        j = i + 6
+        for _ in range(6):
+            if j < len(data) and data[j] == ord(":"):
+                j = _run(data, j + 1, _CPE_URI)
+            else:
+                break
+        while data[j - 1] in b".:":
+            j -= 1
+        return j
+    return -1
+
+
+def _word_runs(data: bytes) -> list[tuple[int, int, int]]:
+    """(run start, run end, stripped end) of each maximal run of word bytes."""
+    out = []
+    n = len(data)
+    i = 0
+    while i < n:
+        if data[i] not in _WORD:
+            i += 1
+            continue
+        j = i
+        while j < n and data[j] in _WORD:
+            j += 1
+        end = j
+        while end > i:
+            c = data[end - 1]
+            if c == ord(".") or c == ord("-"):
+                end -= 1
+            elif c == ord(":") and not (end - 2 >= i and data[end - 2] == ord(":")):
+                end -= 1
+            else:
+                break
+        out.append((i, j, end))
+        i = j
+    return out
+
+
+def _word_match(w: bytes, types) -> tuple[int, int]:
+    """(span length, type) of the first enabled word recognizer accepting ``w``, else (0, 0)."""
+    checks = (
+        (KIND_MAC, lambda: len(w) if is_mac(w) else 0),
+        (KIND_IPV6, lambda: len(w) if is_ipv6(w) else 0),
+        (KIND_IPV4, lambda: ipv4_len(w)),
+        (KIND_CVE, lambda: len(w) if is_cve(w) else 0),
+        (KIND_HOSTNAME, lambda: hostname_len(w)),
+        (KIND_HASH, lambda: len(w) if is_hash(w) else 0),
+        (KIND_UUID, lambda: len(w) if is_uuid(w) else 0),
+        (KIND_CERT_FP, lambda: len(w) if is_cert_fingerprint(w) else 0),
+        (KIND_OID, lambda: len(w) if is_oid(w) else 0),
+    )
+    for kind, check in checks:
+        if types[kind]:
+            n = check()
+            if n > 0:
+                return n, types[kind]
+    return 0, 0
+
+
+def candidates(data: bytes, types=None) -> list[tuple[int, int, int]]:
+    """Every recognizer candidate (start, length, type), one per word run, before resolution."""
+    types = DEFAULT_TYPES if types is None else tuple(types)
+    assert len(types) == N_KINDS
+    out = []
+    for s, _, e in _word_runs(data):
+        hit = None
+        for kind, find in ((KIND_PEM, pem_end), (KIND_URL, url_end), (KIND_CPE, cpe_end)):
+            if types[kind]:
+                end = find(data, s)
+                if end > s:
+                    hit = (s, end - s, types[kind])
+                    break
+        if hit is None and e > s:
+            n, t = _word_match(data[s:e], types)
+            if n > 0:
+                hit = (s, n, t)
+        if hit is not None:
+            out.append(hit)
+    return out
+
+
+def recognize(data: bytes, types=None) -> list[tuple[int, int, int]]:
+    """Entity spans (start, length, type) of one record, in order of start.
+
+    ``types`` is the kind -> entity type table (``N_KINDS`` entries, 0 = off);
+    None selects ``DEFAULT_TYPES``."""
     spans = []
-    for s, e in words(data):
-        w = data[s:e]
-        if is_mac(w):
-            spans.append((s, e - s, MAC_ADDRESS))
-        elif is_ipv6(w):
-            spans.append((s, e - s, IP_ADDRESS))
-        elif (n := ipv4_len(w)) > 0:
-            spans.append((s, n, IP_ADDRESS))
-        elif is_cve(w):
-            spans.append((s, e - s, CVE_ID))
-        elif (n := hostname_len(w)) > 0:
-            spans.append((s, n, HOSTNAME))
+    kept_end = 0
+    for s, n, t in candidates(data, types):
+        if s < kept_end:
+            continue
+        spans.append((s, n, t))
+        kept_end = s + n
     return spans

@@ -25,6 +25,17 @@ MODE = {"packed": 0, "per_record": 1}
 EPI = {"bias": 0, "bias_gelu": 1, "bias_resid": 2}
 ENGINE = {"auto": 0, "tcgen05": 1, "simt": 2}
 ATTENTION = {"tcgen05": 0, "mma_sync": 1}
+RX_KIND = {"mac": 0, "ipv6": 1, "ipv4": 2, "cve": 3, "hostname": 4, "url": 5, "hash": 6, "uuid": 7, "cpe": 8,
+           "oid": 9, "cert_fp": 10, "pem": 11}
+RX_KINDS = 12
+
+
+def recognizer_table(types: dict[str, int]) -> tuple[int, ...]:
+    """Kind -> entity type table for Schema.recognizers from {kind name: type} (others off)."""
+    t = [0] * RX_KINDS
+    for k, v in types.items():
+        t[RX_KIND[k]] = v
+    return tuple(t)
 
 
 class AnonShieldError(RuntimeError):
@@ -50,7 +61,8 @@ class _Records(C.Structure):
 
 class _Schema(C.Structure):
     _fields_ = [("n_types", C.c_uint32), ("type_names", C.POINTER(C.c_char_p)), ("preserve_mask", C.c_uint64),
-                ("slug_hex_len", C.c_uint32), ("window", C.c_uint32), ("stride", C.c_uint32)]
+                ("slug_hex_len", C.c_uint32), ("window", C.c_uint32), ("stride", C.c_uint32),
+                ("recognizer_types", C.POINTER(C.c_uint8))]
 
 
 class _Entity(C.Structure):
@@ -268,6 +280,9 @@ class Schema:
     slug_hex_len: int = 10
     window: int = 0
     stride: int = 0
+    # entity type per recognizer kind (RX_KIND order, 0 = off); None = the
+    # five address/CVE recognizers to types 1..4 (see recognizer_table)
+    recognizers: tuple[int, ...] | None = None
 
 
 @dataclass
@@ -437,6 +452,12 @@ class Context:
         names = (C.c_char_p * len(s.type_names))(*[n.encode() for n in s.type_names])
         sc = _Schema(n_types=len(s.type_names), type_names=names, preserve_mask=s.preserve_mask,
                      slug_hex_len=s.slug_hex_len, window=s.window, stride=s.stride)
+        if s.recognizers is not None:
+            if len(s.recognizers) != RX_KINDS:
+                raise ValueError(f"recognizers needs {RX_KINDS} entries (one per recognizer kind)")
+            table = (C.c_uint8 * RX_KINDS)(*s.recognizers)
+            sc.recognizer_types = C.cast(table, C.POINTER(C.c_uint8))
+            return sc, (names, table)
         return sc, names
 
     def anonymize(self, data, offsets, schema: Schema, key: bytes) -> Output:

@@ -710,13 +710,34 @@ as_status ensure_encoder_buffers(as_ctx* c, Lane* ln, uint64_t rows, uint64_t n_
   return AS_OK;
 }
 
+RxTypes recognizer_table(const as_schema* s) {
+  static_assert(AS_RX_KINDS == kRxKinds && AS_RX_URL == kRxUrl && AS_RX_CPE == kRxCpe && AS_RX_PEM == kRxPem &&
+                    AS_RX_MAC == kRxMac && AS_RX_OID == kRxOid && AS_RX_CERT_FP == kRxCertFp,
+                "recognizer kinds of the ABI and the kernels agree");
+  RxTypes r{};
+  if (s->recognizer_types) {
+    for (int k = 0; k < kRxKinds; ++k) r.t[k] = s->recognizer_types[k];
+  } else {
+    r.t[kRxMac] = 4;
+    r.t[kRxIpv6] = r.t[kRxIpv4] = 1;
+    r.t[kRxCve] = 3;
+    r.t[kRxHost] = 2;
+  }
+  return r;
+}
+
 as_status validate_schema(as_ctx* c, const as_schema* s) {
   if (!s) return fail(c, AS_ERR_ARG, "schema is NULL");
   const as_config& g = c->cfg;
   if (s->n_types < 1 || s->n_types > 62) return fail(c, AS_ERR_ARG, "n_types must be 1..62");
   if (2 * s->n_types + 1 != g.n_labels)
     return fail(c, AS_ERR_ARG, "n_labels must equal 2 * n_types + 1 (O, B-t, I-t)");
-  if (s->n_types < 4) return fail(c, AS_ERR_ARG, "the pattern recognizers need entity types 1..4");
+  if (!s->recognizer_types && s->n_types < 4)
+    return fail(c, AS_ERR_ARG, "the default pattern recognizers need entity types 1..4");
+  if (s->recognizer_types)
+    for (int k = 0; k < AS_RX_KINDS; ++k)
+      if (s->recognizer_types[k] > s->n_types)
+        return fail(c, AS_ERR_ARG, "recognizer_types[" + std::to_string(k) + "] exceeds n_types");
   if (!s->type_names) return fail(c, AS_ERR_ARG, "type_names is NULL");
   for (uint32_t t = 0; t < s->n_types; ++t)
     if (!s->type_names[t] || !s->type_names[t][0]) return fail(c, AS_ERR_ARG, "empty type name");
@@ -834,8 +855,11 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   // recognizers (pos_b reused after the token emit above)
   CKS(grow(ln->rx_len_b, N * 4));
   CKS(grow(ln->rx_type_b, N + 16));
-  launch_recognize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(),
-                        st);
+  const RxTypes rxt = recognizer_table(sch);
+  launch_recognize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), rxt, ln->rx_len_b.as<uint32_t>(),
+                        ln->rx_type_b.as<uint8_t>(), st);
+  if (rx_any_long(rxt))
+    launch_recognize_resolve(d_off, n, ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), st);
   CKS(grow(ln->rx_pos, (N + 1) * 4));
   exclusive_scan<uint32_t>(NonZeroU8{ln->rx_type_b.as<uint8_t>()}, N, ln->rx_pos.as<uint32_t>(), cnt + 1,
                            ln->scan_tiles.as<uint32_t>(), st);
@@ -1305,6 +1329,7 @@ struct Server {
   as_ctx* c = nullptr;
   std::vector<std::string> names;
   std::vector<const char*> name_ptrs;
+  uint8_t rx_types[AS_RX_KINDS] = {};
   as_schema schema{};
   uint64_t batch_bytes = 0;
   uint32_t max_batch = 0;
@@ -1880,6 +1905,10 @@ as_status as_serve_start(as_ctx* c, const as_schema* schema, const uint8_t* key,
   for (auto& n : sv->names) sv->name_ptrs.push_back(n.c_str());
   sv->schema = *schema;
   sv->schema.type_names = sv->name_ptrs.data();
+  if (schema->recognizer_types) {
+    std::copy(schema->recognizer_types, schema->recognizer_types + AS_RX_KINDS, sv->rx_types);
+    sv->schema.recognizer_types = sv->rx_types;
+  }
   const uint64_t chunk = c->cfg.max_chunk_tokens ? c->cfg.max_chunk_tokens : (1ull << 19);
   sv->batch_bytes = cfg->max_batch_bytes ? cfg->max_batch_bytes : chunk * 3 / 4;
   sv->max_batch = cfg->max_batch_records ? cfg->max_batch_records : 65536;

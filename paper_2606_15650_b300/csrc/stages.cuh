@@ -38,9 +38,25 @@ void launch_token_lengths(const uint32_t* tok_off, uint32_t T, uint32_t N, uint3
 void launch_record_token_offsets(const uint64_t* offsets, uint64_t n_records, const uint32_t* pos, uint32_t N,
                                  const uint32_t* total_T, uint64_t* rec_tok, cudaStream_t st);
 
-// Pattern recognizers: rx_len[i] / rx_type[i] at each word start that is an entity.
-void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, uint32_t* rx_len,
-                           uint8_t* rx_type, cudaStream_t st);
+// Pattern recognizers: rx_len[i] / rx_type[i] at each word start that is an
+// entity candidate. RxTypes maps each recognizer kind (the order of
+// as_rx_kind: MAC, IPv6, IPv4, CVE, host name, URL, hash, UUID, CPE, OID,
+// certificate fingerprint, PEM certificate) to an entity type, 0 = off.
+// Candidates of the multi-word kinds (URL, CPE, PEM) carry kRxLong in their
+// type until launch_recognize_resolve has dropped every candidate that starts
+// inside an accepted multi-word span; it must run whenever one of those
+// kinds is on.
+constexpr int kRxMac = 0, kRxIpv6 = 1, kRxIpv4 = 2, kRxCve = 3, kRxHost = 4, kRxUrl = 5, kRxHash = 6, kRxUuid = 7,
+              kRxCpe = 8, kRxOid = 9, kRxCertFp = 10, kRxPem = 11, kRxKinds = 12;
+constexpr uint8_t kRxLong = 0x80;
+struct RxTypes {
+  uint8_t t[kRxKinds];
+};
+inline bool rx_any_long(const RxTypes& r) { return r.t[kRxUrl] || r.t[kRxCpe] || r.t[kRxPem]; }
+void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, RxTypes types,
+                           uint32_t* rx_len, uint8_t* rx_type, cudaStream_t st);
+void launch_recognize_resolve(const uint64_t* offsets, uint64_t n_records, const uint32_t* rx_len, uint8_t* rx_type,
+                              cudaStream_t st);
 void launch_recognize_emit(const uint32_t* rx_len, const uint8_t* rx_type, const uint32_t* pos, uint32_t N,
                            uint32_t* sp_start, uint32_t* sp_len, uint8_t* sp_type, cudaStream_t st);
 

@@ -8,8 +8,13 @@
 //
 // Recognizers: a word is a maximal run of [A-Za-z0-9.:-]; trailing '.', '-'
 // and a ':' that does not close a final '::' are stripped; the whole word is
-// then tested as MAC, IPv6, IPv4(:port), CVE id, host name(:port), first
-// match wins, port excluded from the span. One thread per word start.
+// then tested as MAC, IPv6, IPv4(:port), CVE id, host name(:port), hash,
+// UUID, certificate fingerprint, OID, first enabled match wins, port excluded
+// from the span. Before the word tests, the multi-word recognizers (PEM
+// certificate at a line start, URL, CPE name) are tried at the word start.
+// One thread per word start. A second pass, one warp per record, takes the
+// candidates left to right and drops those that start inside an accepted
+// multi-word span (the behaviour of a scanning regex engine).
 #include "scan.cuh"
 #include "stages.cuh"
 
@@ -140,8 +145,6 @@ __device__ __forceinline__ bool is_digit(uint32_t c) { return c - '0' < 10u; }
 __device__ __forceinline__ bool is_alpha(uint32_t c) { return (c | 0x20u) - 'a' < 26u; }
 __device__ __forceinline__ bool is_hex(uint32_t c) { return is_digit(c) || (c | 0x20u) - 'a' < 6u; }
 
-constexpr uint8_t kTypeIP = 1, kTypeHost = 2, kTypeCVE = 3, kTypeMAC = 4;
-
 __device__ bool rx_is_mac(const uint8_t* w, uint32_t n) {
   if (n != 17) return false;
   uint32_t sep = w[2];
@@ -262,13 +265,176 @@ __device__ uint32_t rx_host_len(const uint8_t* w, uint32_t n) {
   return (labels >= 2 && last_alpha) ? core : 0;
 }
 
+__device__ bool rx_is_hash(const uint8_t* w, uint32_t n) {
+  if (n != 32 && n != 40 && n != 64 && n != 128) return false;
+  for (uint32_t k = 0; k < n; ++k)
+    if (!is_hex(w[k])) return false;
+  return true;
+}
+
+__device__ bool rx_is_uuid(const uint8_t* w, uint32_t n) {
+  if (n != 36) return false;
+  for (uint32_t k = 0; k < n; ++k) {
+    const bool dash = k == 8 || k == 13 || k == 18 || k == 23;
+    if (dash ? w[k] != '-' : !is_hex(w[k])) return false;
+  }
+  return true;
+}
+
+// 16, 20 or 32 groups of two hex digits joined by ':'
+__device__ bool rx_is_cert_fp(const uint8_t* w, uint32_t n) {
+  if ((n + 1) % 3) return false;
+  const uint32_t g = (n + 1) / 3;
+  if (g != 16 && g != 20 && g != 32) return false;
+  for (uint32_t k = 0; k < g; ++k) {
+    if (!is_hex(w[3 * k]) || !is_hex(w[3 * k + 1])) return false;
+    if (k + 1 < g && w[3 * k + 2] != ':') return false;
+  }
+  return true;
+}
+
+// >= 5 decimal arcs joined by '.', no leading zeros; first arc 0..2, second
+// arc <= 39 below first arc 2
+__device__ bool rx_is_oid(const uint8_t* w, uint32_t n) {
+  uint32_t arcs = 0, start = 0;
+  for (uint32_t k = 0; k <= n; ++k) {
+    if (k == n || w[k] == '.') {
+      const uint32_t L = k - start;
+      if (L == 0 || (L > 1 && w[start] == '0')) return false;
+      if (arcs == 0 && (L != 1 || w[start] > '2')) return false;
+      if (arcs == 1 && w[0] < '2' && (L > 2 || (L == 2 && (w[start] - '0') * 10 + (w[start + 1] - '0') > 39)))
+        return false;
+      ++arcs;
+      start = k + 1;
+    } else if (!is_digit(w[k])) {
+      return false;
+    }
+  }
+  return arcs >= 5;
+}
+
+// byte sets of the multi-word recognizers, as 128-bit masks over ASCII
+constexpr uint64_t set_lo(const char* s, uint64_t m = 0) {
+  return *s ? set_lo(s + 1, (unsigned char)*s < 64 ? m | (1ull << (unsigned char)*s) : m) : m;
+}
+constexpr uint64_t set_hi(const char* s, uint64_t m = 0) {
+  return *s ? set_hi(s + 1, (unsigned char)*s >= 64 && (unsigned char)*s < 128 ? m | (1ull << ((unsigned char)*s - 64)) : m)
+            : m;
+}
+// a byte set is two scalar masks (lo: bytes 0..63, hi: 64..127), passed by value
+#define AS_ALNUM "0123456789ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz"
+#define AS_BYTE_SET(name, chars) \
+  constexpr uint64_t name##_lo = set_lo(chars), name##_hi = set_hi(chars);
+AS_BYTE_SET(kUrlBytes, AS_ALNUM "-._~:/?#[]@!$&*+,;=%")
+AS_BYTE_SET(kUrlTrail, ".,:;!?")
+AS_BYTE_SET(kCpeFsBytes, AS_ALNUM "._~%!*?-")
+AS_BYTE_SET(kCpeUriBytes, AS_ALNUM "._~%-")
+AS_BYTE_SET(kB64Space, AS_ALNUM "+/=\t\n\v\f\r ")
+#undef AS_BYTE_SET
+#undef AS_ALNUM
+#define AS_SET(name) name##_lo, name##_hi
+__device__ __forceinline__ bool in_set(uint32_t c, uint64_t lo, uint64_t hi) {
+  return c < 64 ? (lo >> c) & 1u : c < 128 ? (hi >> (c - 64)) & 1u : false;
+}
+
+__constant__ char kPemBegin[] = "-----BEGIN CERTIFICATE-----";
+__constant__ char kPemEnd[] = "-----END CERTIFICATE-----";
+
+// Scanning helpers for a candidate starting at record position i: a byte
+// p > i belongs to the record while p < N and no record starts at p.
+struct RecScan {
+  const uint8_t* b;
+  uint32_t N;
+  const uint32_t* rs;
+  uint32_t i;
+  __device__ __forceinline__ bool in(uint32_t p) const { return p < N && (p == i || !rs_bit(rs, p)); }
+  __device__ __forceinline__ uint32_t run(uint32_t p, uint64_t lo, uint64_t hi) const {
+    while (in(p) && in_set(b[p], lo, hi)) ++p;
+    return p;
+  }
+  __device__ __forceinline__ bool lit(uint32_t p, const char* s, uint32_t n) const {
+    for (uint32_t k = 0; k < n; ++k)
+      if (!in(p + k) || b[p + k] != (uint8_t)s[k]) return false;
+    return true;
+  }
+};
+
+// End of a PEM certificate block starting at i (a line start), else 0.
+__device__ uint32_t rx_pem_end(const RecScan& r) {
+  const uint32_t i = r.i;
+  if (!(i == 0 || rs_bit(r.rs, i) || r.b[i - 1] == '\n')) return 0;
+  if (!r.lit(i, kPemBegin, sizeof(kPemBegin) - 1)) return 0;
+  const uint32_t j = r.run(i + sizeof(kPemBegin) - 1, AS_SET(kB64Space));
+  if (!r.lit(j, kPemEnd, sizeof(kPemEnd) - 1)) return 0;
+  return j + sizeof(kPemEnd) - 1;
+}
+
+// End of a URL starting at i, else 0.
+__device__ uint32_t rx_url_end(const RecScan& r) {
+  const uint32_t i = r.i;
+  if (!is_alpha(r.b[i])) return 0;
+  uint32_t j = i + 1;
+  while (r.in(j) && is_alnum(r.b[j])) {
+    if (++j - i > 16) return 0;
+  }
+  if (j - i < 2 || !r.lit(j, "://", 3)) return 0;
+  const uint32_t body = j + 3;
+  uint32_t e = r.run(body, AS_SET(kUrlBytes));
+  while (e > body && in_set(r.b[e - 1], AS_SET(kUrlTrail))) --e;
+  return e > body ? e : 0;
+}
+
+// End of a CPE name (formatted string or URI form) starting at i, else 0.
+__device__ uint32_t rx_cpe_end(const RecScan& r) {
+  const uint32_t i = r.i;
+  if (r.lit(i, "cpe:2.3:", 8)) {
+    uint32_t j = i + 8, last = j;
+    for (int comp = 0; comp < 11; ++comp) {
+      if (comp > 0) {
+        if (!r.in(j) || r.b[j] != ':') return 0;
+        ++j;
+      }
+      const uint32_t e = r.run(j, AS_SET(kCpeFsBytes));
+      if (e == j) return 0;
+      if (comp == 0) {
+        const uint32_t p = r.b[j];
+        if (e - j != 1 || !(p == 'a' || p == 'o' || p == 'h' || p == '*' || p == '-')) return 0;
+      }
+      last = j;
+      j = e;
+    }
+    while (j > last + 1 && r.b[j - 1] == '.') --j;
+    return r.b[j - 1] == '.' ? 0 : j;
+  }
+  if (r.lit(i, "cpe:/", 5) && r.in(i + 5) && (r.b[i + 5] == 'a' || r.b[i + 5] == 'o' || r.b[i + 5] == 'h')) {
+    uint32_t j = i + 6;
+    for (int comp = 0; comp < 6 && r.in(j) && r.b[j] == ':'; ++comp) j = r.run(j + 1, AS_SET(kCpeUriBytes));
+    while (r.b[j - 1] == '.' || r.b[j - 1] == ':') --j;
+    return j;
+  }
+  return 0;
+}
+
+#undef AS_SET
+
 __global__ void recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs,
-                                      uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
+                                      RxTypes T, uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     uint32_t len = 0;
     uint8_t type = 0;
     uint32_t c = bytes[i];
     if (in_word(c) && (i == 0 || rs_bit(rs, i) || !in_word(bytes[i - 1]))) {
+      if (T.t[kRxPem] | T.t[kRxUrl] | T.t[kRxCpe]) {
+        const RecScan r{bytes, N, rs, i};
+        uint32_t le = 0;
+        if (T.t[kRxPem] && (le = rx_pem_end(r)) > i) type = T.t[kRxPem];
+        else if (T.t[kRxUrl] && (le = rx_url_end(r)) > i) type = T.t[kRxUrl];
+        else if (T.t[kRxCpe] && (le = rx_cpe_end(r)) > i) type = T.t[kRxCpe];
+        if (type) {
+          len = le - i;
+          type |= kRxLong;
+        }
+      }
       uint32_t e = i + 1;
       while (e < N && in_word(bytes[e]) && !rs_bit(rs, e)) ++e;
       while (e > i) {
@@ -279,13 +445,17 @@ __global__ void recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_
       }
       const uint8_t* w = bytes + i;
       uint32_t n = e - i;
-      if (n > 0) {
+      if (n > 0 && !type) {
         uint32_t k;
-        if (rx_is_mac(w, n)) { len = n; type = kTypeMAC; }
-        else if (rx_is_ipv6(w, n)) { len = n; type = kTypeIP; }
-        else if ((k = rx_ipv4_len(w, n)) > 0) { len = k; type = kTypeIP; }
-        else if (rx_is_cve(w, n)) { len = n; type = kTypeCVE; }
-        else if ((k = rx_host_len(w, n)) > 0) { len = k; type = kTypeHost; }
+        if (T.t[kRxMac] && rx_is_mac(w, n)) { len = n; type = T.t[kRxMac]; }
+        else if (T.t[kRxIpv6] && rx_is_ipv6(w, n)) { len = n; type = T.t[kRxIpv6]; }
+        else if (T.t[kRxIpv4] && (k = rx_ipv4_len(w, n)) > 0) { len = k; type = T.t[kRxIpv4]; }
+        else if (T.t[kRxCve] && rx_is_cve(w, n)) { len = n; type = T.t[kRxCve]; }
+        else if (T.t[kRxHost] && (k = rx_host_len(w, n)) > 0) { len = k; type = T.t[kRxHost]; }
+        else if (T.t[kRxHash] && rx_is_hash(w, n)) { len = n; type = T.t[kRxHash]; }
+        else if (T.t[kRxUuid] && rx_is_uuid(w, n)) { len = n; type = T.t[kRxUuid]; }
+        else if (T.t[kRxCertFp] && rx_is_cert_fp(w, n)) { len = n; type = T.t[kRxCertFp]; }
+        else if (T.t[kRxOid] && rx_is_oid(w, n)) { len = n; type = T.t[kRxOid]; }
       }
     }
     rx_len[i] = len;
@@ -293,10 +463,85 @@ __global__ void recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_
   }
 }
 
-void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, uint32_t* rx_len, uint8_t* rx_type,
-                           cudaStream_t st) {
+void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, RxTypes types, uint32_t* rx_len,
+                           uint8_t* rx_type, cudaStream_t st) {
   if (N == 0) return;
-  recognize_mark_kernel<<<grid_1d(N, 256, 148 * 64), 256, 0, st>>>(bytes, N, rs, rx_len, rx_type);
+  recognize_mark_kernel<<<grid_1d(N, 256, 148 * 64), 256, 0, st>>>(bytes, N, rs, types, rx_len, rx_type);
+  count_launch();
+}
+
+// One warp per record, 512 bytes of rx_type per step (16 per lane, one
+// aligned 16-byte load; rx_type has 16 bytes of slack past N). kept_end is
+// the end of the last accepted multi-word span. Within a step the accepted
+// spans are taken in byte order: the lowest lane holding an open multi-word
+// candidate accepts its first one and every lane drops its candidates that
+// start inside it. Writes touch only this record's bytes.
+__global__ void recognize_resolve_kernel(const uint64_t* __restrict__ offsets, uint64_t n,
+                                         const uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
+    const uint32_t a = (uint32_t)offsets[r], b = (uint32_t)offsets[r + 1];
+    uint32_t kept_end = a;
+    for (uint32_t base = a & ~15u; base < b; base += 512) {
+      const uint32_t q = base + lane * 16;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (q < b) v = *reinterpret_cast<const uint4*>(rx_type + q);
+      const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+      uint32_t cand = 0, open = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t t = (words[k >> 2] >> (8 * (k & 3))) & 0xffu;
+        const uint32_t p = q + k;
+        if (t && p >= a && p < b) {
+          cand |= 1u << k;
+          if (t & kRxLong) open |= 1u << k;
+        }
+      }
+      uint32_t drop = 0, accepted = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (((cand >> k) & 1u) && q + k < kept_end) drop |= 1u << k;
+      open &= ~drop;
+      for (;;) {
+        const uint32_t lanes = __ballot_sync(0xffffffffu, open != 0);
+        if (!lanes) break;
+        const int j = __ffs(lanes) - 1;
+        uint32_t s = 0, e = 0;
+        if ((int)lane == j) {
+          const int k = __ffs(open) - 1;
+          s = q + k;
+          e = s + rx_len[s];
+          accepted |= 1u << k;
+          open &= ~(1u << k);
+        }
+        s = __shfl_sync(0xffffffffu, s, j);
+        e = __shfl_sync(0xffffffffu, e, j);
+        kept_end = e;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (((cand >> k) & 1u) && q + k > s && q + k < e) drop |= 1u << k;
+        open &= ~drop;
+      }
+      const uint32_t touch = drop | accepted;
+      if (touch) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          if ((touch >> k) & 1u) {
+            const uint32_t t = (words[k >> 2] >> (8 * (k & 3))) & 0x7fu;
+            rx_type[q + k] = ((drop >> k) & 1u) ? 0 : (uint8_t)t;
+          }
+        }
+      }
+    }
+  }
+}
+
+void launch_recognize_resolve(const uint64_t* offsets, uint64_t n, const uint32_t* rx_len, uint8_t* rx_type,
+                              cudaStream_t st) {
+  if (n == 0) return;
+  const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, 148 * 16);
+  recognize_resolve_kernel<<<(unsigned)blocks, 256, 0, st>>>(offsets, n, rx_len, rx_type);
   count_launch();
 }
 

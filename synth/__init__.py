@@ -5,8 +5,8 @@ weights and the HMAC key. It holds none of the method's arithmetic (no
 tokenizer, recognizer, encoder, decoder or hash), so a mistake in either
 implementation cannot hide in shared code.
 """
-from .workloads import (C1, C2, C3, C4, C5, WORKLOADS, ModelDims, RecordShape, Workload,
-                        TYPE_NAMES_4, TYPE_NAMES_8, SEED_RECORDS, SEED_WEIGHTS, SEED_KEY,
+from .workloads import (C1, C2, C3, C4, C5, C1X, WORKLOADS, ModelDims, RecordShape, Workload,
+                        TYPE_NAMES_4, TYPE_NAMES_8, TYPE_NAMES_11, RECOGNIZERS_8, RECOGNIZERS_11, EXTRA_KINDS, EXTRA_KIND_TYPE, SEED_RECORDS, SEED_WEIGHTS, SEED_KEY,
                         SEED_ARRIVALS, SEED_CALIB, scaled)
 from .vocab import make_vocab, vocab_arrays, FIRST_WORD_ID
 from .records import RecordSet, make_records, records_from_list
@@ -14,8 +14,8 @@ from .fielded import COLUMNS, FieldedRecords, make_fielded_records
 from .model import make_weights, pack_blob, blob_layout, blob_size, make_key
 
 __all__ = ["COLUMNS", "FieldedRecords", "make_fielded_records",
-    "C1", "C2", "C3", "C4", "C5", "WORKLOADS", "ModelDims", "RecordShape", "Workload",
-    "TYPE_NAMES_4", "TYPE_NAMES_8", "SEED_RECORDS", "SEED_WEIGHTS", "SEED_KEY",
+    "C1", "C2", "C3", "C4", "C5", "C1X", "WORKLOADS", "ModelDims", "RecordShape", "Workload",
+    "TYPE_NAMES_4", "TYPE_NAMES_8", "TYPE_NAMES_11", "RECOGNIZERS_8", "RECOGNIZERS_11", "EXTRA_KINDS", "EXTRA_KIND_TYPE", "SEED_RECORDS", "SEED_WEIGHTS", "SEED_KEY",
     "SEED_ARRIVALS", "SEED_CALIB", "scaled", "make_vocab", "vocab_arrays", "FIRST_WORD_ID",
     "RecordSet", "make_records", "records_from_list", "make_weights", "pack_blob",
     "blob_layout", "blob_size", "make_key",

@@ -6,7 +6,9 @@ header line with host address, host name, port and plugin id, then free text
 entities planted at a target density: IPv4 (sometimes with a port), IPv6,
 host names (sometimes with a port), CVE ids and MAC addresses, plus
 look-alikes that are not entities (version strings, file names, out-of-range
-octets).
+octets). A shape with ``extra_kinds`` also plants URLs, hashes, CPE names,
+UUIDs, OIDs, certificate fingerprints and PEM certificate blocks (each PEM
+block on lines of its own), and look-alikes of those.
 
 Record length is set in tokens. The generator cannot tokenize (it holds none
 of the method's arithmetic), so it sizes text with a conservative count: an
@@ -22,11 +24,12 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import lexicon as lx
-from .workloads import RecordShape
+from .workloads import EXTRA_KIND_TYPE, EXTRA_SHARE, RecordShape
 
 T_IP, T_HOST, T_CVE, T_MAC = 1, 2, 3, 4
 
 _HEX = "0123456789abcdef"
+_B64 = "ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz0123456789+/"
 # share of fresh entities by kind: IPv4, host name, CVE, MAC, IPv6
 _KIND_CDF = [0.40, 0.62, 0.80, 0.90, 1.0]
 
@@ -203,6 +206,101 @@ class _Gen:
             s = s.upper()
         return s.encode()
 
+    def _hexs(self, n: int) -> str:
+        return "".join(_HEX[int(self.rng.integers(16))] for _ in range(n))
+
+    def url(self) -> bytes:
+        r = self.rng
+        scheme = r.choice(("http", "https", "https", "ftp", "ldap", "ssh", "smb"))
+        host = self.hostname() if int(r.integers(4)) else self.ipv4()
+        s = scheme.encode() + b"://" + host
+        if int(r.integers(3)) == 0:
+            s += f":{r.choice((80, 443, 8080, 8443, 389, 21))}".encode()
+        for _ in range(int(r.integers(0, 4))):
+            s += b"/" + self.word()
+        if int(r.integers(3)) == 0:
+            s += b"/" + self.word() + r.choice((b".php", b".html", b".jsp", b".cgi"))
+        if int(r.integers(3)) == 0:
+            s += b"?" + self.word() + b"=" + str(int(r.integers(1000))).encode()
+            if int(r.integers(2)):
+                s += b"&" + self.word() + b"=" + self.word() + b"%20" + self.word()
+        if int(r.integers(6)) == 0:
+            s += b"#" + self.word()
+        return s
+
+    def hash_hex(self) -> bytes:
+        r = self.rng
+        n = r.choice((32, 40, 64, 64, 128))
+        h = self._hexs(n)
+        return (h.upper() if int(r.integers(4)) == 0 else h).encode()
+
+    def cpe(self) -> bytes:
+        r = self.rng
+        sv = lx.SERVICES
+        vendor = sv[int(r.integers(len(sv)))]
+        product = sv[int(r.integers(len(sv)))]
+        if int(r.integers(2)):
+            product += "_" + r.choice(("server", "http_server", "client", "daemon", "agent"))
+        version = f"{int(r.integers(0, 12))}.{int(r.integers(0, 20))}"
+        if int(r.integers(2)):
+            version += f".{int(r.integers(0, 60))}"
+        part = r.choice(("a", "a", "o", "h"))
+        if int(r.integers(3)):
+            tail = ":".join(r.choice(("*", "*", "*", "-")) for _ in range(7))
+            return f"cpe:2.3:{part}:{vendor}:{product}:{version}:{tail}".encode()
+        return f"cpe:/{part}:{vendor}:{product}:{version}".encode()
+
+    def uuid(self) -> bytes:
+        h = self._hexs(32)
+        s = f"{h[:8]}-{h[8:12]}-{h[12:16]}-{h[16:20]}-{h[20:]}"
+        return (s.upper() if int(self.rng.integers(5)) == 0 else s).encode()
+
+    def oid(self) -> bytes:
+        r = self.rng
+        k = int(r.integers(3))
+        if k == 0:
+            arcs = [1, 3, 6, 1, 4, 1] + [int(r.integers(1, 60000)) for _ in range(int(r.integers(1, 4)))]
+        elif k == 1:
+            arcs = [1, 2, 840, 113549, 1] + [int(r.integers(1, 20)) for _ in range(int(r.integers(1, 3)))]
+        else:
+            arcs = [2, 5, 29, int(r.integers(1, 40))] + [int(r.integers(0, 10)) for _ in range(int(r.integers(1, 3)))]
+        return ".".join(str(a) for a in arcs).encode()
+
+    def cert_fp(self) -> bytes:
+        r = self.rng
+        g = r.choice((16, 20, 20, 32))
+        s = ":".join(self._hexs(2) for _ in range(g))
+        return (s.upper() if int(r.integers(2)) else s).encode()
+
+    def pem(self) -> bytes:
+        r = self.rng
+        n = int(r.integers(48, 300))
+        body = "".join(_B64[int(r.integers(64))] for _ in range(n)) + "=" * int(r.integers(0, 3))
+        lines = "\n".join(body[i:i + 64] for i in range(0, len(body), 64))
+        return f"-----BEGIN CERTIFICATE-----\n{lines}\n-----END CERTIFICATE-----".encode()
+
+    def extra_entity(self, kind: str) -> bytes:
+        return {"url": self.url, "hash": self.hash_hex, "cpe": self.cpe, "uuid": self.uuid, "oid": self.oid,
+                "cert_fp": self.cert_fp, "pem": self.pem}[kind]()
+
+    def extra_lookalike(self) -> bytes:
+        r = self.rng
+        k = int(r.integers(7))
+        if k == 0:
+            return self._hexs(r.choice((31, 33, 39, 63))).encode()
+        if k == 1:
+            h = self._hexs(32)
+            return f"{h[:8]}-{h[8:13]}-{h[13:16]}-{h[16:20]}-{h[20:]}".encode()
+        if k == 2:
+            return f"1.{int(r.integers(40, 99))}.{int(r.integers(9))}.{int(r.integers(9))}.{int(r.integers(9))}".encode()
+        if k == 3:
+            return f"cpe:2.3:a:{lx.SERVICES[int(r.integers(len(lx.SERVICES)))]}:*".encode()
+        if k == 4:
+            return b"http:/" + self.word()
+        if k == 5:
+            return ":".join(self._hexs(2) for _ in range(int(r.choice((15, 17))))).encode()
+        return f"3.{int(r.integers(9))}.{int(r.integers(9))}.{int(r.integers(9))}.{int(r.integers(9))}".encode()
+
     def _fresh_entity(self, kind: int) -> bytes:
         return (self.ipv4, self.hostname, self.cve, self.mac, self.ipv6)[kind]()
 
@@ -227,6 +325,10 @@ class _Gen:
             k = int(np.searchsorted(self.zipf_cdf, self.rng.random()))
             e, t = self.zipf_pool[min(k, len(self.zipf_pool) - 1)]
             return e, t, False
+        extra = self.shape.extra_kinds
+        if extra and self.rng.random() < EXTRA_SHARE:
+            kind = extra[int(self.rng.integers(len(extra)))]
+            return self.extra_entity(kind), EXTRA_KIND_TYPE[kind], False
         kind = self.rng.weighted(_KIND_CDF)
         return self._fresh_entity(kind), (T_IP, T_HOST, T_CVE, T_MAC, T_IP)[kind], kind in (0, 1)
 
@@ -314,8 +416,11 @@ def make_records(shape: RecordShape, vocab_words: list[bytes], seed: int = 1001)
             if si < len(slots) and used >= slots[si]:
                 si += 1
                 e, et, can_port = g.entity()
-                lead = b" " + g.word() + b" "
-                tail = b"," if rng.integers(3) == 0 else b""
+                if e.startswith(b"-----BEGIN"):      # a PEM block stands on lines of its own
+                    lead, tail = b" " + g.word() + b":\n", b"\n"
+                else:
+                    lead = b" " + g.word() + b" "
+                    tail = b"," if rng.integers(3) == 0 else b""
                 n_e = est(e)
                 if can_port and rng.integers(5) == 0:
                     port = f":{int(rng.integers(1, 65536))}".encode()
@@ -349,7 +454,7 @@ def make_records(shape: RecordShape, vocab_words: list[bytes], seed: int = 1001)
                     put(b".", 1)
                 continue
             if rng.integers(40) == 0 and room >= 12:
-                la = g.lookalike()
+                la = g.extra_lookalike() if g.shape.extra_kinds and rng.integers(2) else g.lookalike()
                 p = b" " + la
                 put(p, est(p))
                 sentence_left -= 1

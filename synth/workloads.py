@@ -7,7 +7,9 @@ c3  packed:    lognormal(median 600, sigma 1.0) clipped 16..4096, windows 512/38
                Zipf(1.1) entity reuse over 50k distinct entities, 12-layer d=768, FP8.
 c4  serving:   lognormal(median 300, sigma 0.6) clipped 32..4096, Poisson arrivals.
 c5  streaming: 1,000,000 records, lognormal(median 1500, sigma 0.8) clipped 16..4096,
-               24-layer d=1024 encoder, 17 labels.
+               24-layer d=1024 encoder, 17 labels; URLs, hashes and CPE names planted
+               besides the address/CVE kinds (the 8-type schema's recognizer types).
+c1x            c1's shape with every recognizer kind planted, 23-label encoder.
 
 Entity density is ~8 entities per 300 tokens (26.7 per 1k tokens) unless a
 workload sets it. Seeds: records 1001, weights 2002, key 3003, arrivals 4004,
@@ -54,6 +56,13 @@ class RecordShape:
     entities_per_1k: float = 8000.0 / 300.0
     zipf_distinct: int = 0        # >0: entities drawn Zipf(zipf_s) from this many distinct
     zipf_s: float = 1.1
+    # extra entity kinds planted besides the five address/CVE kinds, from
+    # EXTRA_KINDS; a share EXTRA_SHARE of fresh entities is drawn from them
+    extra_kinds: tuple[str, ...] = ()
+
+
+EXTRA_KINDS = ("url", "hash", "cpe", "uuid", "oid", "cert_fp", "pem")
+EXTRA_SHARE = 0.35
 
 
 @dataclass(frozen=True)
@@ -69,6 +78,13 @@ class Workload:
 
 TYPE_NAMES_4 = ("IP_ADDRESS", "HOSTNAME", "CVE_ID", "MAC_ADDRESS")
 TYPE_NAMES_8 = TYPE_NAMES_4 + ("URL", "HASH", "CPE", "ORGANIZATION")
+TYPE_NAMES_11 = TYPE_NAMES_8 + ("UUID", "OID", "CERTIFICATE")
+# recognizer kind -> entity type for TYPE_NAMES_8 (kind order MAC, IPv6, IPv4, CVE,
+# host name, URL, hash, UUID, CPE, OID, certificate fingerprint, PEM; 0 = off)
+RECOGNIZERS_8 = (4, 1, 1, 3, 2, 5, 6, 0, 7, 0, 0, 0)
+RECOGNIZERS_11 = (4, 1, 1, 3, 2, 5, 6, 9, 7, 10, 11, 11)
+# entity type (1-based index into TYPE_NAMES_11) of each planted extra kind
+EXTRA_KIND_TYPE = {"url": 5, "hash": 6, "cpe": 7, "uuid": 9, "oid": 10, "cert_fp": 11, "pem": 11}
 
 C1 = Workload(
     "c1-small-fp32",
@@ -98,13 +114,21 @@ C4 = Workload(
 )
 C5 = Workload(
     "c5-streaming-fp8",
-    RecordShape(1_000_000, "lognormal", 16, 4096, median=1500.0, sigma=0.8),
+    RecordShape(1_000_000, "lognormal", 16, 4096, median=1500.0, sigma=0.8, extra_kinds=("url", "hash", "cpe")),
     ModelDims(vocab=8192, d_model=1024, n_heads=16, d_ffn=4096, n_layers=24, n_labels=17),
     window=512, stride=384,
     note="1M records, 24L d1024 encoder, 17 labels",
 )
 
-WORKLOADS = {w.name.split("-")[0]: w for w in (C1, C2, C3, C4, C5)}
+# c1 with every recognizer kind planted and a 23-label (11-type) encoder
+C1X = Workload(
+    "c1x-small-recognizers",
+    RecordShape(256, "uniform", 32, 512, extra_kinds=EXTRA_KINDS),
+    ModelDims(vocab=8192, d_model=128, n_heads=2, d_ffn=512, n_layers=2, n_labels=23),
+    note="c1 records with URLs, hashes, CPE names, UUIDs, OIDs and certificates planted",
+)
+
+WORKLOADS = {w.name.split("-")[0]: w for w in (C1, C2, C3, C4, C5, C1X)}
 
 
 def scaled(w: Workload, n_records: int) -> Workload:

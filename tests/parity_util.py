@@ -10,7 +10,8 @@ MARGIN = 0.05
 
 
 def oracle_schema(s) -> P.Schema:
-    return P.Schema(tuple(s.type_names), s.preserve_mask, s.slug_hex_len, s.window, s.stride)
+    rx = None if s.recognizers is None else tuple(s.recognizers)
+    return P.Schema(tuple(s.type_names), s.preserve_mask, s.slug_hex_len, s.window, s.stride, rx)
 
 
 def split_tokens(tr: dict, n: int) -> list[slice]:

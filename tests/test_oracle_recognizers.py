@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import recognizers as R
+from rx_fuzz import fuzz_record, rand_extra as _rand_extra, rand_word as _rand_word
 
 WORD_RE = re.compile(rb"[A-Za-z0-9.:\-]+")
 STRIP_RE = re.compile(rb"^(.*?)((?:[.\-]|(?<!:):)*)$", re.S)
@@ -94,42 +95,11 @@ def test_hand_cases(data, expect):
     assert ref_recognize(data) == expect
 
 
-def _rand_word(rng):
-    k = rng.integers(9)
-    hx = "0123456789abcdefABCDEF"
-    if k == 0:
-        return ".".join(str(rng.integers(0, 300)) if rng.integers(6) else "0" + str(rng.integers(0, 30))
-                        for _ in range(rng.integers(2, 6))) + (f":{rng.integers(0, 999999)}" if rng.integers(3) == 0 else "")
-    if k == 1:
-        groups = ["".join(rng.choice(list(hx), size=rng.integers(0, 6))) for _ in range(rng.integers(1, 10))]
-        return ":".join(groups)
-    if k == 2:
-        sep = rng.choice([":", "-", "."])
-        return sep.join("".join(rng.choice(list(hx), size=rng.integers(1, 4))) for _ in range(rng.integers(4, 8)))
-    if k == 3:
-        return f"{rng.choice(['CVE', 'cve', 'CVE'])}-{rng.integers(0, 99999)}-{rng.integers(0, 9999999)}"
-    if k == 4:
-        labs = []
-        for _ in range(rng.integers(1, 5)):
-            n = rng.integers(0, 8)
-            labs.append("".join(rng.choice(list("abz09-XY"), size=n)))
-        return ".".join(labs) + (f":{rng.integers(0, 99)}" if rng.integers(4) == 0 else "")
-    if k == 5:
-        return "".join(rng.choice(list("a1.:-f"), size=rng.integers(1, 20)))
-    if k == 6:
-        return "x" * int(rng.integers(60, 70)) + ".com"
-    if k == 7:
-        return ".".join(["a" * 63] * 4) + ".org"
-    return "".join(rng.choice(list("0123456789:."), size=rng.integers(1, 25)))
-
-
 def test_fuzz_against_independent_formulation():
     rng = np.random.default_rng(7)
     n = 0
     for _ in range(6000):
-        parts = [_rand_word(rng) for _ in range(rng.integers(1, 6))]
-        seps = [rng.choice([" ", ", ", "\n", "(", ") ", "/", "=", "\xe9"]) for _ in parts]
-        data = "".join(p + s for p, s in zip(parts, seps)).encode("utf-8")
+        data = fuzz_record(rng, extended=False)
         got = R.recognize(data)
         assert got == ref_recognize(data), data
         n += len(got)
@@ -145,3 +115,172 @@ def test_planted_entities_found(c1_records):
             assert (int(s), int(n), int(t)) in spans, (ri, c1_records.record(ri)[s:s + n])
             found += 1
     assert found == len(planted) > 1000
+
+
+# ---------------------------------------------------------------- the twelve-kind set
+#
+# Independent formulation of the extended recognizers: ``re`` patterns written
+# from the stated rules, ``uuid.UUID`` and ``bytes.fromhex`` for UUIDs and
+# fingerprints, and the left-to-right resolution obtained from ``re.finditer``
+# over an alternation of the multi-word patterns (a scanning regex engine
+# resumes after each match, which is the rule the oracle states).
+
+import uuid
+
+ALL = (R.MAC_ADDRESS, R.IP_ADDRESS, R.IP_ADDRESS, R.CVE_ID, R.HOSTNAME, 5, 6, 9, 7, 10, 11, 12)
+NOT_WORD = rb"(?<![A-Za-z0-9.:\-])"
+PEM_RE = rb"(?:(?<=\n)|^)-----BEGIN CERTIFICATE-----[A-Za-z0-9+/=\s]*-----END CERTIFICATE-----"
+URL_RE = NOT_WORD + rb"[A-Za-z][A-Za-z0-9]{1,15}://[A-Za-z0-9\-._~:/?#\[\]@!$&*+,;=%]*[A-Za-z0-9\-_~/#\[\]@$&*+=%]"
+CPE_COMP = rb"[A-Za-z0-9._~%!*?\-]"
+CPE_FS_RE = NOT_WORD + rb"cpe:2\.3:[aoh*\-](?::" + CPE_COMP + rb"+){9}:" + CPE_COMP + rb"*[A-Za-z0-9_~%!*?\-]"
+CPE_URI_RE = NOT_WORD + rb"cpe:/[aoh](?::[A-Za-z0-9._~%\-]*){0,6}(?<![.:])"
+LONG_RE = re.compile(b"(" + PEM_RE + b")|(" + URL_RE + b")|(" + CPE_FS_RE + b")|(" + CPE_URI_RE + b")")
+HASH_RE = re.compile(rb"[0-9A-Fa-f]{32}|[0-9A-Fa-f]{40}|[0-9A-Fa-f]{64}|[0-9A-Fa-f]{128}")
+OID_RE = re.compile(rb"(?:0|[1-9][0-9]*)(?:\.(?:0|[1-9][0-9]*)){4,}")
+
+
+def ref_uuid(w: bytes) -> bool:
+    if len(w) != 36:
+        return False
+    try:
+        return str(uuid.UUID(w.decode())) == w.decode().lower()
+    except ValueError:
+        return False
+
+
+def ref_fp(w: bytes) -> bool:
+    if not re.fullmatch(rb"[0-9A-Fa-f]{2}(?::[0-9A-Fa-f]{2})*", w):
+        return False
+    return len(bytes.fromhex(w.replace(b":", b"").decode())) in (16, 20, 32)
+
+
+def ref_oid(w: bytes) -> bool:
+    if not OID_RE.fullmatch(w):
+        return False
+    arcs = [int(a) for a in w.split(b".")]
+    return arcs[0] <= 2 and (arcs[0] == 2 or arcs[1] <= 39)
+
+
+def ref_word_all(w: bytes):
+    if MAC_RE.fullmatch(w):
+        return len(w), R.MAC_ADDRESS
+    if ref_ipv6(w):
+        return len(w), R.IP_ADDRESS
+    if n := ref_ipv4(w):
+        return n, R.IP_ADDRESS
+    if CVE_RE.fullmatch(w):
+        return len(w), R.CVE_ID
+    if n := ref_host(w):
+        return n, R.HOSTNAME
+    if HASH_RE.fullmatch(w):
+        return len(w), 6
+    if ref_uuid(w):
+        return len(w), 9
+    if ref_fp(w):
+        return len(w), 11
+    if ref_oid(w):
+        return len(w), 10
+    return 0, 0
+
+
+def ref_recognize_all(data: bytes):
+    longs = []
+    for m in LONG_RE.finditer(data):
+        t = (12, 5, 7, 7)[m.lastindex - 1]
+        longs.append((m.start(), m.end() - m.start(), t))
+    out = list(longs)
+    for m in WORD_RE.finditer(data):
+        s = m.start()
+        if any(ls <= s < ls + ln for ls, ln, _ in longs):
+            continue
+        w = STRIP_RE.fullmatch(m.group(0)).group(1)
+        if w:
+            n, t = ref_word_all(w)
+            if n:
+                out.append((s, n, t))
+    return sorted(out)
+
+
+def _at(data: bytes, *hits):
+    """Expected spans from (substring, type) pairs, each located after the previous one."""
+    out, pos = [], 0
+    for sub, t in hits:
+        k = data.index(sub, pos)
+        out.append((k, len(sub), t))
+        pos = k + len(sub)
+    return data, out
+
+
+EXT_CASES = [
+    _at(b"d41d8cd98f00b204e9800998ecf8427e and " + b"A" * 40 + b" " + b"f" * 31 + b" " + b"0" * 64,
+        (b"d41d8cd98f00b204e9800998ecf8427e", 6), (b"A" * 40, 6), (b"0" * 64, 6)),
+    _at(b"{123e4567-e89b-12d3-a456-426614174000} 123e4567e89b-12d3-a456-426614174000",
+        (b"123e4567-e89b-12d3-a456-426614174000", 9)),
+    _at(b"oid 1.3.6.1.4.1.311 2.5.29.17.1 3.1.2.3.4 1.40.1.2.3 1.39.1.2.3. 01.3.6.1.4 10.3.6.1",
+        (b"1.3.6.1.4.1.311", 10), (b"2.5.29.17.1", 10), (b"1.39.1.2.3", 10), (b"10.3.6.1", 1)),
+    _at(b"fp 3A:5F:00:11:22:33:44:55:66:77:88:99:AA:BB:CC:DD:EE:FF:00:11 aa:bb:cc:dd:ee:ff:00:11:22:33:44:55:66:77:88",
+        (b"3A:5F:00:11:22:33:44:55:66:77:88:99:AA:BB:CC:DD:EE:FF:00:11", 11)),
+    _at(b"go to https://web01.example.com:8443/a/b?x=1&y=%20z#frag. Next",
+        (b"https://web01.example.com:8443/a/b?x=1&y=%20z#frag", 5)),
+    _at(b"(see http://10.0.0.1/index.php), x.http://a.bc",
+        (b"http://10.0.0.1/index.php", 5), (b"x.http", 2), (b"a.bc", 2)),
+    _at(b"http:// ftp://x, h://x verylongschemename12://x", (b"ftp://x", 5)),
+    _at(b"cpe:2.3:a:apache:http_server:2.4.41:*:*:*:*:*:*:*. cpe:/a:apache:tomcat:9.0:. cpe:2.3:x:a:b:c:d:e:f:g:h:i:j",
+        (b"cpe:2.3:a:apache:http_server:2.4.41:*:*:*:*:*:*:*", 7), (b"cpe:/a:apache:tomcat:9.0", 7)),
+    _at(b"cpe:2.3:a:b:c:d:e:f:g:h:i:j:k:extra.example.com", (b"cpe:2.3:a:b:c:d:e:f:g:h:i:j:k", 7)),
+    _at(b"url http://host/?c=cpe:2.3:a:b:c:d:e:f:g:h:i:j:k done", (b"http://host/?c=cpe:2.3:a:b:c:d:e:f:g:h:i:j:k", 5)),
+    _at(b"x\n-----BEGIN CERTIFICATE-----\nMIIB+/=\nd41d8cd98f00b204e9800998ecf8427e\n-----END CERTIFICATE-----\ny",
+        (b"-----BEGIN CERTIFICATE-----\nMIIB+/=\nd41d8cd98f00b204e9800998ecf8427e\n-----END CERTIFICATE-----", 12)),
+    _at(b" -----BEGIN CERTIFICATE-----\nAAAA\n-----END CERTIFICATE-----"),
+    _at(b"-----BEGIN CERTIFICATE-----\nAA:AA\n-----END CERTIFICATE-----"),
+]
+
+
+@pytest.mark.parametrize("data,expect", EXT_CASES)
+def test_extended_hand_cases(data, expect):
+    got = R.recognize(data, ALL)
+    assert got == expect, [(s, n, t, data[s:s + n]) for s, n, t in got]
+    assert ref_recognize_all(data) == expect
+
+
+def test_default_table_is_the_five_address_recognizers():
+    data = b"10.0.0.1 http://a.com/x d41d8cd98f00b204e9800998ecf8427e cpe:/a:b"
+    assert R.recognize(data) == R.recognize(data, R.DEFAULT_TYPES) == [(0, 8, 1), (16, 5, 2)]
+
+
+def test_switched_off_kinds_fall_through():
+    """With the MAC recognizer off a MAC is nothing; with URLs off their host names are found."""
+    t = list(ALL)
+    t[R.KIND_MAC] = 0
+    t[R.KIND_URL] = 0
+    assert R.recognize(b"aa:bb:cc:dd:ee:ff http://a.example.com/x", t) == [(25, 13, 2)]
+
+
+def test_extended_fuzz_against_independent_formulation():
+    rng = np.random.default_rng(11)
+    n = dropped = 0
+    kinds = set()
+    for _ in range(6000):
+        data = fuzz_record(rng, extended=True)
+        got = R.recognize(data, ALL)
+        assert got == ref_recognize_all(data), data
+        n += len(got)
+        dropped += len(R.candidates(data, ALL)) - len(got)
+        kinds |= {t for _, _, t in got}
+    # candidates inside an accepted multi-word span occur, so resolution is exercised
+    assert n > 3000 and dropped > 100 and kinds >= {1, 2, 3, 5, 6, 7, 9, 10, 11, 12}
+
+
+def test_extended_planted_entities_found(vocab_words):
+    import synth
+    recs = synth.make_records(synth.C1X.records, vocab_words)
+    table = ALL[:11] + (11,)         # both certificate forms to type 11, as the generator plants them
+    planted = recs.planted
+    found = 0
+    for ri in range(recs.n):
+        spans = set(R.recognize(recs.record(ri), table))
+        for _, s, n, t in planted[planted[:, 0] == ri]:
+            assert (int(s), int(n), int(t)) in spans, (ri, recs.record(ri)[s:s + n])
+            found += 1
+    assert found == len(planted) > 1500
+    assert set(planted[:, 3].tolist()) == {1, 2, 3, 4, 5, 6, 7, 9, 10, 11}
