@@ -179,6 +179,10 @@ typedef struct {
   uint64_t n_map_entries, n_new_entries;
   uint64_t kernel_launches;
   uint64_t graph_replays;        /* encoder batches run as one graph launch    */
+  /* as_reidentify only: pseudonyms found, replaced by their originals, left
+   * because several entries share the slug, left because the entry did not
+   * verify under the key (the rest name no entry of the map) */
+  uint64_t n_pseudonyms, n_reidentified, n_ambiguous, n_unverified;
 } as_stats;
 
 /* Encoder batches of at most AS_GRAPH_MAX_ROWS rows (BF16 / FP8 contexts,
@@ -258,6 +262,21 @@ typedef struct {
   const uint32_t* final_start; const uint32_t* final_len; const uint8_t* final_type;
 } as_trace;
 as_status as_debug_trace(as_ctx* ctx, as_trace* trace);
+
+/* Controlled re-identification (AnonShield §2 stage (4): the stored mapping
+ * lets an administrator holding both the database and the HMAC key reverse
+ * the pseudonymisation). In `records` (same layout rules as as_anonymize),
+ * every "[NAME_h]" inside one record, NAME = type_names[t-1] and h exactly
+ * schema->slug_hex_len lower-case hex characters, is replaced by the original
+ * bytes of the ctx's map entry of type t whose full hash begins with h, when
+ * exactly one entry does and HMAC-SHA256(key, original) equals its full hash;
+ * other bytes and unresolved pseudonyms are copied. Output in the inputs'
+ * memory space, one record per input record; counts in as_stats
+ * (n_pseudonyms, ...). Import a stored map with as_map_import first.
+ * AS_ERR_ARG: slug_hex_len 0, or a type name containing '[' or ']';
+ * AS_ERR_STATE: key differs from the non-empty map's key, or serving. */
+as_status as_reidentify(as_ctx* ctx, const as_records* records, const as_schema* schema, const uint8_t* key,
+                        size_t key_len, as_output** out);
 
 /* Per-field policy: the schema-aware configuration of AnonShield §2
  * (anonymization_config with force_anonymize, fields_to_anonymize,

@@ -18,6 +18,8 @@ Modules, in pipeline order:
   hmac_sha256    HMAC written from RFC 2104 on top of ``sha256``
   pseudonym      replacement strings, substitution and the entity map
   pipeline       the whole call: records, schema, key -> output records + map
+  fields         per-field policy (detect / exclude / force per field id)
+  reidentify     controlled re-identification: pseudonyms -> originals via map + key
 
 Parity status: every function is pinned by tests under ``tests/`` against
 brute force, closed forms, invariants or independent library routines,

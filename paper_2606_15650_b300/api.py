@@ -75,7 +75,8 @@ class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("n_records", "n_bytes", "n_tokens", "n_encoded_tokens", "n_sequences",
                                           "n_regex_spans", "n_ner_spans", "n_final_spans", "n_out_bytes",
                                           "n_map_entries", "n_new_entries", "kernel_launches",
-                                          "graph_replays")]
+                                          "graph_replays", "n_pseudonyms", "n_reidentified", "n_ambiguous",
+                                          "n_unverified")]
 
 
 class _Trace(C.Structure):
@@ -130,7 +131,7 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_reidentify", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
@@ -176,6 +177,7 @@ def load() -> C.CDLL:
     lib.as_get_tiles.argtypes = [P, C.POINTER(C.c_int32)]
     lib.as_anonymize_fields.argtypes = [P, C.POINTER(_Records), C.POINTER(_Fields), C.POINTER(_FieldPolicy),
                                         C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
+    lib.as_reidentify.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
     lib.as_anonymize_stream.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t,
                                         C.POINTER(_StreamConfig), C.POINTER(P)]
     lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
@@ -476,6 +478,29 @@ class Context:
         sc, names = self._schema(schema)
         out = C.c_void_p()
         st = load().as_anonymize(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(out))
+        del keep, names
+        self._check(st)
+        return Output(self, out.value)
+
+    @staticmethod
+    def _records(data, offsets):
+        """(as_records, objects to keep alive) for numpy host arrays or torch CUDA tensors."""
+        if hasattr(data, "is_cuda") and data.is_cuda:
+            rec = _Records(bytes=data.data_ptr(), offsets=offsets.data_ptr(), n_records=offsets.numel() - 1,
+                           on_device=1)
+            return rec, (data, offsets)
+        d = np.ascontiguousarray(data, dtype=np.uint8)
+        o = np.ascontiguousarray(offsets, dtype=np.uint64)
+        rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
+                       on_device=0)
+        return rec, (d, o)
+
+    def reidentify(self, data, offsets, schema: Schema, key: bytes) -> Output:
+        """Controlled re-identification (as_reidentify) against this context's entity map."""
+        rec, keep = self._records(data, offsets)
+        sc, names = self._schema(schema)
+        out = C.c_void_p()
+        st = load().as_reidentify(self._h, C.byref(rec), C.byref(sc), key, len(key), C.byref(out))
         del keep, names
         self._check(st)
         return Output(self, out.value)

@@ -61,6 +61,9 @@ __device__ __forceinline__ bool is_alnum(uint32_t c) {
   return (c - '0' < 10u) || ((c | 0x20u) - 'a' < 26u);
 }
 
+// bit i of the record-start bitmap: a record begins at byte i
+__device__ __forceinline__ bool rs_bit(const uint32_t* rs, uint32_t i) { return (rs[i >> 5] >> (i & 31)) & 1u; }
+
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_scan(T v) {
   const unsigned lane = threadIdx.x & 31;

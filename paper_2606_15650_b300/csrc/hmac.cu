@@ -176,6 +176,41 @@ __global__ void hmac_spans_kernel(const uint8_t* __restrict__ bytes, const uint3
   }
 }
 
+// ok[i] = 1 when map slot i holds an entry whose stored digest is the HMAC of
+// its stored original under the key (re-identification trusts only those).
+__global__ void hmac_verify_slots_kernel(MapView m, const uint32_t* __restrict__ key_state, uint8_t* __restrict__ ok) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= m.mask; i += (uint64_t)gridDim.x * blockDim.x) {
+    const MapSlot& s = m.slots[i];
+    uint8_t good = 0;
+    if (s.key != 0 && s.arena_off != ~0ull) {
+      uint32_t inner[8], outer[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        inner[k] = key_state[k];
+        outer[k] = key_state[8 + k];
+      }
+      sha256_tail(inner, m.arena + s.arena_off, s.len, 1);
+      uint32_t w[16];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) w[k] = inner[k];
+      w[8] = 0x80000000u;
+#pragma unroll
+      for (int k = 9; k < 15; ++k) w[k] = 0;
+      w[15] = (64 + 32) * 8;
+      sha256_compress(outer, w);
+      good = 1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) good &= outer[k] == s.digest[k];
+    }
+    ok[i] = good;
+  }
+}
+
+void launch_hmac_verify_slots(MapView m, const uint32_t* key_state, uint8_t* ok, cudaStream_t st) {
+  hmac_verify_slots_kernel<<<grid_1d(m.mask + 1, 128, 148 * 32), 128, 0, st>>>(m, key_state, ok);
+  count_launch();
+}
+
 void launch_hmac_spans(const uint8_t* bytes, const uint32_t* sp_start, const uint32_t* sp_len, const uint32_t* n_dev,
                        uint32_t cap, const uint32_t* key_state, uint32_t* digests, cudaStream_t st) {
   if (cap == 0) return;

@@ -161,6 +161,7 @@ struct Lane {
   DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len, attn_items;
   DBuf f_bytes, f_off, f_start, f_sub_off, f_sub, fs_s, fs_l, fs_t, fr_s, fr_l, fr_t, f_keep, f_pos, f_cnt, ff_s, ff_l,
       ff_t;
+  DBuf rid_ok, rid_tk, rid_tv, rid_len, rid_slot, rid_flag, rid_pos, rid_s, rid_l, rid_k;
   DBuf X32, X16, QKV, ATT, Y32, H, X8, ATT8, H8;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
@@ -249,7 +250,8 @@ void Lane::release_all() {
                  &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
                  &name_off, &name_len, &seqs, &attn_items, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
                  &fs_l, &fs_t, &fr_s, &fr_l, &fr_t, &f_keep, &f_pos, &f_cnt, &ff_s, &ff_l, &ff_t, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
-                 &ATT, &Y32, &H, &X8, &ATT8, &H8};
+                 &ATT, &Y32, &H, &X8, &ATT8, &H8,
+                  &rid_ok, &rid_tk, &rid_tv, &rid_len, &rid_slot, &rid_flag, &rid_pos, &rid_s, &rid_l, &rid_k};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
@@ -776,6 +778,76 @@ as_status d2h_vec(as_ctx* c, Lane* ln, std::vector<T>& v, const void* src, uint6
   return AS_OK;
 }
 
+// The inputs of a call on the device: *d_bytes / *d_off are the caller's
+// device arrays, or the lane's copies of its host arrays (checked here: the
+// offsets start at 0 and never decrease). *N_out = total bytes (< 4 GiB).
+as_status stage_records(as_ctx* c, Lane* ln, const as_records* rec, const uint8_t** d_bytes_out,
+                        const uint64_t** d_off_out, uint64_t* N_out) {
+  cudaStream_t st = ln->stream;
+  const uint64_t n = rec->n_records;
+  if (n > 0 && !rec->offsets) return fail(c, AS_ERR_ARG, "offsets is NULL");
+  uint64_t N = 0;
+  const uint8_t* d_bytes;
+  const uint64_t* d_off;
+  if (n > 0) {
+    if (rec->on_device) {
+      CK(cudaMemcpyAsync(&N, rec->offsets + n, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      N = rec->offsets[n];
+      if (rec->offsets[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
+      for (uint64_t r = 0; r < n; ++r)
+        if (rec->offsets[r + 1] < rec->offsets[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
+    }
+  }
+  if (N >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "a call takes less than 4 GiB of text");
+  if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
+  CKS(grow(ln->in_off, (n + 1) * 8));
+  if (rec->on_device) {
+    d_bytes = rec->bytes;
+    d_off = rec->offsets;
+  } else {
+    CKS(grow(ln->in_bytes, N + 16));
+    if (N) CK(cudaMemcpyAsync(ln->in_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+    uint64_t zero = 0;
+    if (n) CK(cudaMemcpyAsync(ln->in_off.p, rec->offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemcpyAsync(ln->in_off.p, &zero, 8, cudaMemcpyHostToDevice, st));
+    d_bytes = ln->in_bytes.as<uint8_t>();
+    d_off = ln->in_off.as<uint64_t>();
+  }
+  if (n == 0) {
+    static const uint64_t zero_off = 0;
+    CK(cudaMemcpyAsync(ln->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
+    d_off = ln->in_off.as<uint64_t>();
+  }
+  *d_bytes_out = d_bytes;
+  *d_off_out = d_off;
+  *N_out = N;
+  return AS_OK;
+}
+
+// Type names on the device: names = concatenation, name_off[t] .. name_off[t+1]
+// = type t's bytes (t = 1..n_types), name_len[t] their length.
+as_status upload_names(as_ctx* c, Lane* ln, const as_schema* sch) {
+  cudaStream_t st = ln->stream;
+  std::vector<uint32_t> noff(sch->n_types + 2, 0), nlen(sch->n_types + 1, 0);
+  std::string all;
+  for (uint32_t t = 1; t <= sch->n_types; ++t) {
+    noff[t] = (uint32_t)all.size();
+    all += sch->type_names[t - 1];
+    noff[t + 1] = (uint32_t)all.size();
+    nlen[t] = noff[t + 1] - noff[t];
+  }
+  CKS(grow(ln->names, all.size() + 16));
+  CKS(grow(ln->name_off, noff.size() * 4));
+  CKS(grow(ln->name_len, nlen.size() * 4));
+  CK(cudaMemcpyAsync(ln->names.p, all.data(), all.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ln->name_off.p, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ln->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+  return AS_OK;
+}
+
 // calibrate = true: run the tokenizer and the BF16 encoder only, recording
 // the amax of every FP8 GEMM input, and set the static activation scales.
 as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_schema* sch, const uint8_t* key,
@@ -795,40 +867,9 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   if (n > 0 && (!rec->offsets)) return fail(c, AS_ERR_ARG, "offsets is NULL");
   // ---- inputs
   uint64_t N = 0;
-  std::vector<uint64_t> h_off_in;
-  if (n > 0) {
-    if (rec->on_device) {
-      CK(cudaMemcpyAsync(&N, rec->offsets + n, 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-    } else {
-      N = rec->offsets[n];
-      if (rec->offsets[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
-      for (uint64_t r = 0; r < n; ++r)
-        if (rec->offsets[r + 1] < rec->offsets[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
-    }
-  }
-  if (N >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "a call takes less than 4 GiB of text");
-  if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
-  const uint8_t* d_bytes;
-  const uint64_t* d_off;
-  CKS(grow(ln->in_off, (n + 1) * 8));
-  if (rec->on_device) {
-    d_bytes = rec->bytes;
-    d_off = rec->offsets;
-  } else {
-    CKS(grow(ln->in_bytes, N + 16));
-    if (N) CK(cudaMemcpyAsync(ln->in_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
-    uint64_t zero = 0;
-    if (n) CK(cudaMemcpyAsync(ln->in_off.p, rec->offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
-    else CK(cudaMemcpyAsync(ln->in_off.p, &zero, 8, cudaMemcpyHostToDevice, st));
-    d_bytes = ln->in_bytes.as<uint8_t>();
-    d_off = ln->in_off.as<uint64_t>();
-  }
-  if (n == 0) {
-    static const uint64_t zero_off = 0;
-    CK(cudaMemcpyAsync(ln->in_off.p, &zero_off, 8, cudaMemcpyHostToDevice, st));
-    d_off = ln->in_off.as<uint64_t>();
-  }
+  const uint8_t* d_bytes = nullptr;
+  const uint64_t* d_off = nullptr;
+  CKI(stage_records(c, ln, rec, &d_bytes, &d_off, &N));
   uint32_t N32 = (uint32_t)N;
   const uint64_t launches0 = t_launches, replays0 = ln->graph_replays;
   const uint32_t call_id = ++c->call_id;
@@ -1093,23 +1134,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
                           rec_base >= 0 ? (uint64_t)rec_base : c->records_done, call_id, ln->dev_err.as<DevError>(),
                           st);
   // ---- substitution
-  {
-    std::vector<uint32_t> noff(sch->n_types + 2, 0), nlen(sch->n_types + 1, 0);
-    std::string all;
-    for (uint32_t t = 1; t <= sch->n_types; ++t) {
-      noff[t] = (uint32_t)all.size();
-      all += sch->type_names[t - 1];
-      noff[t + 1] = (uint32_t)all.size();
-      nlen[t] = noff[t + 1] - noff[t];
-    }
-    CKS(grow(ln->names, all.size() + 16));
-    CKS(grow(ln->name_off, noff.size() * 4));
-    CKS(grow(ln->name_len, nlen.size() * 4));
-    CK(cudaMemcpyAsync(ln->names.p, all.data(), all.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ln->name_off.p, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ln->name_len.p, nlen.data(), nlen.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));  // the host vectors above go out of scope
-  }
+  CKI(upload_names(c, ln, sch));
   CKS(grow(ln->delta, (size_t)(fin_total + 1) * 8));
   CKS(grow(ln->shift, (size_t)(fin_total + 1) * 8));
   CKS(grow(ln->delta_total, 16));
@@ -1715,6 +1740,126 @@ void as_output_free(as_output* o) {
     if (o->d_off) cudaFree(o->d_off);
   }
   delete o;
+}
+
+as_status as_reidentify(as_ctx* c, const as_records* rec, const as_schema* sch, const uint8_t* key, size_t key_len,
+                        as_output** out) {
+  if (!c || !rec || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (c->server) return fail(c, AS_ERR_STATE, "re-identification while serving (the map is changing)");
+  CKI(validate_schema(c, sch));
+  const uint32_t L = sch->slug_hex_len;
+  if (L == 0) return fail(c, AS_ERR_ARG, "slug_hex_len 0: the replacements carry no hash to re-identify");
+  for (uint32_t t = 0; t < sch->n_types; ++t)
+    if (std::strpbrk(sch->type_names[t], "[]")) return fail(c, AS_ERR_ARG, "type names must not contain brackets");
+  CKI(set_key(c, key, key_len));
+  Lane* ln = &c->main;
+  cudaStream_t st = ln->stream;
+  const uint64_t launches0 = t_launches;
+  const uint64_t n = rec->n_records;
+  uint64_t N = 0;
+  const uint8_t* d_bytes = nullptr;
+  const uint64_t* d_off = nullptr;
+  CKI(stage_records(c, ln, rec, &d_bytes, &d_off, &N));
+  const uint32_t N32 = (uint32_t)N;
+  CKI(upload_names(c, ln, sch));
+  // entries verified under the key, indexed by (type, slug prefix)
+  const MapView m = map_view(c);
+  const uint64_t slots = c->map_mask + 1;
+  if (slots >= kReidAmbiguous) return fail(c, AS_ERR_CAPACITY, "map too large to index");
+  CKS(grow(ln->rid_ok, slots));
+  CKS(grow(ln->rid_tk, slots * 8));
+  CKS(grow(ln->rid_tv, slots * 4));
+  CK(cudaMemsetAsync(ln->rid_tk.p, 0, slots * 8, st));
+  CK(cudaMemsetAsync(ln->rid_tv.p, 0xFF, slots * 4, st));
+  const ReidTab tab{ln->rid_tk.as<unsigned long long>(), ln->rid_tv.as<uint32_t>(), slots - 1};
+  launch_hmac_verify_slots(m, c->key_state.as<uint32_t>(), ln->rid_ok.as<uint8_t>(), st);
+  launch_reid_index(m, 4 * std::min<uint32_t>(L, 14), tab, st);
+  // pseudonyms
+  CKS(grow(ln->counters, 64));
+  CK(cudaMemsetAsync(ln->counters.p, 0, 64, st));
+  unsigned long long* ctr = ln->counters.as<unsigned long long>();  // [0..3] stats, [4] low word = span count
+  uint32_t* n_sp_dev = reinterpret_cast<uint32_t*>(ctr + 4);
+  CKS(grow(ln->rs_bits, ((size_t)N / 32 + 1) * 4));
+  CKS(grow(ln->rid_len, N * 4 + 4));
+  CKS(grow(ln->rid_slot, N * 4 + 4));
+  CKS(grow(ln->rid_flag, N + 16));
+  CKS(grow(ln->rid_pos, (N + 1) * 4));
+  CKS(grow(ln->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(N + 1, 1) * 2) + 16) * 8));
+  launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
+  launch_reid_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), ln->names.as<char>(), ln->name_off.as<uint32_t>(),
+                   sch->n_types, L, tab, m, ln->rid_ok.as<uint8_t>(), ln->rid_len.as<uint32_t>(),
+                   ln->rid_slot.as<uint32_t>(), ln->rid_flag.as<uint8_t>(), ctr, st);
+  exclusive_scan<uint32_t>(NonZeroU8{ln->rid_flag.as<uint8_t>()}, N, ln->rid_pos.as<uint32_t>(), n_sp_dev,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  unsigned long long h_ctr[5] = {0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h_ctr, ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t n_sp = (uint32_t)(h_ctr[4] & 0xffffffffull);
+  CKS(grow(ln->rid_s, (n_sp + 1) * 4));
+  CKS(grow(ln->rid_l, (n_sp + 1) * 4));
+  CKS(grow(ln->rid_k, (n_sp + 1) * 4));
+  launch_reid_emit(ln->rid_len.as<uint32_t>(), ln->rid_slot.as<uint32_t>(), ln->rid_flag.as<uint8_t>(),
+                   ln->rid_pos.as<uint32_t>(), N32, ln->rid_s.as<uint32_t>(), ln->rid_l.as<uint32_t>(),
+                   ln->rid_k.as<uint32_t>(), st);
+  CKS(grow(ln->delta, (size_t)(n_sp + 1) * 8));
+  CKS(grow(ln->shift, (size_t)(n_sp + 1) * 8));
+  CKS(grow(ln->delta_total, 16));
+  launch_reid_delta(ln->rid_l.as<uint32_t>(), ln->rid_k.as<uint32_t>(), n_sp, m, ln->delta.as<int64_t>(), n_sp + 1, st);
+  exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, n_sp + 1, ln->shift.as<int64_t>(),
+                          ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st);
+  int64_t total_delta = 0;
+  CK(cudaMemcpyAsync(&total_delta, ln->delta_total.p, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t out_size = (uint64_t)((int64_t)N + total_delta);
+  as_output* o = new as_output();
+  o->ctx = c;
+  o->device = c->device;
+  o->map_loaded = true;  // re-identification adds no map entries
+  o->on_device = rec->on_device ? 1u : 0u;
+  o->n = n;
+  void* d_out = nullptr;
+  uint64_t* d_out_off = nullptr;
+  if (cudaMallocAsync(&d_out, out_size + 16, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&d_out_off), (n + 1) * 8, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_out) cudaFreeAsync(d_out, st);
+    delete o;
+    return fail(c, AS_ERR_OOM, "output allocation failed");
+  }
+  launch_sub_copy(d_bytes, N32, ln->rid_s.as<uint32_t>(), ln->rid_l.as<uint32_t>(), n_sp_dev, ln->shift.as<int64_t>(),
+                  reinterpret_cast<uint8_t*>(d_out), st);
+  launch_reid_replace(ln->rid_s.as<uint32_t>(), ln->rid_k.as<uint32_t>(), n_sp, ln->shift.as<int64_t>(), m,
+                      reinterpret_cast<uint8_t*>(d_out), st);
+  launch_sub_offsets(d_off, n, ln->rid_s.as<uint32_t>(), n_sp_dev, ln->shift.as<int64_t>(), d_out_off, st);
+  if (o->on_device) {
+    o->d_bytes = d_out;
+    o->d_off = d_out_off;
+  } else {
+    o->h_bytes.resize(out_size);
+    o->h_off.resize(n + 1);
+    cudaMemcpyAsync(o->h_bytes.data(), d_out, out_size, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(o->h_off.data(), d_out_off, (n + 1) * 8, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_out, st);
+    cudaFreeAsync(d_out_off, st);
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    as_output_free(o);
+    return fail(c, AS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  }
+  as_stats& s = o->stats;
+  s.n_records = n;
+  s.n_bytes = N;
+  s.n_out_bytes = out_size;
+  s.n_pseudonyms = h_ctr[0];
+  s.n_reidentified = h_ctr[1];
+  s.n_ambiguous = h_ctr[2];
+  s.n_unverified = h_ctr[3];
+  s.kernel_launches = t_launches - launches0;
+  *out = o;
+  return AS_OK;
 }
 
 as_status as_map_export(as_ctx* c, as_entity** entries, uint64_t* n) {

@@ -147,6 +147,28 @@ void launch_map_select(MapView m, uint32_t call_lo, uint32_t call_hi, uint8_t* k
 void launch_map_gather(MapView m, const uint8_t* keep, const uint32_t* pos, uint32_t* idx, cudaStream_t st);
 void launch_map_gather_slots(MapView m, const uint32_t* idx, uint32_t n, MapSlot* out, cudaStream_t st);
 
+// ---- re-identification ----
+// ok[i] = 1: map slot i holds an entry whose digest is the HMAC of its original.
+void launch_hmac_verify_slots(MapView m, const uint32_t* key_state, uint8_t* ok, cudaStream_t st);
+// (type, slug prefix) -> map slot index; key 0 = empty.
+constexpr uint32_t kReidEmpty = 0xffffffffu, kReidAmbiguous = 0xfffffffeu;
+struct ReidTab {
+  unsigned long long* key;
+  uint32_t* val;
+  uint64_t mask;
+};
+void launch_reid_index(MapView m, uint32_t p_bits, ReidTab tab, cudaStream_t st);
+void launch_reid_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, const char* names,
+                      const uint32_t* name_off, uint32_t n_types, uint32_t slug_len, ReidTab tab, MapView m,
+                      const uint8_t* ok, uint32_t* plen, uint32_t* pslot, uint8_t* flag, unsigned long long* ctr,
+                      cudaStream_t st);
+void launch_reid_emit(const uint32_t* plen, const uint32_t* pslot, const uint8_t* flag, const uint32_t* pos, uint32_t N,
+                      uint32_t* sp_s, uint32_t* sp_l, uint32_t* sp_k, cudaStream_t st);
+void launch_reid_delta(const uint32_t* sp_l, const uint32_t* sp_k, uint32_t n, MapView m, int64_t* delta, uint32_t cap,
+                       cudaStream_t st);
+void launch_reid_replace(const uint32_t* sp_s, const uint32_t* sp_k, uint32_t n, const int64_t* shift, MapView m,
+                         uint8_t* out, cudaStream_t st);
+
 // ---- substitution ----
 // delta[k] = replacement length - span length (int64).
 void launch_sub_delta(const uint32_t* sp_len, const uint8_t* sp_type, const uint32_t* n_dev, uint32_t cap,

@@ -20,8 +20,6 @@
 
 namespace as {
 
-__device__ __forceinline__ bool rs_bit(const uint32_t* rs, uint32_t i) { return (rs[i >> 5] >> (i & 31)) & 1u; }
-
 __global__ void mark_record_starts_kernel(const uint64_t* offsets, uint64_t n, uint32_t N, uint32_t* rs) {
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t o = offsets[r];
