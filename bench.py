@@ -437,6 +437,7 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
         out["streaming"] = streaming_leg(args, words, key, local)
     if args.field_records > 0:
         out["field_policy"] = field_policy_leg(args, w, words, blob, key, local)
+        out["jsonl"] = jsonl_leg(args, w, words, blob, key, local)
     return out
 
 
@@ -484,6 +485,56 @@ def field_policy_leg(args, w, words, blob, key, local) -> dict:
     res["speedup"] = res["field_policy"]["records_per_s"] / res["whole_record"]["records_per_s"]
     res["workload"] = (f"{fr.records.n} CSV-like scan records ({nbytes} bytes, columns {', '.join(synth.COLUMNS)}); "
                        "policy: host address and name forced, plugin output detected, the rest excluded")
+    return res
+
+
+# JSON Lines policy: host address / name and MAC forced, plugin output, CVE list
+# and notes detected, every other member key excluded (keys of synth.JSONL_KEYS).
+JSONL_POLICY = {"host_ip": ("force", 1), "host_name": ("force", 2), "mac": ("force", 4), "plugin_output": "detect",
+                "cves": "detect", "note": "detect"}
+
+
+def jsonl_leg(args, w, words, blob, key, local) -> dict:
+    """Scan findings as JSON Lines: each line through detection whole vs the device JSONL scan + key policy."""
+    import torch
+    import paper_2606_15650_b300.api as api
+    rs = synth.make_jsonl_records(synth.scaled(synth.C2, args.field_records).records, words,
+                                  seed=synth.SEED_RECORDS + 9)
+    schema = api.Schema(synth.TYPE_NAMES_4, window=512, stride=384)
+    data = torch.from_numpy(rs.data).to(f"cuda:{local}")
+    offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(f"cuda:{local}")
+    nbytes = len(rs.data)
+    res = {}
+    for mode in ("whole_line", "jsonl_policy"):
+        ctx = api.Context(w.dims, blob, words, precision="bf16", mode="packed", device=local)
+        stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{local}")
+
+        def call():
+            if mode == "whole_line":
+                return ctx.anonymize(data, offs, schema, key)
+            return ctx.anonymize_jsonl(data, offs, list(synth.JSONL_KEYS), JSONL_POLICY, schema, key,
+                                       default="exclude")
+        call().free()
+        ms = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = call()
+            e1.record(stream)
+            e1.synchronize()
+            st = o.stats()
+            o.free()
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.mean(ms)) / 1e3
+        res[mode] = {"records_per_s": rs.n / t, "kb_per_s": nbytes / 1024 / t,
+                     "encoded_tokens": int(st["n_encoded_tokens"]), "ms": t * 1e3}
+        if mode == "jsonl_policy":
+            res[mode].update({"fields": int(st["n_fields"]), "malformed_lines": int(st["n_malformed"])})
+        ctx.close()
+    res["speedup"] = res["jsonl_policy"]["records_per_s"] / res["whole_line"]["records_per_s"]
+    res["workload"] = (f"{rs.n} JSON lines ({nbytes} bytes; members {', '.join(synth.JSONL_KEYS)}; 1 in 50 cut short); "
+                       "policy: host address, name and MAC forced, plugin output, CVE list and note detected, "
+                       "other keys excluded")
     return res
 
 

@@ -183,6 +183,8 @@ typedef struct {
    * because several entries share the slug, left because the entry did not
    * verify under the key (the rest name no entry of the map) */
   uint64_t n_pseudonyms, n_reidentified, n_ambiguous, n_unverified;
+  /* as_anonymize_jsonl only: fields found in the lines, lines that did not parse */
+  uint64_t n_fields, n_malformed;
 } as_stats;
 
 /* Encoder batches of at most AS_GRAPH_MAX_ROWS rows (BF16 / FP8 contexts,
@@ -317,6 +319,30 @@ typedef struct {
 as_status as_anonymize_fields(as_ctx* ctx, const as_records* records, const as_fields* fields,
                               const as_field_policy* policy, const as_schema* schema, const uint8_t* key,
                               size_t key_len, as_output** out);
+
+/* JSON Lines ingest (AnonShield §2: JSON / JSONL inputs keep their structure,
+ * only sensitive values are replaced, with per-field control). Each record is
+ * one line (no newline). On the device, a line that is one JSON value
+ * (RFC 8259; white space around it; at most 64 nested containers; strings
+ * without raw bytes below 0x20, escapes \" \\ \/ \b \f \n \r \t \uXXXX)
+ * yields one field per run of a string VALUE's raw bytes outside escape
+ * sequences, so replacements keep the line valid JSON; member keys, numbers,
+ * literals and punctuation are structure and pass through. A field's action
+ * is that of its innermost enclosing member key (key_names compared as raw
+ * bytes): action[i] / force_type[i] for key_names[i], default_action for
+ * other keys and for values in no member. A line that does not parse is
+ * detected as free text as a whole (never passed through unchanged); an
+ * empty line has no fields. Then as for as_anonymize_fields. Stats:
+ * n_fields, n_malformed. */
+typedef struct {
+  uint32_t n_keys;
+  const char* const* key_names;
+  const uint8_t* action;       /* per key: AS_FIELD_*                          */
+  const uint8_t* force_type;   /* per key: entity type for AS_FIELD_FORCE      */
+  uint8_t default_action;      /* AS_FIELD_DETECT or AS_FIELD_EXCLUDE          */
+} as_jsonl_policy;
+as_status as_anonymize_jsonl(as_ctx* ctx, const as_records* records, const as_jsonl_policy* policy,
+                             const as_schema* schema, const uint8_t* key, size_t key_len, as_output** out);
 
 /* Streaming (AnonShield §2 stage (1) reads large inputs as a stream): the
  * same result as one as_anonymize call over `records` (host memory only),

@@ -65,6 +65,11 @@ class _Schema(C.Structure):
                 ("recognizer_types", C.POINTER(C.c_uint8))]
 
 
+class _JsonlPolicy(C.Structure):
+    _fields_ = [("n_keys", C.c_uint32), ("key_names", C.POINTER(C.c_char_p)), ("action", C.POINTER(C.c_uint8)),
+                ("force_type", C.POINTER(C.c_uint8)), ("default_action", C.c_uint8)]
+
+
 class _Entity(C.Structure):
     _fields_ = [("type", C.c_uint32), ("original_len", C.c_uint32), ("original", C.POINTER(C.c_uint8)),
                 ("full_hash", C.c_char * 65), ("slug", C.c_char * 65),
@@ -76,7 +81,7 @@ class _Stats(C.Structure):
                                           "n_regex_spans", "n_ner_spans", "n_final_spans", "n_out_bytes",
                                           "n_map_entries", "n_new_entries", "kernel_launches",
                                           "graph_replays", "n_pseudonyms", "n_reidentified", "n_ambiguous",
-                                          "n_unverified")]
+                                          "n_unverified", "n_fields", "n_malformed")]
 
 
 class _Trace(C.Structure):
@@ -131,7 +136,7 @@ class _Profile(C.Structure):
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
-            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_reidentify", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
+            "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_anonymize_jsonl", "as_reidentify", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
             "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
@@ -178,6 +183,8 @@ def load() -> C.CDLL:
     lib.as_anonymize_fields.argtypes = [P, C.POINTER(_Records), C.POINTER(_Fields), C.POINTER(_FieldPolicy),
                                         C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
     lib.as_reidentify.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(P)]
+    lib.as_anonymize_jsonl.argtypes = [P, C.POINTER(_Records), C.POINTER(_JsonlPolicy), C.POINTER(_Schema), C.c_char_p,
+                                       C.c_size_t, C.POINTER(P)]
     lib.as_anonymize_stream.argtypes = [P, C.POINTER(_Records), C.POINTER(_Schema), C.c_char_p, C.c_size_t,
                                         C.POINTER(_StreamConfig), C.POINTER(P)]
     lib.as_serve_start.argtypes = [P, C.POINTER(_Schema), C.c_char_p, C.c_size_t, C.POINTER(_ServeConfig)]
@@ -494,6 +501,31 @@ class Context:
         rec = _Records(bytes=d.ctypes.data if d.size else None, offsets=o.ctypes.data, n_records=o.size - 1,
                        on_device=0)
         return rec, (d, o)
+
+    def anonymize_jsonl(self, data, offsets, key_names, policy: dict, schema: Schema, key: bytes,
+                        default: str = "detect") -> Output:
+        """JSON Lines (as_anonymize_jsonl): one JSON line per record. policy maps a key name
+        to "detect", "exclude" or ("force", entity_type); other keys take ``default``."""
+        rec, keep = self._records(data, offsets)
+        names = [k.encode() if isinstance(k, str) else bytes(k) for k in key_names]
+        nk = len(names)
+        acts = np.zeros(max(nk, 1), np.uint8)
+        ftyp = np.zeros(max(nk, 1), np.uint8)
+        for i, k in enumerate(key_names):
+            a = policy.get(k, default)
+            if isinstance(a, tuple):
+                acts[i], ftyp[i] = FIELD_ACTION[a[0]], a[1]
+            else:
+                acts[i] = FIELD_ACTION[a]
+        cnames = (C.c_char_p * max(nk, 1))(*names)
+        jp = _JsonlPolicy(n_keys=nk, key_names=cnames, action=acts.ctypes.data_as(C.POINTER(C.c_uint8)),
+                          force_type=ftyp.ctypes.data_as(C.POINTER(C.c_uint8)), default_action=FIELD_ACTION[default])
+        sc, snames = self._schema(schema)
+        out = C.c_void_p()
+        st = load().as_anonymize_jsonl(self._h, C.byref(rec), C.byref(jp), C.byref(sc), key, len(key), C.byref(out))
+        del keep, snames, cnames, acts, ftyp
+        self._check(st)
+        return Output(self, out.value)
 
     def reidentify(self, data, offsets, schema: Schema, key: bytes) -> Output:
         """Controlled re-identification (as_reidentify) against this context's entity map."""

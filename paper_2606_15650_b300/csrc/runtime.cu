@@ -92,6 +92,10 @@ struct LoadI64 {
   const int64_t* p;
   __device__ int64_t operator()(uint64_t i) const { return p[i]; }
 };
+struct LoadU32 {
+  const uint32_t* p;
+  __device__ uint32_t operator()(uint64_t i) const { return p[i]; }
+};
 
 // A call with a per-field policy: the detection steps run on `rec` (the
 // compact arena of fields, one sub-record per field); the rest of the path on
@@ -162,6 +166,7 @@ struct Lane {
   DBuf f_bytes, f_off, f_start, f_sub_off, f_sub, fs_s, fs_l, fs_t, fr_s, fr_l, fr_t, f_keep, f_pos, f_cnt, ff_s, ff_l,
       ff_t;
   DBuf rid_ok, rid_tk, rid_tv, rid_len, rid_slot, rid_flag, rid_pos, rid_s, rid_l, rid_k;
+  DBuf j_names, j_koff, j_cnt, j_bad, j_pos, j_fs, j_fl, j_fid;
   DBuf X32, X16, QKV, ATT, Y32, H, X8, ATT8, H8;
   // last call results kept for as_debug_trace
   uint64_t last_n = 0, last_T = 0, last_nrx = 0, last_nfin = 0;
@@ -251,7 +256,8 @@ void Lane::release_all() {
                  &name_off, &name_len, &seqs, &attn_items, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
                  &fs_l, &fs_t, &fr_s, &fr_l, &fr_t, &f_keep, &f_pos, &f_cnt, &ff_s, &ff_l, &ff_t, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
                  &ATT, &Y32, &H, &X8, &ATT8, &H8,
-                  &rid_ok, &rid_tk, &rid_tv, &rid_len, &rid_slot, &rid_flag, &rid_pos, &rid_s, &rid_l, &rid_k};
+                  &rid_ok, &rid_tk, &rid_tv, &rid_len, &rid_slot, &rid_flag, &rid_pos, &rid_s, &rid_l, &rid_k,
+                  &j_names, &j_koff, &j_cnt, &j_bad, &j_pos, &j_fs, &j_fl, &j_fid};
   for (DBuf* b : all) release(*b);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
@@ -2300,13 +2306,9 @@ as_status as_get_tiles(as_ctx* c, int32_t* cfg) {
   return AS_OK;
 }
 
-as_status as_anonymize_fields(as_ctx* c, const as_records* rec, const as_fields* fl, const as_field_policy* pol,
-                              const as_schema* sch, const uint8_t* key, size_t key_len, as_output** out) {
-  if (!c || !rec || !fl || !pol || !out) return AS_ERR_ARG;
-  *out = nullptr;
-  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
-  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
-  CKI(validate_schema(c, sch));
+// staged: host records already copied to ln->f_bytes / ln->f_off (JSONL ingest)
+as_status fields_impl(as_ctx* c, const as_records* rec, const as_fields* fl, const as_field_policy* pol,
+                      const as_schema* sch, const uint8_t* key, size_t key_len, as_output** out, bool staged) {
   Lane* ln = &c->main;
   cudaStream_t st = ln->stream;
   const uint64_t n = rec->n_records, nf = fl->n_fields;
@@ -2374,10 +2376,12 @@ as_status as_anonymize_fields(as_ctx* c, const as_records* rec, const as_fields*
     d_bytes = rec->bytes;
     d_off = rec->offsets;
   } else {
-    CKS(grow(ln->f_bytes, N + 16));
-    CKS(grow(ln->f_off, (n + 1) * 8));
-    if (N) CK(cudaMemcpyAsync(ln->f_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ln->f_off.p, off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (!staged) {
+      CKS(grow(ln->f_bytes, N + 16));
+      CKS(grow(ln->f_off, (n + 1) * 8));
+      if (N) CK(cudaMemcpyAsync(ln->f_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(ln->f_off.p, off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    }
     d_bytes = ln->f_bytes.as<uint8_t>();
     d_off = ln->f_off.as<uint64_t>();
   }
@@ -2422,6 +2426,122 @@ as_status as_anonymize_fields(as_ctx* c, const as_records* rec, const as_fields*
   as_records sub{ln->f_sub.as<uint8_t>(), ln->f_sub_off.as<uint64_t>(), nf, 1};
   as_status s = anonymize_impl(c, ln, &sub, sch, key, key_len, out, false, -1, &fj);
   if (s == AS_ERR_CUDA) cudaGetLastError();
+  return s;
+}
+
+as_status as_anonymize_fields(as_ctx* c, const as_records* rec, const as_fields* fl, const as_field_policy* pol,
+                              const as_schema* sch, const uint8_t* key, size_t key_len, as_output** out) {
+  if (!c || !rec || !fl || !pol || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
+  CKI(validate_schema(c, sch));
+  return fields_impl(c, rec, fl, pol, sch, key, key_len, out, false);
+}
+
+as_status as_anonymize_jsonl(as_ctx* c, const as_records* rec, const as_jsonl_policy* jp, const as_schema* sch,
+                             const uint8_t* key, size_t key_len, as_output** out) {
+  if (!c || !rec || !jp || !out) return AS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, AS_ERR_CUDA, "cudaSetDevice failed");
+  if (c->server) return fail(c, AS_ERR_STATE, "the ctx is serving: use as_submit / as_poll or stop serving");
+  CKI(validate_schema(c, sch));
+  const uint32_t nk = jp->n_keys;
+  if (nk > 0 && (!jp->key_names || !jp->action || !jp->force_type))
+    return fail(c, AS_ERR_ARG, "policy arrays are NULL");
+  if (nk > (1u << 20)) return fail(c, AS_ERR_ARG, "at most 2^20 key names");
+  Lane* ln = &c->main;
+  cudaStream_t st = ln->stream;
+  const uint64_t n = rec->n_records;
+  if (n > 0 && !rec->offsets) return fail(c, AS_ERR_ARG, "offsets is NULL");
+  // the lines on the device: the caller's arrays, or copies in the lane's field staging buffers
+  std::vector<uint64_t> off(n + 1, 0);
+  if (n > 0) {
+    if (rec->on_device) {
+      CK(cudaMemcpyAsync(off.data(), rec->offsets, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      memcpy(off.data(), rec->offsets, (n + 1) * 8);
+    }
+    if (off[0] != 0) return fail(c, AS_ERR_ARG, "offsets[0] must be 0");
+    for (uint64_t r = 0; r < n; ++r)
+      if (off[r + 1] < off[r]) return fail(c, AS_ERR_ARG, "offsets must be non-decreasing");
+  }
+  const uint64_t N = off[n];
+  if (N >= (1ull << 32) - 64) return fail(c, AS_ERR_ARG, "a call takes less than 4 GiB of text");
+  if (N > 0 && !rec->bytes) return fail(c, AS_ERR_ARG, "bytes is NULL");
+  const uint8_t* d_bytes;
+  const uint64_t* d_off;
+  if (rec->on_device) {
+    d_bytes = rec->bytes;
+    d_off = rec->offsets;
+  } else {
+    CKS(grow(ln->f_bytes, N + 16));
+    CKS(grow(ln->f_off, (n + 1) * 8));
+    if (N) CK(cudaMemcpyAsync(ln->f_bytes.p, rec->bytes, N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ln->f_off.p, off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+    d_bytes = ln->f_bytes.as<uint8_t>();
+    d_off = ln->f_off.as<uint64_t>();
+  }
+  // key names on the device
+  std::vector<uint32_t> koff(nk + 1, 0);
+  std::string kall;
+  for (uint32_t t = 0; t < nk; ++t) {
+    if (!jp->key_names[t]) return fail(c, AS_ERR_ARG, "key name is NULL");
+    kall += jp->key_names[t];
+    koff[t + 1] = (uint32_t)kall.size();
+  }
+  CKS(grow(ln->j_names, kall.size() + 16));
+  CKS(grow(ln->j_koff, (nk + 1) * 4));
+  if (!kall.empty()) CK(cudaMemcpyAsync(ln->j_names.p, kall.data(), kall.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ln->j_koff.p, koff.data(), (nk + 1) * 4, cudaMemcpyHostToDevice, st));
+  const JsonKeys K{ln->j_names.as<char>(), ln->j_koff.as<uint32_t>(), nk};
+  const uint64_t launches0 = t_launches;
+  // fields: count per line, prefix sum, emit; then to the host for the per-field call
+  CKS(grow(ln->j_cnt, (n + 1) * 4));
+  CKS(grow(ln->j_bad, n + 16));
+  CKS(grow(ln->j_pos, (n + 1) * 4));
+  CKS(grow(ln->counters, 64));
+  CKS(grow(ln->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(n + 1, 1) * 2) + 16) * 8));
+  CK(cudaMemsetAsync(ln->counters.p, 0, 64, st));
+  unsigned long long* n_bad_dev = ln->counters.as<unsigned long long>();
+  uint32_t* n_fields_dev = reinterpret_cast<uint32_t*>(n_bad_dev + 1);
+  launch_jsonl_count(d_bytes, d_off, n, K, ln->j_cnt.as<uint32_t>(), ln->j_bad.as<uint8_t>(), n_bad_dev, st);
+  exclusive_scan<uint32_t>(LoadU32{ln->j_cnt.as<uint32_t>()}, n, ln->j_pos.as<uint32_t>(), n_fields_dev,
+                           ln->scan_tiles.as<uint32_t>(), st);
+  unsigned long long h_cnt[2] = {0, 0};
+  CK(cudaMemcpyAsync(h_cnt, ln->counters.p, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t n_bad = h_cnt[0], nf = (uint32_t)(h_cnt[1] & 0xffffffffull);
+  CKS(grow(ln->j_fs, (nf + 1) * 8));
+  CKS(grow(ln->j_fl, (nf + 1) * 4));
+  CKS(grow(ln->j_fid, (nf + 1) * 4));
+  launch_jsonl_emit(d_bytes, d_off, n, K, ln->j_pos.as<uint32_t>(), ln->j_bad.as<uint8_t>(), ln->j_fs.as<uint64_t>(),
+                    ln->j_fl.as<uint32_t>(), ln->j_fid.as<uint32_t>(), st);
+  std::vector<uint64_t> fs(nf);
+  std::vector<uint32_t> fln(nf), fid(nf);
+  if (nf) {
+    CK(cudaMemcpyAsync(fs.data(), ln->j_fs.p, nf * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fln.data(), ln->j_fl.p, nf * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fid.data(), ln->j_fid.p, nf * 4, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  // policy over ids: the listed keys, then "other keys" (default), then malformed lines (detect)
+  std::vector<uint8_t> act(nk + 2), ft(nk + 2, 0);
+  for (uint32_t t = 0; t < nk; ++t) {
+    act[t] = jp->action[t];
+    ft[t] = jp->force_type[t];
+  }
+  act[nk] = jp->default_action;
+  act[nk + 1] = AS_FIELD_DETECT;
+  const as_fields fields{fs.data(), fln.data(), fid.data(), nf};
+  const as_field_policy pol{nk + 2, act.data(), ft.data(), jp->default_action};
+  as_status s = fields_impl(c, rec, &fields, &pol, sch, key, key_len, out, !rec->on_device);
+  if (s == AS_OK && *out) {
+    (*out)->stats.n_fields = nf;
+    (*out)->stats.n_malformed = n_bad;
+    (*out)->stats.kernel_launches = t_launches - launches0;  // the scan's launches and the per-field call's
+  }
   return s;
 }
 

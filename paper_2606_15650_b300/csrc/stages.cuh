@@ -147,6 +147,20 @@ void launch_map_select(MapView m, uint32_t call_lo, uint32_t call_hi, uint8_t* k
 void launch_map_gather(MapView m, const uint8_t* keep, const uint32_t* pos, uint32_t* idx, cudaStream_t st);
 void launch_map_gather_slots(MapView m, const uint32_t* idx, uint32_t n, MapSlot* out, cudaStream_t st);
 
+// ---- JSON Lines ingest ----
+constexpr int kJsonMaxDepth = 64;
+struct JsonKeys {
+  const char* names;    // key i = names[off[i] .. off[i+1])
+  const uint32_t* off;
+  uint32_t n;
+};
+// cnt[r] = fields of line r (1 for a malformed line, bad[r] = 1, *n_bad += 1).
+void launch_jsonl_count(const uint8_t* bytes, const uint64_t* off, uint64_t n, JsonKeys K, uint32_t* cnt, uint8_t* bad,
+                        unsigned long long* n_bad, cudaStream_t st);
+// Writes line r's fields at pos[r] (exclusive prefix sum of cnt).
+void launch_jsonl_emit(const uint8_t* bytes, const uint64_t* off, uint64_t n, JsonKeys K, const uint32_t* pos,
+                       const uint8_t* bad, uint64_t* f_start, uint32_t* f_len, uint32_t* f_id, cudaStream_t st);
+
 // ---- re-identification ----
 // ok[i] = 1: map slot i holds an entry whose digest is the HMAC of its original.
 void launch_hmac_verify_slots(MapView m, const uint32_t* key_state, uint8_t* ok, cudaStream_t st);

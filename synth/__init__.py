@@ -10,10 +10,10 @@ from .workloads import (C1, C2, C3, C4, C5, C1X, WORKLOADS, ModelDims, RecordSha
                         SEED_ARRIVALS, SEED_CALIB, scaled)
 from .vocab import make_vocab, vocab_arrays, FIRST_WORD_ID
 from .records import RecordSet, make_records, records_from_list
-from .fielded import COLUMNS, FieldedRecords, make_fielded_records
+from .fielded import COLUMNS, JSONL_KEYS, FieldedRecords, make_fielded_records, make_jsonl_records
 from .model import make_weights, pack_blob, blob_layout, blob_size, make_key
 
-__all__ = ["COLUMNS", "FieldedRecords", "make_fielded_records",
+__all__ = ["COLUMNS", "JSONL_KEYS", "FieldedRecords", "make_fielded_records", "make_jsonl_records",
     "C1", "C2", "C3", "C4", "C5", "C1X", "WORKLOADS", "ModelDims", "RecordShape", "Workload",
     "TYPE_NAMES_4", "TYPE_NAMES_8", "TYPE_NAMES_11", "RECOGNIZERS_8", "RECOGNIZERS_11", "EXTRA_KINDS", "EXTRA_KIND_TYPE", "SEED_RECORDS", "SEED_WEIGHTS", "SEED_KEY",
     "SEED_ARRIVALS", "SEED_CALIB", "scaled", "make_vocab", "vocab_arrays", "FIRST_WORD_ID",
