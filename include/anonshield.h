@@ -97,6 +97,12 @@ typedef struct {
   uint32_t no_graphs;            /* 1: never replay CUDA graphs (see below)    */
   uint32_t attention;            /* BF16/FP8 attention engine: AS_ATTN_TCGEN05
                                     (0, default) or AS_ATTN_MMA_SYNC           */
+  uint32_t no_fused_ln;          /* BF16/FP8 post-LN residual blocks run as one
+                                    kernel (a row split over a cluster of CTAs;
+                                    d_model 128, 256, 384, 512, 768 or 1024)
+                                    unless set here as two kernels (GEMM, then
+                                    LayerNorm): bit 0 the attention block,
+                                    bit 1 the feed-forward block               */
 } as_config;
 
 /* Attention engines of BF16 and FP8 contexts: persistent tcgen05 kernel with

@@ -46,6 +46,18 @@ as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t 
 as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_t K, const void* A8, const void* B8,
                         float alpha, float out_scale, const float* bias, const float* resid, void* out, void* stream);
 
+/* Post-LN residual block of the encoder in one kernel (AnonShield §2 stage
+ * (2) encoder, post-LN form): x32 <- LN(x32 + alpha (A . B^T) + bias) with
+ * gain ln_g[N] and bias ln_b[N], eps 1e-5, biased variance, in place
+ * (float[M][N]); out16 (bf16[M][N]) or out8 (E4M3 bytes of value /
+ * out8_scale, saturated) receives a copy when not NULL (at most one). A, B BF16 (in_e4m3 =
+ * 0, K % 64 == 0) or E4M3 (in_e4m3 = 1, K % 128 == 0). Each 128-row block
+ * runs on a cluster of CTAs that split the row: N must be 128, 256, 384,
+ * 512, 768 or 1024. 16-byte aligned pointers. AS_ERR_ARG otherwise. */
+as_status as_k_gemm_resid_ln(int in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
+                             const float* bias, float* x32, const float* ln_g, const float* ln_b, void* out16,
+                             void* out8, float out8_scale, float alpha, void* stream);
+
 /* Multi-head self-attention over packed variable-length sequences.
  * qkv: [rows][3*d] (Q | K | V column blocks; head j owns columns j*64..j*64+63
  * of each), act type of `precision`; out: [rows][d] act type. Sequence s

@@ -52,7 +52,7 @@ class _Config(C.Structure):
                 ("vocab_bytes", C.POINTER(C.c_uint8)), ("vocab_offsets", C.POINTER(C.c_uint32)),
                 ("n_vocab_words", C.c_uint32), ("max_chunk_tokens", C.c_uint64), ("map_capacity", C.c_uint64),
                 ("map_arena_bytes", C.c_uint64), ("device", C.c_int32), ("keep_trace", C.c_uint32),
-                ("no_graphs", C.c_uint32), ("attention", C.c_uint32)]
+                ("no_graphs", C.c_uint32), ("attention", C.c_uint32), ("no_fused_ln", C.c_uint32)]
 
 
 class _Records(C.Structure):
@@ -198,6 +198,8 @@ def load() -> C.CDLL:
     lib.as_k_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P]
     lib.as_k_gemm_fp8.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, C.c_float, C.c_float,
                                   P, P, P, P]
+    lib.as_k_gemm_resid_ln.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P, P, P, C.c_float,
+                                       C.c_float, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_attention_tc.argtypes = [P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
@@ -255,6 +257,17 @@ def gemm_fp8(epilogue: str, A8, B8, alpha: float, bias=None, resid=None, out=Non
     _check_k(load().as_k_gemm_fp8(EPI[epilogue], out_e4m3, M, N, K, _ptr(A8), _ptr(B8), alpha, out_scale or 1.0,
                                   _ptr(bias), _ptr(resid), _ptr(out), stream))
     return out
+
+
+def gemm_resid_ln(A, B, bias, x32, ln_g, ln_b, out16=None, out8=None, out8_scale: float = 1.0, alpha: float = 1.0,
+                  stream=None):
+    """x32 <- LayerNorm(x32 + alpha * A @ B^T + bias) in place (BF16 or E4M3 operands), plus copies."""
+    M, K = A.shape
+    N = B.shape[0]
+    in8 = 1 if A.element_size() == 1 else 0
+    _check_k(load().as_k_gemm_resid_ln(in8, M, N, K, _ptr(A), _ptr(B), _ptr(bias), _ptr(x32), _ptr(ln_g),
+                                       _ptr(ln_b), _ptr(out16), _ptr(out8), out8_scale, alpha, stream))
+    return x32
 
 
 def attention(precision: str, qkv, out, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
@@ -425,7 +438,9 @@ class Context:
 
     def __init__(self, dims, weights_blob: np.ndarray, vocab_words: list[bytes], precision: str = "bf16",
                  mode: str = "packed", max_chunk_tokens: int = 0, map_capacity: int = 0, map_arena_bytes: int = 0,
-                 keep_trace: bool = False, device: int = 0, attention: str = "tcgen05", graphs: bool = True):
+                 keep_trace: bool = False, device: int = 0, attention: str = "tcgen05", graphs: bool = True,
+                 fused_ln: bool | str = True):
+        """fused_ln: True (both post-LN blocks as one kernel each), False, "attn" or "ffn" (that block only)."""
         lib = load()
         self.dims = dims
         self.device = device
@@ -444,7 +459,8 @@ class Context:
                       n_vocab_words=len(vocab_words), max_chunk_tokens=max_chunk_tokens,
                       map_capacity=map_capacity, map_arena_bytes=map_arena_bytes, device=device,
                       keep_trace=1 if keep_trace else 0, no_graphs=0 if graphs else 1,
-                      attention=ATTENTION[attention])
+                      attention=ATTENTION[attention],
+                      no_fused_ln={True: 0, False: 3, "attn": 2, "ffn": 1}[fused_ln])
         h = C.c_void_p()
         st = lib.as_create(C.byref(cfg), C.byref(h))
         if st != AS_OK:

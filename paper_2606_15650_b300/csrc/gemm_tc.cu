@@ -20,6 +20,17 @@
 // the main loop of tile i+1. Every mbarrier wait is bounded (globaltimer):
 // on timeout the kernel records the failure, every role leaves its loop,
 // TMEM is freed and the kernel returns.
+//
+// Residual + LayerNorm epilogue (kEpiResidLN: X = LN(X + alpha A.B^T + bias),
+// the post-LN block of the encoder): a row of N = C x BN columns is split over
+// a cluster of C CTAs (C <= 4), which walk the same 128-row blocks. Each
+// epilogue warp (32 rows x BN/2 columns) writes y = alpha acc + bias + X back
+// into TMEM, takes the mean and the centred sum of squares of its part of each
+// row, and stores them into every CTA of the cluster (distributed shared
+// memory) with a release-arrive on that CTA's exchange barrier. Once all 2C
+// partials of its rows are in, a warp combines them (Chan et al.'s pairwise
+// update), normalizes y from TMEM and writes X in place (FP32) and its BF16
+// or E4M3 copy.
 #include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -34,6 +45,9 @@ constexpr int kBM = 128;
 // Operand / output element types of one instantiation
 constexpr int kInBF16 = 0, kInE4M3 = 1;
 constexpr int kOutBF16 = 0, kOutF32 = 1, kOutE4M3 = 2;
+// Epilogue code of the fused residual + LayerNorm (next to the public AS_EPI_*)
+constexpr int kEpiResidLN = 3;
+constexpr int kMaxLnCluster = 4;
 // elements per k-block: a 128-byte swizzled row holds 64 BF16 or 128 E4M3
 __host__ __device__ constexpr int bk_elems(int in) { return in == kInE4M3 ? 128 : 64; }
 constexpr int kEpiWarps = 8;
@@ -51,6 +65,12 @@ struct Params {
   DevError* err;
   float alpha;          // accumulator scale (product of the FP8 operand scales; 1 for BF16)
   float out_scale_inv;  // 1 / scale of an FP8 output
+  // kEpiResidLN: LN gain / bias; out (= resid) gets the FP32 rows, out16 / out8 the copy
+  const float* ln_g;
+  const float* ln_b;
+  __nv_bfloat16* out16;
+  uint8_t* out8;
+  int copy;             // kEpiResidLN: 0 none, 1 BF16 (out16), 2 E4M3 (out8); tensor map tmC
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -258,6 +278,84 @@ __device__ __forceinline__ void gelu_erf2(float& x0, float& x1) {
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---- thread-block cluster helpers (the LayerNorm epilogue)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, float a, float b) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded, warp-uniform wait with cluster-scope acquire (the partials of the peers).
+__device__ __forceinline__ bool warp_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  DevError* err, uint32_t where) {
+  bool ok = mbar_try_wait_cluster(bar, parity);
+  if (!ok) {
+    const uint64_t t0 = globaltimer();
+    uint32_t n = 0;
+    while (!(ok = mbar_try_wait_cluster(bar, parity))) {
+      if ((++n & 255u) == 0) {
+        if (*abort_flag) break;
+        if (globaltimer() - t0 > kTimeoutNs) {
+          report_error(err, kErrTimeout, where, blockIdx.x, parity);
+          *abort_flag = 1;
+          break;
+        }
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // TMA tensor store of one box from shared memory (bulk-group completion).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, uint32_t src, int c0, int c1) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
@@ -286,16 +384,22 @@ struct EpiTraits {
   static constexpr int kChunkBytes = 32 * kCols * kEsize;
 };
 
-template <int BN, int STAGES, int OUT>
+template <int BN, int STAGES, int OUT, bool LN = false>
 struct Smem {
   static constexpr int kABytes = kBM * 128;       // 16 KB: 128 rows x 128 bytes
   static constexpr int kBBytes = BN * 128;        // 16 or 32 KB
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStgOff = STAGES * kStageBytes;                       // 1024-aligned
   static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<OUT>::kChunkBytes;
-  static constexpr int kBarOff = kStgOff + kStgBytes;
-  // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][2]; tmem slot + abort flag
-  static constexpr int kNumBars = 2 * STAGES + 4 + 2 * kEpiWarps;
+  // LayerNorm copy staging (BF16 or E4M3 chunks of 16 columns x 32 rows, two per warp)
+  static constexpr int kStg2Off = kStgOff + kStgBytes;
+  static constexpr int kStg2Bytes = LN ? kEpiWarps * 2 * 1024 : 0;
+  // LayerNorm partials: [2 tile parities][2 * kMaxLnCluster parts][128 rows] x (mean, m2)
+  static constexpr int kXOff = kStg2Off + kStg2Bytes;
+  static constexpr int kXBytes = LN ? 2 * 2 * kMaxLnCluster * kBM * 8 : 0;
+  static constexpr int kBarOff = kXOff + kXBytes;
+  // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][2], xbar[2]; tmem slot + abort flag
+  static constexpr int kNumBars = 2 * STAGES + 4 + 2 * kEpiWarps + 2;
   static constexpr int kBytes = kBarOff + kNumBars * 8 + 16;
   static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
 };
@@ -304,9 +408,10 @@ template <int BN, int STAGES, int EPI, int IN, int OUT>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR, Params p) {
-  using L = Smem<BN, STAGES, OUT>;
+  constexpr bool LN = EPI == kEpiResidLN;
+  using L = Smem<BN, STAGES, OUT, LN>;
   using E = EpiTraits<OUT>;
-  static_assert((EPI == AS_EPI_BIAS_RESID) == (OUT == kOutF32), "the residual epilogue writes FP32");
+  static_assert((EPI == AS_EPI_BIAS_RESID || LN) == (OUT == kOutF32), "the residual epilogues write FP32");
   constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
   constexpr uint32_t kIdesc = IN == kInE4M3 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
   constexpr int kBKe = bk_elems(IN);
@@ -323,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
   auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
   auto resid_bar = [&](int w, int b) { return bar0 + 8u * (2 * STAGES + 4 + 2 * w + b); };
+  auto xbar = [&](int b) { return bar0 + 8u * (2 * STAGES + 4 + 2 * kEpiWarps + b); };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kBarOff + L::kNumBars * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -342,6 +448,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(resid_bar(w, 0), 1);
       mbar_init(resid_bar(w, 1), 1);
     }
+    if (LN) {
+      // every epilogue thread of every CTA of the cluster arrives once per tile
+      mbar_init(xbar(0), cluster_size() * kEpiWarps * 32);
+      mbar_init(xbar(1), cluster_size() * kEpiWarps * 32);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -358,15 +469,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   fence_before();
   __syncthreads();
   fence_after();
+  if constexpr (LN) cluster_sync_all();  // the peers' barriers are initialised before anyone arrives on them
   const uint32_t tmem_base = *tmem_slot;
+  // Tile walk: all output tiles, or (LayerNorm) the 128-row blocks, one per
+  // cluster at a time, each CTA taking the column block of its cluster rank.
+  int t_first = blockIdx.x, t_step = gridDim.x, t_count = p.n_tiles;
+  uint32_t crank = 0, csize = 1;
+  if constexpr (LN) {
+    crank = cluster_rank();
+    csize = cluster_size();
+    t_first = (int)cluster_index();
+    t_step = (int)cluster_count();
+    t_count = p.n_tiles / p.n_tiles_n;
+  }
+  auto origin = [&](int t, int& m0, int& n0) {
+    if constexpr (LN) {
+      m0 = t * kBM;
+      n0 = (int)crank * BN;
+    } else {
+      tile_origin(p, t, BN, m0, n0);
+    }
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+      for (int tile = t_first; tile < t_count; tile += t_step) {
         int m0, n0;
-        tile_origin(p, tile, BN, m0, n0);
+        origin(tile, m0, n0);
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -382,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issuer
       uint32_t it = 0, lt = 0;
-      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
+      for (int tile = t_first; tile < t_count; tile += t_step, ++lt) {
         const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
         if (!mbar_wait(tempty_bar(acc), aph ^ 1u, abort_flag, p.err, 20)) goto done;
         fence_after();
@@ -417,10 +548,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* stg_ptr = smem + L::kStgOff + ew * 2 * E::kChunkBytes;
     const int r = lane;
     uint32_t lt = 0;
-    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++lt) {
+    for (int tile = t_first; tile < t_count; tile += t_step, ++lt) {
       const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
       int m0, n0;
-      tile_origin(p, tile, BN, m0, n0);
+      origin(tile, m0, n0);
       const int row0 = m0 + sub * 32;
       if (E::kF32) {
         // residual chunks of this tile: fetched before the accumulator is ready
@@ -436,6 +567,149 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!warp_wait(tfull_bar(acc), aph, abort_flag, p.err, 30)) break;
       fence_after();
+      if constexpr (LN) {
+        const uint32_t t_row = tmem_base + ((uint32_t)(sub * 32) << 16) + acc * BN;
+        const uint64_t alpha2 = f2splat(p.alpha);
+        // pass 1: y = alpha acc + bias + x, written back to TMEM; sums of y - y0 and
+        // (y - y0)^2 over this warp's columns, y0 = the first y of the row (a shift
+        // that keeps the one-pass variance free of cancellation)
+        float s1 = 0.f, s2 = 0.f, y0 = 0.f;
+        bool ok = true;
+#pragma unroll 1
+        for (int i = 0; i < CH; ++i) {
+          const int c = half * CH + i;
+          const int buf = i & 1;
+          const int n = n0 + c * CW;
+          uint32_t rr[16];
+          tmem_ld16(t_row + c * CW, rr);
+          const uint32_t par = (lt * (CH / 2) + (i >> 1)) & 1u;
+          if (!warp_wait(resid_bar(ew, buf), par, abort_flag, p.err, 32)) {
+            ok = false;
+            break;
+          }
+          const uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + 4 * j))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x = *reinterpret_cast<const float4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
+            float y[4];
+            f2unpack(add2(fma2(f2pack(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1])), alpha2,
+                               f2pack(b.x, b.y)), f2pack(x.x, x.y)), y[0], y[1]);
+            f2unpack(add2(fma2(f2pack(__uint_as_float(rr[4 * j + 2]), __uint_as_float(rr[4 * j + 3])), alpha2,
+                               f2pack(b.z, b.w)), f2pack(x.z, x.w)), y[2], y[3]);
+            if (i == 0 && j == 0) y0 = y[0];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float dy = y[e] - y0;
+              s1 += dy;
+              s2 = fmaf(dy, dy, s2);
+              rr[4 * j + e] = __float_as_uint(y[e]);
+            }
+          }
+          tmem_st16(t_row + c * CW, rr);
+          // the residual chunk two ahead into this buffer, once every lane has read it
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0 && i + 2 < CH) {
+            mbar_expect_tx(resid_bar(ew, buf), E::kChunkBytes);
+            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + 2 * CW, row0);
+          }
+        }
+        if (!ok) break;
+        tmem_wait_st();
+        constexpr float kPart = (float)(CH * CW);
+        const float mean_h = y0 + s1 / kPart;
+        const float m2 = fmaxf(s2 - s1 * s1 / kPart, 0.f);
+        // exchange: (mean, m2) of part (rank, half) of row sub*32+lane into every CTA of the cluster
+        const uint32_t pb = lt & 1u;
+        const int prow = sub * 32 + lane;
+        const uint32_t xaddr =
+            sbase + L::kXOff + ((pb * (2 * kMaxLnCluster) + crank * 2 + half) * kBM + prow) * 8;
+        for (uint32_t q = 0; q < csize; ++q) {
+          st_cluster_v2(mapa(xaddr, q), mean_h, m2);
+          mbar_arrive_cluster(mapa(xbar(pb), q));
+        }
+        if (!warp_wait_cluster(xbar(pb), (lt >> 1) & 1u, abort_flag, p.err, 33)) break;
+        // combine the 2C partials of equal size (Chan et al.)
+        const int nparts = 2 * (int)csize;
+        const float2* xs = reinterpret_cast<const float2*>(smem + L::kXOff) + pb * (2 * kMaxLnCluster) * kBM + prow;
+        float msum = 0.f;
+        for (int k = 0; k < nparts; ++k) msum += xs[k * kBM].x;
+        const float mean = msum / (float)nparts;
+        float m2t = 0.f;
+        for (int k = 0; k < nparts; ++k) {
+          const float2 pk = xs[k * kBM];
+          const float dm = pk.x - mean;
+          m2t += pk.y + kPart * dm * dm;
+        }
+        const float rstd = rsqrtf(m2t / ((float)nparts * kPart) + 1e-5f);
+        // pass 2: normalize; FP32 rows (in place) and the copy leave through
+        // swizzled staging and TMA tensor stores (rows past M are clipped)
+        uint8_t* c2_ptr = smem + L::kStg2Off + ew * 2 * 1024;
+        const uint32_t c2 = sbase + L::kStg2Off + ew * 2 * 1024;
+#pragma unroll 1
+        for (int i = 0; i < CH; ++i) {
+          const int c = half * CH + i;
+          const int n = n0 + c * CW;
+          const int buf = i & 1;
+          uint32_t rr[16];
+          tmem_ld16(t_row + c * CW, rr);
+          float o[16];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 g = __ldg(reinterpret_cast<const float4*>(p.ln_g + n + 4 * j));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(p.ln_b + n + 4 * j));
+            o[4 * j + 0] = (__uint_as_float(rr[4 * j + 0]) - mean) * rstd * g.x + b.x;
+            o[4 * j + 1] = (__uint_as_float(rr[4 * j + 1]) - mean) * rstd * g.y + b.y;
+            o[4 * j + 2] = (__uint_as_float(rr[4 * j + 2]) - mean) * rstd * g.z + b.z;
+            o[4 * j + 3] = (__uint_as_float(rr[4 * j + 3]) - mean) * rstd * g.w + b.w;
+          }
+          if (lane == 0) bulk_wait_read<1>();  // the stores two chunks back have read this buffer pair
+          __syncwarp();
+          uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4)) =
+                make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+          uint8_t* cc = c2_ptr + buf * 1024;
+          if (p.copy == 1) {
+            // BF16: 32-byte rows, 32-byte swizzle (piece j of row r at j ^ ((r >> 2) & 1))
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              __nv_bfloat162 h = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+              w[j] = *reinterpret_cast<uint32_t*>(&h);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+              *reinterpret_cast<uint4*>(cc + r * 32 + ((j ^ ((r >> 2) & 1)) << 4)) =
+                  make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+          } else if (p.copy == 2) {
+            // E4M3: 16-byte rows, no swizzle
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              uint16_t lo, hi;
+              asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;"
+                  : "=h"(lo) : "f"(o[4 * j + 1] * p.out_scale_inv), "f"(o[4 * j] * p.out_scale_inv));
+              asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;"
+                  : "=h"(hi) : "f"(o[4 * j + 3] * p.out_scale_inv), "f"(o[4 * j + 2] * p.out_scale_inv));
+              q[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+            *reinterpret_cast<uint4*>(cc + r * 16) = make_uint4(q[0], q[1], q[2], q[3]);
+          }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmR, stg + buf * E::kChunkBytes, n, row0);
+            if (p.copy) tma_store_2d(&tmC, c2 + buf * 1024, n, row0);
+            bulk_commit();
+          }
+        }
+        fence_before();
+        mbar_arrive(tempty_bar(acc));
+      } else {
 #pragma unroll 1
       for (int i = 0; i < CH; ++i) {
         const int c = half * CH + i;
@@ -527,6 +801,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_before();
       mbar_arrive(tempty_bar(acc));
+      }
     }
     if (lane == 0) bulk_wait_all();
   }
@@ -538,6 +813,8 @@ done:
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
   }
+  // no CTA leaves while a peer may still write its partials into it
+  if constexpr (LN) cluster_sync_all();
 }
 
 }  // namespace tc
@@ -625,6 +902,70 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   return AS_OK;
 }
 
+// Residual + LayerNorm GEMM: a cluster of C = N / BN CTAs per 128-row block.
+template <int BN, int STAGES, int IN>
+as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, cudaStream_t st) {
+  using L = tc::Smem<BN, STAGES, tc::kOutF32, true>;
+  auto kern = tc::gemm_kernel<BN, STAGES, tc::kEpiResidLN, IN, tc::kOutF32>;
+  static std::atomic<bool> attr_set[64] = {};
+  static std::atomic<int> max_clusters[64][tc::kMaxLnCluster + 1] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!attr_set[dev & 63]) {
+    AS_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
+    attr_set[dev & 63] = true;
+  }
+  CUtensorMap tmA, tmB, tmR;
+  const auto bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const auto u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const auto ein = IN == tc::kInE4M3 ? u8 : bf;
+  const uint32_t isz = IN == tc::kInE4M3 ? 1 : 2, bke = tc::bk_elems(IN);
+  as_status s = make_map(&tmA, A, ein, isz, (uint64_t)p0.M, (uint64_t)p0.K, bke, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK) s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK)
+    s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32,
+                 CU_TENSOR_MAP_SWIZZLE_64B);
+  // the copy: BF16 chunks with 32-byte rows (32-byte swizzle), E4M3 with 16-byte rows
+  CUtensorMap tmO = tmR;
+  if (s == AS_OK && p0.copy == 1)
+    s = make_map(&tmO, p0.out16, bf, 2, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32, CU_TENSOR_MAP_SWIZZLE_32B);
+  if (s == AS_OK && p0.copy == 2)
+    s = make_map(&tmO, p0.out8, u8, 1, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (s != AS_OK) return s;
+  tc::Params p = p0;
+  p.n_tiles_n = C;
+  const int m_blocks = (p.M + tc::kBM - 1) / tc::kBM;
+  p.n_tiles = C * m_blocks;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(tc::kThreads);
+  cfg.dynamicSmemBytes = L::kAlloc;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // persistent: as many clusters as fit on the GPU at once (asked once per device and size)
+  int mc = max_clusters[dev & 63][C].load();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if (mc == 0 && cap != cudaStreamCaptureStatusNone) {
+    mc = g_num_sms.load() > 0 ? g_num_sms.load() / C : 1;  // not asked while capturing a graph
+  } else if (mc == 0) {
+    cfg.gridDim = dim3((unsigned)(C * m_blocks));
+    int q = 0;
+    AS_CUDA_OK(cudaOccupancyMaxActiveClusters(&q, kern, &cfg));
+    mc = q > 0 ? q : 1;
+    max_clusters[dev & 63][C].store(mc);
+  }
+  cfg.gridDim = dim3((unsigned)(C * std::min(m_blocks, mc)));
+  AS_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, tmA, tmB, tmO, tmR, p));
+  count_launch();
+  return AS_OK;
+}
+
 // Tile configurations (the autotuner's choices): cfg & 1 = raster order,
 // cfg & 2 = 128-column tiles (6 stages) instead of 256-column tiles (4 stages).
 template <int IN>
@@ -698,6 +1039,55 @@ as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64
   }
   return in_e4m3 ? dispatch<tc::kInE4M3>(p, epi, out_e4m3, A, B, st, cfg)
                  : dispatch<tc::kInBF16>(p, epi, out_e4m3, A, B, st, cfg);
+}
+
+int gemm_resid_ln_cluster(int64_t N) {
+  const int bn = N % 256 == 0 ? 256 : 128;
+  const int64_t c = N % 128 == 0 ? N / bn : 0;
+  return (c >= 1 && c <= tc::kMaxLnCluster) ? (int)c : 0;
+}
+
+as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
+                                const float* bias, float* x32, const float* ln_g, const float* ln_b,
+                                __nv_bfloat16* out16, uint8_t* out8, float out8_scale, float alpha, DevError* err,
+                                cudaStream_t st) {
+  as_status s = ensure_driver();
+  if (s != AS_OK) return s;
+  if (g_num_sms.load() == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms.store(n > 0 ? n : kDefaultSMs);
+  }
+  const int C = gemm_resid_ln_cluster(N);
+  const int bke = tc::bk_elems(in_e4m3 ? tc::kInE4M3 : tc::kInBF16);
+  auto mis = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) != 0; };
+  if (C == 0 || M < 1 || K % bke != 0 || K < bke || M > (1ll << 31) - 1 || mis(A) || mis(B) || mis(x32) ||
+      !ln_g || !ln_b || mis(ln_g) || mis(ln_b) || (bias && mis(bias)) || (out16 && mis(out16)) ||
+      (out8 && (mis(out8) || !(out8_scale > 0.f))) || (out16 && out8)) {
+    set_k_error("gemm_tcgen05_resid_ln: unsupported shape, alignment or scale");
+    return AS_ERR_ARG;
+  }
+  tc::Params p{};
+  p.M = (int)M;
+  p.N = (int)N;
+  p.K = (int)K;
+  p.epi = tc::kEpiResidLN;
+  p.bias = bias;
+  p.resid = x32;
+  p.out = x32;
+  p.err = err;
+  p.alpha = alpha;
+  p.out_scale_inv = out8 ? 1.0f / out8_scale : 1.0f;
+  p.ln_g = ln_g;
+  p.ln_b = ln_b;
+  p.out16 = out16;
+  p.out8 = out8;
+  p.copy = out16 ? 1 : (out8 ? 2 : 0);
+  const bool wide = N % 256 == 0;
+  if (in_e4m3)
+    return wide ? launch_ln<256, 3, tc::kInE4M3>(p, A, B, C, st) : launch_ln<128, 4, tc::kInE4M3>(p, A, B, C, st);
+  return wide ? launch_ln<256, 3, tc::kInBF16>(p, A, B, C, st) : launch_ln<128, 4, tc::kInBF16>(p, A, B, C, st);
 }
 
 as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,

@@ -537,6 +537,9 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
                   c->pos_emb, c->emb_g, c->emb_b, X32, X16, X8, f8 ? as8[0] : 1.0f, R, d, st));
   if (mode == kEncCalib) amax_bf16(X16, Rd, amax + 0, st);
   DevError* err = ln->dev_err.as<DevError>();
+  // post-LN residual blocks as one clustered kernel (BF16 / FP8)
+  const bool ln_ok = (bf || f8) && gemm_resid_ln_cluster(d) > 0;
+  const bool fuse_ln = ln_ok && !(g.no_fused_ln & 1u), fuse_ln2 = ln_ok && !(g.no_fused_ln & 2u);
   for (uint32_t l = 0; l < g.n_layers; ++l) {
     const LayerW& L = c->layers[l];
     const bool last = l + 1 == g.n_layers;
@@ -555,13 +558,25 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
         else
           CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
                                   (int32_t)max_len, d, (int32_t)g.n_heads, st)); }
-      { ProfScope ps(ln, 0, 2.0 * R * d * d);
-        CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
-                            1.0f, err, st, c->gemm_cfg[1])); }
-      CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
+      if (fuse_ln) {
+        ProfScope ps(ln, 0, 2.0 * R * d * d);
+        CKS(gemm_tcgen05_resid_ln(true, R, d, d, ATT8, L.w_o8, L.b_o, X32, L.ln1_g, L.ln1_b, nullptr, X8, sc[2],
+                                  sc[1] * L.s_o, err, st));
+      } else {
+        { ProfScope ps(ln, 0, 2.0 * R * d * d);
+          CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
+                              1.0f, err, st, c->gemm_cfg[1])); }
+        CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
+      }
       { ProfScope ps(ln, 0, 2.0 * R * f * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, true, true, R, f, d, X8, L.w_1_8, L.b_1, nullptr, H8, sc[2] * L.s_1,
                             sc[3], err, st, c->gemm_cfg[2])); }
+      if (fuse_ln2 && !last) {
+        ProfScope ps(ln, 0, 2.0 * R * d * f);
+        CKS(gemm_tcgen05_resid_ln(true, R, d, f, H8, L.w_2_8, L.b_2, X32, L.ln2_g, L.ln2_b, nullptr, X8,
+                                  as8[kActPerLayer * (l + 1)], sc[3] * L.s_2, err, st));
+        continue;
+      }
       { ProfScope ps(ln, 0, 2.0 * R * d * f);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, f, H8, L.w_2_8, L.b_2, X32, Y32, sc[3] * L.s_2,
                             1.0f, err, st, c->gemm_cfg[3])); }
@@ -580,11 +595,24 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
                            (int32_t)g.n_heads, st));
       }
       if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
-      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
-      CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
+      if (fuse_ln) {
+        ProfScope ps(ln, 0, 2.0 * R * d * d);
+        CKS(gemm_tcgen05_resid_ln(false, R, d, d, ATT, L.w_o16, L.b_o, X32, L.ln1_g, L.ln1_b, X16, nullptr, 1.0f,
+                                  1.0f, err, st));
+      } else {
+        { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
+        CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
+      }
       if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * l + 2, st);
       { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, false, false, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, 1.0f, 1.0f, err, st, c->gemm_cfg[2])); }
       if (mode == kEncCalib) amax_bf16(H, (uint64_t)R * f, amax + kActPerLayer * l + 3, st);
+      if (fuse_ln2 && !last) {
+        { ProfScope ps(ln, 0, 2.0 * R * d * f);
+          CKS(gemm_tcgen05_resid_ln(false, R, d, f, H, L.w_2_16, L.b_2, X32, L.ln2_g, L.ln2_b, X16, nullptr, 1.0f,
+                                    1.0f, err, st)); }
+        if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * (l + 1), st);
+        continue;
+      }
       { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[3])); }
     } else {
       float* QKV = ln->QKV.as<float>();
