@@ -408,8 +408,12 @@ as_status as_serve_stop(as_ctx* ctx);
  * layer: QKV, attention output + residual, FFN1 + GELU, FFN2 + residual).
  * Configurations: bit 0 = tile order (0: along N within a 128-row block,
  * 1: along M within a column block), bit 1 = 128-column tiles with 6
- * pipeline stages instead of 256-column tiles with 4 (cfg 0 and 1 need
- * N % 256 == 0); -1 = the built-in default (cfg 0 when valid, else 2).
+ * pipeline stages instead of 256-column tiles with 4 (configurations
+ * without bit 1 need N % 256 == 0), bit 2 = pairs of CTAs (a cluster of
+ * two, on the tiles of two adjacent 128-row blocks) that load the shared
+ * weight tile once, half each, by TMA multicast into both; -1 = the built-in
+ * default (cfg 0 when valid, else 2). With fused post-LN blocks (see
+ * as_config.no_fused_ln) roles 1 and 3 apply only when unfused.
  * as_autotune times every valid configuration of each projection at `rows`
  * rows (0 = the ctx's batch size, max_chunk_tokens) on the ctx's stream with
  * the ctx's weights and scratch activations, keeps the fastest for later
@@ -418,11 +422,12 @@ as_status as_serve_stop(as_ctx* ctx);
  * AS_ERR_UNSUPPORTED for FP32 contexts (CUDA-core GEMM). as_set_tiles /
  * as_get_tiles store or read the choices, e.g. to reuse a saved tuning. */
 #define AS_TUNE_ROLES 4
+#define AS_TUNE_CONFIGS 8
 typedef struct {
   uint32_t role;       /* 0 QKV, 1 attention output, 2 FFN1, 3 FFN2        */
   uint64_t m, n, k;
   int32_t chosen;
-  float ms[4];         /* per configuration; negative = not valid           */
+  float ms[AS_TUNE_CONFIGS]; /* per configuration; negative = not valid    */
 } as_tune_entry;
 as_status as_autotune(as_ctx* ctx, uint64_t rows, as_tune_entry entries[AS_TUNE_ROLES]);
 as_status as_set_tiles(as_ctx* ctx, const int32_t cfg[AS_TUNE_ROLES]);

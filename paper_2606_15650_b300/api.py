@@ -122,7 +122,7 @@ class _StreamConfig(C.Structure):
 
 class _TuneEntry(C.Structure):
     _fields_ = [("role", C.c_uint32), ("m", C.c_uint64), ("n", C.c_uint64), ("k", C.c_uint64),
-                ("chosen", C.c_int32), ("ms", C.c_float * 4)]
+                ("chosen", C.c_int32), ("ms", C.c_float * 8)]
 
 
 TUNE_ROLES = ("qkv", "attn_out", "ffn1", "ffn2")

@@ -151,6 +151,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// TMA load into this CTA's shared memory whose transaction completes on an
+// mbarrier of either CTA of the pair (a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* tm, uint32_t cluster_bar, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(cluster_bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -195,6 +206,30 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 2-SM forms (a CTA pair, the even rank issuing): M = 256 over the two CTAs'
+// TMEM, A rows and B columns split between their shared memories; commits
+// arrive on the mbarrier at this offset in both CTAs.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(bar), "h"((uint16_t)0x3)
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -384,10 +419,10 @@ struct EpiTraits {
   static constexpr int kChunkBytes = 32 * kCols * kEsize;
 };
 
-template <int BN, int STAGES, int OUT, bool LN = false>
+template <int BN, int STAGES, int OUT, bool LN = false, bool BHALF = false>
 struct Smem {
   static constexpr int kABytes = kBM * 128;       // 16 KB: 128 rows x 128 bytes
-  static constexpr int kBBytes = BN * 128;        // 16 or 32 KB
+  static constexpr int kBBytes = BN * (BHALF ? 64 : 128);  // B rows of this CTA (half of them in a 2-SM pair)
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStgOff = STAGES * kStageBytes;                       // 1024-aligned
   static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<OUT>::kChunkBytes;
@@ -404,16 +439,26 @@ struct Smem {
   static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
 };
 
-template <int BN, int STAGES, int EPI, int IN, int OUT>
+template <int BN, int STAGES, int EPI, int IN, int OUT, int PAIR = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR, Params p) {
   constexpr bool LN = EPI == kEpiResidLN;
-  using L = Smem<BN, STAGES, OUT, LN>;
+  // PAIR = 2: 2-SM MMA. A cluster of two CTAs computes a 256 x BN tile: each
+  // loads its 128 A rows and half of the B rows; the even CTA issues
+  // tcgen05.mma.cta_group::2 (M = 256) reading both CTAs' shared memory and
+  // writing each CTA's 128 rows into its own TMEM; both CTAs' loads complete
+  // on the even CTA's full barrier; its commits free the stage and hand over
+  // the accumulator in both CTAs; both epilogues release the accumulator on
+  // the even CTA's barrier.
+  constexpr bool MC = PAIR == 2;
+  static_assert(!(MC && LN), "the LayerNorm epilogue clusters along N");
+  using L = Smem<BN, STAGES, OUT, LN, MC>;
   using E = EpiTraits<OUT>;
   static_assert((EPI == AS_EPI_BIAS_RESID || LN) == (OUT == kOutF32), "the residual epilogues write FP32");
   constexpr uint32_t kTmemCols = 2 * BN;   // power of two: 256 or 512
-  constexpr uint32_t kIdesc = IN == kInE4M3 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
+  constexpr int kMmaM = MC ? 2 * kBM : kBM;
+  constexpr uint32_t kIdesc = IN == kInE4M3 ? idesc_e4m3(kMmaM, BN) : idesc_bf16(kMmaM, BN);
   constexpr int kBKe = bk_elems(IN);
   constexpr int CW = E::kCols;             // columns per chunk
   constexpr int CH = BN / 2 / CW;          // chunks per epilogue warp and tile (a warp owns half the columns)
@@ -442,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), kEpiWarps * 32);
+      mbar_init(tempty_bar(a), (MC ? 2 : 1) * kEpiWarps * 32);   // a pair: both CTAs' epilogues
     }
     for (int w = 0; w < kEpiWarps; ++w) {
       mbar_init(resid_bar(w, 0), 1);
@@ -461,31 +506,51 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (E::kF32) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (MC) {
+      // collective over the pair: the same columns in both CTAs' TMEM
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if constexpr (LN) cluster_sync_all();  // the peers' barriers are initialised before anyone arrives on them
+  if constexpr (LN || MC) cluster_sync_all();  // the peers' barriers are initialised before anyone arrives on them
   const uint32_t tmem_base = *tmem_slot;
   // Tile walk: all output tiles, or (LayerNorm) the 128-row blocks, one per
   // cluster at a time, each CTA taking the column block of its cluster rank.
   int t_first = blockIdx.x, t_step = gridDim.x, t_count = p.n_tiles;
   uint32_t crank = 0, csize = 1;
+  const int n_mpairs = (p.n_tiles / p.n_tiles_n + 1) / 2;
   if constexpr (LN) {
     crank = cluster_rank();
     csize = cluster_size();
     t_first = (int)cluster_index();
     t_step = (int)cluster_count();
     t_count = p.n_tiles / p.n_tiles_n;
+  } else if constexpr (MC) {
+    crank = cluster_rank();
+    t_first = (int)cluster_index();
+    t_step = (int)cluster_count();
+    t_count = n_mpairs * p.n_tiles_n;
   }
   auto origin = [&](int t, int& m0, int& n0) {
     if constexpr (LN) {
       m0 = t * kBM;
       n0 = (int)crank * BN;
+    } else if constexpr (MC) {
+      // pair tiles: 256 rows x BN columns, the CTA of rank r takes rows 128 r ..
+      const int mp = p.raster == 0 ? t / p.n_tiles_n : t % n_mpairs;
+      const int nt = p.raster == 0 ? t % p.n_tiles_n : t / n_mpairs;
+      m0 = (2 * mp + (int)crank) * kBM;
+      n0 = nt * BN;
     } else {
       tile_origin(p, t, BN, m0, n0);
     }
@@ -502,16 +567,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.err, 10)) goto done;
-          mbar_expect_tx(full_bar(s), L::kStageBytes);
           const uint32_t a_dst = sbase + s * L::kStageBytes;
-          tma_load_2d(a_dst, &tmA, full_bar(s), kb * kBKe, m0);
-          tma_load_2d(a_dst + L::kABytes, &tmB, full_bar(s), kb * kBKe, n0);
+          if constexpr (MC) {
+            // both CTAs' halves complete on the even CTA's full barrier
+            const uint32_t fb = mapa(full_bar(s), 0);
+            if (crank == 0) mbar_expect_tx(full_bar(s), 2 * L::kStageBytes);
+            tma_load_2d_pair(a_dst, &tmA, fb, kb * kBKe, m0);
+            tma_load_2d_pair(a_dst + L::kABytes, &tmB, fb, kb * kBKe, n0 + (int)crank * (BN / 2));
+          } else {
+            mbar_expect_tx(full_bar(s), L::kStageBytes);
+            tma_load_2d(a_dst, &tmA, full_bar(s), kb * kBKe, m0);
+            tma_load_2d(a_dst + L::kABytes, &tmB, full_bar(s), kb * kBKe, n0);
+          }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
+    if (lane == 0 && (!MC || crank == 0)) {
+      // ---------------- MMA issuer (the even CTA of a 2-SM pair)
       uint32_t it = 0, lt = 0;
       for (int tile = t_first; tile < t_count; tile += t_step, ++lt) {
         const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
@@ -528,14 +601,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           // four MMAs per 128-byte k-block (K = 16 BF16 or 32 E4M3 each): 32 bytes apart
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            if (IN == kInE4M3)
-              mma_e4m3(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
-            else
-              mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+            const uint32_t en = (kb > 0 || k > 0) ? 1u : 0u;
+            if constexpr (MC) {
+              if (IN == kInE4M3) mma_e4m3_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+              else mma_bf16_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+            } else {
+              if (IN == kInE4M3) mma_e4m3(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+              else mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+            }
           }
-          mma_commit(empty_bar(s));
+          if constexpr (MC) mma_commit_pair(empty_bar(s));
+          else mma_commit(empty_bar(s));
         }
-        mma_commit(tfull_bar(acc));
+        if constexpr (MC) mma_commit_pair(tfull_bar(acc));
+        else mma_commit(tfull_bar(acc));
       }
     }
   } else {
@@ -800,7 +879,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       fence_before();
-      mbar_arrive(tempty_bar(acc));
+      if constexpr (MC) {
+        if (crank == 0) mbar_arrive(tempty_bar(acc));
+        else mbar_arrive_cluster(mapa(tempty_bar(acc), 0));
+      } else {
+        mbar_arrive(tempty_bar(acc));
+      }
       }
     }
     if (lane == 0) bulk_wait_all();
@@ -811,10 +895,13 @@ done:
   if (warp == 1) {
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+    if constexpr (MC)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
   }
-  // no CTA leaves while a peer may still write its partials into it
-  if constexpr (LN) cluster_sync_all();
+  // no CTA leaves while a peer may still write into its shared memory or barriers
+  if constexpr (LN || MC) cluster_sync_all();
 }
 
 }  // namespace tc
@@ -857,14 +944,15 @@ as_status make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dtype, 
   return AS_OK;
 }
 
-template <int BN, int STAGES, int EPI, int IN, int OUT>
+template <int BN, int STAGES, int EPI, int IN, int OUT, int PAIR>
 as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStream_t st) {
-  using L = tc::Smem<BN, STAGES, OUT>;
+  using L = tc::Smem<BN, STAGES, OUT, false, PAIR == 2>;
+  static_assert(L::kAlloc <= 232448, "shared memory per CTA");
   static std::atomic<bool> attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
-    AS_CUDA_OK(cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, EPI, IN, OUT>,
+    AS_CUDA_OK(cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, EPI, IN, OUT, PAIR>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc));
     attr_set[dev & 63] = true;
   }
@@ -874,7 +962,9 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   const auto ein = IN == tc::kInE4M3 ? u8 : bf;
   const uint32_t isz = IN == tc::kInE4M3 ? 1 : 2, bke = tc::bk_elems(IN);
   as_status s = make_map(&tmA, A, ein, isz, (uint64_t)p0.M, (uint64_t)p0.K, bke, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
-  if (s == AS_OK) s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  // B boxes: the whole BN-row tile, or half of it per CTA of a 2-SM pair
+  if (s == AS_OK)
+    s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN / PAIR, CU_TENSOR_MAP_SWIZZLE_128B);
   if (s == AS_OK) {
     if (OUT == tc::kOutF32) {
       s = make_map(&tmC, p0.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32,
@@ -895,10 +985,31 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   p.n_tiles_n = p.N / BN;
   p.n_tiles = p.n_tiles_n * ((p.M + tc::kBM - 1) / tc::kBM);
   const int n_sms = g_num_sms.load();
-  int grid = p.n_tiles < n_sms ? p.n_tiles : n_sms;
-  tc::gemm_kernel<BN, STAGES, EPI, IN, OUT><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
+  if (PAIR == 1) {
+    int grid = p.n_tiles < n_sms ? p.n_tiles : n_sms;
+    tc::gemm_kernel<BN, STAGES, EPI, IN, OUT, PAIR><<<grid, tc::kThreads, L::kAlloc, st>>>(tmA, tmB, tmC, tmR, p);
+    count_launch();
+    AS_CUDA_OK(cudaGetLastError());
+    return AS_OK;
+  }
+  // pairs of CTAs (a cluster of two), persistent over 256 x BN pair tiles
+  const int m_blocks = (p.M + tc::kBM - 1) / tc::kBM;
+  const int pair_tiles = (m_blocks + 1) / 2 * p.n_tiles_n;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(tc::kThreads);
+  cfg.dynamicSmemBytes = L::kAlloc;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int pairs = std::max(1, std::min(pair_tiles, n_sms / 2));
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  AS_CUDA_OK(cudaLaunchKernelEx(&cfg, tc::gemm_kernel<BN, STAGES, EPI, IN, OUT, PAIR>, tmA, tmB, tmC, tmR, p));
   count_launch();
-  AS_CUDA_OK(cudaGetLastError());
   return AS_OK;
 }
 
@@ -967,36 +1078,48 @@ as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, c
 }
 
 // Tile configurations (the autotuner's choices): cfg & 1 = raster order,
-// cfg & 2 = 128-column tiles (6 stages) instead of 256-column tiles (4 stages).
-template <int IN>
-as_status dispatch(const tc::Params& p0, int epi, bool out_e4m3, const void* A, const void* B, cudaStream_t st,
-                   int cfg) {
-  tc::Params p = p0;
-  bool wide = p.N % 256 == 0;
-  if (cfg >= 0) {
-    p.raster = cfg & 1;
-    if (cfg & 2) wide = false;
-  }
+// cfg & 2 = 128-column tiles (6 stages) instead of 256-column tiles (4 stages),
+// cfg & 4 = 2-SM MMA (CTA pairs, 256-row tiles, half the B rows per CTA).
+template <int IN, int PAIR>
+as_status dispatch_pair(const tc::Params& p, int epi, bool out_e4m3, bool wide, const void* A, const void* B,
+                        cudaStream_t st) {
+  // a 2-SM pair keeps half the B rows per CTA: 32 KB (wide) / 24 KB stages, so 6 / 8 of them
+  constexpr int SW = PAIR == 2 ? 6 : 4, SN = PAIR == 2 ? 8 : 6;
   switch (epi) {
     case AS_EPI_BIAS:
       if (out_e4m3) break;
-      return wide ? launch_bn<256, 4, AS_EPI_BIAS, IN, tc::kOutBF16>(p, A, B, st)
-                  : launch_bn<128, 6, AS_EPI_BIAS, IN, tc::kOutBF16>(p, A, B, st);
+      return wide ? launch_bn<256, SW, AS_EPI_BIAS, IN, tc::kOutBF16, PAIR>(p, A, B, st)
+                  : launch_bn<128, SN, AS_EPI_BIAS, IN, tc::kOutBF16, PAIR>(p, A, B, st);
     case AS_EPI_BIAS_GELU:
       if (out_e4m3)
-        return wide ? launch_bn<256, 4, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3>(p, A, B, st)
-                    : launch_bn<128, 6, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3>(p, A, B, st);
-      return wide ? launch_bn<256, 4, AS_EPI_BIAS_GELU, IN, tc::kOutBF16>(p, A, B, st)
-                  : launch_bn<128, 6, AS_EPI_BIAS_GELU, IN, tc::kOutBF16>(p, A, B, st);
+        return wide ? launch_bn<256, SW, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3, PAIR>(p, A, B, st)
+                    : launch_bn<128, SN, AS_EPI_BIAS_GELU, IN, tc::kOutE4M3, PAIR>(p, A, B, st);
+      return wide ? launch_bn<256, SW, AS_EPI_BIAS_GELU, IN, tc::kOutBF16, PAIR>(p, A, B, st)
+                  : launch_bn<128, SN, AS_EPI_BIAS_GELU, IN, tc::kOutBF16, PAIR>(p, A, B, st);
     case AS_EPI_BIAS_RESID:
       if (out_e4m3) break;
-      return wide ? launch_bn<256, 4, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st)
-                  : launch_bn<128, 6, AS_EPI_BIAS_RESID, IN, tc::kOutF32>(p, A, B, st);
+      return wide ? launch_bn<256, SW, AS_EPI_BIAS_RESID, IN, tc::kOutF32, PAIR>(p, A, B, st)
+                  : launch_bn<128, SN, AS_EPI_BIAS_RESID, IN, tc::kOutF32, PAIR>(p, A, B, st);
     default:
       break;
   }
   set_k_error("gemm_tcgen05: unsupported epilogue / output combination");
   return AS_ERR_ARG;
+}
+
+template <int IN>
+as_status dispatch(const tc::Params& p0, int epi, bool out_e4m3, const void* A, const void* B, cudaStream_t st,
+                   int cfg) {
+  tc::Params p = p0;
+  bool wide = p.N % 256 == 0;
+  bool pair = false;
+  if (cfg >= 0) {
+    p.raster = cfg & 1;
+    if (cfg & 2) wide = false;
+    pair = (cfg & 4) != 0;
+  }
+  return pair ? dispatch_pair<IN, 2>(p, epi, out_e4m3, wide, A, B, st)
+              : dispatch_pair<IN, 1>(p, epi, out_e4m3, wide, A, B, st);
 }
 
 }  // namespace

@@ -2272,6 +2272,7 @@ as_status as_autotune(as_ctx* c, uint64_t rows, as_tune_entry* entries) {
   cudaEventCreate(&e1);
   DevError* err = c->main.dev_err.as<DevError>();
   as_status status = AS_OK;
+  static_assert(kGemmCfgs <= AS_TUNE_CONFIGS, "one timing slot per tile configuration");
   for (int r = 0; r < AS_TUNE_ROLES && status == AS_OK; ++r) {
     const Role& ro = roles[r];
     as_tune_entry& en = entries[r];

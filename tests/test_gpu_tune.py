@@ -15,7 +15,7 @@ from synth.workloads import ModelDims
 pytestmark = pytest.mark.gpu
 
 SCHEMA = api.Schema(synth.TYPE_NAMES_4)
-# d = 256 makes every projection width a multiple of 256 (all four configurations valid)
+# d = 256 makes every projection width a multiple of 256 (all eight configurations valid)
 DIMS = ModelDims(vocab=8192, d_model=256, n_heads=4, d_ffn=1024, n_layers=2, n_labels=9)
 
 
@@ -26,15 +26,17 @@ def setup(vocab_words, c1_records):
     return blob, rs
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_all_tile_configurations_identical(setup, vocab_words, prec):
+@pytest.mark.parametrize("prec,fused_ln", [("bf16", True), ("bf16", False), ("fp8", False)])
+def test_all_tile_configurations_identical(setup, vocab_words, prec, fused_ln):
+    """Every configuration, CTA pairs with multicast weight tiles included (the
+    residual projections run on them only when the LayerNorm is not fused)."""
     blob, rs = setup
-    ctx = api.Context(DIMS, blob, vocab_words, precision=prec, keep_trace=True)
+    ctx = api.Context(DIMS, blob, vocab_words, precision=prec, keep_trace=True, fused_ln=fused_ln)
     if prec == "fp8":
         ctx.calibrate(rs.data, rs.offsets, SCHEMA)
     key = synth.make_key()
     ref = None
-    for cfg in (-1, 0, 1, 2, 3):
+    for cfg in (-1, 0, 1, 2, 3, 4, 5, 6, 7):
         ctx.set_tiles([cfg] * 4)
         assert ctx.tiles() == [cfg] * 4
         ctx.map_clear()
@@ -56,7 +58,7 @@ def test_autotune_reports_and_keeps_fastest(setup, vocab_words):
     for e in ent:
         assert e["m"] == 8192 and e["k"] in (256, 1024)
         valid = [x for x in e["ms"] if x >= 0]
-        assert len(valid) == 4 and all(x > 0 for x in valid)
+        assert len(valid) == 8 and all(x > 0 for x in valid)
         assert e["ms"][e["chosen"]] == min(valid)
     assert ctx.tiles() == [e["chosen"] for e in ent]
     ctx.close()
