@@ -47,9 +47,9 @@ METRIC = "tokens/s per B300, BF16/FP8 vs FP32 at >=99.9% label match; p50/p99 la
 # prefix (profiles/gemm_tc_c2_layer_65536rows.md); reported only while the
 # source is unchanged. A, C and the residual scale with the rows, so a launch
 # of R rows moves about mean(bytes) * R / 65,536.
-GEMM_TRAFFIC = {"source_sha256": "ec7789aaf220d122", "rows": 65536,
-                "bytes": {"qkv": 862670336 + 275248640, "attn_out": 502045440 + 167456000,
-                          "ffn1": 105011712 + 347317504, "ffn2": 632662528 + 176786688},
+GEMM_TRAFFIC = {"source_sha256": "90069e689c683a1a", "rows": 65536,
+                "bytes": {"qkv": 103793664 + 248344832, "attn_out": 302273024 + 245979904,
+                          "ffn1": 104975360 + 347247104, "ffn2": 621098752 + 255003136},
                 "profile": "profiles/gemm_tc_c2_layer_65536rows.md"}
 
 
