@@ -412,8 +412,10 @@ as_status as_serve_stop(as_ctx* ctx);
  * without bit 1 need N % 256 == 0), bit 2 = pairs of CTAs (a cluster of
  * two, on the tiles of two adjacent 128-row blocks) that load the shared
  * weight tile once, half each, by TMA multicast into both; -1 = the built-in
- * default (cfg 0 when valid, else 2). With fused post-LN blocks (see
- * as_config.no_fused_ln) roles 1 and 3 apply only when unfused.
+ * default (cfg 0 when valid, else 2). A post-LN block run as one fused
+ * kernel (roles 1 and 3, see as_config.no_fused_ln) has two choices: cfg 0
+ * (single-CTA tiles) or cfg 4 (2-SM pairs); its default is 0 for role 1 and
+ * 4 for role 3, and the other configurations report ms < 0.
  * as_autotune times every valid configuration of each projection at `rows`
  * rows (0 = the ctx's batch size, max_chunk_tokens) on the ctx's stream with
  * the ctx's weights and scratch activations, keeps the fastest for later

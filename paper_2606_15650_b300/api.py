@@ -199,7 +199,7 @@ def load() -> C.CDLL:
     lib.as_k_gemm_fp8.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, C.c_float, C.c_float,
                                   P, P, P, P]
     lib.as_k_gemm_resid_ln.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, P, P, P, P, P, P, P, P, C.c_float,
-                                       C.c_float, P]
+                                       C.c_float, C.c_int, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_attention_tc.argtypes = [P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
@@ -260,13 +260,14 @@ def gemm_fp8(epilogue: str, A8, B8, alpha: float, bias=None, resid=None, out=Non
 
 
 def gemm_resid_ln(A, B, bias, x32, ln_g, ln_b, out16=None, out8=None, out8_scale: float = 1.0, alpha: float = 1.0,
-                  stream=None):
+                  pair: bool = False, stream=None):
     """x32 <- LayerNorm(x32 + alpha * A @ B^T + bias) in place (BF16 or E4M3 operands), plus copies."""
     M, K = A.shape
     N = B.shape[0]
     in8 = 1 if A.element_size() == 1 else 0
     _check_k(load().as_k_gemm_resid_ln(in8, M, N, K, _ptr(A), _ptr(B), _ptr(bias), _ptr(x32), _ptr(ln_g),
-                                       _ptr(ln_b), _ptr(out16), _ptr(out8), out8_scale, alpha, stream))
+                                       _ptr(ln_b), _ptr(out16), _ptr(out8), out8_scale, alpha, 1 if pair else 0,
+                                       stream))
     return x32
 
 

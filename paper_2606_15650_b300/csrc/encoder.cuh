@@ -24,12 +24,13 @@ bool gemm_tcgen05_cfg_valid(int cfg, int64_t N);
 // with gain ln_g and bias ln_b (eps 1e-5, biased variance), in place, plus a
 // BF16 copy (out16) or an E4M3 copy of value / out8_scale (out8) when
 // non-null (not both). A row of N columns is one cluster of gemm_resid_ln_cluster(N) CTAs
-// (0: N not supported, use the residual GEMM and layernorm_rows instead).
+// (0: N not supported, use the residual GEMM and layernorm_rows instead); pair:
+// 2-SM MMA pairs along M as well (a cluster of twice that many CTAs).
 int gemm_resid_ln_cluster(int64_t N);
 as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                                 const float* bias, float* x32, const float* ln_g, const float* ln_b,
                                 __nv_bfloat16* out16, uint8_t* out8, float out8_scale, float alpha, DevError* err,
-                                cudaStream_t st);
+                                cudaStream_t st, bool pair = false);
 as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
                           const void* B, const float* bias, const float* resid, void* out, float alpha,
                           float out_scale, DevError* err, cudaStream_t st, int cfg = -1);

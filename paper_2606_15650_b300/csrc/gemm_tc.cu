@@ -226,9 +226,10 @@ __device__ __forceinline__ void mma_e4m3_pair(uint32_t d_tmem, uint64_t a, uint6
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
-__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+// mask: the pair's two cluster ranks (0x3 << rank of the even CTA)
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(bar), "h"((uint16_t)0x3)
+                   "r"(bar), "h"(mask)
                : "memory");
 }
 
@@ -451,8 +452,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // on the even CTA's full barrier; its commits free the stage and hand over
   // the accumulator in both CTAs; both epilogues release the accumulator on
   // the even CTA's barrier.
+  // With both (LayerNorm + pairs): cluster rank = 2 x column block + row half;
+  // ranks 2j, 2j+1 form a 2-SM pair, the LayerNorm exchange runs among the
+  // ranks of the same row half.
   constexpr bool MC = PAIR == 2;
-  static_assert(!(MC && LN), "the LayerNorm epilogue clusters along N");
   using L = Smem<BN, STAGES, OUT, LN, MC>;
   using E = EpiTraits<OUT>;
   static_assert((EPI == AS_EPI_BIAS_RESID || LN) == (OUT == kOutF32), "the residual epilogues write FP32");
@@ -494,9 +497,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(resid_bar(w, 1), 1);
     }
     if (LN) {
-      // every epilogue thread of every CTA of the cluster arrives once per tile
-      mbar_init(xbar(0), cluster_size() * kEpiWarps * 32);
-      mbar_init(xbar(1), cluster_size() * kEpiWarps * 32);
+      // every epilogue thread of every CTA of the exchange group arrives once per tile
+      const uint32_t group = MC ? cluster_size() / 2 : cluster_size();
+      mbar_init(xbar(0), group * kEpiWarps * 32);
+      mbar_init(xbar(1), group * kEpiWarps * 32);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -527,26 +531,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   // Tile walk: all output tiles, or (LayerNorm) the 128-row blocks, one per
   // cluster at a time, each CTA taking the column block of its cluster rank.
   int t_first = blockIdx.x, t_step = gridDim.x, t_count = p.n_tiles;
-  uint32_t crank = 0, csize = 1;
-  const int n_mpairs = (p.n_tiles / p.n_tiles_n + 1) / 2;
-  if constexpr (LN) {
-    crank = cluster_rank();
-    csize = cluster_size();
+  // crank: the row half in a 2-SM pair (0 = the CTA that issues the MMAs);
+  // lrank / csize: position and size of the LayerNorm exchange group;
+  // lead: cluster rank of the pair's issuing CTA
+  uint32_t crank = 0, csize = 1, lrank = 0, lead = 0;
+  const int n_mblocks = p.n_tiles / p.n_tiles_n;
+  const int n_mpairs = (n_mblocks + 1) / 2;
+  if constexpr (LN || MC) {
+    const uint32_t cr = cluster_rank();
+    crank = MC ? (cr & 1u) : 0u;
+    lead = cr & ~1u;
+    lrank = MC ? (cr >> 1) : cr;
+    csize = MC ? cluster_size() / 2 : cluster_size();
     t_first = (int)cluster_index();
     t_step = (int)cluster_count();
-    t_count = p.n_tiles / p.n_tiles_n;
-  } else if constexpr (MC) {
-    crank = cluster_rank();
-    t_first = (int)cluster_index();
-    t_step = (int)cluster_count();
-    t_count = n_mpairs * p.n_tiles_n;
+    t_count = LN ? (MC ? n_mpairs : n_mblocks) : n_mpairs * p.n_tiles_n;
   }
   auto origin = [&](int t, int& m0, int& n0) {
     if constexpr (LN) {
-      m0 = t * kBM;
-      n0 = (int)crank * BN;
+      m0 = (MC ? 2 * t + (int)crank : t) * kBM;
+      n0 = (int)lrank * BN;
     } else if constexpr (MC) {
-      // pair tiles: 256 rows x BN columns, the CTA of rank r takes rows 128 r ..
+      // pair tiles: 256 rows x BN columns, the CTA of row half h takes rows 128 h ..
       const int mp = p.raster == 0 ? t / p.n_tiles_n : t % n_mpairs;
       const int nt = p.raster == 0 ? t % p.n_tiles_n : t / n_mpairs;
       m0 = (2 * mp + (int)crank) * kBM;
@@ -570,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_dst = sbase + s * L::kStageBytes;
           if constexpr (MC) {
             // both CTAs' halves complete on the even CTA's full barrier
-            const uint32_t fb = mapa(full_bar(s), 0);
+            const uint32_t fb = mapa(full_bar(s), lead);
             if (crank == 0) mbar_expect_tx(full_bar(s), 2 * L::kStageBytes);
             tma_load_2d_pair(a_dst, &tmA, fb, kb * kBKe, m0);
             tma_load_2d_pair(a_dst + L::kABytes, &tmB, fb, kb * kBKe, n0 + (int)crank * (BN / 2));
@@ -610,10 +616,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               else mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
             }
           }
-          if constexpr (MC) mma_commit_pair(empty_bar(s));
+          if constexpr (MC) mma_commit_pair(empty_bar(s), (uint16_t)(0x3u << lead));
           else mma_commit(empty_bar(s));
         }
-        if constexpr (MC) mma_commit_pair(tfull_bar(acc));
+        if constexpr (MC) mma_commit_pair(tfull_bar(acc), (uint16_t)(0x3u << lead));
         else mma_commit(tfull_bar(acc));
       }
     }
@@ -704,10 +710,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t pb = lt & 1u;
         const int prow = sub * 32 + lane;
         const uint32_t xaddr =
-            sbase + L::kXOff + ((pb * (2 * kMaxLnCluster) + crank * 2 + half) * kBM + prow) * 8;
+            sbase + L::kXOff + ((pb * (2 * kMaxLnCluster) + lrank * 2 + half) * kBM + prow) * 8;
         for (uint32_t q = 0; q < csize; ++q) {
-          st_cluster_v2(mapa(xaddr, q), mean_h, m2);
-          mbar_arrive_cluster(mapa(xbar(pb), q));
+          const uint32_t qr = MC ? 2 * q + crank : q;   // cluster rank of group member q
+          st_cluster_v2(mapa(xaddr, qr), mean_h, m2);
+          mbar_arrive_cluster(mapa(xbar(pb), qr));
         }
         if (!warp_wait_cluster(xbar(pb), (lt >> 1) & 1u, abort_flag, p.err, 33)) break;
         // combine the 2C partials of equal size (Chan et al.)
@@ -787,7 +794,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         fence_before();
-        mbar_arrive(tempty_bar(acc));
+        if (MC && crank != 0) mbar_arrive_cluster(mapa(tempty_bar(acc), lead));
+        else mbar_arrive(tempty_bar(acc));
       } else {
 #pragma unroll 1
       for (int i = 0; i < CH; ++i) {
@@ -881,7 +889,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_before();
       if constexpr (MC) {
         if (crank == 0) mbar_arrive(tempty_bar(acc));
-        else mbar_arrive_cluster(mapa(tempty_bar(acc), 0));
+        else mbar_arrive_cluster(mapa(tempty_bar(acc), lead));
       } else {
         mbar_arrive(tempty_bar(acc));
       }
@@ -1013,13 +1021,15 @@ as_status launch_bn(const tc::Params& p0, const void* A, const void* B, cudaStre
   return AS_OK;
 }
 
-// Residual + LayerNorm GEMM: a cluster of C = N / BN CTAs per 128-row block.
-template <int BN, int STAGES, int IN>
+// Residual + LayerNorm GEMM: a cluster of C = N / BN CTAs per 128-row block,
+// or (PAIR = 2) of 2C CTAs per 256-row block, 2-SM pairs along M.
+template <int BN, int STAGES, int IN, int PAIR>
 as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, cudaStream_t st) {
-  using L = tc::Smem<BN, STAGES, tc::kOutF32, true>;
-  auto kern = tc::gemm_kernel<BN, STAGES, tc::kEpiResidLN, IN, tc::kOutF32>;
+  using L = tc::Smem<BN, STAGES, tc::kOutF32, true, PAIR == 2>;
+  static_assert(L::kAlloc <= 232448, "shared memory per CTA");
+  auto kern = tc::gemm_kernel<BN, STAGES, tc::kEpiResidLN, IN, tc::kOutF32, PAIR>;
   static std::atomic<bool> attr_set[64] = {};
-  static std::atomic<int> max_clusters[64][tc::kMaxLnCluster + 1] = {};
+  static std::atomic<int> max_clusters[64][2 * tc::kMaxLnCluster + 1] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
@@ -1032,7 +1042,8 @@ as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, c
   const auto ein = IN == tc::kInE4M3 ? u8 : bf;
   const uint32_t isz = IN == tc::kInE4M3 ? 1 : 2, bke = tc::bk_elems(IN);
   as_status s = make_map(&tmA, A, ein, isz, (uint64_t)p0.M, (uint64_t)p0.K, bke, tc::kBM, CU_TENSOR_MAP_SWIZZLE_128B);
-  if (s == AS_OK) s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (s == AS_OK)
+    s = make_map(&tmB, B, ein, isz, (uint64_t)p0.N, (uint64_t)p0.K, bke, BN / PAIR, CU_TENSOR_MAP_SWIZZLE_128B);
   if (s == AS_OK)
     s = make_map(&tmR, p0.resid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)p0.M, (uint64_t)p0.N, 16, 32,
                  CU_TENSOR_MAP_SWIZZLE_64B);
@@ -1047,10 +1058,12 @@ as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, c
   p.n_tiles_n = C;
   const int m_blocks = (p.M + tc::kBM - 1) / tc::kBM;
   p.n_tiles = C * m_blocks;
+  const int csz = C * PAIR;
+  const int units = (m_blocks + PAIR - 1) / PAIR;   // row blocks (or block pairs) to walk
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.x = (unsigned)csz;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(tc::kThreads);
@@ -1059,19 +1072,19 @@ as_status launch_ln(const tc::Params& p0, const void* A, const void* B, int C, c
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // persistent: as many clusters as fit on the GPU at once (asked once per device and size)
-  int mc = max_clusters[dev & 63][C].load();
+  int mc = max_clusters[dev & 63][csz].load();
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
   if (mc == 0 && cap != cudaStreamCaptureStatusNone) {
-    mc = g_num_sms.load() > 0 ? g_num_sms.load() / C : 1;  // not asked while capturing a graph
+    mc = g_num_sms.load() > 0 ? g_num_sms.load() / csz : 1;  // not asked while capturing a graph
   } else if (mc == 0) {
-    cfg.gridDim = dim3((unsigned)(C * m_blocks));
+    cfg.gridDim = dim3((unsigned)(csz * units));
     int q = 0;
     AS_CUDA_OK(cudaOccupancyMaxActiveClusters(&q, kern, &cfg));
     mc = q > 0 ? q : 1;
-    max_clusters[dev & 63][C].store(mc);
+    max_clusters[dev & 63][csz].store(mc);
   }
-  cfg.gridDim = dim3((unsigned)(C * std::min(m_blocks, mc)));
+  cfg.gridDim = dim3((unsigned)(csz * std::min(units, mc)));
   AS_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, tmA, tmB, tmO, tmR, p));
   count_launch();
   return AS_OK;
@@ -1173,7 +1186,7 @@ int gemm_resid_ln_cluster(int64_t N) {
 as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                                 const float* bias, float* x32, const float* ln_g, const float* ln_b,
                                 __nv_bfloat16* out16, uint8_t* out8, float out8_scale, float alpha, DevError* err,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool pair) {
   as_status s = ensure_driver();
   if (s != AS_OK) return s;
   if (g_num_sms.load() == 0) {
@@ -1208,9 +1221,14 @@ as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, c
   p.out8 = out8;
   p.copy = out16 ? 1 : (out8 ? 2 : 0);
   const bool wide = N % 256 == 0;
+  if (pair) {
+    if (in_e4m3)
+      return wide ? launch_ln<256, 5, tc::kInE4M3, 2>(p, A, B, C, st) : launch_ln<128, 6, tc::kInE4M3, 2>(p, A, B, C, st);
+    return wide ? launch_ln<256, 5, tc::kInBF16, 2>(p, A, B, C, st) : launch_ln<128, 6, tc::kInBF16, 2>(p, A, B, C, st);
+  }
   if (in_e4m3)
-    return wide ? launch_ln<256, 3, tc::kInE4M3>(p, A, B, C, st) : launch_ln<128, 4, tc::kInE4M3>(p, A, B, C, st);
-  return wide ? launch_ln<256, 3, tc::kInBF16>(p, A, B, C, st) : launch_ln<128, 4, tc::kInBF16>(p, A, B, C, st);
+    return wide ? launch_ln<256, 3, tc::kInE4M3, 1>(p, A, B, C, st) : launch_ln<128, 4, tc::kInE4M3, 1>(p, A, B, C, st);
+  return wide ? launch_ln<256, 3, tc::kInBF16, 1>(p, A, B, C, st) : launch_ln<128, 4, tc::kInBF16, 1>(p, A, B, C, st);
 }
 
 as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,

@@ -42,10 +42,10 @@ as_status as_k_gemm(int precision, int engine, int epilogue, int64_t M, int64_t 
 
 as_status as_k_gemm_resid_ln(int in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                              const float* bias, float* x32, const float* ln_g, const float* ln_b, void* out16,
-                             void* out8, float out8_scale, float alpha, void* stream) {
+                             void* out8, float out8_scale, float alpha, int pair, void* stream) {
   return gemm_tcgen05_resid_ln(in_e4m3 != 0, M, N, K, A, B, bias, x32, ln_g, ln_b,
                                static_cast<__nv_bfloat16*>(out16), static_cast<uint8_t*>(out8), out8_scale, alpha,
-                               nullptr, reinterpret_cast<cudaStream_t>(stream));
+                               nullptr, reinterpret_cast<cudaStream_t>(stream), pair != 0);
 }
 
 as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_t K, const void* A8, const void* B8,
