@@ -47,9 +47,9 @@ METRIC = "tokens/s per B300, BF16/FP8 vs FP32 at >=99.9% label match; p50/p99 la
 # prefix (profiles/gemm_tc_c2_layer_65536rows.md); reported only while the
 # source is unchanged. A, C and the residual scale with the rows, so a launch
 # of R rows moves about mean(bytes) * R / 65,536.
-GEMM_TRAFFIC = {"source_sha256": "90069e689c683a1a", "rows": 65536,
-                "bytes": {"qkv": 103793664 + 248344832, "attn_out": 302273024 + 245979904,
-                          "ffn1": 104975360 + 347247104, "ffn2": 621098752 + 255003136},
+GEMM_TRAFFIC = {"source_sha256": "3b3e99830bc15657", "rows": 65536,
+                "bytes": {"qkv": 103815168 + 248664320, "attn_out": 302192384 + 246129664,
+                          "ffn1": 105082112 + 346799104, "ffn2": 615945216 + 253349376},
                 "profile": "profiles/gemm_tc_c2_layer_65536rows.md"}
 
 
@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true", help="skip FP32 / CPU baselines (profiling runs)")
     ap.add_argument("--chunk", type=int, default=0, help="encoder rows per packed batch (0 = library default)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMM tiles (profiling runs)")
+    ap.add_argument("--tiles", default="", help="GEMM tile configuration per projection, e.g. 4,0,0,4 "
+                                                "(instead of autotuning; profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="measured seconds per offered rate of the serving leg (0 = skip it)")
     ap.add_argument("--stream-records", type=int, default=3000,
@@ -238,7 +240,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
 
     # ---- tile autotuner at the batch size (outside the timed region)
-    tune = [] if args.no_autotune else ctx.autotune()
+    if args.tiles:
+        ctx.set_tiles([int(x) for x in args.tiles.split(",")])
+        tune = []
+    else:
+        tune = [] if args.no_autotune else ctx.autotune()
 
     # ---- warm-up
     stats = None
