@@ -413,9 +413,10 @@ as_status as_serve_stop(as_ctx* ctx);
  * two, on the tiles of two adjacent 128-row blocks) that load the shared
  * weight tile once, half each, by TMA multicast into both; -1 = the built-in
  * default (cfg 0 when valid, else 2). A post-LN block run as one fused
- * kernel (roles 1 and 3, see as_config.no_fused_ln) has two choices: cfg 0
- * (single-CTA tiles) or cfg 4 (2-SM pairs); its default is 0 for role 1 and
- * 4 for role 3, and the other configurations report ms < 0.
+ * kernel (roles 1 and 3, see as_config.no_fused_ln) has four choices: cfg 0
+ * (single-CTA tiles), 4 (2-SM pairs), and each | 2 (a shorter main-loop ring
+ * for more residual / output bytes in flight in the epilogue); its default is
+ * 0 for role 1 and 4 for role 3; odd configurations report ms < 0.
  * as_autotune times every valid configuration of each projection at `rows`
  * rows (0 = the ctx's batch size, max_chunk_tokens) on the ctx's stream with
  * the ctx's weights and scratch activations, keeps the fastest for later

@@ -53,8 +53,10 @@ as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_
  * out8_scale, saturated) receives a copy when not NULL (at most one). A, B BF16 (in_e4m3 =
  * 0, K % 64 == 0) or E4M3 (in_e4m3 = 1, K % 128 == 0). Each 128-row block
  * runs on a cluster of CTAs that split the row: N must be 128, 256, 384,
- * 512, 768 or 1024; pair = 1 adds 2-SM MMA pairs along M (256-row blocks on
- * twice as many CTAs). 16-byte aligned pointers. AS_ERR_ARG otherwise. */
+ * 512, 768 or 1024. pair: bit 0 adds 2-SM MMA pairs along M (256-row blocks
+ * on twice as many CTAs); bit 1 trades main-loop stages for four residual /
+ * output buffers per epilogue warp (results identical in every mode).
+ * 16-byte aligned pointers. AS_ERR_ARG otherwise. */
 as_status as_k_gemm_resid_ln(int in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                              const float* bias, float* x32, const float* ln_g, const float* ln_b, void* out16,
                              void* out8, float out8_scale, float alpha, int pair, void* stream);

@@ -260,14 +260,14 @@ def gemm_fp8(epilogue: str, A8, B8, alpha: float, bias=None, resid=None, out=Non
 
 
 def gemm_resid_ln(A, B, bias, x32, ln_g, ln_b, out16=None, out8=None, out8_scale: float = 1.0, alpha: float = 1.0,
-                  pair: bool = False, stream=None):
+                  pair: bool = False, deep: bool = False, stream=None):
     """x32 <- LayerNorm(x32 + alpha * A @ B^T + bias) in place (BF16 or E4M3 operands), plus copies."""
     M, K = A.shape
     N = B.shape[0]
     in8 = 1 if A.element_size() == 1 else 0
     _check_k(load().as_k_gemm_resid_ln(in8, M, N, K, _ptr(A), _ptr(B), _ptr(bias), _ptr(x32), _ptr(ln_g),
-                                       _ptr(ln_b), _ptr(out16), _ptr(out8), out8_scale, alpha, 1 if pair else 0,
-                                       stream))
+                                       _ptr(ln_b), _ptr(out16), _ptr(out8), out8_scale, alpha,
+                                       (1 if pair else 0) | (2 if deep else 0), stream))
     return x32
 
 

@@ -25,12 +25,14 @@ bool gemm_tcgen05_cfg_valid(int cfg, int64_t N);
 // BF16 copy (out16) or an E4M3 copy of value / out8_scale (out8) when
 // non-null (not both). A row of N columns is one cluster of gemm_resid_ln_cluster(N) CTAs
 // (0: N not supported, use the residual GEMM and layernorm_rows instead); pair:
-// 2-SM MMA pairs along M as well (a cluster of twice that many CTAs).
+// 2-SM MMA pairs along M as well (a cluster of twice that many CTAs); deep: a
+// shorter main-loop ring for four residual / output buffers per epilogue warp
+// (for K = d, where the epilogue's bytes bound the kernel).
 int gemm_resid_ln_cluster(int64_t N);
 as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                                 const float* bias, float* x32, const float* ln_g, const float* ln_b,
                                 __nv_bfloat16* out16, uint8_t* out8, float out8_scale, float alpha, DevError* err,
-                                cudaStream_t st, bool pair = false);
+                                cudaStream_t st, bool pair = false, bool deep = false);
 as_status gemm_tcgen05_ex(int epi, bool in_e4m3, bool out_e4m3, int64_t M, int64_t N, int64_t K, const void* A,
                           const void* B, const float* bias, const float* resid, void* out, float alpha,
                           float out_scale, DevError* err, cudaStream_t st, int cfg = -1);

@@ -420,22 +420,37 @@ struct EpiTraits {
   static constexpr int kChunkBytes = 32 * kCols * kEsize;
 };
 
+// Residual / output staging buffers per epilogue warp: 4 for the LayerNorm
+// epilogue on a short main-loop ring (2 stages, or 3 half-B stages of a 2-SM
+// pair), which the attention-output block can afford (K = d) and which keeps
+// more of its residual and output bytes in flight; else 2.
+__host__ __device__ constexpr int stg_bufs(bool ln, int stages, bool bhalf) {
+  return ln && (stages == 2 || (bhalf && stages == 3)) ? 4 : 2;
+}
+
 template <int BN, int STAGES, int OUT, bool LN = false, bool BHALF = false>
 struct Smem {
+  static constexpr int kRB = stg_bufs(LN, STAGES, BHALF);
   static constexpr int kABytes = kBM * 128;       // 16 KB: 128 rows x 128 bytes
   static constexpr int kBBytes = BN * (BHALF ? 64 : 128);  // B rows of this CTA (half of them in a 2-SM pair)
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStgOff = STAGES * kStageBytes;                       // 1024-aligned
-  static constexpr int kStgBytes = kEpiWarps * 2 * EpiTraits<OUT>::kChunkBytes;
+  static constexpr int kStgBytes = kEpiWarps * kRB * EpiTraits<OUT>::kChunkBytes;
   // LayerNorm copy staging (BF16 or E4M3 chunks of 16 columns x 32 rows, two per warp)
   static constexpr int kStg2Off = kStgOff + kStgBytes;
-  static constexpr int kStg2Bytes = LN ? kEpiWarps * 2 * 1024 : 0;
+  static constexpr int kStg2Bytes = LN ? kEpiWarps * kRB * 1024 : 0;
   // LayerNorm partials: [2 tile parities][2 * kMaxLnCluster parts][128 rows] x (mean, m2)
   static constexpr int kXOff = kStg2Off + kStg2Bytes;
   static constexpr int kXBytes = LN ? 2 * 2 * kMaxLnCluster * kBM * 8 : 0;
-  static constexpr int kBarOff = kXOff + kXBytes;
-  // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][2], xbar[2]; tmem slot + abort flag
-  static constexpr int kNumBars = 2 * STAGES + 4 + 2 * kEpiWarps + 2;
+  // LayerNorm: bias, gain and LayerNorm bias of this CTA's BN columns (fixed
+  // per CTA) in shared memory when they fit, else read from global memory
+  static constexpr int kVecOff = kXOff + kXBytes;
+  static constexpr int kNumBarsPre = 2 * STAGES + 4 + kRB * kEpiWarps + 2;
+  static constexpr bool kVecSmem = LN && kVecOff + 3 * BN * 4 + kNumBarsPre * 8 + 16 + 1024 <= 232448;
+  static constexpr int kVecBytes = kVecSmem ? 3 * BN * 4 : 0;
+  static constexpr int kBarOff = kVecOff + kVecBytes;
+  // full[S], empty[S], tfull[2], tempty[2], resid[kEpiWarps][kRB], xbar[2]; tmem slot + abort flag
+  static constexpr int kNumBars = 2 * STAGES + 4 + kRB * kEpiWarps + 2;
   static constexpr int kBytes = kBarOff + kNumBars * 8 + 16;
   static constexpr int kAlloc = kBytes + 1024;    // room to align the base to 1024
 };
@@ -466,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int CW = E::kCols;             // columns per chunk
   constexpr int CH = BN / 2 / CW;          // chunks per epilogue warp and tile (a warp owns half the columns)
   static_assert(CH % 2 == 0, "chunks alternate between two staging buffers");
+  static_assert(CH % L::kRB == 0, "chunks cycle through the staging buffers");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -475,8 +491,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
   auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
-  auto resid_bar = [&](int w, int b) { return bar0 + 8u * (2 * STAGES + 4 + 2 * w + b); };
-  auto xbar = [&](int b) { return bar0 + 8u * (2 * STAGES + 4 + 2 * kEpiWarps + b); };
+  constexpr int RB = L::kRB;   // staging buffers per epilogue warp
+  auto resid_bar = [&](int w, int b) { return bar0 + 8u * (2 * STAGES + 4 + RB * w + b); };
+  auto xbar = [&](int b) { return bar0 + 8u * (2 * STAGES + 4 + RB * kEpiWarps + b); };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kBarOff + L::kNumBars * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -492,10 +509,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(tfull_bar(a), 1);
       mbar_init(tempty_bar(a), (MC ? 2 : 1) * kEpiWarps * 32);   // a pair: both CTAs' epilogues
     }
-    for (int w = 0; w < kEpiWarps; ++w) {
-      mbar_init(resid_bar(w, 0), 1);
-      mbar_init(resid_bar(w, 1), 1);
-    }
+    for (int w = 0; w < kEpiWarps; ++w)
+      for (int b = 0; b < RB; ++b) mbar_init(resid_bar(w, b), 1);
     if (LN) {
       // every epilogue thread of every CTA of the exchange group arrives once per tile
       const uint32_t group = MC ? cluster_size() / 2 : cluster_size();
@@ -561,6 +576,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       tile_origin(p, t, BN, m0, n0);
     }
   };
+  if constexpr (L::kVecSmem) {
+    // the column block is fixed per CTA: its bias / gain / LayerNorm bias go to shared memory once
+    float* vec = reinterpret_cast<float*>(smem + L::kVecOff);
+    const int nb = (int)lrank * BN;
+    for (int j = threadIdx.x; j < BN; j += blockDim.x) {
+      vec[j] = p.bias ? p.bias[nb + j] : 0.f;
+      vec[BN + j] = p.ln_g[nb + j];
+      vec[2 * BN + j] = p.ln_b[nb + j];
+    }
+    __syncthreads();
+  }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -629,8 +655,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp - 2;
     const int sub = warp & 3;
     const int half = ew >> 2;
-    const uint32_t stg = sbase + L::kStgOff + ew * 2 * E::kChunkBytes;
-    uint8_t* stg_ptr = smem + L::kStgOff + ew * 2 * E::kChunkBytes;
+    const uint32_t stg = sbase + L::kStgOff + ew * RB * E::kChunkBytes;
+    uint8_t* stg_ptr = smem + L::kStgOff + ew * RB * E::kChunkBytes;
     const int r = lane;
     uint32_t lt = 0;
     for (int tile = t_first; tile < t_count; tile += t_step, ++lt) {
@@ -643,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
           bulk_wait_read<0>();  // earlier stores have left the staging buffers
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
+          for (int i = 0; i < RB; ++i) {
             mbar_expect_tx(resid_bar(ew, i), E::kChunkBytes);
             tma_load_2d(stg + i * E::kChunkBytes, &tmR, resid_bar(ew, i), n0 + (half * CH + i) * CW, row0);
           }
@@ -663,20 +689,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int i = 0; i < CH; ++i) {
           const int c = half * CH + i;
-          const int buf = i & 1;
+          const int buf = i % RB;
           const int n = n0 + c * CW;
           uint32_t rr[16];
           tmem_ld16(t_row + c * CW, rr);
-          const uint32_t par = (lt * (CH / 2) + (i >> 1)) & 1u;
+          const uint32_t par = (lt * (CH / RB) + i / RB) & 1u;
           if (!warp_wait(resid_bar(ew, buf), par, abort_flag, p.err, 32)) {
             ok = false;
             break;
           }
           const uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
+          const float4* vb = L::kVecSmem ? reinterpret_cast<const float4*>(smem + L::kVecOff) + (c * CW) / 4 : nullptr;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const float4 b = p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + 4 * j))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 b = L::kVecSmem ? vb[j]
+                             : (p.bias ? __ldg(reinterpret_cast<const float4*>(p.bias + n + 4 * j))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f));
             const float4 x = *reinterpret_cast<const float4*>(cb + r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
             float y[4];
             f2unpack(add2(fma2(f2pack(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1])), alpha2,
@@ -693,12 +721,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           tmem_st16(t_row + c * CW, rr);
-          // the residual chunk two ahead into this buffer, once every lane has read it
-          fence_proxy_async();
+          // the residual chunk RB ahead into this buffer, once every lane has read it
+          // (the warp barrier orders the reads before the copy is issued)
           __syncwarp();
-          if (lane == 0 && i + 2 < CH) {
+          if (lane == 0 && i + RB < CH) {
             mbar_expect_tx(resid_bar(ew, buf), E::kChunkBytes);
-            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + 2 * CW, row0);
+            tma_load_2d(stg + buf * E::kChunkBytes, &tmR, resid_bar(ew, buf), n + RB * CW, row0);
           }
         }
         if (!ok) break;
@@ -732,26 +760,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float rstd = rsqrtf(m2t / ((float)nparts * kPart) + 1e-5f);
         // pass 2: normalize; FP32 rows (in place) and the copy leave through
         // swizzled staging and TMA tensor stores (rows past M are clipped)
-        uint8_t* c2_ptr = smem + L::kStg2Off + ew * 2 * 1024;
-        const uint32_t c2 = sbase + L::kStg2Off + ew * 2 * 1024;
+        uint8_t* c2_ptr = smem + L::kStg2Off + ew * RB * 1024;
+        const uint32_t c2 = sbase + L::kStg2Off + ew * RB * 1024;
 #pragma unroll 1
         for (int i = 0; i < CH; ++i) {
           const int c = half * CH + i;
           const int n = n0 + c * CW;
-          const int buf = i & 1;
+          const int buf = i % RB;
           uint32_t rr[16];
           tmem_ld16(t_row + c * CW, rr);
           float o[16];
+          const float4* vg = reinterpret_cast<const float4*>(smem + L::kVecOff + BN * 4) + (c * CW) / 4;
+          const float4* vbb = reinterpret_cast<const float4*>(smem + L::kVecOff + 2 * BN * 4) + (c * CW) / 4;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const float4 g = __ldg(reinterpret_cast<const float4*>(p.ln_g + n + 4 * j));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(p.ln_b + n + 4 * j));
+            const float4 g = L::kVecSmem ? vg[j] : __ldg(reinterpret_cast<const float4*>(p.ln_g + n + 4 * j));
+            const float4 b = L::kVecSmem ? vbb[j] : __ldg(reinterpret_cast<const float4*>(p.ln_b + n + 4 * j));
             o[4 * j + 0] = (__uint_as_float(rr[4 * j + 0]) - mean) * rstd * g.x + b.x;
             o[4 * j + 1] = (__uint_as_float(rr[4 * j + 1]) - mean) * rstd * g.y + b.y;
             o[4 * j + 2] = (__uint_as_float(rr[4 * j + 2]) - mean) * rstd * g.z + b.z;
             o[4 * j + 3] = (__uint_as_float(rr[4 * j + 3]) - mean) * rstd * g.w + b.w;
           }
-          if (lane == 0) bulk_wait_read<1>();  // the stores two chunks back have read this buffer pair
+          if (lane == 0) bulk_wait_read<RB - 1>();  // the stores RB chunks back have read this buffer pair
           __syncwarp();
           uint8_t* cb = stg_ptr + buf * E::kChunkBytes;
 #pragma unroll
@@ -1186,7 +1216,7 @@ int gemm_resid_ln_cluster(int64_t N) {
 as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                                 const float* bias, float* x32, const float* ln_g, const float* ln_b,
                                 __nv_bfloat16* out16, uint8_t* out8, float out8_scale, float alpha, DevError* err,
-                                cudaStream_t st, bool pair) {
+                                cudaStream_t st, bool pair, bool deep) {
   as_status s = ensure_driver();
   if (s != AS_OK) return s;
   if (g_num_sms.load() == 0) {
@@ -1221,10 +1251,21 @@ as_status gemm_tcgen05_resid_ln(bool in_e4m3, int64_t M, int64_t N, int64_t K, c
   p.out8 = out8;
   p.copy = out16 ? 1 : (out8 ? 2 : 0);
   const bool wide = N % 256 == 0;
+  // deep: a short main-loop ring and four staging buffers per epilogue warp
   if (pair) {
+    if (deep) {
+      if (in_e4m3)
+        return wide ? launch_ln<256, 3, tc::kInE4M3, 2>(p, A, B, C, st) : launch_ln<128, 3, tc::kInE4M3, 2>(p, A, B, C, st);
+      return wide ? launch_ln<256, 3, tc::kInBF16, 2>(p, A, B, C, st) : launch_ln<128, 3, tc::kInBF16, 2>(p, A, B, C, st);
+    }
     if (in_e4m3)
       return wide ? launch_ln<256, 5, tc::kInE4M3, 2>(p, A, B, C, st) : launch_ln<128, 6, tc::kInE4M3, 2>(p, A, B, C, st);
     return wide ? launch_ln<256, 5, tc::kInBF16, 2>(p, A, B, C, st) : launch_ln<128, 6, tc::kInBF16, 2>(p, A, B, C, st);
+  }
+  if (deep) {
+    if (in_e4m3)
+      return wide ? launch_ln<256, 2, tc::kInE4M3, 1>(p, A, B, C, st) : launch_ln<128, 2, tc::kInE4M3, 1>(p, A, B, C, st);
+    return wide ? launch_ln<256, 2, tc::kInBF16, 1>(p, A, B, C, st) : launch_ln<128, 2, tc::kInBF16, 1>(p, A, B, C, st);
   }
   if (in_e4m3)
     return wide ? launch_ln<256, 3, tc::kInE4M3, 1>(p, A, B, C, st) : launch_ln<128, 4, tc::kInE4M3, 1>(p, A, B, C, st);

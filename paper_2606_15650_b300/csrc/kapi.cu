@@ -45,7 +45,7 @@ as_status as_k_gemm_resid_ln(int in_e4m3, int64_t M, int64_t N, int64_t K, const
                              void* out8, float out8_scale, float alpha, int pair, void* stream) {
   return gemm_tcgen05_resid_ln(in_e4m3 != 0, M, N, K, A, B, bias, x32, ln_g, ln_b,
                                static_cast<__nv_bfloat16*>(out16), static_cast<uint8_t*>(out8), out8_scale, alpha,
-                               nullptr, reinterpret_cast<cudaStream_t>(stream), pair != 0);
+                               nullptr, reinterpret_cast<cudaStream_t>(stream), (pair & 1) != 0, (pair & 2) != 0);
 }
 
 as_status as_k_gemm_fp8(int epilogue, int out_e4m3, int64_t M, int64_t N, int64_t K, const void* A8, const void* B8,

@@ -522,6 +522,8 @@ bool ln_fused(const as_config& g, int block) {
   return g.precision != AS_FP32 && gemm_resid_ln_cluster(g.d_model) > 0 && !(g.no_fused_ln & (1u << block));
 }
 bool ln_pair(const int cfg, int block) { return cfg < 0 ? block == 1 : (cfg & 4) != 0; }
+// deep epilogue staging (tile configuration bit 1 of a fused block; off by default)
+bool ln_deep(const int cfg, int) { return cfg >= 0 && (cfg & 2) != 0; }
 
 // Embedding, the layers and the classifier over R rows (everything of an
 // encoder batch whose launch shapes depend only on R and n_items).
@@ -549,6 +551,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
   // post-LN residual blocks as one clustered kernel (BF16 / FP8)
   const bool fuse_ln = ln_fused(g, 0), fuse_ln2 = ln_fused(g, 1);
   const bool pair1 = ln_pair(c->gemm_cfg[1], 0), pair2 = ln_pair(c->gemm_cfg[3], 1);
+  const bool deep1 = ln_deep(c->gemm_cfg[1], 0), deep2 = ln_deep(c->gemm_cfg[3], 1);
   for (uint32_t l = 0; l < g.n_layers; ++l) {
     const LayerW& L = c->layers[l];
     const bool last = l + 1 == g.n_layers;
@@ -570,7 +573,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       if (fuse_ln) {
         ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_resid_ln(true, R, d, d, ATT8, L.w_o8, L.b_o, X32, L.ln1_g, L.ln1_b, nullptr, X8, sc[2],
-                                  sc[1] * L.s_o, err, st, pair1));
+                                  sc[1] * L.s_o, err, st, pair1, deep1));
       } else {
         { ProfScope ps(ln, 0, 2.0 * R * d * d);
           CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
@@ -583,7 +586,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       if (fuse_ln2 && !last) {
         ProfScope ps(ln, 0, 2.0 * R * d * f);
         CKS(gemm_tcgen05_resid_ln(true, R, d, f, H8, L.w_2_8, L.b_2, X32, L.ln2_g, L.ln2_b, nullptr, X8,
-                                  as8[kActPerLayer * (l + 1)], sc[3] * L.s_2, err, st, pair2));
+                                  as8[kActPerLayer * (l + 1)], sc[3] * L.s_2, err, st, pair2, deep2));
         continue;
       }
       { ProfScope ps(ln, 0, 2.0 * R * d * f);
@@ -607,7 +610,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       if (fuse_ln) {
         ProfScope ps(ln, 0, 2.0 * R * d * d);
         CKS(gemm_tcgen05_resid_ln(false, R, d, d, ATT, L.w_o16, L.b_o, X32, L.ln1_g, L.ln1_b, X16, nullptr, 1.0f,
-                                  1.0f, err, st, pair1));
+                                  1.0f, err, st, pair1, deep1));
       } else {
         { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
         CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
@@ -618,7 +621,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       if (fuse_ln2 && !last) {
         { ProfScope ps(ln, 0, 2.0 * R * d * f);
           CKS(gemm_tcgen05_resid_ln(false, R, d, f, H, L.w_2_16, L.b_2, X32, L.ln2_g, L.ln2_b, X16, nullptr, 1.0f,
-                                    1.0f, err, st, pair2)); }
+                                    1.0f, err, st, pair2, deep2)); }
         if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * (l + 1), st);
         continue;
       }
@@ -2291,18 +2294,19 @@ as_status as_autotune(as_ctx* c, uint64_t rows, as_tune_entry* entries) {
     en.k = ro.k;
     float best = 0.f;
     int best_cfg = -1;
-    // a fused post-LN block has two choices: single-CTA tiles (cfg 0) or 2-SM pairs (cfg 4)
+    // a fused post-LN block has four choices: single-CTA tiles (cfg 0) or 2-SM
+    // pairs (cfg 4), each with the long or the short main-loop ring (cfg | 2)
     const int block = r == 1 ? 0 : (r == 3 ? 1 : -1);
     const bool fused = block >= 0 && ln_fused(g, block);
     for (int cfg = 0; cfg < kGemmCfgs && status == AS_OK; ++cfg) {
       en.ms[cfg] = -1.f;
-      if (fused ? (cfg != 0 && cfg != 4) : !gemm_tcgen05_cfg_valid(cfg, (int64_t)ro.n)) continue;
+      if (fused ? (cfg & 1) != 0 : !gemm_tcgen05_cfg_valid(cfg, (int64_t)ro.n)) continue;
       auto launch = [&]() {
         if (fused)
           return gemm_tcgen05_resid_ln(f8, (int64_t)rows, (int64_t)ro.n, (int64_t)ro.k, A.p, ro.w, ro.b, Rz.as<float>(),
                                        block == 0 ? L.ln1_g : L.ln2_g, block == 0 ? L.ln1_b : L.ln2_b,
                                        f8 ? nullptr : O.as<__nv_bfloat16>(), f8 ? O.as<uint8_t>() : nullptr, 1.0f,
-                                       1.0f, err, st, cfg == 4);
+                                       1.0f, err, st, (cfg & 4) != 0, (cfg & 2) != 0);
         return gemm_tcgen05_ex(ro.epi, f8, ro.out8, (int64_t)rows, (int64_t)ro.n, (int64_t)ro.k, A.p, ro.w, ro.b,
                                ro.epi == AS_EPI_BIAS_RESID ? Rz.as<float>() : nullptr, O.p, 1.0f, 1.0f, err, st, cfg);
       };

@@ -41,15 +41,15 @@ def _torch_ref(A, B, bias, x, gam, bet, alpha):
     return torch.nn.functional.layer_norm(y, (y.shape[1],), gam, bet, eps=1e-5)
 
 
-@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("pair,deep", [(False, False), (True, False), (False, True), (True, True)])
 @pytest.mark.parametrize("M,N,K", [(1, 768, 768), (200, 768, 3072), (4096, 768, 768), (300, 128, 512),
                                    (1000, 384, 384), (513, 512, 512), (777, 1024, 1024), (256, 256, 1024)])
-def test_bf16_against_torch_and_two_kernels(M, N, K, pair):
+def test_bf16_against_torch_and_two_kernels(M, N, K, pair, deep):
     A, B, bias, x, gam, bet = _inputs(M, N, K, seed=M + N + K)
     ref = _torch_ref(A, B, bias, x, gam, bet, 1.0)
     x_fused = x.clone()
     out16 = torch.empty(M, N, device=DEV, dtype=torch.bfloat16)
-    api.gemm_resid_ln(A, B, bias, x_fused, gam, bet, out16=out16, pair=pair)
+    api.gemm_resid_ln(A, B, bias, x_fused, gam, bet, out16=out16, pair=pair, deep=deep)
     torch.cuda.synchronize()
     err = (x_fused - ref).abs().max().item()
     assert err < 2e-3, err
@@ -65,16 +65,17 @@ def test_bf16_against_torch_and_two_kernels(M, N, K, pair):
     assert (x_fused - two).abs().max().item() < 2e-5
 
 
-@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("pair,deep", [(False, False), (True, False), (False, True), (True, True)])
 @pytest.mark.parametrize("M,N,K", [(1000, 768, 768), (130, 768, 3072), (64, 1024, 1024)])
-def test_e4m3_operands_and_copy(M, N, K, pair):
+def test_e4m3_operands_and_copy(M, N, K, pair, deep):
     A8, B8, bias, x, gam, bet = _inputs(M, N, K, seed=7 * M + N, e4m3=True)
     alpha = 1.0 / 16
     ref = _torch_ref(A8, B8, bias, x, gam, bet, alpha)
     x_fused = x.clone()
     out8 = torch.empty(M, N, device=DEV, dtype=torch.uint8)
     scale = 0.0625
-    api.gemm_resid_ln(A8, B8, bias, x_fused, gam, bet, out8=out8, out8_scale=scale, alpha=alpha, pair=pair)
+    api.gemm_resid_ln(A8, B8, bias, x_fused, gam, bet, out8=out8, out8_scale=scale, alpha=alpha, pair=pair,
+                      deep=deep)
     torch.cuda.synchronize()
     assert (x_fused - ref).abs().max().item() < 2e-3
     want = (x_fused / scale).clamp(-448, 448).to(torch.float8_e4m3fn).view(torch.uint8)
@@ -89,10 +90,14 @@ def test_unsupported_width_is_refused():
 
 @pytest.mark.parametrize("M,N,K", [(1, 768, 768), (1000, 768, 3072), (513, 128, 512), (777, 1024, 1024)])
 def test_pairs_bit_identical(M, N, K):
-    """2-SM pairs change which SM multiplies, not the accumulation order."""
+    """2-SM pairs and the staging depth change which SM multiplies and when bytes
+    move, not the accumulation order."""
     A, B, bias, x, gam, bet = _inputs(M, N, K, seed=3 * M + K)
-    a, b = x.clone(), x.clone()
-    api.gemm_resid_ln(A, B, bias, a, gam, bet, pair=False)
-    api.gemm_resid_ln(A, B, bias, b, gam, bet, pair=True)
+    outs = []
+    for pair in (False, True):
+        for deep in (False, True):
+            y = x.clone()
+            api.gemm_resid_ln(A, B, bias, y, gam, bet, pair=pair, deep=deep)
+            outs.append(y)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    assert all(torch.equal(outs[0], y) for y in outs[1:])

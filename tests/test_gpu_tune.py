@@ -58,11 +58,12 @@ def test_autotune_reports_and_keeps_fastest(setup, vocab_words):
     for e in ent:
         assert e["m"] == 8192 and e["k"] in (256, 1024)
         valid = [x for x in e["ms"] if x >= 0]
-        # the fused post-LN blocks choose between single-CTA tiles (0) and 2-SM pairs (4)
+        # the fused post-LN blocks: single-CTA tiles (0) or 2-SM pairs (4), each with
+        # the long or the short main-loop ring (| 2)
         fused = e["role"] in ("attn_out", "ffn2")
-        assert len(valid) == (2 if fused else 8) and all(x > 0 for x in valid)
+        assert len(valid) == (4 if fused else 8) and all(x > 0 for x in valid)
         if fused:
-            assert e["ms"][0] > 0 and e["ms"][4] > 0
+            assert all(e["ms"][k] > 0 for k in (0, 2, 4, 6))
         assert e["ms"][e["chosen"]] == min(valid)
     assert ctx.tiles() == [e["chosen"] for e in ent]
     ctx.close()
