@@ -467,10 +467,37 @@ __global__ void __launch_bounds__(kThreads, 2)
       const Work w = work_of(p, u);
       const uint32_t ocol = kColO;
       float m = -INFINITY, l = 0.f;              // m: the maximum P is taken against
+      // a warp whose 32 query rows all lie past the sequence end (the ragged last
+      // query tile) computes nothing: its P and O rows only feed output rows that
+      // are never stored, and MMA rows do not mix; it keeps the barrier protocol
+      // and its share of the V-tail zeroing
+      const bool live = w.q0 + sub * 32 < w.L;
       for (int t = 0; t < w.n_t; ++t, ++g) {
         const int valid = min(kKT, w.L - t * kKT);  // keys of this tile inside the sequence
         if (!warp_wait(bar(kBarSFull + (g & 1)), (g >> 1) & 1, abort_flag, p.err, 60)) { ok = false; break; }
         fence_after();
+        // keys past the sequence end have P = 0, but the MMA still multiplies
+        // their V rows: zero those rows of the landed V tile (a 128-byte row
+        // holds all its swizzled pieces), so that whatever lies past the
+        // sequence (another sequence's rows, padding, non-finite data)
+        // contributes exactly nothing (every softmax warp takes a share)
+        auto zero_v_tail = [&]() -> bool {
+          if (valid >= kKT) return true;
+          const int vst = g % kVStages;
+          if (!warp_wait(bar(kBarVFull + vst), (g / kVStages) & 1, abort_flag, p.err, 64)) return false;
+          uint4* vt = reinterpret_cast<uint4*>(smem + kOffV + vst * kVBytes);
+          for (int q = valid * 8 + (warp - 3) * 32 + lane; q < kKT * 8; q += 128) vt[q] = make_uint4(0u, 0u, 0u, 0u);
+          fence_proxy_async();
+          return true;
+        };
+        if (!live) {
+          fence_before();
+          mbar_arrive(bar(kBarSEmpty + (g & 1)));
+          if (!zero_v_tail()) { ok = false; break; }
+          fence_before();
+          mbar_arrive(bar(kBarPFull + (g & 1)));
+          continue;
+        }
         uint32_t v[64];
         tmem_ld64(trow + 64u * (uint32_t)(g & 1), v);
         fence_before();
@@ -529,18 +556,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         f2unpack(add2(s2[0], s2[1]), sl[0], sl[1]);
         f2unpack(add2(s2[2], s2[3]), sl[2], sl[3]);
         l += (sl[0] + sl[1]) + (sl[2] + sl[3]);
-        if (valid < kKT) {
-          // keys past the sequence end have P = 0, but the MMA still multiplies
-          // their V rows: zero those rows of the landed V tile (a 128-byte row
-          // holds all its swizzled pieces), so that whatever lies past the
-          // sequence (another sequence's rows, padding, non-finite data)
-          // contributes exactly nothing
-          const int vst = g % kVStages;
-          if (!warp_wait(bar(kBarVFull + vst), (g / kVStages) & 1, abort_flag, p.err, 64)) { ok = false; break; }
-          uint4* vt = reinterpret_cast<uint4*>(smem + kOffV + vst * kVBytes);
-          for (int q = valid * 8 + (warp - 3) * 32 + lane; q < kKT * 8; q += 128) vt[q] = make_uint4(0u, 0u, 0u, 0u);
-          fence_proxy_async();
-        }
+        if (!zero_v_tail()) { ok = false; break; }
         // P_g goes to TMEM buffer g&1 once O += P_{g-2} V_{g-2} has read it
         if (g >= 2 && !wait_o(g - 2, 62)) { ok = false; break; }
         fence_after();
@@ -549,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         mbar_arrive(bar(kBarPFull + (g & 1)));
       }
       if (!ok) break;
+      if (!live) continue;
       // epilogue: O_{g-1} is this unit's last update (the next unit's first
       // O MMA waits for P, which these warps write only after this read)
       if (!wait_o(g - 1, 63)) { ok = false; break; }
