@@ -494,6 +494,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           fence_before();
           mbar_arrive(bar(kBarSEmpty + (g & 1)));
           if (!zero_v_tail()) { ok = false; break; }
+          // as in the live path, arrive for P_g only once O_{g-2} is done: that
+          // orders this warp's P-full arrivals after the phase of tile g-2 has
+          // completed (without it a warp that computes nothing could run two
+          // tiles ahead and arrive in the phase of an unfinished tile)
+          if (g >= 2 && !wait_o(g - 2, 65)) { ok = false; break; }
           fence_before();
           mbar_arrive(bar(kBarPFull + (g & 1)));
           continue;
