@@ -228,3 +228,28 @@ def test_layernorm(d):
     ref = torch.nn.functional.layer_norm(x.double(), (d,), gam.double(), bet.double(), eps=1e-5)
     assert (out.double() - ref).abs().max().item() < 2e-5
     assert torch.equal(out16, out.to(torch.bfloat16))
+
+
+def test_attention_tcgen05_ragged_query_tiles_stress():
+    """Many sequences whose last 128-query tile is mostly empty: softmax warps
+    with no valid query row compute nothing but must keep the pipeline's
+    barrier phases in step. Several persistent units per CTA and repeated
+    launches give those warps every chance to run ahead. The result equals the
+    mma.sync engine's (same BF16 inputs) within BF16 rounding of P, on every
+    launch, and every launch completes (no bounded wait runs out)."""
+    d, h = 768, 12
+    g = torch.Generator(device="cpu").manual_seed(99)
+    base = torch.tensor([129, 130, 140, 159, 257, 260, 288, 385, 390, 400, 1, 2, 31, 33], dtype=torch.int32)
+    lens = base.repeat(120)[torch.randperm(14 * 120, generator=g)]
+    starts = torch.zeros_like(lens)
+    starts[1:] = torch.cumsum(lens, 0)[:-1]
+    rows = int(lens.sum())
+    qkv = torch.randn(rows, 3 * d, generator=g).to(DEV).to(torch.bfloat16)
+    ref = torch.empty(rows, d, device=DEV, dtype=torch.bfloat16)
+    api.attention("bf16", qkv, ref, starts.to(DEV), lens.to(DEV), d, h)
+    for _ in range(5):
+        out = torch.empty(rows, d, device=DEV, dtype=torch.bfloat16)
+        api.attention_tc(qkv, out, starts.to(DEV), lens.to(DEV), d, h)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out.float()).all()
+        assert (out.float() - ref.float()).abs().max().item() < 2.5e-2
