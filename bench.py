@@ -70,6 +70,10 @@ def parse():
                     help="measured seconds per offered rate of the serving leg (0 = skip it)")
     ap.add_argument("--stream-records", type=int, default=3000,
                     help="records of the streaming leg (24-layer d1024 FP8 model; 0 = skip it)")
+    ap.add_argument("--c3-records", type=int, default=8000,
+                    help="records of the packed-batch FP8 sample (windows, Zipf entities); 0 skips it")
+    ap.add_argument("--stream-densities", default="2,8,32",
+                    help="entity densities (per 1k tokens) of the streaming sweep; empty skips it")
     ap.add_argument("--field-records", type=int, default=20000,
                     help="records of the per-field policy leg (0 = skip it)")
     ap.add_argument("--serve-rates", default="1000,5000,20000,50000", help="offered records/s of the serving leg")
@@ -441,6 +445,8 @@ def baselines(args, w, words, recs, weights, blob, key, schema, local) -> dict:
         out["serving"] = serving_leg(args, words, blob, key, local)
     if args.stream_records > 0:
         out["streaming"] = streaming_leg(args, words, key, local)
+    if args.c3_records > 0:
+        out["c3_packed_fp8"] = c3_leg(args, words, key, local)
     if args.field_records > 0:
         out["field_policy"] = field_policy_leg(args, w, words, blob, key, local)
         out["jsonl"] = jsonl_leg(args, w, words, blob, key, local)
@@ -582,15 +588,72 @@ def streaming_leg(args, words, key, local) -> dict:
     host_ms = 1e3 * (time.perf_counter() - t0)
     n_out = len(o.arrays()[0])
     o.free()
+    # entity density sweep (2 / 8 / 32 entities per 1k tokens), streamed, same model and key
+    sweep = []
+    for dens in (float(x) for x in args.stream_densities.split(",") if x):
+        from dataclasses import replace
+        rs = synth.make_records(replace(w5.records, entities_per_1k=dens), words, seed=synth.SEED_RECORDS + 5)
+        ctx.map_clear()
+        ctx.anonymize_stream(rs.data, rs.offsets, schema, key, batch_bytes=batch, lanes=2).free()  # warm-up
+        t0 = time.perf_counter()
+        od = ctx.anonymize_stream(rs.data, rs.offsets, schema, key, batch_bytes=batch, lanes=2)
+        dt = time.perf_counter() - t0
+        sd = od.stats()
+        od.free()
+        sweep.append({"entities_per_1k_tokens": dens, "stream_tokens_per_s": sd["n_encoded_tokens"] / dt,
+                      "final_spans": int(sd["n_final_spans"]), "map_entries": int(sd["n_map_entries"])})
     ctx.close()
     return {"workload": f"{synth.C5.name} sample: {recs.n} records, {len(recs.data)} bytes, {enc} encoded tokens "
                         f"(lognormal(1500, 0.8) clipped 16..4096, windows 512/384)",
+            "density_sweep": sweep,
             "model": "encoder 24L d1024 h16 ffn4096, 17 BIO labels, FP8 e4m3 GEMMs (static scales)",
             "stream_tokens_per_s": enc / (host_ms / 1e3), "device_resident_tokens_per_s": enc / (dev_ms / 1e3),
             "overlap_efficiency": dev_ms / host_ms, "batch_bytes": batch, "lanes": 2,
             "h2d_bytes": int(len(recs.data) + recs.offsets.nbytes), "d2h_bytes": int(n_out + recs.offsets.nbytes),
             "timing": "stream: host clock around the call (pageable numpy in, host bytes out); "
                       "device-resident: CUDA events on the ctx stream"}
+
+
+def c3_leg(args, words, key, local) -> dict:
+    """Packed variable-length batches + FP8 sample: records 16..4096 tokens (lognormal(600, 1.0)),
+    sliding windows 512/384 with the centre merge, Zipf(1.1) reuse over 50k distinct entities,
+    12-layer d=768 encoder with E4M3 GEMMs (static scales from 64 calibration records) and
+    autotuned tiles; device-resident, CUDA events, median of 3 calls."""
+    import torch
+    import paper_2606_15650_b300.api as api
+    w3 = synth.scaled(synth.C3, args.c3_records)
+    recs = synth.make_records(w3.records, words, seed=synth.SEED_RECORDS + 3)
+    blob = synth.pack_blob(w3.dims, synth.make_weights(w3.dims))
+    schema = api.Schema(synth.TYPE_NAMES_4, window=w3.window, stride=w3.stride)
+    ctx = api.Context(w3.dims, blob, words, precision="fp8", mode="packed", device=local)
+    del blob
+    cal = synth.make_records(synth.scaled(w3, 64).records, words, seed=synth.SEED_CALIB)
+    ctx.calibrate(cal.data, cal.offsets, schema)
+    tune = ctx.autotune()
+    stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{local}")
+    d_data = torch.from_numpy(recs.data).to(f"cuda:{local}")
+    d_offs = torch.from_numpy(recs.offsets.astype(np.int64)).to(f"cuda:{local}")
+    o = ctx.anonymize(d_data, d_offs, schema, key)  # warm-up
+    st = o.stats()
+    o.free()
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.anonymize(d_data, d_offs, schema, key).free()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms)) / 1e3
+    ent = ctx.map_export()
+    ctx.close()
+    return {"workload": f"{synth.C3.name} sample: {recs.n} records, {len(recs.data)} bytes, {st['n_tokens']} tokens, "
+                        f"{st['n_sequences']} windows / sequences",
+            "encoded_tokens_per_s": st["n_encoded_tokens"] / t, "record_tokens_per_s": st["n_tokens"] / t,
+            "records_per_s": recs.n / t, "ms": t * 1e3, "map_entries": len(ent),
+            "final_spans": int(st["n_final_spans"]),
+            "autotune": {e["role"]: e["chosen"] for e in tune},
+            "timing": "inputs in HBM, CUDA events on the ctx stream, median of 3 calls after one warm-up"}
 
 
 def serving_leg(args, words, blob, key, local) -> dict:
