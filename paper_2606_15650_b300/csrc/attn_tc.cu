@@ -42,12 +42,12 @@ constexpr int kKT = 64;        // keys per tile
 constexpr int kThreads = 224;  // Q/K loader, V loader, MMA issuer, 4 softmax warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
-// Work item = one 128-query tile of one sequence: (sequence << 6) | q-tile.
-// A work unit is an (item, head) pair; CTA b takes units b, b + grid, ...
+// Work item = one 128-query tile of one sequence, self-contained so that one
+// 8-byte load describes it: x = the sequence's first row, y = L | (q0 << 16)
+// (L = 0: a padding item). A work unit is an (item, head) pair; CTA b takes
+// units b, b + grid, ...
 struct Params {
-  const int32_t* seq_start;
-  const int32_t* seq_len;
-  const int32_t* items;
+  const int2* items;
   int n_items;
   void* out;            // BF16, or E4M3 of value * out_inv_scale
   float out_inv_scale;
@@ -253,31 +253,50 @@ constexpr float kRescaleSlack = 8.0f;
 struct Work {
   int L, row0, q0, h, n_t;
 };
-__device__ __forceinline__ Work work_of(const Params& p, int u) {
-  const int it = p.items[u / p.n_heads];
-  const int s = it >> 6;
-  Work w;
-  w.h = u % p.n_heads;
-  w.L = p.seq_len[s];
-  w.row0 = p.seq_start[s];
-  w.q0 = (it & 63) * kQ;
-  w.n_t = (w.L + kKT - 1) / kKT;
-  return w;
-}
+__device__ __forceinline__ int2 item_at(const Params& p, int u) { return __ldg(p.items + u / p.n_heads); }
+__device__ __forceinline__ bool item_empty(int2 it) { return (it.y & 0xFFFF) == 0; }
+
+// A CTA's walk over its units (u = b, b + grid, ...), skipping padding items
+// the same way in every role. The descriptor of the unit after the current
+// one is loaded when the current one starts, so that a unit boundary does not
+// wait on a global load (it is only read a whole unit later).
+struct UnitWalk {
+  int u = 0, n = 0, step = 0;
+  int2 cur{0, 0}, nxt{0, 0};
+  __device__ __forceinline__ void start(const Params& p, int n_units) {
+    n = n_units;
+    step = (int)gridDim.x;
+    u = (int)blockIdx.x;
+    while (u < n && item_empty(cur = item_at(p, u))) u += step;
+    if (u < n && u + step < n) nxt = item_at(p, u + step);
+  }
+  __device__ __forceinline__ void advance(const Params& p) {
+    u += step;
+    if (u >= n) return;
+    cur = nxt;
+    if (item_empty(cur)) {
+      do u += step;
+      while (u < n && item_empty(cur = item_at(p, u)));
+      if (u >= n) return;
+    }
+    if (u + step < n) nxt = item_at(p, u + step);
+  }
+  __device__ __forceinline__ bool done() const { return u >= n; }
+  __device__ __forceinline__ Work work(const Params& p) const {
+    Work w;
+    w.h = u % p.n_heads;
+    w.row0 = cur.x;
+    w.L = cur.y & 0xFFFF;
+    w.q0 = cur.y >> 16;
+    w.n_t = (w.L + kKT - 1) / kKT;
+    return w;
+  }
+};
 
 __device__ __forceinline__ uint16_t e4m3x2(float lo, float hi) {
   uint16_t r;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
   return r;
-}
-
-// The first unit at or after u (stepping by the grid) that has keys: items
-// that point at an empty sequence (padding of a fixed-size launch) are
-// skipped, in the same way by every role.
-__device__ __forceinline__ int next_unit(const Params& p, int u, int n_units) {
-  for (; u < n_units; u += gridDim.x)
-    if (p.seq_len[p.items[u / p.n_heads] >> 6] > 0) break;
-  return u;
 }
 
 // Persistent: a CTA loops over its work units; tiles are numbered globally
@@ -328,14 +347,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t tmem = *tmem_slot;
   const int d = p.d;
 
-  const int step = gridDim.x;
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- Q and K loads, in unit order
       int i = 0, g = 0;
       bool ok = true;
-      for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + step, n_units), ++i) {
-        const Work w = work_of(p, u);
+      UnitWalk uw;
+      for (uw.start(p, n_units); !uw.done() && ok; uw.advance(p), ++i) {
+        const Work w = uw.work(p);
         const int b = i & 1;
         if (i >= 2 && !mbar_wait(bar(kBarQEmpty + b), ((i >> 1) - 1) & 1, abort_flag, p.err, 40)) { ok = false; break; }
         mbar_expect_tx(bar(kBarQFull + b), kQBytes);
@@ -364,8 +383,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       // frees only after O += P V, later than the K stage of the same tile)
       int g = 0;
       bool ok = true;
-      for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + step, n_units)) {
-        const Work w = work_of(p, u);
+      UnitWalk uw;
+      for (uw.start(p, n_units); !uw.done() && ok; uw.advance(p)) {
+        const Work w = uw.work(p);
         for (int t = 0; t < w.n_t; ++t, ++g) {
           const int st = g % kVStages;
           if (!mbar_wait(bar(kBarVEmpty + st), ((g / kVStages) & 1) ^ 1u, abort_flag, p.err, 42)) { ok = false; break; }
@@ -385,10 +405,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       // ---------------- MMA issuer: S_0, S_1, then S_{g+2} before O_g for every g:
       // S runs two tiles ahead of the softmax warps (two S buffers in TMEM)
       constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
-      int us = next_unit(p, blockIdx.x, n_units), is = 0, ts = 0, gs = 0;  // S cursor
-      int uo = us, io = 0, to = 0, go = 0;                                 // O cursor
+      UnitWalk cs, co;                          // S and O cursors
+      cs.start(p, n_units);
+      co.start(p, n_units);
+      int is = 0, ts = 0, gs = 0, io = 0, to = 0, go = 0;
       Work ws{}, wo{};
-      if (us < n_units) ws = wo = work_of(p, us);
+      if (!cs.done()) ws = wo = cs.work(p);
       bool ok = true, issued = false;
       auto issue_s = [&]() -> bool {
         const int st = gs % kKStages;
@@ -408,10 +430,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++gs;
         if (++ts == ws.n_t) {
           mma_commit(bar(kBarQEmpty + (is & 1)));
-          us = next_unit(p, us + step, n_units);
+          cs.advance(p);
           ++is;
           ts = 0;
-          if (us < n_units) ws = work_of(p, us);
+          if (!cs.done()) ws = cs.work(p);
         }
         return true;
       };
@@ -430,17 +452,17 @@ __global__ void __launch_bounds__(kThreads, 2)
         mma_commit(bar(kBarVEmpty + st));
         ++go;
         if (++to == wo.n_t) {
-          uo = next_unit(p, uo + step, n_units);
+          co.advance(p);
           ++io;
           to = 0;
-          if (uo < n_units) wo = work_of(p, uo);
+          if (!co.done()) wo = co.work(p);
         }
         return true;
       };
-      if (us < n_units) ok = issue_s();
-      if (ok && us < n_units) ok = issue_s();
-      while (ok && uo < n_units) {
-        if (us < n_units) ok = issue_s();
+      if (!cs.done()) ok = issue_s();
+      if (ok && !cs.done()) ok = issue_s();
+      while (ok && !co.done()) {
+        if (!cs.done()) ok = issue_s();
         if (ok) ok = issue_o();
       }
       if (!ok && issued) {
@@ -463,8 +485,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     };
     int g = 0, i = 0;
     bool ok = true;
-    for (int u = next_unit(p, blockIdx.x, n_units); u < n_units && ok; u = next_unit(p, u + gridDim.x, n_units), ++i) {
-      const Work w = work_of(p, u);
+    UnitWalk uw;
+    for (uw.start(p, n_units); !uw.done() && ok; uw.advance(p), ++i) {
+      const Work w = uw.work(p);
       const uint32_t ocol = kColO;
       float m = -INFINITY, l = 0.f;              // m: the maximum P is taken against
       // a warp whose 32 query rows all lie past the sequence end (the ragged last
@@ -648,22 +671,32 @@ as_status make_map_bf16(CUtensorMap* tm, const void* ptr, uint64_t rows, uint64_
 }
 }  // namespace
 
-void attention_items(const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items) {
-  for (int32_t s = 0; s < n_seq; ++s)
-    for (int32_t qt = 0; qt * atc::kQ < seq_len[s]; ++qt) items.push_back((s << 6) | qt);
+void attention_items(const int32_t* seq_start, const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items) {
+  // longest sequences first: CTAs take units round-robin, and a descending
+  // cost order evens out their totals (the q-tiles of one sequence stay
+  // adjacent, so its K and V rows are read by CTAs working at the same time)
+  std::vector<int32_t> order(n_seq > 0 ? n_seq : 0);
+  for (int32_t s = 0; s < n_seq; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return seq_len[a] > seq_len[b]; });
+  for (int32_t s : order)
+    for (int32_t q0 = 0; q0 < seq_len[s]; q0 += atc::kQ) {
+      items.push_back(seq_start[s]);
+      items.push_back(seq_len[s] | (q0 << 16));
+    }
 }
 
 namespace {
-as_status attention_tc_launch(bool out8, const __nv_bfloat16* qkv, void* out, float out_scale, const int32_t* seq_start,
-                              const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
+as_status attention_tc_launch(bool out8, const __nv_bfloat16* qkv, void* out, float out_scale, const int32_t* items,
+                              int32_t n_items, int32_t max_len,
                               int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
   if (n_items == 0 || max_len == 0 || rows == 0) return AS_OK;
   if (d_model != n_heads * 64 || d_model % 64 || max_len > 4096 || rows > (1ll << 31) - 8 ||
-      (reinterpret_cast<uintptr_t>(qkv) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) {
-    set_k_error("attention_tcgen05: head dim 64, sequences <= 4096 tokens, 16-byte aligned buffers");
+      (reinterpret_cast<uintptr_t>(qkv) & 15) || (reinterpret_cast<uintptr_t>(out) & 15) ||
+      (reinterpret_cast<uintptr_t>(items) & 7)) {
+    set_k_error("attention_tcgen05: head dim 64, sequences <= 4096 tokens, 16-byte aligned buffers, 8-byte aligned items");
     return AS_ERR_ARG;
   }
-  if ((int64_t)n_items * n_heads > 0x7FFFFFFFll) {
+  if ((int64_t)n_items * n_heads > 0x7FFFFFFFll - 65536) {
     set_k_error("attention_tcgen05: too many work items in one batch");
     return AS_ERR_ARG;
   }
@@ -694,9 +727,7 @@ as_status attention_tc_launch(bool out8, const __nv_bfloat16* qkv, void* out, fl
   if (s == AS_OK) s = make_map_bf16(&tmKV, qkv, (uint64_t)rows, 3ull * d_model, 3ull * d_model, 64, atc::kKT);
   if (s != AS_OK) return s;
   atc::Params p;
-  p.seq_start = seq_start;
-  p.seq_len = seq_len;
-  p.items = items;
+  p.items = reinterpret_cast<const int2*>(items);
   p.n_items = n_items;
   p.out = out;
   p.out_inv_scale = out8 ? 1.0f / out_scale : 1.0f;
@@ -716,22 +747,20 @@ as_status attention_tc_launch(bool out8, const __nv_bfloat16* qkv, void* out, fl
 
 }  // namespace
 
-as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
-                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
-                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
-  return attention_tc_launch(false, qkv, out, 1.0f, seq_start, seq_len, items, n_items, max_len, rows, d_model,
-                             n_heads, err, st);
+as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* items, int32_t n_items,
+                            int32_t max_len, int64_t rows, int32_t d_model, int32_t n_heads, DevError* err,
+                            cudaStream_t st) {
+  return attention_tc_launch(false, qkv, out, 1.0f, items, n_items, max_len, rows, d_model, n_heads, err, st);
 }
 
-as_status attention_tcgen05_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* seq_start,
-                                 const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
-                                 int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st) {
+as_status attention_tcgen05_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* items,
+                                 int32_t n_items, int32_t max_len, int64_t rows, int32_t d_model, int32_t n_heads,
+                                 DevError* err, cudaStream_t st) {
   if (!(out_scale > 0.f)) {
     set_k_error("attention_tcgen05_e4m3: out_scale must be positive");
     return AS_ERR_ARG;
   }
-  return attention_tc_launch(true, qkv, out, out_scale, seq_start, seq_len, items, n_items, max_len, rows, d_model,
-                             n_heads, err, st);
+  return attention_tc_launch(true, qkv, out, out_scale, items, n_items, max_len, rows, d_model, n_heads, err, st);
 }
 
 }  // namespace as

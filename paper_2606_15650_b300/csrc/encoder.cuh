@@ -48,16 +48,18 @@ as_status attention_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int
                          cudaStream_t st);
 
 // Self-attention on tcgen05 (see attn_tc.cu), persistent over work items:
-// attention_items appends one item per 128-query tile of each sequence
-// ((s << 6) | tile); rows of each sequence inside [0, rows).
-void attention_items(const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items);
-as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* seq_start,
-                            const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
-                            int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st);
+// attention_items appends one item per 128-query tile of each sequence, two
+// int32 each (the sequence's first row; L | (q0 << 16)), longest sequences
+// first; rows of each sequence inside [0, rows). An item with L = 0 is
+// padding. n_items counts items (pairs); the array is 8-byte aligned.
+void attention_items(const int32_t* seq_start, const int32_t* seq_len, int32_t n_seq, std::vector<int32_t>& items);
+as_status attention_tcgen05(const __nv_bfloat16* qkv, __nv_bfloat16* out, const int32_t* items, int32_t n_items,
+                            int32_t max_len, int64_t rows, int32_t d_model, int32_t n_heads, DevError* err,
+                            cudaStream_t st);
 // The same writing E4M3 (value / out_scale, saturating), for FP8 contexts.
-as_status attention_tcgen05_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* seq_start,
-                                 const int32_t* seq_len, const int32_t* items, int32_t n_items, int32_t max_len,
-                                 int64_t rows, int32_t d_model, int32_t n_heads, DevError* err, cudaStream_t st);
+as_status attention_tcgen05_e4m3(const __nv_bfloat16* qkv, uint8_t* out, float out_scale, const int32_t* items,
+                                 int32_t n_items, int32_t max_len, int64_t rows, int32_t d_model, int32_t n_heads,
+                                 DevError* err, cudaStream_t st);
 
 // Row LayerNorm; writes FP32 and (optionally) BF16 copies.
 as_status layernorm_rows(const float* in, const float* g, const float* b, float* out_f32, __nv_bfloat16* out_bf16,

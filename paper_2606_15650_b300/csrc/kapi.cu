@@ -99,15 +99,15 @@ as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start
     mx = lens[i] > mx ? lens[i] : mx;
   }
   std::vector<int32_t> items;
-  attention_items(lens.data(), n_seq, items);
+  attention_items(starts.data(), lens.data(), n_seq, items);
   if (items.empty()) return AS_OK;
   int32_t* d_items = nullptr;
   AS_CUDA_OK(cudaMallocAsync(reinterpret_cast<void**>(&d_items), items.size() * 4, st));
   cudaError_t e = cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st);
   as_status s = e == cudaSuccess ? AS_OK : AS_ERR_CUDA;
   if (s == AS_OK)
-    s = attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(out), seq_start, seq_len,
-                          d_items, (int32_t)items.size(), mx, rows, d_model, n_heads, nullptr, st);
+    s = attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(out), d_items,
+                          (int32_t)(items.size() / 2), mx, rows, d_model, n_heads, nullptr, st);
   cudaFreeAsync(d_items, st);
   if (e != cudaSuccess) set_k_error(std::string("as_k_attention_tc: ") + cudaGetErrorString(e));
   return s;

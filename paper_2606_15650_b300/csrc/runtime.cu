@@ -565,8 +565,8 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
                             sc[0] * L.s_qkv, 1.0f, err, st, c->gemm_cfg[0])); }
       { ProfScope ps(ln, 1, attn_flops);
         if (g.attention == AS_ATTN_TCGEN05)
-          CKS(attention_tcgen05_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(),
-                                     attn_items, n_items, (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
+          CKS(attention_tcgen05_e4m3(QKV, ATT8, sc[1], attn_items, n_items, (int32_t)max_len, R, d,
+                                     (int32_t)g.n_heads, err, st));
         else
           CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
                                   (int32_t)max_len, d, (int32_t)g.n_heads, st)); }
@@ -599,8 +599,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS, false, false, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, 1.0f, 1.0f, err, st, c->gemm_cfg[0])); }
       if (g.attention == AS_ATTN_TCGEN05) {
         ProfScope ps(ln, 1, attn_flops);
-        CKS(attention_tcgen05(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), attn_items, n_items,
-                              (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
+        CKS(attention_tcgen05(QKV, ATT, attn_items, n_items, (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
       } else {
         ProfScope ps(ln, 1, attn_flops);
         CKS(attention_bf16(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)max_len, d,
@@ -1043,20 +1042,25 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     c->calibrating = true;
     CK(cudaMemsetAsync(c->amax_dev.p, 0, (size_t)kActPerLayer * g.n_layers * 4, st));
   }
-  // tcgen05 attention work items (one per 128-query tile), all chunks in one upload
+  // tcgen05 attention work items (one per 128-query tile, two int32 each),
+  // all chunks in one upload
   std::vector<int32_t> items;
   std::vector<size_t> item_off{0};
   const bool tc_attn = g.attention == AS_ATTN_TCGEN05 && g.precision != AS_FP32;
   if (tc_attn) {
-    std::vector<int32_t> lens;
+    std::vector<int32_t> lens, starts;
     for (const Chunk& ch : chunks) {
       lens.clear();
-      for (uint64_t i = ch.s0; i < ch.s1; ++i) lens.push_back((int32_t)seqs[i].len);
-      attention_items(lens.data(), (int32_t)lens.size(), items);
+      starts.clear();
+      for (uint64_t i = ch.s0; i < ch.s1; ++i) {
+        lens.push_back((int32_t)seqs[i].len);
+        starts.push_back((int32_t)seqs[i].row);
+      }
+      attention_items(starts.data(), lens.data(), (int32_t)lens.size(), items);
       if (graphable(g, ch.rows)) {
-        // pad to a power of two with items of the empty sequence (index ns)
-        const size_t n = items.size() - item_off.back();
-        items.resize(item_off.back() + pow2_at_least(n, 16), (int32_t)((ch.s1 - ch.s0) << 6));
+        // pad to a power of two with padding items (L = 0)
+        const size_t n = (items.size() - item_off.back()) / 2;
+        items.resize(item_off.back() + 2 * pow2_at_least(n, 16), 0);
       }
       item_off.push_back(items.size());
     }
@@ -1070,7 +1074,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
     as_status es = run_encoder_chunk(c, ln, ch, ln->seqs.as<SeqDesc>(), af, want_logits,
                                      tc_attn ? ln->attn_items.as<int32_t>() + item_off[ci] : nullptr,
-                                     tc_attn ? (int32_t)(item_off[ci + 1] - item_off[ci]) : 0);
+                                     tc_attn ? (int32_t)((item_off[ci + 1] - item_off[ci]) / 2) : 0);
     if (es != AS_OK) {
       c->calibrating = false;
       return es;
