@@ -210,7 +210,7 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared memory (offsets from a 1024-aligned base): 96 KB, two CTAs per SM.
+// Shared memory (offsets from a 1024-aligned base): 104 KB, two CTAs per SM.
 constexpr int kQBytes = kQ * 64 * 2;                 // 16 KB per buffer: Q tile, one 128-byte-swizzle panel
 constexpr int kKBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
 constexpr int kVBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
@@ -221,7 +221,12 @@ constexpr int kVStages = 4;
 constexpr int kOffQ = 0;                             // 2 buffers (consecutive work units)
 constexpr int kOffK = kOffQ + 2 * kQBytes;
 constexpr int kOffV = kOffK + kKStages * kKBytes;
-constexpr int kOffBar = kOffV + kVStages * kVBytes;
+// Epilogue staging, 2 KB per softmax warp: a warp's output rows pass through
+// it so that each global store writes whole rows (a lane per 16-byte piece)
+// instead of one 16-byte piece of 32 different rows
+constexpr int kStgBytes = 2048;
+constexpr int kOffStg = kOffV + kVStages * kVBytes;
+constexpr int kOffBar = kOffStg + 4 * kStgBytes;
 // mbarriers (8 bytes each)
 enum {
   kBarQFull = 0,     // [2] Q of a unit landed
@@ -476,7 +481,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   } else {
     // ---------------- softmax + epilogue: warp w owns TMEM lanes (query rows) 32*(w%4)..
     const int sub = warp & 3;
-    const int r = sub * 32 + lane;               // query row in the tile
     const uint32_t trow = tmem + ((uint32_t)(sub * 32) << 16);
     const float c = 0.125f * 1.4426950408889634f;  // 1/sqrt(64) * log2(e)
     // O += P_k V_k completes phase k/2 of o_done[k&1]
@@ -600,39 +604,65 @@ __global__ void __launch_bounds__(kThreads, 2)
       fence_after();
       uint32_t v[64];
       tmem_ld64(trow + ocol, v);
-      if (w.q0 + r < w.L) {
-        const size_t off = (size_t)(w.row0 + w.q0 + r) * d + w.h * 64;
-        if (OUT8) {
-          const float inv = p.out_inv_scale / l;
-          uint8_t* o = static_cast<uint8_t*>(p.out) + off;
+      // rows of this warp inside the sequence (at least one: the warp is live)
+      const int rows_here = min(32, w.L - (w.q0 + sub * 32));
+      uint8_t* stg = smem + kOffStg + sub * kStgBytes;
+      const size_t row_base = (size_t)(w.row0 + w.q0 + sub * 32);
+      if (OUT8) {
+        // 64-byte rows: 32 rows x 4 pieces of 16 bytes, one pass; piece c of row
+        // r sits at slot c ^ ((r >> 1) & 3) (conflict-free both ways)
+        const float inv = p.out_inv_scale / l;
 #pragma unroll
-          for (int q = 0; q < 64; q += 16) {
-            uint4 x;
-            uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
+        for (int q = 0; q < 64; q += 16) {
+          uint4 x;
+          uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              xw[k] = (uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k]) * inv, __uint_as_float(v[q + 4 * k + 1]) * inv) |
-                      ((uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k + 2]) * inv,
-                                        __uint_as_float(v[q + 4 * k + 3]) * inv)
-                       << 16);
-            *reinterpret_cast<uint4*>(o + q) = x;
+          for (int k = 0; k < 4; ++k)
+            xw[k] = (uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k]) * inv, __uint_as_float(v[q + 4 * k + 1]) * inv) |
+                    ((uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k + 2]) * inv, __uint_as_float(v[q + 4 * k + 3]) * inv)
+                     << 16);
+          *reinterpret_cast<uint4*>(stg + lane * 64 + (((q >> 4) ^ ((lane >> 1) & 3)) << 4)) = x;
+        }
+        __syncwarp();
+        uint8_t* o = static_cast<uint8_t*>(p.out) + w.h * 64;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int rr = (lane >> 2) + 8 * j, c = lane & 3;
+          const uint4 x = *reinterpret_cast<const uint4*>(stg + rr * 64 + ((c ^ ((rr >> 1) & 3)) << 4));
+          if (rr < rows_here) *reinterpret_cast<uint4*>(o + (row_base + rr) * d + c * 16) = x;
+        }
+        __syncwarp();
+      } else {
+        // 128-byte rows: two passes of 16 rows x 8 pieces; piece c of row r sits
+        // at slot c ^ (r & 7)
+        const float inv = 1.f / l;
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(p.out) + w.h * 64;
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          if ((lane >> 4) == pass) {
+#pragma unroll
+            for (int q = 0; q < 64; q += 8) {
+              uint4 x;
+              __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
+              __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
+              __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
+              __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
+              x.x = *reinterpret_cast<uint32_t*>(&a0);
+              x.y = *reinterpret_cast<uint32_t*>(&a1);
+              x.z = *reinterpret_cast<uint32_t*>(&a2);
+              x.w = *reinterpret_cast<uint32_t*>(&a3);
+              *reinterpret_cast<uint4*>(stg + (lane & 15) * 128 + (((q >> 3) ^ (lane & 7)) << 4)) = x;
+            }
           }
-        } else {
-          const float inv = 1.f / l;
-          __nv_bfloat16* o = static_cast<__nv_bfloat16*>(p.out) + off;
+          __syncwarp();
 #pragma unroll
-          for (int q = 0; q < 64; q += 8) {
-            uint4 x;
-            __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
-            __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
-            __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
-            x.x = *reinterpret_cast<uint32_t*>(&a0);
-            x.y = *reinterpret_cast<uint32_t*>(&a1);
-            x.z = *reinterpret_cast<uint32_t*>(&a2);
-            x.w = *reinterpret_cast<uint32_t*>(&a3);
-            *reinterpret_cast<uint4*>(o + q) = x;
+          for (int j = 0; j < 4; ++j) {
+            const int rr = (lane >> 3) + 4 * j, c = lane & 7;
+            const uint4 x = *reinterpret_cast<const uint4*>(stg + rr * 128 + ((c ^ (rr & 7)) << 4));
+            const int row = pass * 16 + rr;
+            if (row < rows_here) *reinterpret_cast<uint4*>(o + (row_base + row) * d + c * 8) = x;
           }
+          __syncwarp();
         }
       }
     }
