@@ -5,7 +5,8 @@
 // tile of one sequence, one head); keys in tiles of 64, numbered globally
 // across a CTA's units (g), which fixes every buffer index and barrier phase.
 //   S_g = Q K_g^T           tcgen05.mma M=128 N=64 K=64 into one of two S
-//                           buffers in TMEM, issued two tiles ahead
+//                           buffers in TMEM, issued right after O_{g-2}
+//                           (so, a whole softmax ahead of its use)
 //   P_g = exp2(S_g*c - m)   four softmax warps, one query row per thread: the
 //                           64-key row of S is read in one pass and released,
 //                           P rounded to BF16 and stored back into one of two
@@ -22,6 +23,12 @@
 // stages) have rings of their own; Q is double-buffered across units.
 // Warps: Q/K loader, V loader, MMA issuer (one thread each, blocking on their
 // own barriers), four softmax warps. 96 KB shared memory, 256 TMEM columns.
+// One thread issues every MMA, in the order S_0, S_1, O_0, S_2, O_1, S_3, ...,
+// and tcgen05 MMAs of one thread complete in issue order: once S_g is complete
+// (the softmax warps wait for it anyway) so is O_{g-2}, which frees P buffer
+// g&1 for P_g without a wait of its own. And S_{g+2} is issued only after P_g
+// is full, which the softmax warps signal after reading S_g, so the S buffer
+// needs no release barrier either.
 // Keys past the sequence end are masked to -inf; query rows past it are not
 // stored. Every mbarrier wait is bounded (see gemm_tc.cu); on a timeout each
 // issuing thread waits (bounded) for its copies and MMAs in flight before the
@@ -236,11 +243,10 @@ enum {
   kBarVFull = 12,    // [kVStages]
   kBarVEmpty = 16,   // [kVStages]
   kBarSFull = 20,    // [2] S_g in TMEM (by S buffer)
-  kBarSEmpty = 22,   // [2] softmax holds S_g in registers (128 arrivals)
-  kBarPFull = 24,    // [2] P_g in TMEM (128 arrivals)
-  kBarODone = 26,    // [2] O += P_g V_g done (by P buffer)
-  kBarDrain = 28,
-  kNumBars = 29
+  kBarPFull = 22,    // [2] P_g in TMEM, S_g read (128 arrivals)
+  kBarODone = 24,    // [2] O += P_g V_g done (by P buffer)
+  kBarDrain = 26,
+  kNumBars = 27
 };
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
 constexpr int kSmemAlloc = kSmemBytes + 1024;        // room to align the base to 1024 bytes
@@ -326,7 +332,6 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_init(bar(kBarPFull + i), 128);
       mbar_init(bar(kBarODone + i), 1);
       mbar_init(bar(kBarSFull + i), 1);
-      mbar_init(bar(kBarSEmpty + i), 128);
     }
     for (int i = 0; i < kKStages; ++i) {
       mbar_init(bar(kBarKFull + i), 1);
@@ -407,8 +412,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   } else if (warp == 2) {
     if (lane == 0) {
-      // ---------------- MMA issuer: S_0, S_1, then S_{g+2} before O_g for every g:
-      // S runs two tiles ahead of the softmax warps (two S buffers in TMEM)
+      // ---------------- MMA issuer: S_0, S_1, then O_g followed by S_{g+2} for every
+      // g: S_{g+1} is computed while the softmax warps work on S_g
       constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
       UnitWalk cs, co;                          // S and O cursors
       cs.start(p, n_units);
@@ -421,8 +426,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int st = gs % kKStages;
         if (ts == 0 && !mbar_wait(bar(kBarQFull + (is & 1)), (is >> 1) & 1, abort_flag, p.err, 50)) return false;
         if (!mbar_wait(bar(kBarKFull + st), (gs / kKStages) & 1, abort_flag, p.err, 51)) return false;
-        const int sbuf = gs & 1;
-        if (gs >= 2 && !mbar_wait(bar(kBarSEmpty + sbuf), ((gs >> 1) - 1) & 1, abort_flag, p.err, 52)) return false;
+        const int sbuf = gs & 1;  // free: S_{gs-2} was read before P_{gs-2} (issue_o waited for it)
         fence_after();
         const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
         const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
@@ -467,8 +471,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (!cs.done()) ok = issue_s();
       if (ok && !cs.done()) ok = issue_s();
       while (ok && !co.done()) {
-        if (!cs.done()) ok = issue_s();
-        if (ok) ok = issue_o();
+        ok = issue_o();
+        if (ok && !cs.done()) ok = issue_s();
       }
       if (!ok && issued) {
         // wait (bounded) for the MMAs in flight before the TMEM is freed
@@ -518,22 +522,16 @@ __global__ void __launch_bounds__(kThreads, 2)
           return true;
         };
         if (!live) {
-          fence_before();
-          mbar_arrive(bar(kBarSEmpty + (g & 1)));
           if (!zero_v_tail()) { ok = false; break; }
-          // as in the live path, arrive for P_g only once O_{g-2} is done: that
-          // orders this warp's P-full arrivals after the phase of tile g-2 has
-          // completed (without it a warp that computes nothing could run two
-          // tiles ahead and arrive in the phase of an unfinished tile)
-          if (g >= 2 && !wait_o(g - 2, 65)) { ok = false; break; }
+          // S_g being complete, so are O_{g-2} and the P-full phase of tile g-2:
+          // this arrival lands in tile g's phase even from a warp that computes
+          // nothing and could otherwise run ahead
           fence_before();
           mbar_arrive(bar(kBarPFull + (g & 1)));
           continue;
         }
         uint32_t v[64];
         tmem_ld64(trow + 64u * (uint32_t)(g & 1), v);
-        fence_before();
-        mbar_arrive(bar(kBarSEmpty + (g & 1)));  // S_g is in registers: S_{g+2} may overwrite it
         // row maximum of the raw scores (keys past the end masked to -inf); the
         // scale c > 0 is applied in the exp2 argument: t = s * c - m
         if (valid < kKT) {
@@ -589,9 +587,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         f2unpack(add2(s2[2], s2[3]), sl[2], sl[3]);
         l += (sl[0] + sl[1]) + (sl[2] + sl[3]);
         if (!zero_v_tail()) { ok = false; break; }
-        // P_g goes to TMEM buffer g&1 once O += P_{g-2} V_{g-2} has read it
-        if (g >= 2 && !wait_o(g - 2, 62)) { ok = false; break; }
-        fence_after();
+        // P_g goes to TMEM buffer g&1: O += P_{g-2} V_{g-2} has read it, since
+        // it completed before S_g (issue order), which these warps waited for
         tmem_st32(trow + kColP + 32u * (uint32_t)(g & 1), *reinterpret_cast<uint32_t(*)[32]>(&v[0]));
         fence_before();
         mbar_arrive(bar(kBarPFull + (g & 1)));
