@@ -357,6 +357,13 @@ __device__ __forceinline__ void st_cluster_v2(uint32_t addr, float a, float b) {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote_bar) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
 }
+// A release made of one cluster-scope fence and relaxed arrivals: after
+// several remote stores, one fence orders them all before each of the
+// following arrivals (instead of one release, and its wait, per arrival).
+__device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t remote_bar) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -739,11 +746,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int prow = sub * 32 + lane;
         const uint32_t xaddr =
             sbase + L::kXOff + ((pb * (2 * kMaxLnCluster) + lrank * 2 + half) * kBM + prow) * 8;
-        for (uint32_t q = 0; q < csize; ++q) {
-          const uint32_t qr = MC ? 2 * q + crank : q;   // cluster rank of group member q
-          st_cluster_v2(mapa(xaddr, qr), mean_h, m2);
-          mbar_arrive_cluster(mapa(xbar(pb), qr));
-        }
+        for (uint32_t q = 0; q < csize; ++q)   // cluster rank of group member q: 2q + crank with pairs
+          st_cluster_v2(mapa(xaddr, MC ? 2 * q + crank : q), mean_h, m2);
+        fence_acq_rel_cluster();
+        for (uint32_t q = 0; q < csize; ++q) mbar_arrive_cluster_relaxed(mapa(xbar(pb), MC ? 2 * q + crank : q));
         if (!warp_wait_cluster(xbar(pb), (lt >> 1) & 1u, abort_flag, p.err, 33)) break;
         // combine the 2C partials of equal size (Chan et al.)
         const int nparts = 2 * (int)csize;
