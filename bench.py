@@ -229,7 +229,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "sample_records_per_step": per_step},
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.records.n_records} records, lognormal({w.records.median:g}, "
+                                   f"{w.records.sigma:g}) clipped {w.records.lo}..{w.records.hi}",
+                       "model": f"encoder {w.dims.n_layers}L d{w.dims.d_model} h{w.dims.n_heads} "
+                                f"ffn{w.dims.d_ffn}, {w.dims.n_labels} BIO labels",
+                       "precision": "f64 oracle, whole path", "sample_records_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": "tokens/s", "cores": int(cores), "kind": "oracle",
                              "sample": f"{per_step} records of {w.name} per step, FP64 oracle, whole path"},
             "e2e": {"value": value, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
