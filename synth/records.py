@@ -14,8 +14,10 @@ Record length is set in tokens. The generator cannot tokenize (it holds none
 of the method's arithmetic), so it sizes text with a conservative count: an
 isolated vocabulary word counts as one token, every other alphanumeric run
 counts one token per byte, every other byte counts one. The true count is at
-most this estimate, so records never exceed the length cap; runs that merge
-into fewer tokens make a record a few tokens shorter than its target.
+most this estimate, and a record whose pieces add up to more than its target
+loses trailing pieces until they fit, so records never exceed the length cap;
+runs that merge into fewer tokens make a record a few tokens shorter than its
+target.
 """
 from __future__ import annotations
 
@@ -387,12 +389,14 @@ def make_records(shape: RecordShape, vocab_words: list[bytes], seed: int = 1001)
     for ri in range(shape.n_records):
         target = int(targets[ri])
         parts: list[bytes] = []
+        part_tok: list[int] = []
         nbytes = 0
         used = 0
 
         def put(piece: bytes, n_tok: int):
             nonlocal nbytes, used
             parts.append(piece)
+            part_tok.append(n_tok)
             nbytes += len(piece)
             used += n_tok
 
@@ -467,6 +471,15 @@ def make_records(shape: RecordShape, vocab_words: list[bytes], seed: int = 1001)
             else:
                 put(b".", 1)
             sentence_left -= 1
+        # a sentence opener, field label or look-alike can take more than the
+        # room left: drop trailing pieces (and the entities planted in them)
+        # until the estimate is within the target, after every random draw of
+        # the record, so that records which fit are unchanged
+        while used > target and parts:
+            nbytes -= len(parts.pop())
+            used -= part_tok.pop()
+            while planted and planted[-1][0] == ri and planted[-1][1] + planted[-1][2] > nbytes:
+                planted.pop()
         rec = b"".join(parts)
         chunks.append(rec)
         pos += len(rec)
