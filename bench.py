@@ -393,7 +393,9 @@ def run_ours(args):
                      "flops_per_launch": gemm_flops_launch,
                      "share_of_step": prof["gemm_ms"] / max(total_ms, 1e-9) if world == 1 else None},
         "attention": {"launches": int(prof["attn_launches"]), "ms": prof["attn_ms"],
-                      "tflops": prof["attn_flops"] / max(prof["attn_ms"], 1e-9) / 1e9},
+                      "tflops": prof["attn_flops"] / max(prof["attn_ms"], 1e-9) / 1e9,
+                      "frac_of_bf16_sustained": prof["attn_flops"] / max(prof["attn_ms"], 1e-9) / 1e9 / peak},
+        "integer_stages": integer_stages(prof, stats, float(peaks.get("hbm_gbs", 6400.0)), src, total_ms),
         "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": int(len(recs.data) + recs.offsets.nbytes),
                 "d2h_bytes_per_step": int(out_bytes + recs.offsets.nbytes)},
         "gpu_launches": int(launches),
@@ -408,6 +410,43 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def integer_stages(prof: dict, st: dict, hbm_gbs: float, src: str, total_ms: float) -> dict:
+    """Device time of the integer stages of one step (CUDA events around each
+    stage's launches, recorded by the library) against their algorithmic bytes.
+
+    Algorithmic bytes per call (the least a single pass must move):
+      text          read the text once (N), write 12 B per token (id, offset,
+                    length), 8 B per record (first token), 9 B per recognizer
+                    span (start, length, type);
+      spans         read 1 B label per token, 16 B per NER span (offset and
+                    length of its two boundary tokens), 9 B per recognizer
+                    span; write 9 B per final span;
+      substitution  read the text (N) and 49 B per final span (start, length,
+                    type, output shift, 32-byte digest), 8 B per record
+                    offset; write the output (N') and its offsets.
+    HMAC + map is bound by SHA-256 compressions (ALU), reported as spans/s.
+    """
+    calls = max(1, int(prof.get("stage_calls", 0)))
+    ms = {k: v / calls for k, v in prof.get("stage_ms", {}).items()}
+    N, T, n = st["n_bytes"], st["n_tokens"], st["n_records"]
+    nrx, nner, nfin, nout = st["n_regex_spans"], st["n_ner_spans"], st["n_final_spans"], st["n_out_bytes"]
+    alg = {"text": N + 12 * T + 8 * (n + 1) + 9 * nrx,
+           "spans": T + 16 * nner + 9 * nrx + 9 * nfin,
+           "substitution": N + nout + 49 * nfin + 16 * (n + 1)}
+    out = {"timing": "CUDA events around each stage inside the timed steps (L2 flushed before each step); "
+                     "per call", "hbm_peak_gbs": hbm_gbs, "peak_source": f"hbm_gbs of {src}", "calls": calls}
+    for k, b in alg.items():
+        t = ms.get(k, 0.0)
+        gbs = b / (t / 1e3) / 1e9 if t > 0 else None
+        out[k] = {"bound": "hbm", "ms": t, "alg_bytes": int(b), "gb_s": gbs,
+                  "frac": gbs / hbm_gbs if gbs else None, "share_of_step": t * calls / max(total_ms, 1e-9)}
+    t = ms.get("hash_map", 0.0)
+    out["hash_map"] = {"bound": "alu", "ms": t, "spans": int(nfin),
+                       "spans_per_s": nfin / (t / 1e3) if t > 0 else None,
+                       "share_of_step": t * calls / max(total_ms, 1e-9)}
+    return out
 
 
 def reidentify_leg(ctx, d_data, d_offs, schema, key, recs, stream) -> dict:
@@ -778,8 +817,16 @@ def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32) -> dic
         ms.append(e0.elapsed_time(e1))
     prof = ctx.profile_read()
     ctx.close()
+    peaks, src = measured_peaks()
+    # dense E4M3 tensor peak: the measured sustained BF16 peak x the nominal
+    # FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s)
+    fp8_peak = 2.0 * float(peaks.get("bf16_tflops_sustained", 1400.0))
+    gemm_tflops = prof["gemm_flops"] / max(prof["gemm_ms"], 1e-9) / 1e9
     return {"value": st["n_encoded_tokens"] / (np.mean(ms) / 1e3), "unit": "tokens/s", "steps": len(ms),
-            "gemm_tflops": prof["gemm_flops"] / max(prof["gemm_ms"], 1e-9) / 1e9,
+            "gemm_tflops": gemm_tflops,
+            "gemm_roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": fp8_peak, "unit": "TFLOP/s",
+                              "frac": gemm_tflops / fp8_peak,
+                              "peak_source": f"2 x bf16_tflops_sustained of {src} (nominal FP8/BF16 ratio)"},
             "label_agreement_vs_fp32": agree, "max_abs_logit_diff_vs_fp32": max_d,
             "sample": f"agreement on the first {sample.n} records; timing on the whole workload; "
                       f"scales from 64 calibration records (seed {synth.SEED_CALIB})"}

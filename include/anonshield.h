@@ -457,12 +457,21 @@ as_status as_get_stream(as_ctx* ctx, void** stream);
  * encoder GEMM and attention launch of later calls and accumulates their
  * device time and algorithmic FLOPs (GEMM 2*M*N*K; attention 4*L^2*d per
  * sequence of L tokens); enable = 0 stops and clears. Timing adds a few
- * microseconds per launch. */
+ * microseconds per launch. The integer stages of the ctx's own batch calls
+ * (as_anonymize, as_anonymize_fields, as_anonymize_jsonl) are timed the same
+ * way, one event pair around each stage's launches (host syncs and output
+ * allocation excluded): stage_ms[0] tokenizer + recognizers (§2 stage (2)
+ * patterns), [1] BIO decode, overlap rule, preserve list and span merge,
+ * [2] HMAC-SHA256 + entity-map upsert (§2 stages (3), (4)), [3] substitution
+ * (replacement lengths, output shifts, pass-through copy, pseudonym writes,
+ * output offsets; §2 stage (5)); stage_calls counts the timed calls. */
 typedef struct {
   uint64_t gemm_launches;
   double gemm_ms, gemm_flops;
   uint64_t attn_launches;
   double attn_ms, attn_flops;
+  uint64_t stage_calls;
+  double stage_ms[4];
 } as_profile_stats;
 as_status as_profile(as_ctx* ctx, uint32_t enable);
 as_status as_profile_read(as_ctx* ctx, as_profile_stats* stats);

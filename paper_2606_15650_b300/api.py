@@ -130,7 +130,11 @@ TUNE_ROLES = ("qkv", "attn_out", "ffn1", "ffn2")
 
 class _Profile(C.Structure):
     _fields_ = [("gemm_launches", C.c_uint64), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
-                ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double)]
+                ("attn_launches", C.c_uint64), ("attn_ms", C.c_double), ("attn_flops", C.c_double),
+                ("stage_calls", C.c_uint64), ("stage_ms", C.c_double * 4)]
+
+# order of _Profile.stage_ms (as_profile_stats.stage_ms)
+PROFILE_STAGES = ("text", "spans", "hash_map", "substitution")
 
 
 EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_output_stats", "as_output_map",
@@ -702,7 +706,9 @@ class Context:
     def profile_read(self) -> dict:
         s = _Profile()
         self._check(load().as_profile_read(self._h, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in _Profile._fields_}
+        d = {k: getattr(s, k) for k, _ in _Profile._fields_ if k != "stage_ms"}
+        d["stage_ms"] = dict(zip(PROFILE_STAGES, list(s.stage_ms)))
+        return d
 
     def map_clear(self):
         self._check(load().as_map_clear(self._h))

@@ -455,7 +455,11 @@ as_status load_weights(as_ctx* c) {
 
 // ---------------------------------------------------------------- encoder
 
-// Event pair around one launch when profiling is on (kind 0 GEMM, 1 attention).
+// Event pair around one launch when profiling is on (kind 0 GEMM, 1 attention),
+// or around one integer stage of a batch call (kinds 2..5, the order of
+// as_profile_stats.stage_ms). Scopes never nest: event i of the pool belongs
+// to pending entry i / 2.
+constexpr int kProfGemm = 0, kProfAttn = 1, kProfText = 2, kProfSpans = 3, kProfHash = 4, kProfSubst = 5;
 struct ProfScope {
   Lane* ln;
   bool on;
@@ -471,11 +475,14 @@ struct ProfScope {
     cudaEventRecord(ln->ev_pool[ln->ev_used], ln->stream);
     ln->ev_pending.push_back({kind, flops});
   }
-  ~ProfScope() {
+  // records the closing event (once; the destructor closes a scope still open)
+  void end() {
     if (!on) return;
+    on = false;
     cudaEventRecord(ln->ev_pool[ln->ev_used + 1], ln->stream);
     ln->ev_used += 2;
   }
+  ~ProfScope() { end(); }
 };
 
 // After a stream sync: fold the recorded event pairs into the totals.
@@ -483,14 +490,18 @@ void prof_collect(Lane* ln) {
   for (size_t i = 0; i < ln->ev_pending.size(); ++i) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ln->ev_pool[2 * i], ln->ev_pool[2 * i + 1]);
-    if (ln->ev_pending[i].first == 0) {
+    const int kind = ln->ev_pending[i].first;
+    if (kind == kProfGemm) {
       ln->prof_acc.gemm_launches++;
       ln->prof_acc.gemm_ms += ms;
       ln->prof_acc.gemm_flops += ln->ev_pending[i].second;
-    } else {
+    } else if (kind == kProfAttn) {
       ln->prof_acc.attn_launches++;
       ln->prof_acc.attn_ms += ms;
       ln->prof_acc.attn_flops += ln->ev_pending[i].second;
+    } else {
+      if (kind == kProfText) ln->prof_acc.stage_calls++;
+      ln->prof_acc.stage_ms[kind - kProfText] += ms;
     }
   }
   ln->ev_pending.clear();
@@ -931,6 +942,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   CKS(grow(ln->tok_len, N * 4));
   CKS(grow(ln->rec_tok, (n + 1) * 8));
   VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask};
+  ProfScope ps_text(ln, kProfText, 0);
   launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
   launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st);
   exclusive_scan<uint32_t>(NonZeroU16{ln->tok_at.as<uint16_t>()}, N, ln->pos_b.as<uint32_t>(), cnt + 0,
@@ -954,6 +966,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   CKS(grow(ln->rx_t, N / 2 + 2));
   launch_recognize_emit(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), ln->rx_pos.as<uint32_t>(), N32,
                         ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), st);
+  ps_text.end();
   // ---- sync 1: token counts
   uint32_t h_cnt[2] = {0, 0};
   CK(cudaMemcpyAsync(h_cnt, cnt, 8, cudaMemcpyDeviceToHost, st));
@@ -1100,6 +1113,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     return AS_OK;
   }
   // ---- BIO decode
+  ProfScope ps_spans(ln, kProfSpans, 0);
   CKS(grow(ln->tok_flags, T + 16));
   CK(cudaMemsetAsync(ln->tok_flags.p, 0, T + 1, st));
   launch_token_flags(ln->rec_tok.as<uint64_t>(), n, ln->tok_flags.as<uint8_t>(), st);
@@ -1152,6 +1166,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   // the HMAC / map / substitution kernels read the final span count from cnt[5]
   sum_kept_kernel<<<1, 32, 0, st>>>(cnt);
   count_launch();
+  ps_spans.end();
   uint32_t fin_total = fin_cap;
   const uint64_t n_detect = n;  // records the detection steps saw (sub-records with a field policy)
   if (fj) {
@@ -1177,21 +1192,25 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   }
   // ---- HMAC + map
   CKS(grow(ln->digests, (size_t)(fin_total + 1) * 32));
+  ProfScope ps_hash(ln, kProfHash, 0);
   launch_hmac_spans(d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, fin_total,
                     c->key_state.as<uint32_t>(), ln->digests.as<uint32_t>(), st);
   launch_map_insert_spans(map_view(c), d_bytes, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(),
                           ln->fin_t.as<uint8_t>(), ln->digests.as<uint32_t>(), cnt + 5, fin_total, d_off, n,
                           rec_base >= 0 ? (uint64_t)rec_base : c->records_done, call_id, ln->dev_err.as<DevError>(),
                           st);
+  ps_hash.end();
   // ---- substitution
   CKI(upload_names(c, ln, sch));
   CKS(grow(ln->delta, (size_t)(fin_total + 1) * 8));
   CKS(grow(ln->shift, (size_t)(fin_total + 1) * 8));
   CKS(grow(ln->delta_total, 16));
+  ProfScope ps_sub1(ln, kProfSubst, 0);
   launch_sub_delta(ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_total + 1, ln->name_len.as<uint32_t>(),
                    sch->slug_hex_len, ln->delta.as<int64_t>(), st);
   exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, fin_total + 1, ln->shift.as<int64_t>(),
                           ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st);
+  ps_sub1.end();
   // ---- sync 2: output size and counts
   int64_t total_delta = 0;
   uint32_t h_cnt2[6];
@@ -1215,12 +1234,14 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     delete o;
     return fail(c, AS_ERR_OOM, "output allocation failed");
   }
+  ProfScope ps_sub2(ln, kProfSubst, 0);
   launch_sub_copy(d_bytes, N32, ln->fin_s.as<uint32_t>(), ln->fin_l.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(),
                   reinterpret_cast<uint8_t*>(d_out), st);
   launch_sub_replace(ln->fin_s.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_total, ln->shift.as<int64_t>(),
                      ln->digests.as<uint32_t>(), ln->names.as<char>(), ln->name_off.as<uint32_t>(), sch->slug_hex_len,
                      reinterpret_cast<uint8_t*>(d_out), st);
   launch_sub_offsets(d_off, n, ln->fin_s.as<uint32_t>(), cnt + 5, ln->shift.as<int64_t>(), d_out_off, st);
+  ps_sub2.end();
   if (out_dev) {
     o->d_bytes = d_out;
     o->d_off = d_out_off;
