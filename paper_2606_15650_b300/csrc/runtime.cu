@@ -215,6 +215,7 @@ struct as_ctx {
   std::vector<LayerW> layers;
   // vocab
   DBuf vocab_slots;
+  DBuf vocab_lenmask;
   uint32_t vocab_mask = 0;
   // map
   DBuf map_slots, map_arena, map_ctr;  // map_ctr: arena_used, n_entries
@@ -339,8 +340,11 @@ uint64_t pow2_at_least(uint64_t x) {
 as_status build_vocab(as_ctx* c) {
   const as_config& g = c->cfg;
   uint64_t n = g.n_vocab_words;
-  uint64_t size = std::max<uint64_t>(1024, pow2_at_least(2 * n + 1));
+  // about 8 slots per string: a lookup of a string that is not there
+  // usually ends at its first slot
+  uint64_t size = std::max<uint64_t>(1024, pow2_at_least(8 * n + 1));
   std::vector<uint4> slots(size, make_uint4(0, 0, 0, 0));
+  std::vector<uint16_t> lenmask((size_t)kAlnumCodes * kAlnumCodes, 0);
   for (uint64_t k = 0; k < n; ++k) {
     uint32_t a = g.vocab_offsets[k], b = g.vocab_offsets[k + 1];
     if (b <= a) return fail(c, AS_ERR_ARG, "vocab offsets must increase");
@@ -354,6 +358,7 @@ as_status build_vocab(as_ctx* c) {
       w[i >> 2] |= (uint32_t)ch << (8 * (i & 3));
     }
     uint32_t id = (uint32_t)(257 + k);
+    lenmask[alnum_code(g.vocab_bytes[a]) * kAlnumCodes + alnum_code(g.vocab_bytes[a + 1])] |= (uint16_t)(1u << len);
     uint32_t h = vocab_hash(w[0], w[1], w[2], len) & (uint32_t)(size - 1);
     while (true) {
       uint4& s = slots[h];
@@ -368,6 +373,8 @@ as_status build_vocab(as_ctx* c) {
   }
   CKS(grow(c->vocab_slots, size * sizeof(uint4)));
   CK(cudaMemcpy(c->vocab_slots.p, slots.data(), size * sizeof(uint4), cudaMemcpyHostToDevice));
+  CKS(grow(c->vocab_lenmask, lenmask.size() * sizeof(uint16_t)));
+  CK(cudaMemcpy(c->vocab_lenmask.p, lenmask.data(), lenmask.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   c->vocab_mask = (uint32_t)(size - 1);
   return AS_OK;
 }
@@ -941,7 +948,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   CKS(grow(ln->tok_off, N * 4));
   CKS(grow(ln->tok_len, N * 4));
   CKS(grow(ln->rec_tok, (n + 1) * 8));
-  VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask};
+  VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask, c->vocab_lenmask.as<uint16_t>()};
   ProfScope ps_text(ln, kProfText, 0);
   launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
   launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st);
@@ -1140,7 +1147,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   launch_ner_keep(ln->ner_s.as<uint32_t>(), ln->ner_l.as<uint32_t>(), ln->ner_t.as<uint8_t>(), cnt + 2, ner_cap,
                   ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), cnt + 1, sch->preserve_mask, keep.as<uint8_t>(), st);
   exclusive_scan<uint32_t>(NonZeroU8{keep.as<uint8_t>()}, ner_cap, ln->pos_k.as<uint32_t>(), cnt + 3,
-                           ln->scan_tiles.as<uint32_t>(), st);
+                           ln->scan_tiles.as<uint32_t>(), st, cnt + 2);  // over the NER spans found
   CKS(grow(ln->nk_s, (T + 1) * 4));
   CKS(grow(ln->nk_l, (T + 1) * 4));
   CKS(grow(ln->nk_t, T + 16));
@@ -1209,7 +1216,8 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   launch_sub_delta(ln->fin_l.as<uint32_t>(), ln->fin_t.as<uint8_t>(), cnt + 5, fin_total + 1, ln->name_len.as<uint32_t>(),
                    sch->slug_hex_len, ln->delta.as<int64_t>(), st);
   exclusive_scan<int64_t>(LoadI64{ln->delta.as<int64_t>()}, fin_total + 1, ln->shift.as<int64_t>(),
-                          ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st);
+                          ln->delta_total.as<int64_t>(), reinterpret_cast<int64_t*>(ln->scan_tiles.p), st, cnt + 5,
+                          1);  // over the final spans + 1 (shift[n] = total)
   ps_sub1.end();
   // ---- sync 2: output size and counts
   int64_t total_delta = 0;
@@ -1301,8 +1309,13 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   s.n_final_spans = h_cnt2[5];
   s.n_out_bytes = out_size;
   s.n_map_entries = n_entries;
-  const uint64_t seen = c->n_entries_seen.exchange(n_entries);
-  s.n_new_entries = n_entries >= seen ? n_entries - seen : 0;
+  // the largest map size any call has reported so far, raised atomically:
+  // calls on other lanes read the counter and report in any order, and a
+  // plain exchange could move it back and count entries twice
+  uint64_t seen = c->n_entries_seen.load();
+  while (seen < n_entries && !c->n_entries_seen.compare_exchange_weak(seen, n_entries)) {
+  }
+  s.n_new_entries = n_entries > seen ? n_entries - seen : 0;
   s.kernel_launches = t_launches - launches0;
   s.graph_replays = ln->graph_replays - replays0;
   if (rec_base < 0) c->records_done += n;
@@ -1389,6 +1402,7 @@ bool ctx_vocab(const as_ctx* ctx, VocabTable* vt, int* device) {
   if (!ctx || !ctx->vocab_slots.p) return false;
   vt->slots = ctx->vocab_slots.as<uint4>();
   vt->mask = ctx->vocab_mask;
+  vt->lenmask = ctx->vocab_lenmask.as<uint16_t>();
   *device = ctx->device;
   return true;
 }
@@ -1598,7 +1612,7 @@ void as_destroy(as_ctx* c) {
   cudaSetDevice(c->device);
   as_serve_stop(c);
   if (c->main.stream) cudaStreamSynchronize(c->main.stream);
-  DBuf* all[] = {&c->w32, &c->w16, &c->w8, &c->amax_dev, &c->vocab_slots, &c->map_slots, &c->map_arena, &c->map_ctr,
+  DBuf* all[] = {&c->w32, &c->w16, &c->w8, &c->amax_dev, &c->vocab_slots, &c->vocab_lenmask, &c->map_slots, &c->map_arena, &c->map_ctr,
                  &c->key_dev, &c->key_state};
   for (DBuf* b : all) release(*b);
   c->main.release_all();

@@ -1,6 +1,10 @@
 // Device-wide exclusive prefix sum in three passes (tile sums, scan of tile
 // sums, tile scan with offsets). Values come from a load functor so callers
 // can scan predicates (e.g. "byte starts a token") without materialising them.
+// The element count is the host's n, or, when a device count is given,
+// min(n, *n_dev + add): the grid is sized for the host capacity n and the
+// blocks past the device count return at once, so a scan over the spans
+// that a kernel produced costs what those spans cost, not the capacity.
 #pragma once
 
 #include "common.cuh"
@@ -11,9 +15,16 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+__device__ __forceinline__ uint64_t scan_count(uint64_t n, const uint32_t* n_dev, uint32_t add) {
+  return n_dev ? min(n, (uint64_t)*n_dev + add) : n;
+}
+
 template <typename T, typename Load>
-__global__ void __launch_bounds__(kScanThreads) scan_tile_sums(Load load, uint64_t n, T* tile_sums) {
+__global__ void __launch_bounds__(kScanThreads)
+    scan_tile_sums(Load load, uint64_t n, T* tile_sums, const uint32_t* n_dev, uint32_t add) {
   __shared__ T sm[33];
+  n = scan_count(n, n_dev, add);
+  if ((uint64_t)blockIdx.x * kScanTile >= n) return;  // the whole block: past the count
   uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   T s = 0;
 #pragma unroll
@@ -28,8 +39,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_tile_sums(Load load, uint64
 
 // One block scans all tile sums in place (exclusive) and writes the total.
 template <typename T>
-__global__ void __launch_bounds__(1024) scan_tile_offsets(T* tile_sums, uint64_t n_tiles, T* total) {
+__global__ void __launch_bounds__(1024)
+    scan_tile_offsets(T* tile_sums, uint64_t n, T* total, const uint32_t* n_dev, uint32_t add) {
   __shared__ T sm[33];
+  const uint64_t n_tiles = (scan_count(n, n_dev, add) + kScanTile - 1) / kScanTile;
   T carry = 0;
   for (uint64_t b = 0; b < n_tiles; b += blockDim.x) {
     uint64_t i = b + threadIdx.x;
@@ -43,8 +56,11 @@ __global__ void __launch_bounds__(1024) scan_tile_offsets(T* tile_sums, uint64_t
 }
 
 template <typename T, typename Load>
-__global__ void __launch_bounds__(kScanThreads) scan_tiles(Load load, uint64_t n, const T* tile_offsets, T* out) {
+__global__ void __launch_bounds__(kScanThreads)
+    scan_tiles(Load load, uint64_t n, const T* tile_offsets, T* out, const uint32_t* n_dev, uint32_t add) {
   __shared__ T sm[33];
+  n = scan_count(n, n_dev, add);
+  if ((uint64_t)blockIdx.x * kScanTile >= n) return;  // the whole block: past the count
   uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   T v[kScanItems];
   T s = 0;
@@ -68,16 +84,19 @@ inline uint64_t scan_tiles_needed(uint64_t n) { return (n + kScanTile - 1) / kSc
 
 // out[i] = sum_{j<i} load(j); *total_dev = sum of all. tile_scratch needs
 // scan_tiles_needed(n) elements. n may be 0 (then only *total_dev = 0).
+// With n_dev, the count is min(n, *n_dev + add) and out[] is written for
+// that many elements only.
 template <typename T, typename Load>
-inline void exclusive_scan(Load load, uint64_t n, T* out, T* total_dev, T* tile_scratch, cudaStream_t st) {
+inline void exclusive_scan(Load load, uint64_t n, T* out, T* total_dev, T* tile_scratch, cudaStream_t st,
+                           const uint32_t* n_dev = nullptr, uint32_t add = 0) {
   uint64_t tiles = scan_tiles_needed(n);
   if (tiles == 0) {
     cudaMemsetAsync(total_dev, 0, sizeof(T), st);
     return;
   }
-  scan_tile_sums<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch);
-  scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_scratch, tiles, total_dev);
-  scan_tiles<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, out);
+  scan_tile_sums<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, n_dev, add);
+  scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_scratch, n, total_dev, n_dev, add);
+  scan_tiles<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, out, n_dev, add);
   count_launch(3);
 }
 

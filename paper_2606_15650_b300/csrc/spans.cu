@@ -112,7 +112,9 @@ __global__ void ner_keep_kernel(const uint32_t* __restrict__ ns, const uint32_t*
                                 const uint32_t* __restrict__ rs, const uint32_t* __restrict__ rl,
                                 const uint32_t* n_rx_dev, uint64_t preserve, uint8_t* keep, uint32_t cap) {
   uint32_t n = *n_ner_dev, nr = *n_rx_dev;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) {
+  // keep[0..n): the scan and the compaction after it read no further
+  const uint32_t end = min(cap, n);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < end; k += gridDim.x * blockDim.x) {
     uint8_t kp = 0;
     if (k < n && nl[k] > 0) {
       uint32_t s = ns[k], e = s + nl[k];

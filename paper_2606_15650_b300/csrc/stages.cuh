@@ -19,9 +19,19 @@ __host__ __device__ inline uint32_t vocab_hash(uint32_t w0, uint32_t w1, uint32_
   return h;
 }
 
+// Open-addressing table of the vocabulary strings (slot = the string's
+// bytes in x,y,z and len | id << 16 in w; w == 0 marks an empty slot), and
+// for each pair of leading alphanumeric bytes the set of vocabulary lengths
+// that start with that pair (bit L set: some string of length L does), so
+// the greedy match probes only lengths that can hit.
+constexpr int kAlnumCodes = 62;
+__host__ __device__ inline uint32_t alnum_code(uint32_t c) {
+  return c <= '9' ? c - '0' : c <= 'Z' ? c - 'A' + 10 : c - 'a' + 36;
+}
 struct VocabTable {
   const uint4* slots;
   uint32_t mask;
+  const uint16_t* lenmask;  // [kAlnumCodes * kAlnumCodes]
 };
 
 // ---- stage launchers (all asynchronous on `st`) ----

@@ -18,7 +18,9 @@ __global__ void sub_delta_kernel(const uint32_t* __restrict__ sp_len, const uint
                                  const uint32_t* n_dev, const uint32_t* __restrict__ name_len, uint32_t slug_len,
                                  int64_t* __restrict__ delta, uint32_t cap) {
   uint32_t n = *n_dev;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) {
+  // delta[0..n] (delta[n] = 0): the shift scan reads no further
+  const uint32_t end = min(cap, n + 1);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < end; k += gridDim.x * blockDim.x) {
     int64_t d = 0;
     if (k < n) {
       int64_t rep = 2 + (int64_t)name_len[sp_type[k]] + (slug_len ? 1 + (int64_t)slug_len : 0);

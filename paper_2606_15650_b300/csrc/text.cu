@@ -15,6 +15,9 @@
 // One thread per word start. A second pass, one warp per record, takes the
 // candidates left to right and drops those that start inside an accepted
 // multi-word span (the behaviour of a scanning regex engine).
+#include <algorithm>
+#include <atomic>
+
 #include "scan.cuh"
 #include "stages.cuh"
 
@@ -49,46 +52,111 @@ __device__ __forceinline__ uint32_t vocab_lookup(VocabTable vt, const uint32_t b
   return 0;
 }
 
-__global__ void tokenize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs,
-                                     VocabTable vt, uint16_t* __restrict__ tok_at) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    uint32_t c = bytes[i];
-    if (!is_alnum(c)) {
-      tok_at[i] = (uint16_t)(c + 1);
-      continue;
-    }
-    if (!rs_bit(rs, i) && i > 0 && is_alnum(bytes[i - 1])) continue;  // written by the run's first thread
-    uint32_t p = i;
-    while (true) {
-      uint32_t b[kMaxPiece];
-      uint32_t avail = 0;
+// Greedy longest-match split of the alphanumeric run that starts at byte i:
+// the id of each piece at its first byte, 0 at its other bytes.
+__device__ __forceinline__ void tokenize_run(const uint8_t* __restrict__ bytes, uint32_t N,
+                                             const uint32_t* __restrict__ rs, VocabTable vt,
+                                             uint16_t* __restrict__ tok_at, uint32_t i) {
+  uint32_t p = i;
+  while (true) {
+    uint32_t b[kMaxPiece];
+    uint32_t avail = 0;
 #pragma unroll
-      for (int k = 0; k < kMaxPiece; ++k) b[k] = 0;
-      for (uint32_t k = 0; k < (uint32_t)kMaxPiece; ++k) {
-        uint32_t q = p + k;
-        if (q >= N) break;
-        uint32_t ch = bytes[q];
-        if (!is_alnum(ch) || (k > 0 && rs_bit(rs, q))) break;
-        b[k] = ch;
-        avail = k + 1;
-      }
-      uint32_t take = 1, id = b[0] + 1;
-      for (uint32_t L = avail; L >= 2; --L) {
-        uint32_t v = vocab_lookup(vt, b, L);
-        if (v) { take = L; id = v; break; }
-      }
-      tok_at[p] = (uint16_t)id;
-      for (uint32_t k = 1; k < take; ++k) tok_at[p + k] = 0;
-      p += take;
-      if (p >= N || !is_alnum(bytes[p]) || rs_bit(rs, p)) break;
+    for (int k = 0; k < kMaxPiece; ++k) b[k] = 0;
+    for (uint32_t k = 0; k < (uint32_t)kMaxPiece; ++k) {
+      uint32_t q = p + k;
+      if (q >= N) break;
+      uint32_t ch = bytes[q];
+      if (!is_alnum(ch) || (k > 0 && rs_bit(rs, q))) break;
+      b[k] = ch;
+      avail = k + 1;
     }
+    // longest vocabulary prefix: only lengths that some string starting
+    // with b[0] b[1] has, at most avail, longest first
+    uint32_t take = 1, id = b[0] + 1;
+    if (avail >= 2) {
+      uint32_t lens = __ldg(&vt.lenmask[alnum_code(b[0]) * kAlnumCodes + alnum_code(b[1])]);
+      lens &= (2u << avail) - 1u;
+      while (lens) {
+        const uint32_t L = 31u - __clz(lens);
+        const uint32_t v = vocab_lookup(vt, b, L);
+        if (v) { take = L; id = v; break; }
+        lens &= ~(1u << L);
+      }
+    }
+    tok_at[p] = (uint16_t)id;
+    for (uint32_t k = 1; k < take; ++k) tok_at[p + k] = 0;
+    p += take;
+    if (p >= N || !is_alnum(bytes[p]) || rs_bit(rs, p)) break;
+  }
+}
+
+// A block takes tiles of kMarkTile bytes. It first writes the id of every
+// non-alphanumeric byte and collects the tile's run starts in shared memory
+// (one ballot per warp and step), then its threads split whole runs, one run
+// per thread: every lane of a warp has a run to work on, where one thread per
+// byte would leave most lanes idle while a few walk their runs. A run that
+// continues past the tile is finished by its own thread.
+constexpr uint32_t kMarkThreads = 256;
+constexpr uint32_t kMarkTile = 4096;
+
+// Blocks of a mark kernel that fit on the device at once (the kernels loop
+// over tiles with a grid stride, so a second wave of blocks would start late
+// with a full share of tiles), looked up once per kernel.
+template <typename Kernel>
+unsigned resident_blocks(Kernel kernel, uint64_t tiles) {
+  static std::atomic<int> cap{0};
+  int c = cap.load();
+  if (c == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kMarkThreads, 0);
+    c = std::max(1, per_sm * sms);
+    cap.store(c);
+  }
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)c));
+}
+
+__device__ __forceinline__ void collect_start(bool start, uint32_t i, uint32_t* starts, uint32_t* n_starts) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t m = __ballot_sync(0xffffffffu, start);
+  uint32_t at = 0;
+  if (lane == 0 && m) at = atomicAdd(n_starts, (uint32_t)__popc(m));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (start) starts[at + __popc(m & ((1u << lane) - 1u))] = i;  // < kMarkTile: one start per byte at most
+}
+
+__global__ void __launch_bounds__(kMarkThreads, 4)
+    tokenize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs, VocabTable vt,
+                         uint16_t* __restrict__ tok_at) {
+  __shared__ uint32_t starts[kMarkTile];
+  __shared__ uint32_t n_starts;
+  for (uint64_t base = (uint64_t)blockIdx.x * kMarkTile; base < N; base += (uint64_t)gridDim.x * kMarkTile) {
+    if (threadIdx.x == 0) n_starts = 0;
+    __syncthreads();
+    for (uint32_t k = 0; k < kMarkTile / kMarkThreads; ++k) {
+      const uint64_t i = base + k * kMarkThreads + threadIdx.x;
+      bool start = false;
+      if (i < N) {
+        const uint32_t c = bytes[i];
+        if (!is_alnum(c)) tok_at[i] = (uint16_t)(c + 1);
+        else start = i == 0 || rs_bit(rs, (uint32_t)i) || !is_alnum(bytes[i - 1]);
+      }
+      collect_start(start, (uint32_t)i, starts, &n_starts);
+    }
+    __syncthreads();
+    const uint32_t ns = n_starts;
+    for (uint32_t j = threadIdx.x; j < ns; j += kMarkThreads) tokenize_run(bytes, N, rs, vt, tok_at, starts[j]);
+    __syncthreads();  // starts and n_starts are reused by the next tile
   }
 }
 
 void launch_tokenize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, VocabTable vt, uint16_t* tok_at,
                           cudaStream_t st) {
   if (N == 0) return;
-  tokenize_mark_kernel<<<grid_1d(N, 256, 148 * 64), 256, 0, st>>>(bytes, N, rs, vt, tok_at);
+  const unsigned grid = resident_blocks(tokenize_mark_kernel, (N + kMarkTile - 1) / kMarkTile);
+  tokenize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, vt, tok_at);
   count_launch();
 }
 
@@ -415,56 +483,103 @@ __device__ uint32_t rx_cpe_end(const RecScan& r) {
 
 #undef AS_SET
 
-__global__ void recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs,
-                                      RxTypes T, uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    uint32_t len = 0;
-    uint8_t type = 0;
-    uint32_t c = bytes[i];
-    if (in_word(c) && (i == 0 || rs_bit(rs, i) || !in_word(bytes[i - 1]))) {
-      if (T.t[kRxPem] | T.t[kRxUrl] | T.t[kRxCpe]) {
-        const RecScan r{bytes, N, rs, i};
-        uint32_t le = 0;
-        if (T.t[kRxPem] && (le = rx_pem_end(r)) > i) type = T.t[kRxPem];
-        else if (T.t[kRxUrl] && (le = rx_url_end(r)) > i) type = T.t[kRxUrl];
-        else if (T.t[kRxCpe] && (le = rx_cpe_end(r)) > i) type = T.t[kRxCpe];
-        if (type) {
-          len = le - i;
-          type |= kRxLong;
+// The recognizers at the word that starts at byte i: the entity length and
+// type (kRxLong set for a multi-word match), 0 and 0 when nothing matches.
+__device__ __forceinline__ void recognize_word(const uint8_t* __restrict__ bytes, uint32_t N,
+                                               const uint32_t* __restrict__ rs, const RxTypes& T, uint32_t i,
+                                               uint32_t& len, uint8_t& type) {
+  len = 0;
+  type = 0;
+  const uint32_t c = bytes[i];
+  if (T.t[kRxPem] | T.t[kRxUrl] | T.t[kRxCpe]) {
+    const RecScan r{bytes, N, rs, i};
+    uint32_t le = 0;
+    if (T.t[kRxPem] && (le = rx_pem_end(r)) > i) type = T.t[kRxPem];
+    else if (T.t[kRxUrl] && (le = rx_url_end(r)) > i) type = T.t[kRxUrl];
+    else if (T.t[kRxCpe] && (le = rx_cpe_end(r)) > i) type = T.t[kRxCpe];
+    if (type) {
+      len = le - i;
+      type |= kRxLong;
+    }
+  }
+  // which separators the word holds ('.' 1, ':' 2, '-' 4): every test
+  // below except the hash needs one, so words without them skip it
+  auto sep_bit = [](uint32_t ch) -> uint32_t { return ch == '.' ? 1u : ch == ':' ? 2u : ch == '-' ? 4u : 0u; };
+  uint32_t sep = sep_bit(c);
+  uint32_t e = i + 1;
+  while (e < N && !rs_bit(rs, e)) {
+    const uint32_t ch = bytes[e];
+    if (!in_word(ch)) break;
+    sep |= sep_bit(ch);
+    ++e;
+  }
+  while (e > i) {
+    uint32_t t = bytes[e - 1];
+    if (t == '.' || t == '-') --e;
+    else if (t == ':' && !(e >= i + 2 && bytes[e - 2] == ':')) --e;
+    else break;
+  }
+  const uint8_t* w = bytes + i;
+  uint32_t n = e - i;
+  if (n > 0 && !type) {
+    uint32_t k;
+    // a test skipped for want of its separator would have failed (MAC: ':'
+    // or '-'; IPv6, fingerprint: ':'; IPv4, host name, OID: '.'; CVE,
+    // UUID: '-'), so the first match is the same
+    if (T.t[kRxMac] && (sep & 6u) && rx_is_mac(w, n)) { len = n; type = T.t[kRxMac]; }
+    else if (T.t[kRxIpv6] && (sep & 2u) && rx_is_ipv6(w, n)) { len = n; type = T.t[kRxIpv6]; }
+    else if (T.t[kRxIpv4] && (sep & 1u) && (k = rx_ipv4_len(w, n)) > 0) { len = k; type = T.t[kRxIpv4]; }
+    else if (T.t[kRxCve] && (sep & 4u) && rx_is_cve(w, n)) { len = n; type = T.t[kRxCve]; }
+    else if (T.t[kRxHost] && (sep & 1u) && (k = rx_host_len(w, n)) > 0) { len = k; type = T.t[kRxHost]; }
+    else if (T.t[kRxHash] && rx_is_hash(w, n)) { len = n; type = T.t[kRxHash]; }
+    else if (T.t[kRxUuid] && (sep & 4u) && rx_is_uuid(w, n)) { len = n; type = T.t[kRxUuid]; }
+    else if (T.t[kRxCertFp] && (sep & 2u) && rx_is_cert_fp(w, n)) { len = n; type = T.t[kRxCertFp]; }
+    else if (T.t[kRxOid] && (sep & 1u) && rx_is_oid(w, n)) { len = n; type = T.t[kRxOid]; }
+  }
+}
+
+// Tiles of kMarkTile bytes as in the tokenizer: the block writes 0 for every
+// byte that starts no word and collects the word starts, then one thread per
+// word runs the recognizers.
+__global__ void __launch_bounds__(kMarkThreads)
+    recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs, RxTypes T,
+                          uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
+  __shared__ uint32_t starts[kMarkTile];
+  __shared__ uint32_t n_starts;
+  for (uint64_t base = (uint64_t)blockIdx.x * kMarkTile; base < N; base += (uint64_t)gridDim.x * kMarkTile) {
+    if (threadIdx.x == 0) n_starts = 0;
+    __syncthreads();
+    for (uint32_t k = 0; k < kMarkTile / kMarkThreads; ++k) {
+      const uint64_t i = base + k * kMarkThreads + threadIdx.x;
+      bool start = false;
+      if (i < N) {
+        start = in_word(bytes[i]) && (i == 0 || rs_bit(rs, (uint32_t)i) || !in_word(bytes[i - 1]));
+        if (!start) {
+          rx_len[i] = 0;
+          rx_type[i] = 0;
         }
       }
-      uint32_t e = i + 1;
-      while (e < N && in_word(bytes[e]) && !rs_bit(rs, e)) ++e;
-      while (e > i) {
-        uint32_t t = bytes[e - 1];
-        if (t == '.' || t == '-') --e;
-        else if (t == ':' && !(e >= i + 2 && bytes[e - 2] == ':')) --e;
-        else break;
-      }
-      const uint8_t* w = bytes + i;
-      uint32_t n = e - i;
-      if (n > 0 && !type) {
-        uint32_t k;
-        if (T.t[kRxMac] && rx_is_mac(w, n)) { len = n; type = T.t[kRxMac]; }
-        else if (T.t[kRxIpv6] && rx_is_ipv6(w, n)) { len = n; type = T.t[kRxIpv6]; }
-        else if (T.t[kRxIpv4] && (k = rx_ipv4_len(w, n)) > 0) { len = k; type = T.t[kRxIpv4]; }
-        else if (T.t[kRxCve] && rx_is_cve(w, n)) { len = n; type = T.t[kRxCve]; }
-        else if (T.t[kRxHost] && (k = rx_host_len(w, n)) > 0) { len = k; type = T.t[kRxHost]; }
-        else if (T.t[kRxHash] && rx_is_hash(w, n)) { len = n; type = T.t[kRxHash]; }
-        else if (T.t[kRxUuid] && rx_is_uuid(w, n)) { len = n; type = T.t[kRxUuid]; }
-        else if (T.t[kRxCertFp] && rx_is_cert_fp(w, n)) { len = n; type = T.t[kRxCertFp]; }
-        else if (T.t[kRxOid] && rx_is_oid(w, n)) { len = n; type = T.t[kRxOid]; }
-      }
+      collect_start(start, (uint32_t)i, starts, &n_starts);
     }
-    rx_len[i] = len;
-    rx_type[i] = type;
+    __syncthreads();
+    const uint32_t ns = n_starts;
+    for (uint32_t j = threadIdx.x; j < ns; j += kMarkThreads) {
+      const uint32_t i = starts[j];
+      uint32_t len;
+      uint8_t type;
+      recognize_word(bytes, N, rs, T, i, len, type);
+      rx_len[i] = len;
+      rx_type[i] = type;
+    }
+    __syncthreads();  // starts and n_starts are reused by the next tile
   }
 }
 
 void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, RxTypes types, uint32_t* rx_len,
                            uint8_t* rx_type, cudaStream_t st) {
   if (N == 0) return;
-  recognize_mark_kernel<<<grid_1d(N, 256, 148 * 64), 256, 0, st>>>(bytes, N, rs, types, rx_len, rx_type);
+  const unsigned grid = resident_blocks(recognize_mark_kernel, (N + kMarkTile - 1) / kMarkTile);
+  recognize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, types, rx_len, rx_type);
   count_launch();
 }
 
