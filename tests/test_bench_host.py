@@ -48,3 +48,26 @@ def test_missing_nvidia_smi_is_reported_not_rejected():
     cs.proc = None
     clk = cs.stop()
     assert clk["reasons"] == ["nvidia-smi unavailable"] and bench.clocks_rejected(clk) is None
+
+
+def test_integer_stage_rooflines():
+    # one call: 1,000 bytes in 10 records, 400 tokens, 20 recognizer / 30 NER / 40 final spans,
+    # 1,100 output bytes; two profiled calls, each stage timed over both
+    st = {"n_bytes": 1000, "n_tokens": 400, "n_records": 10, "n_regex_spans": 20, "n_ner_spans": 30,
+          "n_final_spans": 40, "n_out_bytes": 1100}
+    prof = {"stage_calls": 2, "stage_ms": {"text": 2e-3, "spans": 1e-3, "hash_map": 4e-3, "substitution": 1e-3}}
+    out = bench.integer_stages(prof, st, 6000.0, "measured", total_ms=10.0)
+    text = 1000 + 12 * 400 + 8 * 11 + 9 * 20          # text once, token table, record offsets, spans
+    spans = 400 + 16 * 30 + 9 * 20 + 9 * 40          # labels, NER boundaries, recognizer spans, final spans
+    subst = 1000 + 1100 + 49 * 40 + 16 * 11           # text in, output out, final spans, offsets in and out
+    assert out["calls"] == 2
+    assert out["text"]["alg_bytes"] == text and out["spans"]["alg_bytes"] == spans
+    assert out["substitution"]["alg_bytes"] == subst
+    # per call: 1e-3 ms for the text stage -> bytes / 1 us
+    assert abs(out["text"]["gb_s"] - text / 1e-6 / 1e9) < 1e-9
+    assert abs(out["text"]["frac"] - out["text"]["gb_s"] / 6000.0) < 1e-12
+    assert abs(out["hash_map"]["spans_per_s"] - 40 / 2e-6) < 1e-3
+    assert abs(out["substitution"]["share_of_step"] - 1e-3 / 10.0) < 1e-12
+    # no profiled call: no rates, no division by zero
+    empty = bench.integer_stages({"stage_calls": 0, "stage_ms": {}}, st, 6000.0, "measured", total_ms=10.0)
+    assert empty["text"]["gb_s"] is None and empty["hash_map"]["spans_per_s"] is None
