@@ -155,10 +155,10 @@ __global__ void expand_rows_kernel(const SeqDesc* __restrict__ seqs, int32_t* ro
 struct Lane {
   cudaStream_t stream = nullptr;
   DBuf dev_err;
-  DBuf in_bytes, in_off, rs_bits, tok_at, pos_b, scan_tiles, counters, delta_total;
+  DBuf in_bytes, in_off, rs_bits, tok_at, scan_tiles, counters, delta_total;
   DBuf tok_ids, tok_off, tok_len, rec_tok;
   DBuf rx_len_b, rx_type_b, rx_s, rx_l, rx_t;
-  DBuf labels, logits, tok_flags, rx_pos, bio_start, bio_end, pos_t;
+  DBuf labels, logits, tok_flags, bio_start, bio_end, pos_t;
   DBuf ner_s, ner_l, ner_t, keep, pos_k, nk_s, nk_l, nk_t, rk_s, rk_l, rk_t;
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
@@ -250,9 +250,9 @@ struct as_output {
 };
 
 void Lane::release_all() {
-  DBuf* all[] = {&dev_err, &in_bytes, &in_off, &rs_bits, &tok_at, &pos_b, &scan_tiles, &counters, &delta_total,
+  DBuf* all[] = {&dev_err, &in_bytes, &in_off, &rs_bits, &tok_at, &scan_tiles, &counters, &delta_total,
                  &tok_ids, &tok_off, &tok_len, &rec_tok, &rx_len_b, &rx_type_b, &rx_s, &rx_l, &rx_t, &labels, &logits,
-                 &tok_flags, &rx_pos, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
+                 &tok_flags, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
                  &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
                  &name_off, &name_len, &seqs, &attn_items, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
                  &fs_l, &fs_t, &fr_s, &fr_l, &fr_t, &f_keep, &f_pos, &f_cnt, &ff_s, &ff_l, &ff_t, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
@@ -942,7 +942,6 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   CK(cudaMemsetAsync(cnt, 0, 64, st));
   CKS(grow(ln->rs_bits, ((size_t)N / 32 + 1) * 4));
   CKS(grow(ln->tok_at, N * 2));
-  CKS(grow(ln->pos_b, (N + 1) * 4));
   CKS(grow(ln->scan_tiles, (scan_tiles_needed(std::max<uint64_t>(N + 1, 1) * 2) + 16) * 8));
   CKS(grow(ln->tok_ids, N * 4));
   CKS(grow(ln->tok_off, N * 4));
@@ -952,12 +951,10 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   ProfScope ps_text(ln, kProfText, 0);
   launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
   launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st);
-  exclusive_scan<uint32_t>(NonZeroU16{ln->tok_at.as<uint16_t>()}, N, ln->pos_b.as<uint32_t>(), cnt + 0,
-                           ln->scan_tiles.as<uint32_t>(), st);
-  launch_tokenize_emit(ln->tok_at.as<uint16_t>(), ln->pos_b.as<uint32_t>(), N32, ln->tok_ids.as<int32_t>(),
-                       ln->tok_off.as<uint32_t>(), st);
-  launch_record_token_offsets(d_off, n, ln->pos_b.as<uint32_t>(), N32, cnt + 0, ln->rec_tok.as<uint64_t>(), st);
-  // recognizers (pos_b reused after the token emit above)
+  launch_tokenize_compact(ln->tok_at.as<uint16_t>(), N32, ln->tok_ids.as<int32_t>(), ln->tok_off.as<uint32_t>(),
+                          cnt + 0, ln->scan_tiles.as<uint32_t>(), st);
+  launch_record_token_starts(d_off, n, ln->tok_off.as<uint32_t>(), cnt + 0, N32, ln->rec_tok.as<uint64_t>(), st);
+  // recognizers
   CKS(grow(ln->rx_len_b, N * 4));
   CKS(grow(ln->rx_type_b, N + 16));
   const RxTypes rxt = recognizer_table(sch);
@@ -965,14 +962,11 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
                         ln->rx_type_b.as<uint8_t>(), st);
   if (rx_any_long(rxt))
     launch_recognize_resolve(d_off, n, ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), st);
-  CKS(grow(ln->rx_pos, (N + 1) * 4));
-  exclusive_scan<uint32_t>(NonZeroU8{ln->rx_type_b.as<uint8_t>()}, N, ln->rx_pos.as<uint32_t>(), cnt + 1,
-                           ln->scan_tiles.as<uint32_t>(), st);
   CKS(grow(ln->rx_s, (N / 2 + 2) * 4));
   CKS(grow(ln->rx_l, (N / 2 + 2) * 4));
   CKS(grow(ln->rx_t, N / 2 + 2));
-  launch_recognize_emit(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), ln->rx_pos.as<uint32_t>(), N32,
-                        ln->rx_s.as<uint32_t>(), ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), st);
+  launch_recognize_compact(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), N32, ln->rx_s.as<uint32_t>(),
+                           ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), cnt + 1, ln->scan_tiles.as<uint32_t>(), st);
   ps_text.end();
   // ---- sync 1: token counts
   uint32_t h_cnt[2] = {0, 0};

@@ -80,6 +80,31 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
+// The last pass of a compaction: instead of the prefix of every element, the
+// rank of each nonzero element goes to emit(i, rank), so no per-element
+// position array is written and read back.
+template <typename T, typename Load, typename Emit>
+__global__ void __launch_bounds__(kScanThreads)
+    scan_emit_tiles(Load load, uint64_t n, const T* tile_offsets, Emit emit) {
+  __shared__ T sm[33];
+  uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    v[k] = i < n ? load(i) : T(0);
+    s += v[k];
+  }
+  T tot;
+  T run = block_exclusive_scan(s, sm, &tot) + tile_offsets[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (v[k]) emit(base + k, run);  // v[k] != 0 only for base + k < n
+    run += v[k];
+  }
+}
+
 inline uint64_t scan_tiles_needed(uint64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
 // out[i] = sum_{j<i} load(j); *total_dev = sum of all. tile_scratch needs
@@ -97,6 +122,21 @@ inline void exclusive_scan(Load load, uint64_t n, T* out, T* total_dev, T* tile_
   scan_tile_sums<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, n_dev, add);
   scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_scratch, n, total_dev, n_dev, add);
   scan_tiles<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, out, n_dev, add);
+  count_launch(3);
+}
+
+// emit(i, rank) for every i < n with load(i) != 0, rank = the number of such
+// elements before i (in index order); *total_dev = their count.
+template <typename T, typename Load, typename Emit>
+inline void compact_emit(Load load, uint64_t n, Emit emit, T* total_dev, T* tile_scratch, cudaStream_t st) {
+  uint64_t tiles = scan_tiles_needed(n);
+  if (tiles == 0) {
+    cudaMemsetAsync(total_dev, 0, sizeof(T), st);
+    return;
+  }
+  scan_tile_sums<T, Load><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, nullptr, 0);
+  scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_scratch, n, total_dev, nullptr, 0);
+  scan_emit_tiles<T, Load, Emit><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_scratch, emit);
   count_launch(3);
 }
 

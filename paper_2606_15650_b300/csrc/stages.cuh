@@ -47,6 +47,13 @@ void launch_tokenize_emit(const uint16_t* tok_at, const uint32_t* pos, uint32_t 
 void launch_token_lengths(const uint32_t* tok_off, uint32_t T, uint32_t N, uint32_t* tok_len, cudaStream_t st);
 void launch_record_token_offsets(const uint64_t* offsets, uint64_t n_records, const uint32_t* pos, uint32_t N,
                                  const uint32_t* total_T, uint64_t* rec_tok, cudaStream_t st);
+// Token table (id, first byte) in byte order from the marks; *n_tokens = T.
+// tile_scratch: scan_tiles_needed(N) elements.
+void launch_tokenize_compact(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* n_tokens,
+                             uint32_t* tile_scratch, cudaStream_t st);
+// rec_tok[r] = first token of record r (T for offsets at N), from the token offsets.
+void launch_record_token_starts(const uint64_t* offsets, uint64_t n, const uint32_t* tok_off, const uint32_t* total_T,
+                                uint32_t N, uint64_t* rec_tok, cudaStream_t st);
 
 // Pattern recognizers: rx_len[i] / rx_type[i] at each word start that is an
 // entity candidate. RxTypes maps each recognizer kind (the order of
@@ -67,8 +74,10 @@ void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_
                            uint32_t* rx_len, uint8_t* rx_type, cudaStream_t st);
 void launch_recognize_resolve(const uint64_t* offsets, uint64_t n_records, const uint32_t* rx_len, uint8_t* rx_type,
                               cudaStream_t st);
-void launch_recognize_emit(const uint32_t* rx_len, const uint8_t* rx_type, const uint32_t* pos, uint32_t N,
-                           uint32_t* sp_start, uint32_t* sp_len, uint8_t* sp_type, cudaStream_t st);
+// Recognizer spans (start, length, type) in byte order; *n_spans = their count.
+void launch_recognize_compact(const uint32_t* rx_len, const uint8_t* rx_type, uint32_t N, uint32_t* sp_start,
+                              uint32_t* sp_len, uint8_t* sp_type, uint32_t* n_spans, uint32_t* tile_scratch,
+                              cudaStream_t st);
 
 // BIO decode: token flags (bit0 first token of record, bit1 last).
 void launch_token_flags(const uint64_t* rec_tok, uint64_t n_records, uint8_t* tok_flags, cudaStream_t st);

@@ -204,6 +204,46 @@ void launch_record_token_offsets(const uint64_t* offsets, uint64_t n, const uint
   count_launch();
 }
 
+// Token table straight from the marks: one compaction whose last pass writes
+// each token's id and first byte at its rank (no per-byte position array).
+struct TokStart {
+  const uint16_t* tok_at;
+  __device__ uint32_t operator()(uint64_t i) const { return tok_at[i] != 0; }
+};
+struct EmitToken {
+  const uint16_t* tok_at;
+  int32_t* ids;
+  uint32_t* off;
+  __device__ void operator()(uint64_t i, uint32_t t) const {
+    ids[t] = (int32_t)tok_at[i];
+    off[t] = (uint32_t)i;
+  }
+};
+
+void launch_tokenize_compact(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* n_tokens,
+                             uint32_t* tile_scratch, cudaStream_t st) {
+  compact_emit<uint32_t>(TokStart{tok_at}, N, EmitToken{tok_at, ids, off}, n_tokens, tile_scratch, st);
+}
+
+// First token of each record from the token table: a record start is always
+// a token start, so it is the number of tokens that start before the record
+// (binary search of the sorted token offsets); offsets at N give T.
+__global__ void record_token_starts_kernel(const uint64_t* __restrict__ offsets, uint64_t n,
+                                           const uint32_t* __restrict__ off, const uint32_t* total_T, uint32_t N,
+                                           uint64_t* __restrict__ rec_tok) {
+  const uint32_t T = *total_T;
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r <= n; r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t o = offsets[r];
+    rec_tok[r] = o >= N ? T : o == 0 ? 0 : (uint64_t)(upper_index(off, (int64_t)T, (uint32_t)(o - 1)) + 1);
+  }
+}
+
+void launch_record_token_starts(const uint64_t* offsets, uint64_t n, const uint32_t* tok_off, const uint32_t* total_T,
+                                uint32_t N, uint64_t* rec_tok, cudaStream_t st) {
+  record_token_starts_kernel<<<grid_1d(n + 1, 256, 65535), 256, 0, st>>>(offsets, n, tok_off, total_T, N, rec_tok);
+  count_launch();
+}
+
 // ---------------------------------------------------------------- recognizers
 
 __device__ __forceinline__ bool in_word(uint32_t c) { return is_alnum(c) || c == '.' || c == ':' || c == '-'; }
@@ -658,25 +698,29 @@ void launch_recognize_resolve(const uint64_t* offsets, uint64_t n, const uint32_
   count_launch();
 }
 
-__global__ void recognize_emit_kernel(const uint32_t* __restrict__ rx_len, const uint8_t* __restrict__ rx_type,
-                                      const uint32_t* __restrict__ pos, uint32_t N, uint32_t* sp_start,
-                                      uint32_t* sp_len, uint8_t* sp_type) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    uint8_t t = rx_type[i];
-    if (t) {
-      uint32_t k = pos[i];
-      sp_start[k] = i;
-      sp_len[k] = rx_len[i];
-      sp_type[k] = t;
-    }
+// Recognizer spans in byte order: one compaction of the per-byte marks whose
+// last pass writes each span at its rank.
+struct RxStart {
+  const uint8_t* rx_type;
+  __device__ uint32_t operator()(uint64_t i) const { return rx_type[i] != 0; }
+};
+struct EmitRxSpan {
+  const uint32_t* rx_len;
+  const uint8_t* rx_type;
+  uint32_t *sp_start, *sp_len;
+  uint8_t* sp_type;
+  __device__ void operator()(uint64_t i, uint32_t k) const {
+    sp_start[k] = (uint32_t)i;
+    sp_len[k] = rx_len[i];
+    sp_type[k] = rx_type[i];
   }
-}
+};
 
-void launch_recognize_emit(const uint32_t* rx_len, const uint8_t* rx_type, const uint32_t* pos, uint32_t N,
-                           uint32_t* sp_start, uint32_t* sp_len, uint8_t* sp_type, cudaStream_t st) {
-  if (N == 0) return;
-  recognize_emit_kernel<<<grid_1d(N, 256, 148 * 64), 256, 0, st>>>(rx_len, rx_type, pos, N, sp_start, sp_len, sp_type);
-  count_launch();
+void launch_recognize_compact(const uint32_t* rx_len, const uint8_t* rx_type, uint32_t N, uint32_t* sp_start,
+                              uint32_t* sp_len, uint8_t* sp_type, uint32_t* n_spans, uint32_t* tile_scratch,
+                              cudaStream_t st) {
+  compact_emit<uint32_t>(RxStart{rx_type}, N, EmitRxSpan{rx_len, rx_type, sp_start, sp_len, sp_type}, n_spans,
+                         tile_scratch, st);
 }
 
 }  // namespace as
