@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "encoder.cuh"
 #include "scan.cuh"
 #include "stages.cuh"
@@ -466,11 +468,23 @@ as_status load_weights(as_ctx* c) {
 // or around one integer stage of a batch call (kinds 2..5, the order of
 // as_profile_stats.stage_ms). Scopes never nest: event i of the pool belongs
 // to pending entry i / 2.
+// A stage scope is also an NVTX range (named below, whether or not event
+// timing is on), so that a profiler can select a stage's kernels by name.
 constexpr int kProfGemm = 0, kProfAttn = 1, kProfText = 2, kProfSpans = 3, kProfHash = 4, kProfSubst = 5;
+constexpr const char* kStageRange[4] = {"as.text", "as.spans", "as.hash_map", "as.substitution"};
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 struct ProfScope {
   Lane* ln;
   bool on;
+  bool range = false;
   ProfScope(Lane* ln_, int kind, double flops) : ln(ln_), on(ln_->prof) {
+    if (kind >= kProfText) {
+      nvtxRangePushA(kStageRange[kind - kProfText]);
+      range = true;
+    }
     if (!on) return;
     if (ln->ev_used + 2 > ln->ev_pool.size()) {
       for (int i = 0; i < 64; ++i) {
@@ -484,6 +498,10 @@ struct ProfScope {
   }
   // records the closing event (once; the destructor closes a scope still open)
   void end() {
+    if (range) {
+      nvtxRangePop();
+      range = false;
+    }
     if (!on) return;
     on = false;
     cudaEventRecord(ln->ev_pool[ln->ev_used + 1], ln->stream);
@@ -1083,6 +1101,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
       CK(cudaMemcpyAsync(ln->attn_items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
   }
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    NvtxRange nvtx_batch("as.encoder_batch");
     const Chunk& ch = chunks[ci];
     double af = 0;  // attention FLOPs of the batch: QK^T and PV, 2 * 2 * L^2 * d per sequence
     for (uint64_t i = ch.s0; i < ch.s1; ++i) af += 4.0 * (double)seqs[i].len * seqs[i].len * g.d_model;
