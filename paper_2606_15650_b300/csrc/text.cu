@@ -2,9 +2,12 @@
 //
 // Tokenizer: maximal runs of [0-9A-Za-z] are split greedily into the longest
 // vocabulary strings (2..12 bytes), falling back to single bytes; every other
-// byte is a token of its own (id = byte + 1). One thread walks each run; the
-// starts are then compacted in byte order by a prefix sum, so token order is
-// byte order and every record owns a contiguous token range.
+// byte is a token of its own (id = byte + 1). A block collects the run
+// starts of a tile and one thread walks each run; the token starts are then
+// compacted in byte order by a prefix sum whose last pass writes each token
+// at its rank, so token order is byte order and every record owns a
+// contiguous token range. (as_tokenize_static keeps the scan + emit pair
+// over a per-byte position array, which lives in its fixed scratch.)
 //
 // Recognizers: a word is a maximal run of [A-Za-z0-9.:-]; trailing '.', '-'
 // and a ':' that does not close a final '::' are stripped; the whole word is
@@ -12,9 +15,10 @@
 // UUID, certificate fingerprint, OID, first enabled match wins, port excluded
 // from the span. Before the word tests, the multi-word recognizers (PEM
 // certificate at a line start, URL, CPE name) are tried at the word start.
-// One thread per word start. A second pass, one warp per record, takes the
-// candidates left to right and drops those that start inside an accepted
-// multi-word span (the behaviour of a scanning regex engine).
+// One thread per word start (collected per tile, as for the tokenizer). A
+// second pass, one warp per record, takes the candidates left to right and
+// drops those that start inside an accepted multi-word span (the behaviour
+// of a scanning regex engine).
 #include <algorithm>
 #include <atomic>
 
