@@ -44,13 +44,12 @@ METRIC = "tokens/s per B300, BF16/FP8 vs FP32 at >=99.9% label match; p50/p99 la
 
 # DRAM bytes (read + write) of the four projection GEMMs of one layer at
 # 65,536 rows, from one ncu capture of the GEMM source with this SHA-256
-# prefix (profiles/gemm_tc_c2_layer_65536rows.md); reported only while the
-# source is unchanged. A, C and the residual scale with the rows, so a launch
-# of R rows moves about mean(bytes) * R / 65,536.
+# prefix; reported only while the source is unchanged. A, C and the residual
+# scale with the rows, so a launch of R rows moves about
+# mean(bytes) * R / 65,536.
 GEMM_TRAFFIC = {"source_sha256": "2d587374f11ccc47", "rows": 65536,
                 "bytes": {"qkv": 103788800 + 247970560, "attn_out": 302105088 + 245901312,
-                          "ffn1": 105139968 + 347319552, "ffn2": 614247936 + 256188672},
-                "profile": "profiles/gemm_tc_c2_layer_65536rows.md"}
+                          "ffn1": 105139968 + 347319552, "ffn2": 614247936 + 256188672}}
 
 
 def parse():

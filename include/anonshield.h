@@ -409,9 +409,9 @@ as_status as_serve_stop(as_ctx* ctx);
  * Configurations: bit 0 = tile order (0: along N within a 128-row block,
  * 1: along M within a column block), bit 1 = 128-column tiles with 6
  * pipeline stages instead of 256-column tiles with 4 (configurations
- * without bit 1 need N % 256 == 0), bit 2 = pairs of CTAs (a cluster of
- * two, on the tiles of two adjacent 128-row blocks) that load the shared
- * weight tile once, half each, by TMA multicast into both; -1 = the built-in
+ * without bit 1 need N % 256 == 0), bit 2 = 2-SM pairs (a cluster of two
+ * CTAs computing one 256-row tile with cta_group::2 MMAs; each CTA loads its
+ * own 128 A rows and half of the weight tile, no multicast); -1 = the built-in
  * default (cfg 0 when valid, else 2). A post-LN block run as one fused
  * kernel (roles 1 and 3, see as_config.no_fused_ln) has four choices: cfg 0
  * (single-CTA tiles), 4 (2-SM pairs), and each | 2 (a shorter main-loop ring
@@ -477,11 +477,12 @@ as_status as_profile(as_ctx* ctx, uint32_t enable);
 as_status as_profile_read(as_ctx* ctx, as_profile_stats* stats);
 
 /* Tokenizer that allocates no memory. The paper has no counterpart: this is
- * for callers that cannot call cudaMalloc, such as code running while a CUDA
- * graph is being captured, hosts whose device memory belongs to their own
- * allocator, or latency-bound loops where an allocation would synchronize
- * the device. It runs the same tokenizer as as_anonymize, with its scratch
- * memory in a fixed-size array inside the library instead of ctx buffers.
+ * for callers that cannot call cudaMalloc, such as hosts whose device memory
+ * belongs to their own allocator (reserved up front and handed out by the
+ * host itself), or latency-bound loops where an allocation would synchronize
+ * the device and stall work already queued on it. It runs the same tokenizer
+ * as as_anonymize, with its scratch memory in a fixed-size array inside the
+ * library instead of ctx buffers.
  * All pointers are device pointers on the ctx's device:
  *   bytes[n_bytes], offsets[n_records + 1] (offsets[n_records] == n_bytes),
  *   outputs tok_ids / tok_off (byte offset in `bytes`) / tok_len with room
@@ -492,7 +493,9 @@ as_status as_profile_read(as_ctx* ctx, as_profile_stats* stats);
  * 6.4 MB) stays on every device that loads the library until exit. The first
  * call on a device looks the array up (cudaGetSymbolAddress): make it before
  * any stream capture. Every call reuses the same array, so calls that overlap
- * on the GPU (other streams or host threads) race: serialize them. */
+ * on the GPU (other streams or host threads) race: serialize them. The call
+ * makes the ctx's device current while it runs and restores the caller's
+ * current device before returning. */
 #define AS_STATIC_MAX_BYTES (1u << 20)
 as_status as_tokenize_static(as_ctx* ctx, const uint8_t* bytes, const uint64_t* offsets, uint64_t n_records,
                              uint64_t n_bytes, int32_t* tok_ids, uint32_t* tok_off, uint32_t* tok_len,

@@ -747,13 +747,34 @@ class Context:
 STATIC_MAX_BYTES = 1 << 20
 
 
+def _require_device_tensor(t, name: str, dtypes: tuple, device: int):
+    """Refuse anything the kernels cannot read in place: a host tensor, another GPU's
+    memory, a strided view or the wrong element type would hand the device a pointer it
+    cannot use (a fault) or bytes it misreads (wrong tokens)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise AnonShieldError(-1, f"{name} must be a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda or t.device.index != device:
+        raise AnonShieldError(-1, f"{name} must be on cuda:{device} (the context's device), got {t.device}")
+    if not t.is_contiguous():
+        raise AnonShieldError(-1, f"{name} must be contiguous")
+    if t.dtype not in dtypes:
+        raise AnonShieldError(-1, f"{name} has dtype {t.dtype}, expected one of {', '.join(map(str, dtypes))}")
+
+
 def tokenize_static(ctx: "Context", data, offsets, stream=None) -> dict:
     """Tokenize device-resident records without any allocation inside the call.
 
-    data (uint8) and offsets (int64/uint64, n+1) are CUDA tensors. The output
-    tensors are allocated here, by the caller side, before the call; the
-    library call itself allocates nothing. Returns the outputs as tensors."""
+    data (uint8) and offsets (int64/uint64, n+1) are contiguous CUDA tensors
+    on the context's device; anything else is refused with AS_ERR_ARG before
+    the library is called. The output tensors are allocated here, by the
+    caller side, before the call; the library call itself allocates nothing.
+    Returns the outputs as tensors."""
     import torch
+    _require_device_tensor(data, "data", (torch.uint8,), ctx.device)
+    _require_device_tensor(offsets, "offsets", (torch.int64, torch.uint64), ctx.device)
+    if offsets.dim() != 1 or offsets.numel() < 1:
+        raise AnonShieldError(-1, "offsets must be a 1-D tensor of n_records + 1 entries")
     n = offsets.numel() - 1
     n_bytes = int(data.numel())
     dev = data.device

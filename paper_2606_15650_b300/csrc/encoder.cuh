@@ -15,9 +15,10 @@ as_status gemm_tcgen05(int epi, int64_t M, int64_t N, int64_t K, const void* A, 
 // epilogue) or E4M3 (out_e4m3, GELU epilogue only, value / out_scale with
 // saturation); out = epi(alpha * (A . B^T)). cfg: tile configuration
 // 0..kGemmCfgs-1 (bit 0: tile order along M instead of N; bit 1: 128-column
-// tiles, 6 stages, instead of 256-column tiles, 4 stages; bit 2: CTA pairs
-// sharing the weight tile by TMA multicast), -1 = the default (256-column
-// tiles when N allows, order along N, no pairs).
+// tiles, 6 stages, instead of 256-column tiles, 4 stages; bit 2: 2-SM
+// cta_group::2 pairs on a 256-row tile, each CTA loading its own A rows and
+// half of the weight tile, no multicast), -1 = the default (256-column tiles
+// when N allows, order along N, no pairs).
 constexpr int kGemmCfgs = 8;
 bool gemm_tcgen05_cfg_valid(int cfg, int64_t N);
 // Post-LN residual block in one kernel: x32 <- LN(x32 + alpha (A . B^T) + bias)

@@ -1,8 +1,9 @@
 // Tokenizer entry point that allocates no memory (as_tokenize_static).
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, hosts whose device memory is owned by their own allocator,
-// and latency-bound loops where an allocation would synchronize the device.
+// Some callers cannot call cudaMalloc: hosts whose device memory is owned by
+// their own allocator (a framework that reserved the GPU's memory up front and
+// hands out pieces of it itself), and latency-bound loops where an allocation
+// would synchronize the device and stall work already queued on it.
 // This entry point runs the same tokenizer kernels as as_anonymize, but its
 // scratch memory (record-start bitmap, per-byte token ids, per-byte prefix
 // sums, scan tile sums) lives in one file-scope __device__ array of fixed
@@ -19,7 +20,9 @@
 //     that first call before any stream capture;
 //   - all calls share the one array and it keeps the last call's contents:
 //     what must start at zero is cleared on every call, but two calls that
-//     overlap on the GPU (different streams or host threads) race.
+//     overlap on the GPU (different streams or host threads) race;
+//   - the call makes the ctx's device current while it runs and restores the
+//     caller's current device before it returns.
 #include <mutex>
 
 #include "scan.cuh"
@@ -68,6 +71,17 @@ void* scratch_address(int device, cudaError_t* err) {
   return g_scratch_addr[device];
 }
 
+// Restores the caller's current device when the entry point returns.
+struct DeviceRestore {
+  int saved = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&saved) != cudaSuccess) saved = -1;
+  }
+  ~DeviceRestore() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
+
 struct NonZeroTok {
   const uint16_t* p;
   __device__ uint32_t operator()(uint64_t i) const { return p[i] != 0; }
@@ -104,6 +118,7 @@ extern "C" as_status as_tokenize_static(as_ctx* ctx, const uint8_t* bytes, const
     set_k_error("as_tokenize_static: NULL input or output pointer");
     return AS_ERR_ARG;
   }
+  DeviceRestore restore;
   AS_CUDA_OK(cudaSetDevice(device));
   cudaError_t e;
   uint8_t* base = static_cast<uint8_t*>(scratch_address(device, &e));

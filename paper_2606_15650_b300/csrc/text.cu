@@ -106,18 +106,22 @@ constexpr uint32_t kMarkTile = 4096;
 
 // Blocks of a mark kernel that fit on the device at once (the kernels loop
 // over tiles with a grid stride, so a second wave of blocks would start late
-// with a full share of tiles), looked up once per kernel.
+// with a full share of tiles), looked up once per kernel and device (the
+// current one: every launcher runs with the ctx's device current).
 template <typename Kernel>
 unsigned resident_blocks(Kernel kernel, uint64_t tiles) {
-  static std::atomic<int> cap{0};
-  int c = cap.load();
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cap[kMaxDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+  int c = cap[slot].load();
   if (c == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kMarkThreads, 0);
     c = std::max(1, per_sm * sms);
-    cap.store(c);
+    if (dev >= 0 && dev < kMaxDevices) cap[slot].store(c);
   }
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)c));
 }

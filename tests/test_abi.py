@@ -2,6 +2,8 @@
 import os
 import re
 
+import pytest
+
 import paper_2606_15650_b300.api as api
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -35,3 +37,23 @@ def test_structs_match_header_sizes():
     import ctypes as C
     assert C.sizeof(api._Records) == 32
     assert C.sizeof(api._Entity) == 4 + 4 + 8 + 65 + 65 + 6 + 24
+
+
+def test_tokenize_static_refuses_unusable_tensors():
+    """The no-allocation tokenizer's binding refuses, before any library call, tensors the
+    kernels could not read in place: host memory, wrong dtypes, strided views."""
+    import torch
+
+    class FakeCtx:
+        device = 0
+        _h = None
+
+    good_offs = torch.tensor([0, 4], dtype=torch.int64)
+    cases = [
+        (torch.zeros(4, dtype=torch.uint8), good_offs, "cuda:0"),            # host tensor
+        (b"abcd", good_offs, "torch CUDA tensor"),                            # not a tensor
+    ]
+    for data, offs, msg in cases:
+        with pytest.raises(api.AnonShieldError) as e:
+            api.tokenize_static(FakeCtx(), data, offs)
+        assert e.value.status == -1 and msg in str(e.value)

@@ -28,8 +28,9 @@ def setup(vocab_words, c1_records):
 
 @pytest.mark.parametrize("prec,fused_ln", [("bf16", True), ("bf16", False), ("fp8", False)])
 def test_all_tile_configurations_identical(setup, vocab_words, prec, fused_ln):
-    """Every configuration, CTA pairs with multicast weight tiles included (the
-    residual projections run on them only when the LayerNorm is not fused)."""
+    """Every configuration, 2-SM pairs included (each CTA of a pair loads half of the
+    weight tile; the residual projections run on them only when the LayerNorm is not
+    fused)."""
     blob, rs = setup
     ctx = api.Context(DIMS, blob, vocab_words, precision=prec, keep_trace=True, fused_ln=fused_ln)
     if prec == "fp8":

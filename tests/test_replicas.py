@@ -17,6 +17,7 @@ import paper_2606_15650_b300.api as api
 from paper_2606_15650_b300 import replicas
 from oracle import pipeline as P
 from oracle.encoder import Encoder
+from oracle.tokenizer import build_vocab_index
 from oracle.pseudonym import merge_maps
 
 DIMS = synth.C1.dims
@@ -29,7 +30,7 @@ def _tuples(entries):
 
 def _oracle_run(recs, base=0):
     w = synth.make_weights(DIMS, seed=31, random_affine=True)
-    vocab = {wd: i for i, wd in enumerate(synth.make_vocab())}
+    vocab = build_vocab_index(synth.make_vocab())
     sch = P.Schema(synth.TYPE_NAMES_4)
     return P.anonymize(recs, sch, synth.make_key(), Encoder(DIMS, w), vocab, record_base=base, keep_traces=False)
 

@@ -1,8 +1,8 @@
 """The tokenizer entry point that allocates nothing (as_tokenize_static).
 
-It exists for callers that cannot call cudaMalloc (code running under CUDA
-graph capture, hosts that own all device memory through their own allocator,
-loops where an allocation would synchronize the device). Its scratch is a
+It exists for callers that cannot call cudaMalloc (hosts that own all device
+memory through their own allocator, loops where an allocation would
+synchronize the device and stall queued work). Its scratch is a
 fixed array inside the library, shared by every call. This test calls it
 through the C ABI twice in a row, the second time on a smaller batch so that
 stale contents left in the shared array by the first call would show, and
@@ -52,3 +52,17 @@ def test_static_tokenizer_rejects_oversize(vocab_words):
     with pytest.raises(api.AnonShieldError) as e:
         api.tokenize_static(ctx, big, offs)
     assert e.value.status == -1 and "static limit" in str(e.value)
+
+
+def test_static_tokenizer_refuses_unusable_tensors(vocab_words):
+    """Tensors the kernels cannot read in place are refused before the call: int32
+    offsets (the kernels read 64-bit offsets), a strided view of the bytes, host offsets."""
+    dims = synth.C1.dims
+    ctx = api.Context(dims, synth.pack_blob(dims, synth.make_weights(dims, seed=3)), vocab_words)
+    data = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    offs = torch.tensor([0, 32], dtype=torch.int64, device="cuda")
+    for d, o, msg in ((data[:32], offs.int(), "dtype"), (data[::2], offs, "contiguous"),
+                      (data[:32], offs.cpu(), "cuda:0")):
+        with pytest.raises(api.AnonShieldError) as e:
+            api.tokenize_static(ctx, d, o)
+        assert e.value.status == -1 and msg in str(e.value)
