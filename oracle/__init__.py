@@ -11,7 +11,9 @@ Modules, in pipeline order:
   tokenizer      byte pre-tokenization and greedy longest-match subwords
   recognizers    pattern recognizers: MAC, IPv6, IPv4 (+port), CVE, host name (+port), hash,
                  UUID, certificate fingerprint, OID, PEM certificate, URL, CPE
-  encoder        encoder-only token classifier, FP64, with sliding windows
+  encoder        encoder-only token classifier, FP64, with sliding windows; BF16 and
+                 FP8 E4M3 GEMM-input rounding emulated on request
+  lowp           BF16 and E4M3 rounding written from the formats' definitions
   bio            BIO label decoding to token spans
   spans          token -> byte spans, overlap rule, preserve filter
   sha256         SHA-256 written from FIPS 180-4

@@ -107,3 +107,49 @@ def check_final_spans(tr: dict, offsets: np.ndarray, iso_traces, idx=None):
 
 def map_tuples(entries) -> list[tuple]:
     return [(e.type, e.original, e.full_hash, e.first_seen, e.last_seen, e.count) for e in entries]
+
+
+def oracle_logits(enc, records: list[bytes], vocab_index, window: int = 0, stride: int = 0) -> list[np.ndarray]:
+    """Per-record logits of the oracle's encoder on the oracle's own tokens."""
+    from oracle.encoder import record_logits
+    from oracle.tokenizer import tokenize
+    return [record_logits(enc, tokenize(r, vocab_index)[0], window, stride) for r in records]
+
+
+def logit_stats(tr: dict, n: int, ref: list[np.ndarray], idx=None) -> dict:
+    """Max / rms |logit error| of the GPU trace against reference logits per record, and
+    the label agreement over tokens whose reference top-2 margin exceeds MARGIN."""
+    sl = split_tokens(tr, n)
+    idx = range(len(ref)) if idx is None else idx
+    errs, conf, agree, flips = [], 0, 0, []
+    for j, i in enumerate(idx):
+        r = ref[j]
+        if len(r) == 0:
+            continue
+        g = tr["logits"][sl[i]].astype(np.float64)
+        assert g.shape == r.shape, f"record {i}: {g.shape} logits vs {r.shape}"
+        errs.append(np.abs(g - r).ravel())
+        srt = np.sort(r, axis=1)
+        margin = srt[:, -1] - srt[:, -2]
+        lab, rl = tr["labels"][sl[i]].astype(np.int64), np.argmax(r, axis=1)
+        c = margin > MARGIN
+        conf += int(c.sum())
+        agree += int((lab[c] == rl[c]).sum())
+        flips += [float(m) for m in margin[lab != rl]]
+    e = np.concatenate(errs) if errs else np.zeros(1)
+    return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e ** 2))), "tokens": int(e.size // ref[0].shape[1]),
+            "agreement": agree / conf if conf else 1.0, "confident": conf, "flips": flips}
+
+
+def logit_stats_ref(a: list[np.ndarray], b: list[np.ndarray]) -> dict:
+    """Max / rms |a - b| and label agreement of a against b (b's top-2 margin > MARGIN), oracle vs oracle."""
+    e = np.concatenate([np.abs(x - y).ravel() for x, y in zip(a, b) if len(y)])
+    conf = agree = 0
+    for x, y in zip(a, b):
+        if not len(y):
+            continue
+        srt = np.sort(y, axis=1)
+        c = (srt[:, -1] - srt[:, -2]) > MARGIN
+        conf += int(c.sum())
+        agree += int((np.argmax(x, axis=1)[c] == np.argmax(y, axis=1)[c]).sum())
+    return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e ** 2))), "agreement": agree / conf if conf else 1.0}

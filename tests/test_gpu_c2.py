@@ -3,7 +3,7 @@
 This is the launch configuration the benchmark times. The oracle is too
 slow for the whole batch, so it checks seeded samples record by record
 (tokens, recognizer spans, output bytes from the GPU's labels; FP64 logits
-on a few records), and properties that hold at any size are checked on the
+on sampled records), and properties that hold at any size are checked on the
 whole batch: tokens tile every record's bytes; every byte outside the
 final spans is copied to its shifted position; every span is replaced by
 "[TYPE_slug]" at its shifted position with the HMAC slug; record offsets
@@ -19,6 +19,7 @@ import synth
 import paper_2606_15650_b300.api as api
 from oracle import pipeline as P
 from oracle.encoder import Encoder
+from oracle.tokenizer import tokenize
 
 import parity_util as U
 
@@ -56,14 +57,16 @@ def test_sampled_records_exact(c2, vocab_index):
 
 
 def test_sampled_logits_fp64(c2, vocab_index):
+    """FP64 logits of sampled records of the whole-dataset batch (the benchmark's launch
+    configuration), from the oracle's own tokens; 64 more records are compared in
+    test_gpu_precision.py."""
     recs, w, key, ctx, out, tr, _, _ = c2
     rng = np.random.default_rng(7)
-    idx = sorted(rng.choice(recs.n, size=6, replace=False).tolist())
+    idx = sorted(rng.choice(recs.n, size=12, replace=False).tolist())
     enc = Encoder(DIMS, w)
-    sl = U.split_tokens(tr, recs.n)
     traces = {}
     for i in idx:
-        ids = tr["tok_ids"][sl[i]].tolist()
+        ids = tokenize(recs.record(i), vocab_index)[0]
 
         class T:  # minimal trace with the oracle's logits and labels
             pass
