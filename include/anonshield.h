@@ -193,13 +193,17 @@ typedef struct {
   uint64_t n_fields, n_malformed;
 } as_stats;
 
-/* Encoder batches of at most AS_GRAPH_MAX_ROWS rows (BF16 / FP8 contexts,
- * tcgen05 attention, profiling off) are padded to a power-of-two number of
- * rows and of attention work items and run as one launch of a CUDA graph
- * captured the first time that shape is seen (per lane; up to 16 shapes are
- * kept). Padded rows belong to no record and padded work items to an empty
- * sequence, so results are bit-identical to kernel-by-kernel launches. The
- * first encoder batch of a lane always runs kernel by kernel. */
+/* Encoder batches of BF16 / FP8 contexts with the tcgen05 attention
+ * (profiling off) run as one launch of a CUDA graph captured the first time
+ * their shape bucket is seen (per lane; up to 16 buckets are kept). Rows and
+ * attention work items are padded to the bucket: a power of two up to
+ * AS_GRAPH_MAX_ROWS, above that the next multiple of 1/16 of the next power
+ * of two (at most 6.25 % padding; full packed batches of the default 2^19-row
+ * cap fill their bucket exactly, so every full batch of a call replays one
+ * graph). Each batch's work items are copied into one fixed lane buffer
+ * before the replay. Padded rows belong to no record and padded work items to
+ * an empty sequence, so results are bit-identical to kernel-by-kernel
+ * launches. The first encoder batch of a lane always runs kernel by kernel. */
 #define AS_GRAPH_MAX_ROWS 16384
 
 /* Create a context: loads weights and vocabulary onto `device`, creates the
@@ -370,24 +374,44 @@ as_status as_anonymize_stream(as_ctx* ctx, const as_records* records, const as_s
 
 /* Serving loop (continuous batching). After as_serve_start the ctx accepts
  * single records with as_submit from any thread; worker threads (one per
- * lane, each with its own CUDA stream and buffers) take the oldest admitted
- * requests up to max_batch_bytes, run the whole path on them and post the
- * results; with two or more lanes a batch starts while others are still on
- * the GPU. A request's record index (first_seen / last_seen) is its request
- * id, and every step computes a record from that record's data alone, so the
- * result of a request is the same alone and in any mix. The entity map stays
- * on the device; as_map_export gives a snapshot. as_anonymize and
- * as_calibrate return AS_ERR_STATE while serving. */
+ * lane, each with its own CUDA stream and buffers) take the oldest waiting
+ * requests, run the whole path on them and post the results; with two or
+ * more lanes a batch starts while others are still on the GPU.
+ *
+ * Admission is by device memory: activation_budget_bytes bounds the encoder
+ * activations of all lanes together (a 1/lanes share each). A lane's share
+ * fixes its row cap R: the most encoder rows whose activation buffers (per
+ * row: the FP32 residual and pre-LN rows, the BF16 / E4M3 GEMM inputs, QKV,
+ * attention output and FFN rows, row indices; padded to the graph bucket)
+ * fit the share. A worker admits the oldest requests while the
+ * rows they can occupy at most (a record of b bytes has at most b tokens;
+ * windows and the 8-row alignment added) stay within R; the first request is
+ * always admitted, and encoder batches never exceed R rows (a long record
+ * runs as several), so a lane's activation buffers stay within its share.
+ * max_batch_bytes and max_batch_records are further caps (0 = none / 65536).
+ * as_serve_start fails with AS_ERR_ARG if a share cannot hold one full
+ * sequence (max_pos rows).
+ *
+ * A request's record index (first_seen / last_seen) is its request id, and
+ * every step computes a record from that record's data alone, so the result
+ * of a request is the same alone and in any mix. The entity map stays on the
+ * device; as_map_export gives a snapshot. as_anonymize and as_calibrate
+ * return AS_ERR_STATE while serving. */
 typedef struct {
   uint32_t lanes;              /* concurrent batches on the GPU; 0 = 2        */
-  uint64_t max_batch_bytes;    /* admission budget per batch; 0 = 3/4 of max_chunk_tokens */
+  uint64_t max_batch_bytes;    /* record bytes per batch; 0 = no byte cap     */
   uint32_t max_batch_records;  /* 0 = 65536                                    */
   uint64_t max_pending;        /* queue bound (AS_ERR_AGAIN beyond); 0 = 2^20 */
+  uint64_t activation_budget_bytes; /* encoder activations, all lanes; 0 = 40 GiB */
 } as_serve_config;
 typedef struct {
   uint64_t completed, rejected, failed, batches, tokens, pending;
   double seconds;              /* since start or the last reset               */
   double p50_ms, p99_ms, max_ms; /* submit -> result ready, completed requests */
+  uint64_t activation_budget;  /* bytes, all lanes                            */
+  uint64_t row_cap;            /* encoder rows per batch and lane             */
+  uint64_t activation_bytes;   /* activation buffers the lanes hold now       */
+  uint64_t activation_peak;    /* the most they held at once since start      */
 } as_serve_stats_t;
 #define AS_SUBMIT_DISCARD 1u   /* drop the result (load tests): latency only  */
 as_status as_serve_start(as_ctx* ctx, const as_schema* schema, const uint8_t* key, size_t key_len,

@@ -96,12 +96,13 @@ class _Trace(C.Structure):
 
 class _ServeConfig(C.Structure):
     _fields_ = [("lanes", C.c_uint32), ("max_batch_bytes", C.c_uint64), ("max_batch_records", C.c_uint32),
-                ("max_pending", C.c_uint64)]
+                ("max_pending", C.c_uint64), ("activation_budget_bytes", C.c_uint64)]
 
 
 class _ServeStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("completed", "rejected", "failed", "batches", "tokens", "pending")] + \
-               [(n, C.c_double) for n in ("seconds", "p50_ms", "p99_ms", "max_ms")]
+               [(n, C.c_double) for n in ("seconds", "p50_ms", "p99_ms", "max_ms")] + \
+               [(n, C.c_uint64) for n in ("activation_budget", "row_cap", "activation_bytes", "activation_peak")]
 
 
 class _Fields(C.Structure):
@@ -660,10 +661,11 @@ class Context:
 
     # ---- serving loop (continuous batching)
     def serve_start(self, schema: Schema, key: bytes, lanes: int = 2, max_batch_bytes: int = 0,
-                    max_batch_records: int = 0, max_pending: int = 0):
+                    max_batch_records: int = 0, max_pending: int = 0, activation_budget: int = 0):
+        """activation_budget: bytes of encoder activations over all lanes (0 = 40 GiB)."""
         sc, names = self._schema(schema)
         cfg = _ServeConfig(lanes=lanes, max_batch_bytes=max_batch_bytes, max_batch_records=max_batch_records,
-                           max_pending=max_pending)
+                           max_pending=max_pending, activation_budget_bytes=activation_budget)
         self._check(load().as_serve_start(self._h, C.byref(sc), key, len(key), C.byref(cfg)))
         del names
 

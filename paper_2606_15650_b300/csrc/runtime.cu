@@ -8,6 +8,7 @@
 // Device buffers are owned by the ctx and only grow, so a steady stream of
 // calls allocates nothing after warm-up.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -125,8 +126,9 @@ struct SeqDesc {
 
 struct Chunk {
   uint64_t s0, s1;   // sequences
-  uint64_t rows;
+  uint64_t rows;     // rows of the batch (sequences start on multiples of 8)
   uint32_t max_len;
+  uint64_t tokens;   // rows that hold a token (the sum of the sequence lengths)
 };
 
 // cnt[5] = cnt[3] + cnt[4] (kept spans: recognizer + NER), on the device.
@@ -164,7 +166,7 @@ struct Lane {
   DBuf ner_s, ner_l, ner_t, keep, pos_k, nk_s, nk_l, nk_t, rk_s, rk_l, rk_t;
   DBuf fin_s, fin_l, fin_t, digests, delta, shift;
   DBuf names, name_off, name_len;
-  DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len, attn_items;
+  DBuf seqs, row_tok, row_pos, row_own, seq_start, seq_len, attn_items, attn_cur;
   DBuf f_bytes, f_off, f_start, f_sub_off, f_sub, fs_s, fs_l, fs_t, fr_s, fr_l, fr_t, f_keep, f_pos, f_cnt, ff_s, ff_l,
       ff_t;
   DBuf rid_ok, rid_tk, rid_tv, rid_len, rid_slot, rid_flag, rid_pos, rid_s, rid_l, rid_k;
@@ -193,6 +195,10 @@ struct Lane {
   std::vector<EncGraph> graphs;
   uint64_t graph_clock = 0, graph_replays = 0;
   bool enc_warm = false;  // an encoder batch ran kernel by kernel on this lane
+  // encoder batches of this lane hold at most row_cap rows (0: the ctx's
+  // max_chunk_tokens); serving lanes take it from the activation budget
+  uint64_t row_cap = 0;
+  std::atomic<uint64_t> act_bytes{0};  // bytes of the encoder activation buffers now held
   // pinned host staging (streaming): one batch's bytes and rebased offsets
   uint8_t* h_in = nullptr;
   size_t h_in_cap = 0;
@@ -256,7 +262,7 @@ void Lane::release_all() {
                  &tok_ids, &tok_off, &tok_len, &rec_tok, &rx_len_b, &rx_type_b, &rx_s, &rx_l, &rx_t, &labels, &logits,
                  &tok_flags, &bio_start, &bio_end, &pos_t, &ner_s, &ner_l, &ner_t, &keep, &pos_k, &nk_s,
                  &nk_l, &nk_t, &rk_s, &rk_l, &rk_t, &fin_s, &fin_l, &fin_t, &digests, &delta, &shift, &names,
-                 &name_off, &name_len, &seqs, &attn_items, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
+                 &name_off, &name_len, &seqs, &attn_items, &attn_cur, &f_bytes, &f_off, &f_start, &f_sub_off, &f_sub, &fs_s,
                  &fs_l, &fs_t, &fr_s, &fr_l, &fr_t, &f_keep, &f_pos, &f_cnt, &ff_s, &ff_l, &ff_t, &row_tok, &row_pos, &row_own, &seq_start, &seq_len, &X32, &X16, &QKV,
                  &ATT, &Y32, &H, &X8, &ATT8, &H8,
                   &rid_ok, &rid_tk, &rid_tv, &rid_len, &rid_slot, &rid_flag, &rid_pos, &rid_s, &rid_l, &rid_k,
@@ -533,7 +539,7 @@ void prof_collect(Lane* ln) {
   ln->ev_used = 0;
 }
 
-constexpr uint64_t kGraphMaxRows = AS_GRAPH_MAX_ROWS;
+constexpr uint64_t kGraphSmallRows = AS_GRAPH_MAX_ROWS;
 constexpr size_t kGraphCache = 16;
 
 uint64_t pow2_at_least(uint64_t x, uint64_t lo) {
@@ -542,13 +548,24 @@ uint64_t pow2_at_least(uint64_t x, uint64_t lo) {
   return v;
 }
 
-// Rows a batch occupies in the encoder buffers: graph-eligible batches are
-// padded to a power of two so that one captured graph serves every batch of
-// that size.
-bool graphable(const as_config& g, uint64_t rows) {
-  return !g.no_graphs && g.precision != AS_FP32 && g.attention == AS_ATTN_TCGEN05 && rows <= kGraphMaxRows;
+// Graph shape bucket of a count x (rows or attention work items): a power of
+// two (at least lo) up to kGraphSmallRows, above that the next multiple of
+// 1/16 of the next power of two (at most 6.25 % padding), so that one
+// captured graph serves every batch of the same bucket. Full packed batches
+// (just under the row cap, a power of two by default) share one bucket.
+uint64_t graph_bucket(uint64_t x, uint64_t lo) {
+  const uint64_t p = pow2_at_least(x, lo);
+  if (p <= kGraphSmallRows) return p;
+  const uint64_t q = p / 16;
+  return (x + q - 1) / q * q;
 }
-uint64_t encoder_rows(const as_config& g, uint64_t rows) { return graphable(g, rows) ? pow2_at_least(rows, 128) : rows; }
+
+// Encoder batches of BF16 / FP8 contexts with the tcgen05 attention run as
+// graphs (graphs on); their rows are padded to the bucket.
+bool graphable(const as_config& g) {
+  return !g.no_graphs && g.precision != AS_FP32 && g.attention == AS_ATTN_TCGEN05;
+}
+uint64_t encoder_rows(const as_config& g, uint64_t rows) { return graphable(g) ? graph_bucket(rows, 128) : rows; }
 
 // Post-LN residual block `block` (0 attention, 1 feed-forward) as one
 // clustered GEMM + LayerNorm kernel, and whether that kernel runs on 2-SM
@@ -564,7 +581,7 @@ bool ln_deep(const int cfg, int) { return cfg >= 0 && (cfg & 2) != 0; }
 // Embedding, the layers and the classifier over R rows (everything of an
 // encoder batch whose launch shapes depend only on R and n_items).
 as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_len, double attn_flops,
-                       bool want_logits, const int32_t* attn_items, int32_t n_items) {
+                       bool want_logits, const int32_t* attn_items, int32_t n_items, int64_t R_alg) {
   const as_config& g = c->cfg;
   const int32_t d = (int32_t)g.d_model, f = (int32_t)g.d_ffn;
   cudaStream_t st = ln->stream;
@@ -596,7 +613,7 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       __nv_bfloat16* QKV = ln->QKV.as<__nv_bfloat16>();
       uint8_t* ATT8 = ln->ATT8.as<uint8_t>();
       uint8_t* H8 = ln->H8.as<uint8_t>();
-      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d);
+      { ProfScope ps(ln, 0, 2.0 * R_alg * 3 * d * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS, true, false, R, 3 * d, d, X8, L.w_qkv8, L.b_qkv, nullptr, QKV,
                             sc[0] * L.s_qkv, 1.0f, err, st, c->gemm_cfg[0])); }
       { ProfScope ps(ln, 1, attn_flops);
@@ -607,32 +624,32 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
           CKS(attention_bf16_e4m3(QKV, ATT8, sc[1], ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns,
                                   (int32_t)max_len, d, (int32_t)g.n_heads, st)); }
       if (fuse_ln) {
-        ProfScope ps(ln, 0, 2.0 * R * d * d);
+        ProfScope ps(ln, 0, 2.0 * R_alg * d * d);
         CKS(gemm_tcgen05_resid_ln(true, R, d, d, ATT8, L.w_o8, L.b_o, X32, L.ln1_g, L.ln1_b, nullptr, X8, sc[2],
                                   sc[1] * L.s_o, err, st, pair1, deep1));
       } else {
-        { ProfScope ps(ln, 0, 2.0 * R * d * d);
+        { ProfScope ps(ln, 0, 2.0 * R_alg * d * d);
           CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, d, ATT8, L.w_o8, L.b_o, X32, Y32, sc[1] * L.s_o,
                               1.0f, err, st, c->gemm_cfg[1])); }
         CKS(layernorm_rows_ex(Y32, L.ln1_g, L.ln1_b, X32, nullptr, X8, sc[2], R, d, st));
       }
-      { ProfScope ps(ln, 0, 2.0 * R * f * d);
+      { ProfScope ps(ln, 0, 2.0 * R_alg * f * d);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, true, true, R, f, d, X8, L.w_1_8, L.b_1, nullptr, H8, sc[2] * L.s_1,
                             sc[3], err, st, c->gemm_cfg[2])); }
       if (fuse_ln2 && !last) {
-        ProfScope ps(ln, 0, 2.0 * R * d * f);
+        ProfScope ps(ln, 0, 2.0 * R_alg * d * f);
         CKS(gemm_tcgen05_resid_ln(true, R, d, f, H8, L.w_2_8, L.b_2, X32, L.ln2_g, L.ln2_b, nullptr, X8,
                                   as8[kActPerLayer * (l + 1)], sc[3] * L.s_2, err, st, pair2, deep2));
         continue;
       }
-      { ProfScope ps(ln, 0, 2.0 * R * d * f);
+      { ProfScope ps(ln, 0, 2.0 * R_alg * d * f);
         CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, true, false, R, d, f, H8, L.w_2_8, L.b_2, X32, Y32, sc[3] * L.s_2,
                             1.0f, err, st, c->gemm_cfg[3])); }
     } else if (bf) {
       __nv_bfloat16* QKV = ln->QKV.as<__nv_bfloat16>();
       __nv_bfloat16* ATT = ln->ATT.as<__nv_bfloat16>();
       __nv_bfloat16* H = ln->H.as<__nv_bfloat16>();
-      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS, false, false, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, 1.0f, 1.0f, err, st, c->gemm_cfg[0])); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * 3 * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS, false, false, R, 3 * d, d, X16, L.w_qkv16, L.b_qkv, nullptr, QKV, 1.0f, 1.0f, err, st, c->gemm_cfg[0])); }
       if (g.attention == AS_ATTN_TCGEN05) {
         ProfScope ps(ln, 1, attn_flops);
         CKS(attention_tcgen05(QKV, ATT, attn_items, n_items, (int32_t)max_len, R, d, (int32_t)g.n_heads, err, st));
@@ -643,36 +660,36 @@ as_status encoder_body(as_ctx* c, Lane* ln, int64_t R, int32_t ns, uint32_t max_
       }
       if (mode == kEncCalib) amax_bf16(ATT, Rd, amax + kActPerLayer * l + 1, st);
       if (fuse_ln) {
-        ProfScope ps(ln, 0, 2.0 * R * d * d);
+        ProfScope ps(ln, 0, 2.0 * R_alg * d * d);
         CKS(gemm_tcgen05_resid_ln(false, R, d, d, ATT, L.w_o16, L.b_o, X32, L.ln1_g, L.ln1_b, X16, nullptr, 1.0f,
                                   1.0f, err, st, pair1, deep1));
       } else {
-        { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
+        { ProfScope ps(ln, 0, 2.0 * R_alg * d * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, d, ATT, L.w_o16, L.b_o, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[1])); }
         CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, X16, R, d, st));
       }
       if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * l + 2, st);
-      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, false, false, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, 1.0f, 1.0f, err, st, c->gemm_cfg[2])); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * f * d); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_GELU, false, false, R, f, d, X16, L.w_1_16, L.b_1, nullptr, H, 1.0f, 1.0f, err, st, c->gemm_cfg[2])); }
       if (mode == kEncCalib) amax_bf16(H, (uint64_t)R * f, amax + kActPerLayer * l + 3, st);
       if (fuse_ln2 && !last) {
-        { ProfScope ps(ln, 0, 2.0 * R * d * f);
+        { ProfScope ps(ln, 0, 2.0 * R_alg * d * f);
           CKS(gemm_tcgen05_resid_ln(false, R, d, f, H, L.w_2_16, L.b_2, X32, L.ln2_g, L.ln2_b, X16, nullptr, 1.0f,
                                     1.0f, err, st, pair2, deep2)); }
         if (mode == kEncCalib) amax_bf16(X16, Rd, amax + kActPerLayer * (l + 1), st);
         continue;
       }
-      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[3])); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * d * f); CKS(gemm_tcgen05_ex(AS_EPI_BIAS_RESID, false, false, R, d, f, H, L.w_2_16, L.b_2, X32, Y32, 1.0f, 1.0f, err, st, c->gemm_cfg[3])); }
     } else {
       float* QKV = ln->QKV.as<float>();
       float* ATT = ln->ATT.as<float>();
       float* H = ln->H.as<float>();
-      { ProfScope ps(ln, 0, 2.0 * R * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * 3 * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS, R, 3 * d, d, X32, L.w_qkv, L.b_qkv, nullptr, QKV, st)); }
       { ProfScope ps(ln, 1, attn_flops);
         CKS(attention_f32(QKV, ATT, ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>(), ns, (int32_t)max_len, d,
                           (int32_t)g.n_heads, st)); }
-      { ProfScope ps(ln, 0, 2.0 * R * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * d * d); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, d, ATT, L.w_o, L.b_o, X32, Y32, st)); }
       CKS(layernorm_rows(Y32, L.ln1_g, L.ln1_b, X32, nullptr, R, d, st));
-      { ProfScope ps(ln, 0, 2.0 * R * f * d); CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st)); }
-      { ProfScope ps(ln, 0, 2.0 * R * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * f * d); CKS(gemm_simt_f32(AS_EPI_BIAS_GELU, R, f, d, X32, L.w_1, L.b_1, nullptr, H, st)); }
+      { ProfScope ps(ln, 0, 2.0 * R_alg * d * f); CKS(gemm_simt_f32(AS_EPI_BIAS_RESID, R, d, f, H, L.w_2, L.b_2, X32, Y32, st)); }
     }
     if (!last) {
       CKS(layernorm_rows_ex(Y32, L.ln2_g, L.ln2_b, X32, X16, X8, f8 ? as8[kActPerLayer * (l + 1)] : 1.0f, R, d, st));
@@ -690,7 +707,8 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
                             bool want_logits, const int32_t* attn_items, int32_t n_items) {
   const as_config& g = c->cfg;
   const int64_t R = (int64_t)ch.rows;
-  const int64_t Rb = (int64_t)encoder_rows(g, ch.rows);  // R, or its power-of-two bucket
+  const int64_t Rb = (int64_t)encoder_rows(g, ch.rows);  // R, or its graph bucket
+  const int64_t R_alg = (int64_t)ch.tokens;              // rows that hold a token (FLOP accounting)
   const int32_t ns = (int32_t)(ch.s1 - ch.s0);
   cudaStream_t st = ln->stream;
   // padding rows between sequences (and up to the bucket): token 0, position 0, owned by nobody
@@ -703,12 +721,17 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
   expand_rows_kernel<<<ns, 128, 0, st>>>(seq_dev + ch.s0, ln->row_tok.as<int32_t>(), ln->row_pos.as<int32_t>(),
                                          ln->row_own.as<uint8_t>(), ln->seq_start.as<int32_t>(), ln->seq_len.as<int32_t>());
   count_launch();
-  const bool graph = graphable(g, ch.rows);
+  const bool graph = graphable(g);
   if (!graph || !ln->enc_warm || ln->prof || c->calibrating) {
-    CKS(encoder_body(c, ln, graph ? Rb : R, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+    CKS(encoder_body(c, ln, graph ? Rb : R, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items, R_alg));
     ln->enc_warm = true;
     return AS_OK;
   }
+  // the batch's work items go to one fixed lane buffer, so that every batch of
+  // a call (and of later calls) with the same shape bucket replays one graph
+  CKS(grow(ln->attn_cur, std::max<size_t>(1, (size_t)n_items) * 8));
+  if (n_items) CK(cudaMemcpyAsync(ln->attn_cur.p, attn_items, (size_t)n_items * 8, cudaMemcpyDeviceToDevice, st));
+  attn_items = ln->attn_cur.as<int32_t>();
   // one graph launch per batch: look up (or capture) the graph of this shape
   std::vector<uint64_t> sig = {(uint64_t)Rb, (uint64_t)n_items, (uint64_t)want_logits, (uint64_t)g.precision};
   for (const DBuf* b : {&ln->X32, &ln->Y32, &ln->X16, &ln->X8, &ln->QKV, &ln->ATT, &ln->ATT8, &ln->H, &ln->H8,
@@ -736,10 +759,10 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
     const uint64_t l0 = t_launches;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
-      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items, R_alg));
       return AS_OK;
     }
-    const as_status bs = encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items);
+    const as_status bs = encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items, R_alg);
     const cudaError_t ce = cudaStreamEndCapture(st, &gr);
     const uint64_t kernels = t_launches - l0;
     g_launches.fetch_sub(kernels);  // captured, not run: counted when the graph is launched
@@ -749,7 +772,7 @@ as_status run_encoder_chunk(as_ctx* c, Lane* ln, const Chunk& ch, const SeqDesc*
       if (gr) cudaGraphDestroy(gr);
       cudaGetLastError();
       // capture refused: run this batch kernel by kernel
-      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items));
+      CKS(encoder_body(c, ln, Rb, ns, ch.max_len, attn_flops, want_logits, attn_items, n_items, R_alg));
       return AS_OK;
     }
     cudaGraphDestroy(gr);
@@ -790,7 +813,23 @@ as_status ensure_encoder_buffers(as_ctx* c, Lane* ln, uint64_t rows, uint64_t n_
     if (ln->ATT8.p != before) CK(cudaMemsetAsync(ln->ATT8.p, 0, ln->ATT8.cap, ln->stream));
     CKS(grow(ln->H8, rows * f));
   }
+  uint64_t held = 0;
+  for (const DBuf* b : {&ln->row_tok, &ln->row_pos, &ln->row_own, &ln->X32, &ln->Y32, &ln->X16, &ln->QKV, &ln->ATT,
+                        &ln->H, &ln->X8, &ln->ATT8, &ln->H8})
+    held += b->cap;
+  ln->act_bytes.store(held);
   return AS_OK;
+}
+
+// Bytes of encoder activation buffers per encoder row (the buffers
+// ensure_encoder_buffers sizes by rows).
+uint64_t encoder_row_bytes(const as_config& g) {
+  const uint64_t d = g.d_model, f = g.d_ffn;
+  const bool bf = g.precision != AS_FP32, f8 = g.precision == AS_FP8;
+  const uint64_t act = bf ? 2 : 4;
+  uint64_t b = 4 + 4 + 1 + 4 * d + 4 * d + (bf ? 2 * d : 0) + 3 * d * act + d * act + f * act;
+  if (f8) b += d + d + f;
+  return b;
 }
 
 RxTypes recognizer_table(const as_schema* s) {
@@ -1031,10 +1070,11 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
     for (uint64_t r = 0; r < n && i < seqs.size(); ++r) {
       const uint64_t a = rt[r], b = rt[r + 1];
       if (a == b) continue;
-      Chunk ch{i, i, 0, 0};
+      Chunk ch{i, i, 0, 0, 0};
       while (i < seqs.size() && seqs[i].src_tok >= a && seqs[i].src_tok < b) {
         seqs[i].row = (uint32_t)((ch.rows + 7) & ~7ull);
         ch.rows = seqs[i].row + seqs[i].len;
+        ch.tokens += seqs[i].len;
         ch.max_len = std::max(ch.max_len, seqs[i].len);
         ch.s1 = ++i;
       }
@@ -1043,17 +1083,19 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   } else {
     // every sequence starts on a row that is a multiple of 8 (the padding rows
     // in between belong to no sequence and are never written out)
-    const uint64_t cap = g.max_chunk_tokens ? g.max_chunk_tokens : (1ull << 19);
-    Chunk cur{0, 0, 0, 0};
+    // the lane's row cap (serving: from the activation budget), else the ctx's
+    const uint64_t cap = ln->row_cap ? ln->row_cap : g.max_chunk_tokens ? g.max_chunk_tokens : (1ull << 19);
+    Chunk cur{0, 0, 0, 0, 0};
     for (uint64_t i = 0; i < seqs.size(); ++i) {
       const uint64_t start = (cur.rows + 7) & ~7ull;
       if (cur.rows > 0 && start + seqs[i].len > cap) {
         chunks.push_back(cur);
-        cur = Chunk{i, i, 0, 0};
+        cur = Chunk{i, i, 0, 0, 0};
       }
       seqs[i].row = (uint32_t)((cur.rows + 7) & ~7ull);
       cur.s1 = i + 1;
       cur.rows = seqs[i].row + seqs[i].len;
+      cur.tokens += seqs[i].len;
       cur.max_len = std::max(cur.max_len, seqs[i].len);
     }
     if (cur.rows) chunks.push_back(cur);
@@ -1089,10 +1131,10 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
         starts.push_back((int32_t)seqs[i].row);
       }
       attention_items(starts.data(), lens.data(), (int32_t)lens.size(), items);
-      if (graphable(g, ch.rows)) {
-        // pad to a power of two with padding items (L = 0)
+      if (graphable(g)) {
+        // pad to the graph bucket with padding items (L = 0)
         const size_t n = (items.size() - item_off.back()) / 2;
-        items.resize(item_off.back() + 2 * pow2_at_least(n, 16), 0);
+        items.resize(item_off.back() + 2 * graph_bucket(n, 16), 0);
       }
       item_off.push_back(items.size());
     }
@@ -1457,6 +1499,8 @@ struct Server {
   uint64_t batch_bytes = 0;
   uint32_t max_batch = 0;
   uint64_t max_pending = 0;
+  uint64_t act_budget = 0, row_cap = 0, act_peak = 0;
+  uint32_t max_pos = 0;
   std::vector<std::unique_ptr<Lane>> lanes;
   std::vector<std::thread> workers;
   std::mutex mu;
@@ -1471,6 +1515,15 @@ struct Server {
   int64_t t_stats0 = 0;
 
   void worker(Lane* ln);
+  // encoder rows a record of b bytes can occupy at most (<= b tokens; windows
+  // and the 8-row alignment of every sequence added)
+  uint64_t bound_rows(uint64_t b) const {
+    const uint64_t W = schema.window, S = schema.stride;
+    if (b == 0) return 0;
+    if (W == 0 || b <= W) return (std::min<uint64_t>(b, max_pos) + 7) & ~7ull;
+    const uint64_t nw = 1 + (b - W + S - 1) / S;
+    return b + (nw - 1) * (W - S) + 8 * nw;
+  }
 };
 
 void Server::worker(Lane* ln) {
@@ -1484,10 +1537,14 @@ void Server::worker(Lane* ln) {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stop || !queue.empty(); });
       if (queue.empty()) break;  // stop requested and nothing left
-      uint64_t bytes = 0;
-      while (!queue.empty() && batch.size() < max_batch &&
-             (batch.empty() || bytes + queue.front()->bytes.size() <= batch_bytes)) {
-        bytes += queue.front()->bytes.size();
+      // admission by device memory: the rows the batch can occupy stay within
+      // the lane's row cap (the first request always goes in)
+      uint64_t bytes = 0, rows = 0;
+      while (!queue.empty() && batch.size() < max_batch) {
+        const uint64_t b = queue.front()->bytes.size(), r = bound_rows(b);
+        if (!batch.empty() && (bytes + b > batch_bytes || rows + r > row_cap)) break;
+        bytes += b;
+        rows += r;
         batch.push_back(queue.front());
         queue.pop_front();
       }
@@ -1506,8 +1563,11 @@ void Server::worker(Lane* ln) {
     std::vector<uint64_t> rec_tokens(batch.size(), 0);
     if (st == AS_OK && !ln->h_rec_tok.empty() && ln->h_rec_tok.size() == batch.size() + 1)
       for (size_t i = 0; i < batch.size(); ++i) rec_tokens[i] = ln->h_rec_tok[i + 1] - ln->h_rec_tok[i];
+    uint64_t held = 0;
+    for (auto& l : lanes) held += l->act_bytes.load();
     {
       std::lock_guard<std::mutex> lk(mu);
+      act_peak = std::max(act_peak, held);
       ++batches;
       if (st == AS_OK) tokens += o->stats.n_encoded_tokens;
       for (size_t i = 0; i < batch.size(); ++i) {
@@ -2152,13 +2212,32 @@ as_status as_serve_start(as_ctx* c, const as_schema* schema, const uint8_t* key,
     std::copy(schema->recognizer_types, schema->recognizer_types + AS_RX_KINDS, sv->rx_types);
     sv->schema.recognizer_types = sv->rx_types;
   }
-  const uint64_t chunk = c->cfg.max_chunk_tokens ? c->cfg.max_chunk_tokens : (1ull << 19);
-  sv->batch_bytes = cfg->max_batch_bytes ? cfg->max_batch_bytes : chunk * 3 / 4;
+  sv->batch_bytes = cfg->max_batch_bytes ? cfg->max_batch_bytes : UINT64_MAX;
   sv->max_batch = cfg->max_batch_records ? cfg->max_batch_records : 65536;
   sv->max_pending = cfg->max_pending ? cfg->max_pending : (1ull << 20);
   sv->next_id = c->records_done;
   sv->t_stats0 = now_ns();
+  sv->max_pos = c->cfg.max_pos;
   const uint32_t n_lanes = cfg->lanes ? std::min<uint32_t>(cfg->lanes, 8) : 2;
+  // admission by device memory: each lane's share of the activation budget
+  // gives its row cap (largest multiple of 8 whose bucketed rows fit)
+  sv->act_budget = cfg->activation_budget_bytes ? cfg->activation_budget_bytes : (40ull << 30);
+  {
+    const uint64_t share = sv->act_budget / n_lanes, per_row = encoder_row_bytes(c->cfg);
+    uint64_t lo = 0, hi = std::min<uint64_t>(share / per_row, 1ull << 31) / 8;  // in units of 8 rows
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi + 1) / 2;
+      if (encoder_rows(c->cfg, mid * 8) * per_row <= share) lo = mid; else hi = mid - 1;
+    }
+    sv->row_cap = lo * 8;
+    const uint64_t one_seq = ((uint64_t)c->cfg.max_pos + 7) & ~7ull;
+    if (sv->row_cap < one_seq) {
+      delete sv;
+      return fail(c, AS_ERR_ARG, "activation budget of " + std::to_string(cfg->activation_budget_bytes) +
+                                     " bytes cannot hold one full sequence per lane (" + std::to_string(one_seq) +
+                                     " rows of " + std::to_string(per_row) + " bytes)");
+    }
+  }
   for (uint32_t i = 0; i < n_lanes; ++i) {
     auto ln = std::make_unique<Lane>();
     if (cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -2172,6 +2251,7 @@ as_status as_serve_start(as_ctx* c, const as_schema* schema, const uint8_t* key,
       delete sv;
       return fail(c, AS_ERR_CUDA, "serving lane set-up failed");
     }
+    ln->row_cap = sv->row_cap;
     sv->lanes.push_back(std::move(ln));
   }
   c->server = sv;
@@ -2255,6 +2335,10 @@ as_status as_serve_stats(as_ctx* c, as_serve_stats_t* s, uint32_t reset) {
   s->tokens = sv->tokens;
   s->pending = sv->queue.size();
   s->seconds = (now_ns() - sv->t_stats0) * 1e-9;
+  s->activation_budget = sv->act_budget;
+  s->row_cap = sv->row_cap;
+  for (auto& l : sv->lanes) s->activation_bytes += l->act_bytes.load();
+  s->activation_peak = std::max(sv->act_peak, s->activation_bytes);
   if (!sv->lat_ms.empty()) {
     std::vector<double> v = sv->lat_ms;
     auto pct = [&](double q) {

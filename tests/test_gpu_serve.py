@@ -152,3 +152,77 @@ def test_replica_maps_merge_to_single_run(blob, vocab_words, batch_ref):
     assert outs == got
     merged = api.map_merge(shards, [a for a, _ in ranges])
     assert sorted(U.map_tuples(merged)) == emap
+
+
+# ---------------------------------------------------------------- against the oracle, serving-shaped records
+
+@pytest.fixture(scope="module")
+def c4_oracle(vocab_words, vocab_index):
+    """Serving-shaped records (lognormal(300, 0.6) clipped 32..4096 tokens, windows 512/384) through
+    the FP64 oracle end to end, with each record's smallest FP64 top-2 logit margin."""
+    from oracle import pipeline as P
+    from oracle.encoder import Encoder
+    recs = synth.make_records(synth.scaled(synth.C4, 48).records, vocab_words, seed=synth.SEED_RECORDS + 4)
+    recs = recs.records()
+    w = synth.make_weights(DIMS, seed=31, random_affine=True)
+    sch = P.Schema(synth.TYPE_NAMES_4, window=512, stride=384)
+    ref = P.anonymize(recs, sch, KEY, Encoder(DIMS, w), vocab_index)
+    margin = []
+    for t in ref.traces:
+        if t.logits is None or len(t.logits) == 0:
+            margin.append(np.inf)
+            continue
+        s = np.sort(t.logits, axis=1)
+        margin.append(float((s[:, -1] - s[:, -2]).min()))
+    assert max(len(t.ids) for t in ref.traces) > 512      # some records run as several windows
+    return recs, ref, np.array(margin)
+
+
+def _check_vs_oracle(got, recs, ref, margin, tol=1e-4):
+    """Records whose FP64 labels cannot flip under an FP32 error of tol equal the oracle's output."""
+    safe = margin > 2 * tol
+    assert safe.mean() > 0.9
+    for i in np.nonzero(safe)[0]:
+        assert got[i] == ref.outputs[i], f"record {i}"
+    return int(safe.sum())
+
+
+def test_served_fp32_windows_equal_oracle(blob, vocab_words, c4_oracle):
+    """FP32 serving with 512/384 windows and records up to 4,096 tokens: every served record equals
+    the oracle's end-to-end output (records with a near-tie FP64 label excepted), and the served
+    entity map equals the oracle's over those records when all qualify."""
+    recs, ref, margin = c4_oracle
+    ctx = api.Context(DIMS, blob, vocab_words, precision="fp32")
+    ctx.serve_start(api.Schema(synth.TYPE_NAMES_4, window=512, stride=384), KEY, lanes=2)
+    ids = [ctx.submit(r) for r in recs]
+    got = [ctx.poll(i, timeout_s=120) for i in ids]
+    n = _check_vs_oracle(got, recs, ref, margin)
+    if n == len(recs):
+        assert sorted(U.map_tuples(ctx.map_export())) == sorted(U.map_tuples(ref.map))
+    ctx.serve_stop()
+    ctx.close()
+
+
+def test_admission_by_activation_budget(blob, vocab_words, c4_oracle):
+    """A small activation budget: the lanes' encoder activations never exceed it, batches stay
+    within the row cap (records longer than the cap run as several encoder batches), and the
+    results equal the oracle's, as with the default budget."""
+    recs, ref, margin = c4_oracle
+    ctx = api.Context(DIMS, blob, vocab_words, precision="fp32")
+    per_row = 4 + 4 + 1 + 4 * DIMS.d_model * 2 + 4 * 3 * DIMS.d_model + 4 * DIMS.d_model + 4 * DIMS.d_ffn
+    budget = 2 * 1024 * per_row          # room for 1,024 rows per lane: 1-2 records per batch
+    ctx.serve_start(api.Schema(synth.TYPE_NAMES_4, window=512, stride=384), KEY, lanes=2,
+                    activation_budget=budget)
+    st0 = ctx.serve_stats()
+    assert st0["activation_budget"] == budget and st0["row_cap"] == 1024
+    ids = [ctx.submit(r) for r in recs]
+    got = [ctx.poll(i, timeout_s=120) for i in ids]
+    st = ctx.serve_stats()
+    assert st["completed"] == len(recs) and st["failed"] == 0
+    assert 0 < st["activation_peak"] <= budget, st
+    assert st["batches"] > len(recs) // 4
+    _check_vs_oracle(got, recs, ref, margin)
+    ctx.serve_stop()
+    with pytest.raises(api.AnonShieldError):       # a budget below one full sequence per lane
+        ctx.serve_start(SCHEMA, KEY, lanes=2, activation_budget=2 * 256 * per_row)
+    ctx.close()

@@ -89,3 +89,33 @@ def test_stream_indices_continue_and_edges(blob, vocab_words, c1_records):
     with pytest.raises(api.AnonShieldError):
         ctx.anonymize_stream(e.data, e.offsets, SCHEMA, b"other key")
     ctx.close()
+
+
+def test_stream_fp32_windows_equal_oracle(blob, vocab_words, vocab_index):
+    """FP32 streaming of serving/streaming-shaped long records (up to 4,096 tokens, windows
+    512/384) equals the FP64 oracle end to end on every record whose FP64 labels cannot flip
+    under the FP32 tolerance (1e-4), and the map equals the oracle's when all records qualify."""
+    from oracle import pipeline as P
+    from oracle.encoder import Encoder
+    recs = synth.make_records(synth.scaled(synth.C4, 40).records, vocab_words, seed=synth.SEED_RECORDS + 5)
+    recs = recs.records()
+    w = synth.make_weights(DIMS, seed=31, random_affine=True)
+    ref = P.anonymize(recs, P.Schema(synth.TYPE_NAMES_4, window=512, stride=384), KEY, Encoder(DIMS, w),
+                      vocab_index)
+    assert max(len(t.ids) for t in ref.traces) > 512
+    ctx = api.Context(DIMS, blob, vocab_words, precision="fp32")
+    rs = synth.records_from_list(recs)
+    got = ctx.anonymize_stream(rs.data, rs.offsets, api.Schema(synth.TYPE_NAMES_4, window=512, stride=384), KEY,
+                               batch_bytes=6000, lanes=3).records()
+    safe = 0
+    for i, t in enumerate(ref.traces):
+        if len(t.ids):
+            s = np.sort(t.logits, axis=1)
+            if float((s[:, -1] - s[:, -2]).min()) <= 2e-4:
+                continue
+        assert got[i] == ref.outputs[i], f"record {i}"
+        safe += 1
+    assert safe > 0.9 * len(recs)
+    if safe == len(recs):
+        assert sorted(U.map_tuples(ctx.map_export())) == sorted(U.map_tuples(ref.map))
+    ctx.close()
