@@ -821,15 +821,19 @@ as_status ensure_encoder_buffers(as_ctx* c, Lane* ln, uint64_t rows, uint64_t n_
   return AS_OK;
 }
 
-// Bytes of encoder activation buffers per encoder row (the buffers
-// ensure_encoder_buffers sizes by rows).
-uint64_t encoder_row_bytes(const as_config& g) {
+// Bytes the encoder activation buffers of a lane hold for `rows` rows: the
+// buffers ensure_encoder_buffers sizes by rows, each allocated with the 1/8
+// slack of grow().
+uint64_t encoder_held_bytes(const as_config& g, uint64_t rows) {
   const uint64_t d = g.d_model, f = g.d_ffn;
   const bool bf = g.precision != AS_FP32, f8 = g.precision == AS_FP8;
   const uint64_t act = bf ? 2 : 4;
-  uint64_t b = 4 + 4 + 1 + 4 * d + 4 * d + (bf ? 2 * d : 0) + 3 * d * act + d * act + f * act;
-  if (f8) b += d + d + f;
-  return b;
+  const uint64_t per_buffer[] = {4, 4, 1, 4 * d, 4 * d, bf ? 2 * d : 0, 3 * d * act, d * act, f * act,
+                                 f8 ? d : 0, f8 ? d : 0, f8 ? f : 0};
+  uint64_t held = 0;
+  for (uint64_t b : per_buffer)
+    if (b) held += rows * b + rows * b / 8;
+  return held;
 }
 
 RxTypes recognizer_table(const as_schema* s) {
@@ -1007,23 +1011,33 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   VocabTable vt{c->vocab_slots.as<uint4>(), c->vocab_mask, c->vocab_lenmask.as<uint16_t>()};
   ProfScope ps_text(ln, kProfText, 0);
   launch_mark_record_starts(d_off, n, N32, ln->rs_bits.as<uint32_t>(), st);
-  launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st);
-  launch_tokenize_compact(ln->tok_at.as<uint16_t>(), N32, ln->tok_ids.as<int32_t>(), ln->tok_off.as<uint32_t>(),
-                          cnt + 0, ln->scan_tiles.as<uint32_t>(), st);
+  // the mark kernels count each tile's tokens / candidates into scan_tiles,
+  // so the compactions skip their counting pass
+  const size_t text_tiles = scan_tiles_needed(N32);
+  CK(cudaMemsetAsync(ln->scan_tiles.p, 0, std::max<size_t>(1, text_tiles) * 4, st));
+  launch_tokenize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), vt, ln->tok_at.as<uint16_t>(), st,
+                       ln->scan_tiles.as<uint32_t>());
+  launch_tokenize_table(ln->tok_at.as<uint16_t>(), N32, ln->tok_ids.as<int32_t>(), ln->tok_off.as<uint32_t>(),
+                        ln->tok_len.as<uint32_t>(), cnt + 0, ln->scan_tiles.as<uint32_t>(), st);
   launch_record_token_starts(d_off, n, ln->tok_off.as<uint32_t>(), cnt + 0, N32, ln->rec_tok.as<uint64_t>(), st);
   // recognizers
   CKS(grow(ln->rx_len_b, N * 4));
   CKS(grow(ln->rx_type_b, N + 16));
   const RxTypes rxt = recognizer_table(sch);
+  // with a multi-word kind on, the resolve pass may drop candidates: the
+  // compaction then counts them itself
+  const bool rx_long = rx_any_long(rxt);
+  if (!rx_long) CK(cudaMemsetAsync(ln->scan_tiles.p, 0, std::max<size_t>(1, text_tiles) * 4, st));
   launch_recognize_mark(d_bytes, N32, ln->rs_bits.as<uint32_t>(), rxt, ln->rx_len_b.as<uint32_t>(),
-                        ln->rx_type_b.as<uint8_t>(), st);
-  if (rx_any_long(rxt))
+                        ln->rx_type_b.as<uint8_t>(), st, rx_long ? nullptr : ln->scan_tiles.as<uint32_t>());
+  if (rx_long)
     launch_recognize_resolve(d_off, n, ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), st);
   CKS(grow(ln->rx_s, (N / 2 + 2) * 4));
   CKS(grow(ln->rx_l, (N / 2 + 2) * 4));
   CKS(grow(ln->rx_t, N / 2 + 2));
   launch_recognize_compact(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), N32, ln->rx_s.as<uint32_t>(),
-                           ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), cnt + 1, ln->scan_tiles.as<uint32_t>(), st);
+                           ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), cnt + 1, ln->scan_tiles.as<uint32_t>(), st,
+                           !rx_long);
   ps_text.end();
   // ---- sync 1: token counts
   uint32_t h_cnt[2] = {0, 0};
@@ -1033,7 +1047,6 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   CK(cudaMemcpyAsync(rt.data(), ln->rec_tok.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint64_t T = h_cnt[0], n_rx = h_cnt[1];
-  launch_token_lengths(ln->tok_off.as<uint32_t>(), (uint32_t)T, N32, ln->tok_len.as<uint32_t>(), st);
   // ---- sequences (windows) and encoder batches
   const uint32_t W = sch->window, S = sch->stride;
   std::vector<SeqDesc> seqs;
@@ -2223,11 +2236,11 @@ as_status as_serve_start(as_ctx* c, const as_schema* schema, const uint8_t* key,
   // gives its row cap (largest multiple of 8 whose bucketed rows fit)
   sv->act_budget = cfg->activation_budget_bytes ? cfg->activation_budget_bytes : (40ull << 30);
   {
-    const uint64_t share = sv->act_budget / n_lanes, per_row = encoder_row_bytes(c->cfg);
+    const uint64_t share = sv->act_budget / n_lanes, per_row = encoder_held_bytes(c->cfg, 1);
     uint64_t lo = 0, hi = std::min<uint64_t>(share / per_row, 1ull << 31) / 8;  // in units of 8 rows
     while (lo < hi) {
       const uint64_t mid = (lo + hi + 1) / 2;
-      if (encoder_rows(c->cfg, mid * 8) * per_row <= share) lo = mid; else hi = mid - 1;
+      if (encoder_held_bytes(c->cfg, encoder_rows(c->cfg, mid * 8)) <= share) lo = mid; else hi = mid - 1;
     }
     sv->row_cap = lo * 8;
     const uint64_t one_seq = ((uint64_t)c->cfg.max_pos + 7) & ~7ull;

@@ -140,4 +140,19 @@ inline void compact_emit(Load load, uint64_t n, Emit emit, T* total_dev, T* tile
   count_launch(3);
 }
 
+// compact_emit when a producer kernel already wrote each tile's count of
+// nonzero elements into tile_sums[0 .. scan_tiles_needed(n)): the counting
+// pass is skipped.
+template <typename T, typename Load, typename Emit>
+inline void compact_emit_from_sums(Load load, uint64_t n, Emit emit, T* total_dev, T* tile_sums, cudaStream_t st) {
+  uint64_t tiles = scan_tiles_needed(n);
+  if (tiles == 0) {
+    cudaMemsetAsync(total_dev, 0, sizeof(T), st);
+    return;
+  }
+  scan_tile_offsets<T><<<1, 1024, 0, st>>>(tile_sums, n, total_dev, nullptr, 0);
+  scan_emit_tiles<T, Load, Emit><<<(unsigned)tiles, kScanThreads, 0, st>>>(load, n, tile_sums, emit);
+  count_launch(2);
+}
+
 }  // namespace as

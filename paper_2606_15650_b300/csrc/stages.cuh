@@ -38,9 +38,11 @@ struct VocabTable {
 // Bit r of the bitmap is set when a record starts at byte r (n_words = N/32 + 1).
 void launch_mark_record_starts(const uint64_t* offsets, uint64_t n_records, uint32_t N, uint32_t* rs_bits,
                                cudaStream_t st);
-// tok_at[i] = token id when a token starts at byte i, else 0.
+// tok_at[i] = token id when a token starts at byte i, else 0. With
+// tile_sums (scan_tiles_needed(N) elements, zeroed by the caller), also the
+// number of token starts in each 4,096-byte tile.
 void launch_tokenize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, VocabTable vt,
-                          uint16_t* tok_at, cudaStream_t st);
+                          uint16_t* tok_at, cudaStream_t st, uint32_t* tile_sums = nullptr);
 // Compact token starts: ids/offsets in byte order; pos[] is the exclusive scan.
 void launch_tokenize_emit(const uint16_t* tok_at, const uint32_t* pos, uint32_t N, int32_t* tok_ids,
                           uint32_t* tok_off, cudaStream_t st);
@@ -51,6 +53,10 @@ void launch_record_token_offsets(const uint64_t* offsets, uint64_t n_records, co
 // tile_scratch: scan_tiles_needed(N) elements.
 void launch_tokenize_compact(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* n_tokens,
                              uint32_t* tile_scratch, cudaStream_t st);
+// The same table plus token lengths, from the tile counts that
+// launch_tokenize_mark wrote into tile_sums (turned into tile offsets here).
+void launch_tokenize_table(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* len,
+                           uint32_t* n_tokens, uint32_t* tile_sums, cudaStream_t st);
 // rec_tok[r] = first token of record r (T for offsets at N), from the token offsets.
 void launch_record_token_starts(const uint64_t* offsets, uint64_t n, const uint32_t* tok_off, const uint32_t* total_T,
                                 uint32_t N, uint64_t* rec_tok, cudaStream_t st);
@@ -70,14 +76,16 @@ struct RxTypes {
   uint8_t t[kRxKinds];
 };
 inline bool rx_any_long(const RxTypes& r) { return r.t[kRxUrl] || r.t[kRxCpe] || r.t[kRxPem]; }
+// rx_type[i] for every byte (0: no candidate starts there); rx_len[i] only
+// where rx_type[i] != 0. tile_sums as for launch_tokenize_mark (candidates).
 void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs_bits, RxTypes types,
-                           uint32_t* rx_len, uint8_t* rx_type, cudaStream_t st);
+                           uint32_t* rx_len, uint8_t* rx_type, cudaStream_t st, uint32_t* tile_sums = nullptr);
 void launch_recognize_resolve(const uint64_t* offsets, uint64_t n_records, const uint32_t* rx_len, uint8_t* rx_type,
                               cudaStream_t st);
 // Recognizer spans (start, length, type) in byte order; *n_spans = their count.
 void launch_recognize_compact(const uint32_t* rx_len, const uint8_t* rx_type, uint32_t N, uint32_t* sp_start,
                               uint32_t* sp_len, uint8_t* sp_type, uint32_t* n_spans, uint32_t* tile_scratch,
-                              cudaStream_t st);
+                              cudaStream_t st, bool sums_given = false);
 
 // BIO decode: token flags (bit0 first token of record, bit1 last).
 void launch_token_flags(const uint64_t* rec_tok, uint64_t n_records, uint8_t* tok_flags, cudaStream_t st);

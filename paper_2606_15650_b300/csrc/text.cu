@@ -3,11 +3,13 @@
 // Tokenizer: maximal runs of [0-9A-Za-z] are split greedily into the longest
 // vocabulary strings (2..12 bytes), falling back to single bytes; every other
 // byte is a token of its own (id = byte + 1). A block collects the run
-// starts of a tile and one thread walks each run; the token starts are then
-// compacted in byte order by a prefix sum whose last pass writes each token
-// at its rank, so token order is byte order and every record owns a
-// contiguous token range. (as_tokenize_static keeps the scan + emit pair
-// over a per-byte position array, which lives in its fixed scratch.)
+// starts of a tile and one thread walks each run, marking each token's id at
+// its first byte and counting the tile's tokens; the tile counts are scanned,
+// and one block per tile ranks its tokens in shared memory and writes the id
+// / offset / length table in order. So token order is byte order and every
+// record owns a contiguous token range. (as_tokenize_static keeps the scan +
+// emit pair over a per-byte position array, which lives in its fixed
+// scratch.)
 //
 // Recognizers: a word is a maximal run of [A-Za-z0-9.:-]; trailing '.', '-'
 // and a ':' that does not close a final '::' are stripped; the whole word is
@@ -41,6 +43,11 @@ void launch_mark_record_starts(const uint64_t* offsets, uint64_t n, uint32_t N, 
   count_launch();
 }
 
+// Bytes of a mark tile (also one scan tile: the mark kernels can write the
+// scan's tile counts).
+constexpr uint32_t kMarkTileBytes = 4096;
+static_assert(kMarkTileBytes == (uint32_t)kScanTile, "a mark tile is one scan tile");
+
 __device__ __forceinline__ uint32_t vocab_lookup(VocabTable vt, const uint32_t b[kMaxPiece], uint32_t len) {
   uint32_t w[3] = {0, 0, 0};
 #pragma unroll
@@ -58,10 +65,13 @@ __device__ __forceinline__ uint32_t vocab_lookup(VocabTable vt, const uint32_t b
 
 // Greedy longest-match split of the alphanumeric run that starts at byte i:
 // the id of each piece at its first byte, 0 at its other bytes.
-__device__ __forceinline__ void tokenize_run(const uint8_t* __restrict__ bytes, uint32_t N,
-                                             const uint32_t* __restrict__ rs, VocabTable vt,
-                                             uint16_t* __restrict__ tok_at, uint32_t i) {
-  uint32_t p = i;
+// Returns the number of pieces that start before tile_end; with tile_sums,
+// each piece that starts past it is added to its own tile's count.
+__device__ __forceinline__ uint32_t tokenize_run(const uint8_t* __restrict__ bytes, uint32_t N,
+                                                 const uint32_t* __restrict__ rs, VocabTable vt,
+                                                 uint16_t* __restrict__ tok_at, uint32_t i, uint64_t tile_end,
+                                                 uint32_t* __restrict__ tile_sums) {
+  uint32_t p = i, in_tile = 0;
   while (true) {
     uint32_t b[kMaxPiece];
     uint32_t avail = 0;
@@ -90,9 +100,12 @@ __device__ __forceinline__ void tokenize_run(const uint8_t* __restrict__ bytes, 
     }
     tok_at[p] = (uint16_t)id;
     for (uint32_t k = 1; k < take; ++k) tok_at[p + k] = 0;
+    if (p < tile_end) ++in_tile;
+    else if (tile_sums) atomicAdd(&tile_sums[p / kMarkTileBytes], 1u);
     p += take;
     if (p >= N || !is_alnum(bytes[p]) || rs_bit(rs, p)) break;
   }
+  return in_tile;
 }
 
 // A block takes tiles of kMarkTile bytes. It first writes the id of every
@@ -100,9 +113,11 @@ __device__ __forceinline__ void tokenize_run(const uint8_t* __restrict__ bytes, 
 // (one ballot per warp and step), then its threads split whole runs, one run
 // per thread: every lane of a warp has a run to work on, where one thread per
 // byte would leave most lanes idle while a few walk their runs. A run that
-// continues past the tile is finished by its own thread.
+// continues past the tile is finished by its own thread. With tile_sums
+// (zeroed by the caller) the block also adds the number of tokens that start
+// in each tile, so the compaction needs no counting pass.
 constexpr uint32_t kMarkThreads = 256;
-constexpr uint32_t kMarkTile = 4096;
+constexpr uint32_t kMarkTile = kMarkTileBytes;
 
 // Blocks of a mark kernel that fit on the device at once (the kernels loop
 // over tiles with a grid stride, so a second wave of blocks would start late
@@ -137,34 +152,45 @@ __device__ __forceinline__ void collect_start(bool start, uint32_t i, uint32_t* 
 
 __global__ void __launch_bounds__(kMarkThreads, 4)
     tokenize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs, VocabTable vt,
-                         uint16_t* __restrict__ tok_at) {
+                         uint16_t* __restrict__ tok_at, uint32_t* __restrict__ tile_sums) {
   __shared__ uint32_t starts[kMarkTile];
-  __shared__ uint32_t n_starts;
+  __shared__ uint32_t n_starts, n_tok;
   for (uint64_t base = (uint64_t)blockIdx.x * kMarkTile; base < N; base += (uint64_t)gridDim.x * kMarkTile) {
-    if (threadIdx.x == 0) n_starts = 0;
+    if (threadIdx.x == 0) {
+      n_starts = 0;
+      n_tok = 0;
+    }
     __syncthreads();
+    uint32_t my_tok = 0;
     for (uint32_t k = 0; k < kMarkTile / kMarkThreads; ++k) {
       const uint64_t i = base + k * kMarkThreads + threadIdx.x;
       bool start = false;
       if (i < N) {
         const uint32_t c = bytes[i];
-        if (!is_alnum(c)) tok_at[i] = (uint16_t)(c + 1);
-        else start = i == 0 || rs_bit(rs, (uint32_t)i) || !is_alnum(bytes[i - 1]);
+        if (!is_alnum(c)) {
+          tok_at[i] = (uint16_t)(c + 1);
+          ++my_tok;
+        } else {
+          start = i == 0 || rs_bit(rs, (uint32_t)i) || !is_alnum(bytes[i - 1]);
+        }
       }
       collect_start(start, (uint32_t)i, starts, &n_starts);
     }
     __syncthreads();
     const uint32_t ns = n_starts;
-    for (uint32_t j = threadIdx.x; j < ns; j += kMarkThreads) tokenize_run(bytes, N, rs, vt, tok_at, starts[j]);
+    for (uint32_t j = threadIdx.x; j < ns; j += kMarkThreads)
+      my_tok += tokenize_run(bytes, N, rs, vt, tok_at, starts[j], base + kMarkTile, tile_sums);
+    if (tile_sums && my_tok) atomicAdd(&n_tok, my_tok);
     __syncthreads();  // starts and n_starts are reused by the next tile
+    if (tile_sums && threadIdx.x == 0 && n_tok) atomicAdd(&tile_sums[base / kMarkTile], n_tok);
   }
 }
 
 void launch_tokenize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, VocabTable vt, uint16_t* tok_at,
-                          cudaStream_t st) {
+                          cudaStream_t st, uint32_t* tile_sums) {
   if (N == 0) return;
   const unsigned grid = resident_blocks(tokenize_mark_kernel, (N + kMarkTile - 1) / kMarkTile);
-  tokenize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, vt, tok_at);
+  tokenize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, vt, tok_at, tile_sums);
   count_launch();
 }
 
@@ -231,6 +257,75 @@ struct EmitToken {
 void launch_tokenize_compact(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* n_tokens,
                              uint32_t* tile_scratch, cudaStream_t st) {
   compact_emit<uint32_t>(TokStart{tok_at}, N, EmitToken{tok_at, ids, off}, n_tokens, tile_scratch, st);
+}
+
+// Token table of one 4,096-byte tile per block, from the marks and the tile
+// offsets (the exclusive scan of the tile counts): the tile's tokens are
+// ranked in shared memory and then written out in rank order, so that the
+// id / offset / length stores of a warp are contiguous. The last token of a
+// tile takes its length from the next token start past the tile (at most
+// kMaxPiece bytes on: no token is longer), or N.
+__global__ void __launch_bounds__(kScanThreads)
+    token_emit_tiles_kernel(const uint16_t* __restrict__ tok_at, uint32_t N, const uint32_t* __restrict__ tile_off,
+                            int32_t* __restrict__ ids, uint32_t* __restrict__ off, uint32_t* __restrict__ len) {
+  __shared__ uint32_t s_pos[kMarkTile];
+  __shared__ uint16_t s_id[kMarkTile];
+  __shared__ uint32_t sm[33];
+  __shared__ uint32_t next_start;
+  const uint64_t base = (uint64_t)blockIdx.x * kMarkTile;
+  if (base >= N) return;
+  const uint32_t n_here = (uint32_t)min((uint64_t)kMarkTile, (uint64_t)N - base);
+  const uint32_t j0 = threadIdx.x * kScanItems;
+  uint16_t v[kScanItems];
+  if (j0 + kScanItems <= n_here) {
+    const uint4* src = reinterpret_cast<const uint4*>(tok_at + base + j0);
+    const uint4 a = src[0], b = src[1];
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = (uint16_t)(w[k >> 1] >> (16 * (k & 1)));
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = j0 + k < n_here ? tok_at[base + j0 + k] : (uint16_t)0;
+  }
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) cnt += v[k] != 0;
+  if (threadIdx.x == 0) {
+    uint64_t q = base + n_here;
+    while (q < N && tok_at[q] == 0) ++q;
+    next_start = (uint32_t)q;
+  }
+  uint32_t tot;
+  uint32_t r = block_exclusive_scan(cnt, sm, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (v[k]) {
+      s_id[r] = v[k];
+      s_pos[r] = j0 + k;
+      ++r;
+    }
+  }
+  __syncthreads();
+  const uint32_t t0 = tile_off[blockIdx.x];
+  for (uint32_t q = threadIdx.x; q < tot; q += kScanThreads) {
+    const uint32_t o = (uint32_t)base + s_pos[q];
+    const uint32_t e = q + 1 < tot ? (uint32_t)base + s_pos[q + 1] : next_start;
+    ids[t0 + q] = (int32_t)s_id[q];
+    off[t0 + q] = o;
+    len[t0 + q] = e - o;
+  }
+}
+
+void launch_tokenize_table(const uint16_t* tok_at, uint32_t N, int32_t* ids, uint32_t* off, uint32_t* len,
+                           uint32_t* n_tokens, uint32_t* tile_sums, cudaStream_t st) {
+  const uint64_t tiles = scan_tiles_needed(N);
+  if (tiles == 0) {
+    cudaMemsetAsync(n_tokens, 0, sizeof(uint32_t), st);
+    return;
+  }
+  scan_tile_offsets<uint32_t><<<1, 1024, 0, st>>>(tile_sums, N, n_tokens, nullptr, 0);
+  token_emit_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, st>>>(tok_at, N, tile_sums, ids, off, len);
+  count_launch(2);
 }
 
 // First token of each record from the token table: a record start is always
@@ -586,48 +681,59 @@ __device__ __forceinline__ void recognize_word(const uint8_t* __restrict__ bytes
   }
 }
 
-// Tiles of kMarkTile bytes as in the tokenizer: the block writes 0 for every
-// byte that starts no word and collects the word starts, then one thread per
-// word runs the recognizers.
+// Tiles of kMarkTile bytes as in the tokenizer: the block writes type 0 for
+// every byte that starts no word and collects the word starts, then one
+// thread per word runs the recognizers. A candidate's length is written only
+// where its type is not 0 (the only places it is read). With tile_sums
+// (zeroed by the caller) the block adds its number of candidates, so the
+// compaction needs no counting pass; that count is final only when no
+// multi-word kind is on (the resolve pass may drop candidates).
 __global__ void __launch_bounds__(kMarkThreads)
     recognize_mark_kernel(const uint8_t* __restrict__ bytes, uint32_t N, const uint32_t* __restrict__ rs, RxTypes T,
-                          uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type) {
+                          uint32_t* __restrict__ rx_len, uint8_t* __restrict__ rx_type,
+                          uint32_t* __restrict__ tile_sums) {
   __shared__ uint32_t starts[kMarkTile];
-  __shared__ uint32_t n_starts;
+  __shared__ uint32_t n_starts, n_cand;
   for (uint64_t base = (uint64_t)blockIdx.x * kMarkTile; base < N; base += (uint64_t)gridDim.x * kMarkTile) {
-    if (threadIdx.x == 0) n_starts = 0;
+    if (threadIdx.x == 0) {
+      n_starts = 0;
+      n_cand = 0;
+    }
     __syncthreads();
     for (uint32_t k = 0; k < kMarkTile / kMarkThreads; ++k) {
       const uint64_t i = base + k * kMarkThreads + threadIdx.x;
       bool start = false;
       if (i < N) {
         start = in_word(bytes[i]) && (i == 0 || rs_bit(rs, (uint32_t)i) || !in_word(bytes[i - 1]));
-        if (!start) {
-          rx_len[i] = 0;
-          rx_type[i] = 0;
-        }
+        if (!start) rx_type[i] = 0;
       }
       collect_start(start, (uint32_t)i, starts, &n_starts);
     }
     __syncthreads();
     const uint32_t ns = n_starts;
+    uint32_t my_cand = 0;
     for (uint32_t j = threadIdx.x; j < ns; j += kMarkThreads) {
       const uint32_t i = starts[j];
       uint32_t len;
       uint8_t type;
       recognize_word(bytes, N, rs, T, i, len, type);
-      rx_len[i] = len;
       rx_type[i] = type;
+      if (type) {
+        rx_len[i] = len;  // read only where the type is not 0
+        ++my_cand;
+      }
     }
+    if (tile_sums && my_cand) atomicAdd(&n_cand, my_cand);
     __syncthreads();  // starts and n_starts are reused by the next tile
+    if (tile_sums && threadIdx.x == 0 && n_cand) atomicAdd(&tile_sums[base / kMarkTile], n_cand);
   }
 }
 
 void launch_recognize_mark(const uint8_t* bytes, uint32_t N, const uint32_t* rs, RxTypes types, uint32_t* rx_len,
-                           uint8_t* rx_type, cudaStream_t st) {
+                           uint8_t* rx_type, cudaStream_t st, uint32_t* tile_sums) {
   if (N == 0) return;
   const unsigned grid = resident_blocks(recognize_mark_kernel, (N + kMarkTile - 1) / kMarkTile);
-  recognize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, types, rx_len, rx_type);
+  recognize_mark_kernel<<<grid, kMarkThreads, 0, st>>>(bytes, N, rs, types, rx_len, rx_type, tile_sums);
   count_launch();
 }
 
@@ -726,9 +832,12 @@ struct EmitRxSpan {
 
 void launch_recognize_compact(const uint32_t* rx_len, const uint8_t* rx_type, uint32_t N, uint32_t* sp_start,
                               uint32_t* sp_len, uint8_t* sp_type, uint32_t* n_spans, uint32_t* tile_scratch,
-                              cudaStream_t st) {
-  compact_emit<uint32_t>(RxStart{rx_type}, N, EmitRxSpan{rx_len, rx_type, sp_start, sp_len, sp_type}, n_spans,
-                         tile_scratch, st);
+                              cudaStream_t st, bool sums_given) {
+  const EmitRxSpan emit{rx_len, rx_type, sp_start, sp_len, sp_type};
+  if (sums_given)
+    compact_emit_from_sums<uint32_t>(RxStart{rx_type}, N, emit, n_spans, tile_scratch, st);
+  else
+    compact_emit<uint32_t>(RxStart{rx_type}, N, emit, n_spans, tile_scratch, st);
 }
 
 }  // namespace as
