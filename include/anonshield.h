@@ -382,8 +382,8 @@ as_status as_anonymize_stream(as_ctx* ctx, const as_records* records, const as_s
  * activations of all lanes together (a 1/lanes share each). A lane's share
  * fixes its row cap R: the most encoder rows whose activation buffers (per
  * row: the FP32 residual and pre-LN rows, the BF16 / E4M3 GEMM inputs, QKV,
- * attention output and FFN rows, row indices; padded to the graph bucket)
- * fit the share. A worker admits the oldest requests while the
+ * attention output and FFN rows, row indices; padded to the graph bucket,
+ * each buffer allocated with 1/8 slack) fit the share. A worker admits the oldest requests while the
  * rows they can occupy at most (a record of b bytes has at most b tokens;
  * windows and the 8-row alignment added) stay within R; the first request is
  * always admitted, and encoder batches never exceed R rows (a long record
