@@ -346,7 +346,13 @@ def oracle_pool(wname: str, n_records: int, integer_only: bool = False, seed_off
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    pool.map(int, range(n))          # every worker initialised before anything is timed
+    # every worker initialised before anything is timed (bounded: a worker that cannot start
+    # must not hang the benchmark)
+    try:
+        pool.map_async(int, range(n)).get(timeout=600)
+    except Exception:
+        pool.terminate()
+        raise
     return pool, n, cores
 
 
@@ -355,7 +361,7 @@ def cpu_baseline(w, budget_s: float = 15.0) -> dict:
     pool, n, cores = oracle_pool(w.name.split("-")[0], 16 * 32)
     try:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_budget, [(k, n, budget_s) for k in range(n)])
+        res = pool.map_async(_oracle_budget, [(k, n, budget_s) for k in range(n)]).get(timeout=600 + 10 * budget_s)
         wall = time.perf_counter() - t0
     finally:
         pool.terminate()
@@ -372,7 +378,7 @@ def oracle_integer_full(w) -> dict:
     pool, n, cores = oracle_pool(w.name.split("-")[0], w.records.n_records, integer_only=True)
     try:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_integer, [(k, n) for k in range(n)])
+        res = pool.map_async(_oracle_integer, [(k, n) for k in range(n)]).get(timeout=3600)
         wall = time.perf_counter() - t0
     finally:
         pool.terminate()
@@ -397,7 +403,7 @@ def run_reference(args):
             chunks = [[cur + k] for k in range(n)]
             cur += n
             t0 = time.perf_counter()
-            res = pool.map(_oracle_records, chunks)
+            res = pool.map_async(_oracle_records, chunks).get(timeout=1800)
             dt = time.perf_counter() - t0
             if step >= args.warmup:
                 times.append(dt)
