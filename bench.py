@@ -1029,7 +1029,7 @@ def serving_leg(args, words, blob, key, local) -> dict:
 
 
 def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32, peaks_live) -> dict:
-    """FP8 e4m3 GEMMs (static scales from 64 calibration records) on the same workload."""
+    """FP8 e4m3 GEMMs (static scales from 64 calibration records, autotuned tiles) on the same workload."""
     import torch
     import paper_2606_15650_b300.api as api
     ctx = api.Context(w.dims, blob, words, precision="fp8", mode="packed", keep_trace=True, device=local)
@@ -1045,6 +1045,7 @@ def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32, peaks_
     ctx.close()
     ctx = api.Context(w.dims, blob, words, precision="fp8", mode="packed", device=local)
     ctx.calibrate(cal.data, cal.offsets, schema)
+    tune = ctx.autotune()   # the E4M3 GEMMs' own tile choices, outside the timed calls
     stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{local}")
     d_data = torch.from_numpy(recs.data).to(f"cuda:{local}")
     d_offs = torch.from_numpy(recs.offsets.astype(np.int64)).to(f"cuda:{local}")
@@ -1077,6 +1078,7 @@ def fp8_leg(args, w, words, recs, blob, key, schema, local, sample, tr32, peaks_
             "gemm_tflops": gemm_tflops,
             "gemm_roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": fp8_peak, "unit": "TFLOP/s",
                               "frac": gemm_tflops / fp8_peak, "peak_source": fp8_src},
+            "autotune": {e["role"]: e["chosen"] for e in tune},
             "label_agreement_vs_fp32": agree, "max_abs_logit_diff_vs_fp32": max_d,
             "sample": f"agreement on the first {sample.n} records; timing on the whole workload; "
                       f"scales from 64 calibration records (seed {synth.SEED_CALIB})"}

@@ -83,10 +83,6 @@ enum EncMode { kEncF32 = 0, kEncBF16 = 1, kEncFP8 = 2, kEncCalib = 3 };
 // FFN-in and FFN-out projections.
 constexpr int kActPerLayer = 4;
 
-struct NonZeroU16 {
-  const uint16_t* p;
-  __device__ uint32_t operator()(uint64_t i) const { return p[i] != 0; }
-};
 struct NonZeroU8 {
   const uint8_t* p;
   __device__ uint32_t operator()(uint64_t i) const { return p[i] != 0; }
