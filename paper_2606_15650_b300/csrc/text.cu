@@ -645,15 +645,21 @@ __device__ __forceinline__ void recognize_word(const uint8_t* __restrict__ bytes
       type |= kRxLong;
     }
   }
-  // which separators the word holds ('.' 1, ':' 2, '-' 4): every test
-  // below except the hash needs one, so words without them skip it
-  auto sep_bit = [](uint32_t ch) -> uint32_t { return ch == '.' ? 1u : ch == ':' ? 2u : ch == '-' ? 4u : 0u; };
-  uint32_t sep = sep_bit(c);
+  // which separators the stripped word holds ('.' 1, ':' 2, '-' 4): every
+  // test below except the hash needs one inside the word it tests, so words
+  // without them skip it. The first position of each separator is kept, so
+  // that a separator the strip removes (a sentence's final '.') does not count.
+  uint32_t first_sep[3] = {UINT32_MAX, UINT32_MAX, UINT32_MAX};
+  auto note_sep = [&](uint32_t ch, uint32_t at) {
+    const int k = ch == '.' ? 0 : ch == ':' ? 1 : ch == '-' ? 2 : -1;
+    if (k >= 0 && first_sep[k] == UINT32_MAX) first_sep[k] = at;
+  };
+  note_sep(c, i);
   uint32_t e = i + 1;
   while (e < N && !rs_bit(rs, e)) {
     const uint32_t ch = bytes[e];
     if (!in_word(ch)) break;
-    sep |= sep_bit(ch);
+    note_sep(ch, e);
     ++e;
   }
   while (e > i) {
@@ -662,6 +668,7 @@ __device__ __forceinline__ void recognize_word(const uint8_t* __restrict__ bytes
     else if (t == ':' && !(e >= i + 2 && bytes[e - 2] == ':')) --e;
     else break;
   }
+  const uint32_t sep = (first_sep[0] < e ? 1u : 0u) | (first_sep[1] < e ? 2u : 0u) | (first_sep[2] < e ? 4u : 0u);
   const uint8_t* w = bytes + i;
   uint32_t n = e - i;
   if (n > 0 && !type) {

@@ -3,14 +3,19 @@
 Every tile configuration must give bit-identical logits: the configuration
 only changes which CTA computes an output tile and in which order tiles
 are visited, never the accumulation order inside an output. The tuner must
-report a timing for every valid configuration and keep the fastest.
+report a timing for every valid configuration and keep the fastest. The
+2-SM configuration is also checked against the FP64 oracle directly.
 """
 import numpy as np
 import pytest
 
 import synth
 import paper_2606_15650_b300.api as api
+from oracle import pipeline as P
+from oracle.encoder import Encoder
 from synth.workloads import ModelDims
+
+import parity_util as U
 
 pytestmark = pytest.mark.gpu
 
@@ -83,3 +88,23 @@ def test_tile_choices_checked(vocab_words):
     with pytest.raises(api.AnonShieldError):
         f32.autotune()
     f32.close()
+
+
+def test_pair_tiles_match_oracle(setup, vocab_words, vocab_index):
+    """2-SM tiles on every projection (BF16, fused LayerNorm blocks): logits within the BF16
+    tolerance of the FP64 oracle and output bytes equal to the oracle's later stages fed the
+    device labels."""
+    blob, rs = setup
+    recs = rs.records()
+    key = synth.make_key()
+    w = synth.make_weights(DIMS, seed=7, random_affine=True)
+    ref = P.anonymize(recs, U.oracle_schema(SCHEMA), key, Encoder(DIMS, w), vocab_index)
+    ctx = api.Context(DIMS, blob, vocab_words, precision="bf16", keep_trace=True)
+    ctx.set_tiles([4, 4, 4, 4])
+    out = ctx.anonymize(rs.data, rs.offsets, SCHEMA, key)
+    tr = ctx.trace()
+    U.check_tokens(tr, recs, rs.offsets, ref.traces)
+    err, agree, flips = U.check_logits(tr, ref.traces, "bf16")
+    U.check_stage_isolated(out.records(), tr, recs, SCHEMA, key, vocab_index)
+    print(f"2-SM tiles: max|dlogit| {err:.2e}, agreement {agree:.5f}")
+    ctx.close()
