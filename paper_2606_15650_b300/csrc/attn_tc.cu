@@ -21,14 +21,18 @@
 // K-major operands, V as an MN-major B operand (keys along K, features
 // contiguous), so no transposed copy of V is made. K (4 stages) and V (4
 // stages) have rings of their own; Q is double-buffered across units.
-// Warps: Q/K loader, V loader, MMA issuer (one thread each, blocking on their
-// own barriers), four softmax warps. 96 KB shared memory, 256 TMEM columns.
-// One thread issues every MMA, in the order S_0, S_1, O_0, S_2, O_1, S_3, ...,
-// and tcgen05 MMAs of one thread complete in issue order: once S_g is complete
-// (the softmax warps wait for it anyway) so is O_{g-2}, which frees P buffer
-// g&1 for P_g without a wait of its own. And S_{g+2} is issued only after P_g
-// is full, which the softmax warps signal after reading S_g, so the S buffer
-// needs no release barrier either.
+// Warps: Q/K loader, V loader (one thread each, blocking on their own
+// barriers), MMA issuer (one warp, warp-uniform loop, one elected lane issues),
+// four softmax warps. 104 KB shared memory, 256 TMEM columns.
+// Every MMA is issued from that warp, in the order S_0, S_1, O_0, S_2, O_1,
+// S_3, ..., and tcgen05 MMAs of one thread complete in issue order: once S_g is
+// complete (the softmax warps wait for it anyway) so is O_{g-2}, which frees P
+// buffer g&1 for P_g without a wait of its own. And S_{g+2} is issued only
+// after P_g is full, which the softmax warps signal after reading S_g, so the S
+// buffer needs no release barrier either. Per key tile the issuer tests three
+// barriers together (V_g, K of S_{g+2}, and P_g, the only one the softmax
+// warps hold up; the tests' shared-memory round trips overlap) and commits
+// twice (S-full, O-done); the loaders refill a stage on those.
 // Keys past the sequence end are masked to -inf; query rows past it are not
 // stored. Every mbarrier wait is bounded (see gemm_tc.cu); on a timeout each
 // issuing thread waits (bounded) for its copies and MMAs in flight before the
@@ -123,6 +127,17 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
   const bool ok = mbar_wait(bar, parity, abort_flag, err, where);
   return __all_sync(0xffffffffu, ok);
 }
+// Warp-uniform wait for three barrier phases (none of which can be lapped
+// while the warp waits): the three tests are issued back to back, so their
+// shared-memory round trips overlap, and only the phases not yet complete
+// are then waited for one by one.
+__device__ __forceinline__ bool warp_wait3(uint32_t b0, uint32_t p0, uint32_t b1, uint32_t p1, uint32_t b2,
+                                           uint32_t p2, volatile int* abort_flag, DevError* err, uint32_t where) {
+  const bool r0 = mbar_test(b0, p0), r1 = mbar_test(b1, p1), r2 = mbar_test(b2, p2);
+  const bool a0 = __all_sync(0xffffffffu, r0), a1 = __all_sync(0xffffffffu, r1), a2 = __all_sync(0xffffffffu, r2);
+  return (a0 || warp_wait(b0, p0, abort_flag, err, where)) && (a1 || warp_wait(b1, p1, abort_flag, err, where + 1)) &&
+         (a2 || warp_wait(b2, p2, abort_flag, err, where + 2));
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
@@ -203,6 +218,16 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       : "memory");
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+// One lane of a converged warp (the same lane on every call).
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "elect.sync _|p, 0xffffffff;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(pred));
+  return pred != 0;
+}
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -223,8 +248,12 @@ constexpr int kKBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys 
 constexpr int kVBytes = kKT * 64 * 2;                // 8 KB per stage: 64 keys x 64 features
 // K and V have rings of their own: a K stage is free as soon as S_g = Q K_g^T
 // is done, a V stage only after O += P_g V_g, which comes a softmax later.
-constexpr int kKStages = 4;
-constexpr int kVStages = 4;
+// The loaders wait on the S-full and O-done barriers themselves (one per ring
+// slot, so indexed by g % 4 like the stages): no separate release barriers,
+// and the MMA issuer commits twice per key tile instead of four times.
+constexpr int kRing = 4;
+constexpr int kKStages = kRing;
+constexpr int kVStages = kRing;
 constexpr int kOffQ = 0;                             // 2 buffers (consecutive work units)
 constexpr int kOffK = kOffQ + 2 * kQBytes;
 constexpr int kOffV = kOffK + kKStages * kKBytes;
@@ -238,16 +267,17 @@ constexpr int kOffBar = kOffStg + 4 * kStgBytes;
 enum {
   kBarQFull = 0,     // [2] Q of a unit landed
   kBarQEmpty = 2,    // [2] the S MMAs of a unit are done with its Q
-  kBarKFull = 4,     // [kKStages]
-  kBarKEmpty = 8,    // [kKStages]
-  kBarVFull = 12,    // [kVStages]
-  kBarVEmpty = 16,   // [kVStages]
-  kBarSFull = 20,    // [2] S_g in TMEM (by S buffer)
-  kBarPFull = 22,    // [2] P_g in TMEM, S_g read (128 arrivals)
-  kBarODone = 24,    // [2] O += P_g V_g done (by P buffer)
-  kBarDrain = 26,
-  kNumBars = 27
+  kBarKFull = 4,     // [kRing] K_g landed (by g % kRing)
+  kBarVFull = 8,     // [kRing] V_g landed
+  kBarSFull = 12,    // [kRing] S_g = Q K_g^T in TMEM; K stage g % kRing free again
+  kBarPFull = 16,    // [2] P_g in TMEM, S_g read (128 arrivals; by P buffer)
+  kBarODone = 18,    // [kRing] O += P_g V_g done; V stage g % kRing free again
+  kBarDrain = 22,
+  kNumBars = 23
 };
+// A barrier indexed by g % kRing completes phase g / kRing with tile g. No
+// waiter can lag a full ring behind: tile g + kRing needs K or V stage
+// g % kRing refilled, which its loader does only after that wait.
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
 constexpr int kSmemAlloc = kSmemBytes + 1024;        // room to align the base to 1024 bytes
 // TMEM: S buffers at columns 0 and 64, O at 128, P buffers at 192 and 224.
@@ -330,16 +360,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_init(bar(kBarQFull + i), 1);
       mbar_init(bar(kBarQEmpty + i), 1);
       mbar_init(bar(kBarPFull + i), 128);
-      mbar_init(bar(kBarODone + i), 1);
-      mbar_init(bar(kBarSFull + i), 1);
     }
-    for (int i = 0; i < kKStages; ++i) {
+    for (int i = 0; i < kRing; ++i) {
       mbar_init(bar(kBarKFull + i), 1);
-      mbar_init(bar(kBarKEmpty + i), 1);
-    }
-    for (int i = 0; i < kVStages; ++i) {
       mbar_init(bar(kBarVFull + i), 1);
-      mbar_init(bar(kBarVEmpty + i), 1);
+      mbar_init(bar(kBarSFull + i), 1);
+      mbar_init(bar(kBarODone + i), 1);
     }
     mbar_init(bar(kBarDrain), 1);
     *abort_flag = 0;
@@ -371,7 +397,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         tma_load_2d(sb + kOffQ + b * kQBytes, &tmQ, bar(kBarQFull + b), w.h * 64, w.row0 + w.q0);
         for (int t = 0; t < w.n_t; ++t, ++g) {
           const int st = g % kKStages;
-          if (!mbar_wait(bar(kBarKEmpty + st), ((g / kKStages) & 1) ^ 1u, abort_flag, p.err, 41)) { ok = false; break; }
+          // S_{g - kRing} done with this stage (passes at once for g < kRing)
+          if (!mbar_wait(bar(kBarSFull + st), ((g / kKStages) & 1) ^ 1u, abort_flag, p.err, 41)) { ok = false; break; }
           mbar_expect_tx(bar(kBarKFull + st), kKBytes);
           tma_load_2d(sb + kOffK + st * kKBytes, &tmKV, bar(kBarKFull + st), d + w.h * 64, w.row0 + t * kKT);
         }
@@ -398,7 +425,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const Work w = uw.work(p);
         for (int t = 0; t < w.n_t; ++t, ++g) {
           const int st = g % kVStages;
-          if (!mbar_wait(bar(kBarVEmpty + st), ((g / kVStages) & 1) ^ 1u, abort_flag, p.err, 42)) { ok = false; break; }
+          // O += P_{g - kRing} V_{g - kRing} done with this stage
+          if (!mbar_wait(bar(kBarODone + st), ((g / kVStages) & 1) ^ 1u, abort_flag, p.err, 42)) { ok = false; break; }
           mbar_expect_tx(bar(kBarVFull + st), kVBytes);
           tma_load_2d(sb + kOffV + st * kVBytes, &tmKV, bar(kBarVFull + st), 2 * d + w.h * 64, w.row0 + t * kKT);
         }
@@ -411,75 +439,95 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   } else if (warp == 2) {
-    if (lane == 0) {
-      // ---------------- MMA issuer: S_0, S_1, then O_g followed by S_{g+2} for every
-      // g: S_{g+1} is computed while the softmax warps work on S_g
-      constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
-      UnitWalk cs, co;                          // S and O cursors
-      cs.start(p, n_units);
-      co.start(p, n_units);
-      int is = 0, ts = 0, gs = 0, io = 0, to = 0, go = 0;
-      Work ws{}, wo{};
-      if (!cs.done()) ws = wo = cs.work(p);
-      bool ok = true, issued = false;
-      auto issue_s = [&]() -> bool {
-        const int st = gs % kKStages;
-        if (ts == 0 && !mbar_wait(bar(kBarQFull + (is & 1)), (is >> 1) & 1, abort_flag, p.err, 50)) return false;
-        if (!mbar_wait(bar(kBarKFull + st), (gs / kKStages) & 1, abort_flag, p.err, 51)) return false;
-        const int sbuf = gs & 1;  // free: S_{gs-2} was read before P_{gs-2} (issue_o waited for it)
-        fence_after();
-        const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
-        const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
+    // ---------------- MMA issuer: the whole warp runs the loop (its waits and
+    // cursors are warp-uniform) and one elected lane issues each group of MMAs.
+    // Order: S_0, S_1, then O_g followed by S_{g+2} for every g, so S_{g+1} is
+    // computed while the softmax warps work on S_g. The waits that do not
+    // depend on the softmax (V_g, and Q and K of S_{g+2}) come before the wait
+    // for P_g, which is then followed at once by the eight MMAs.
+    constexpr uint32_t idS = idesc_bf16(kQ, kKT), idO = idesc_bf16(kQ, 64) | kIdescTransposeB;
+    UnitWalk cs, co;                          // S and O cursors
+    cs.start(p, n_units);
+    co.start(p, n_units);
+    int is = 0, ts = 0, gs = 0, to = 0, go = 0;
+    Work ws{}, wo{};
+    if (!cs.done()) ws = wo = cs.work(p);
+    bool ok = true, issued = false;
+    auto wait_s = [&]() -> bool {             // Q and K_gs landed
+      if (ts == 0 && !warp_wait(bar(kBarQFull + (is & 1)), (is >> 1) & 1, abort_flag, p.err, 50)) return false;
+      return warp_wait(bar(kBarKFull + gs % kKStages), (gs / kKStages) & 1, abort_flag, p.err, 51);
+    };
+    auto issue_s = [&]() {
+      const int st = gs % kKStages;
+      const int sbuf = gs & 1;  // free: S_{gs-2} was read before P_{gs-2}, which O_{gs-2} waited for
+      const uint64_t qdesc = sw128_desc(sb + kOffQ + (is & 1) * kQBytes);
+      const uint64_t kdesc = sw128_desc(sb + kOffK + st * kKBytes);
+      const bool last = ts + 1 == ws.n_t;
+      if (elect_one()) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           mma_bf16(tmem + 64u * (uint32_t)sbuf, qdesc + 2 * k, kdesc + 2 * k, idS, k > 0 ? 1u : 0u);
-        mma_commit(bar(kBarSFull + sbuf));
-        mma_commit(bar(kBarKEmpty + st));
-        issued = true;
-        ++gs;
-        if (++ts == ws.n_t) {
-          mma_commit(bar(kBarQEmpty + (is & 1)));
-          cs.advance(p);
-          ++is;
-          ts = 0;
-          if (!cs.done()) ws = cs.work(p);
-        }
-        return true;
-      };
-      auto issue_o = [&]() -> bool {
-        const int st = go % kVStages;
-        if (!mbar_wait(bar(kBarPFull + (go & 1)), (go >> 1) & 1, abort_flag, p.err, 54)) return false;
-        if (!mbar_wait(bar(kBarVFull + st), (go / kVStages) & 1, abort_flag, p.err, 55)) return false;
-        fence_after();
-        const uint32_t pcol = tmem + kColP + 32u * (uint32_t)(go & 1);
-        const uint64_t vdesc = sw128_desc_mn(sb + kOffV + st * kVBytes);
-        const uint32_t ocol = tmem + kColO;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_bf16_ta(ocol, pcol + 8 * k, vdesc + 128 * k, idO, (to > 0 || k > 0) ? 1u : 0u);
-        mma_commit(bar(kBarODone + (go & 1)));
-        mma_commit(bar(kBarVEmpty + st));
-        ++go;
-        if (++to == wo.n_t) {
-          co.advance(p);
-          ++io;
-          to = 0;
-          if (!co.done()) wo = co.work(p);
-        }
-        return true;
-      };
-      if (!cs.done()) ok = issue_s();
-      if (ok && !cs.done()) ok = issue_s();
-      while (ok && !co.done()) {
-        ok = issue_o();
-        if (ok && !cs.done()) ok = issue_s();
+        mma_commit(bar(kBarSFull + st));
+        if (last) mma_commit(bar(kBarQEmpty + (is & 1)));
       }
-      if (!ok && issued) {
-        // wait (bounded) for the MMAs in flight before the TMEM is freed
-        mma_commit(bar(kBarDrain));
-        const uint64_t t0 = globaltimer();
-        while (!mbar_test(bar(kBarDrain), 0) && globaltimer() - t0 < kTimeoutNs) {
-        }
+      __syncwarp();
+      issued = true;
+      ++gs;
+      if (++ts == ws.n_t) {
+        cs.advance(p);
+        ++is;
+        ts = 0;
+        if (!cs.done()) ws = cs.work(p);
+      }
+    };
+    auto issue_o = [&]() {
+      const int st = go % kVStages;
+      const uint32_t pcol = tmem + kColP + 32u * (uint32_t)(go & 1);
+      const uint64_t vdesc = sw128_desc_mn(sb + kOffV + st * kVBytes);
+      const uint32_t ocol = tmem + kColO;
+      const uint32_t acc0 = to > 0 ? 1u : 0u;
+      if (elect_one()) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_bf16_ta(ocol, pcol + 8 * k, vdesc + 128 * k, idO, k > 0 ? 1u : acc0);
+        mma_commit(bar(kBarODone + st));
+      }
+      __syncwarp();
+      ++go;
+      if (++to == wo.n_t) {
+        co.advance(p);
+        to = 0;
+        if (!co.done()) wo = co.work(p);
+      }
+    };
+    for (int k = 0; k < 2 && ok && !cs.done(); ++k) {
+      ok = wait_s();
+      if (ok) {
+        fence_after();
+        issue_s();
+      }
+    }
+    while (ok && !co.done()) {
+      const bool more_s = !cs.done();
+      // V_g, K of S_{g+2} (V_g again when no S follows) and P_g, tested together
+      const uint32_t bv = bar(kBarVFull + go % kVStages), pv = (go / kVStages) & 1;
+      uint32_t bk = bv, pk = pv;
+      if (more_s) {
+        if (ts == 0 && !warp_wait(bar(kBarQFull + (is & 1)), (is >> 1) & 1, abort_flag, p.err, 50)) { ok = false; break; }
+        bk = bar(kBarKFull + gs % kKStages);
+        pk = (gs / kKStages) & 1;
+      }
+      ok = warp_wait3(bv, pv, bk, pk, bar(kBarPFull + (go & 1)), (go >> 1) & 1, abort_flag, p.err, 55);
+      if (!ok) break;
+      fence_after();
+      issue_o();
+      if (more_s) issue_s();
+    }
+    if (!ok && issued) {
+      // wait (bounded) for the MMAs in flight before the TMEM is freed
+      if (elect_one()) mma_commit(bar(kBarDrain));
+      __syncwarp();
+      const uint64_t t0 = globaltimer();
+      while (!mbar_test(bar(kBarDrain), 0) && globaltimer() - t0 < kTimeoutNs) {
       }
     }
   } else {
@@ -489,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float c = 0.125f * 1.4426950408889634f;  // 1/sqrt(64) * log2(e)
     // O += P_k V_k completes phase k/2 of o_done[k&1]
     auto wait_o = [&](int k, uint32_t where) {
-      return warp_wait(bar(kBarODone + (k & 1)), (k >> 1) & 1, abort_flag, p.err, where);
+      return warp_wait(bar(kBarODone + (k % kRing)), (k / kRing) & 1, abort_flag, p.err, where);
     };
     int g = 0, i = 0;
     bool ok = true;
@@ -505,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const bool live = w.q0 + sub * 32 < w.L;
       for (int t = 0; t < w.n_t; ++t, ++g) {
         const int valid = min(kKT, w.L - t * kKT);  // keys of this tile inside the sequence
-        if (!warp_wait(bar(kBarSFull + (g & 1)), (g >> 1) & 1, abort_flag, p.err, 60)) { ok = false; break; }
+        if (!warp_wait(bar(kBarSFull + (g % kRing)), (g / kRing) & 1, abort_flag, p.err, 60)) { ok = false; break; }
         fence_after();
         // keys past the sequence end have P = 0, but the MMA still multiplies
         // their V rows: zero those rows of the landed V tile (a 128-byte row
