@@ -656,16 +656,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (OUT8) {
         // 64-byte rows: 32 rows x 4 pieces of 16 bytes, one pass; piece c of row
         // r sits at slot c ^ ((r >> 1) & 3) (conflict-free both ways)
-        const float inv = p.out_inv_scale / l;
+        const uint64_t inv2 = f2splat(p.out_inv_scale / l);
+        // O / l times the output scale in two-lane FP32, rounded to E4M3 pairs
+        auto e4m3_pair = [&](int q) -> uint32_t {
+          float a0, a1;
+          f2unpack(mul2(f2pack(__uint_as_float(v[q]), __uint_as_float(v[q + 1])), inv2), a0, a1);
+          return e4m3x2(a0, a1);
+        };
 #pragma unroll
         for (int q = 0; q < 64; q += 16) {
           uint4 x;
           uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            xw[k] = (uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k]) * inv, __uint_as_float(v[q + 4 * k + 1]) * inv) |
-                    ((uint32_t)e4m3x2(__uint_as_float(v[q + 4 * k + 2]) * inv, __uint_as_float(v[q + 4 * k + 3]) * inv)
-                     << 16);
+          for (int k = 0; k < 4; ++k) xw[k] = e4m3_pair(q + 4 * k) | (e4m3_pair(q + 4 * k + 2) << 16);
           *reinterpret_cast<uint4*>(stg + lane * 64 + (((q >> 4) ^ ((lane >> 1) & 3)) << 4)) = x;
         }
         __syncwarp();
@@ -678,26 +681,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncwarp();
       } else {
-        // 128-byte rows: two passes of 16 rows x 8 pieces; piece c of row r sits
-        // at slot c ^ (r & 7)
-        const float inv = 1.f / l;
+        // 128-byte rows: every lane converts its row at once (O / l in two-lane
+        // FP32, rounded to BF16 pairs), then two passes of 16 rows x 8 pieces
+        // through the staging buffer; piece c of row r sits at slot c ^ (r & 7)
+        const uint64_t inv2 = f2splat(1.f / l);
+        uint32_t pk[32];
+#pragma unroll
+        for (int q = 0; q < 64; q += 2) {
+          float a0, a1;
+          f2unpack(mul2(f2pack(__uint_as_float(v[q]), __uint_as_float(v[q + 1])), inv2), a0, a1);
+          __nv_bfloat162 b = __floats2bfloat162_rn(a0, a1);
+          pk[q >> 1] = *reinterpret_cast<uint32_t*>(&b);
+        }
         __nv_bfloat16* o = static_cast<__nv_bfloat16*>(p.out) + w.h * 64;
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
           if ((lane >> 4) == pass) {
 #pragma unroll
-            for (int q = 0; q < 64; q += 8) {
-              uint4 x;
-              __nv_bfloat162 a0 = __floats2bfloat162_rn(__uint_as_float(v[q]) * inv, __uint_as_float(v[q + 1]) * inv);
-              __nv_bfloat162 a1 = __floats2bfloat162_rn(__uint_as_float(v[q + 2]) * inv, __uint_as_float(v[q + 3]) * inv);
-              __nv_bfloat162 a2 = __floats2bfloat162_rn(__uint_as_float(v[q + 4]) * inv, __uint_as_float(v[q + 5]) * inv);
-              __nv_bfloat162 a3 = __floats2bfloat162_rn(__uint_as_float(v[q + 6]) * inv, __uint_as_float(v[q + 7]) * inv);
-              x.x = *reinterpret_cast<uint32_t*>(&a0);
-              x.y = *reinterpret_cast<uint32_t*>(&a1);
-              x.z = *reinterpret_cast<uint32_t*>(&a2);
-              x.w = *reinterpret_cast<uint32_t*>(&a3);
-              *reinterpret_cast<uint4*>(stg + (lane & 15) * 128 + (((q >> 3) ^ (lane & 7)) << 4)) = x;
-            }
+            for (int c = 0; c < 8; ++c)
+              *reinterpret_cast<uint4*>(stg + (lane & 15) * 128 + ((c ^ (lane & 7)) << 4)) =
+                  make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
           }
           __syncwarp();
 #pragma unroll
