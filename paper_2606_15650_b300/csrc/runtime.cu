@@ -1034,6 +1034,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
   launch_recognize_compact(ln->rx_len_b.as<uint32_t>(), ln->rx_type_b.as<uint8_t>(), N32, ln->rx_s.as<uint32_t>(),
                            ln->rx_l.as<uint32_t>(), ln->rx_t.as<uint8_t>(), cnt + 1, ln->scan_tiles.as<uint32_t>(), st,
                            !rx_long);
+  CK(cudaGetLastError());  // a text-stage launch that was refused (its marks would be stale)
   ps_text.end();
   // ---- sync 1: token counts
   uint32_t h_cnt[2] = {0, 0};
