@@ -1285,6 +1285,7 @@ as_status anonymize_impl(as_ctx* c, Lane* ln, const as_records* rec, const as_sc
                           1);  // over the final spans + 1 (shift[n] = total)
   ps_sub1.end();
   // ---- sync 2: output size and counts
+  CK(cudaGetLastError());  // a refused launch of the encoder or span stages
   int64_t total_delta = 0;
   uint32_t h_cnt2[6];
   CK(cudaMemcpyAsync(&total_delta, ln->delta_total.p, 8, cudaMemcpyDeviceToHost, st));
