@@ -8,9 +8,12 @@
 // Structure (one CTA per SM, persistent over 128 x BN output tiles):
 //   warp 0, one lane : TMA producer, A and B tiles (64 K-elements, 128-byte
 //                      swizzle) into a STAGES-deep shared-memory ring
-//   warp 1, one lane : issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM
+//   warp 1           : issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM
 //                      accumulator; tcgen05.commit frees ring slots and
-//                      signals a finished accumulator
+//                      signals a finished accumulator (the whole warp runs
+//                      the loop and waits, one elected lane issues: issuing
+//                      from a single divergent lane took longer than the
+//                      64-cycle MMAs of BN = 128 tiles)
 //   warps 2..9       : epilogue; two warps per TMEM lane quarter (32 rows),
 //                      each taking half of the tile's columns: tcgen05.ld,
 //                      bias / GELU / residual in FP32, then 32x32 chunks
@@ -142,6 +145,17 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
                                           uint32_t where) {
   const bool ok = mbar_wait(bar, parity, abort_flag, err, where);
   return __all_sync(0xffffffffu, ok);
+}
+
+// One lane of a converged warp (the same lane on every call).
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "elect.sync _|p, 0xffffffff;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(pred));
+  return pred != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1) {
@@ -622,38 +636,45 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && (!MC || crank == 0)) {
-      // ---------------- MMA issuer (the even CTA of a 2-SM pair)
+    if (!MC || crank == 0) {
+      // ---------------- MMA issuer (the even CTA of a 2-SM pair): the whole warp
+      // runs the loop (warp-uniform waits), one elected lane issues each group
       uint32_t it = 0, lt = 0;
       for (int tile = t_first; tile < t_count; tile += t_step, ++lt) {
         const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
-        if (!mbar_wait(tempty_bar(acc), aph ^ 1u, abort_flag, p.err, 20)) goto done;
+        if (!warp_wait(tempty_bar(acc), aph ^ 1u, abort_flag, p.err, 20)) goto done;
         fence_after();
         const uint32_t d_tmem = tmem_base + acc * BN;
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
-          if (!mbar_wait(full_bar(s), ph, abort_flag, p.err, 21)) goto done;
+          if (!warp_wait(full_bar(s), ph, abort_flag, p.err, 21)) goto done;
           fence_after();
           const uint32_t a_addr = sbase + s * L::kStageBytes;
           const uint64_t adesc = sw128_desc(a_addr), bdesc = sw128_desc(a_addr + L::kABytes);
-          // four MMAs per 128-byte k-block (K = 16 BF16 or 32 E4M3 each): 32 bytes apart
+          if (elect_one()) {
+            // four MMAs per 128-byte k-block (K = 16 BF16 or 32 E4M3 each): 32 bytes apart
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t en = (kb > 0 || k > 0) ? 1u : 0u;
-            if constexpr (MC) {
-              if (IN == kInE4M3) mma_e4m3_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
-              else mma_bf16_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
-            } else {
-              if (IN == kInE4M3) mma_e4m3(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
-              else mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t en = (kb > 0 || k > 0) ? 1u : 0u;
+              if constexpr (MC) {
+                if (IN == kInE4M3) mma_e4m3_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+                else mma_bf16_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+              } else {
+                if (IN == kInE4M3) mma_e4m3(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+                else mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, kIdesc, en);
+              }
             }
+            if constexpr (MC) mma_commit_pair(empty_bar(s), (uint16_t)(0x3u << lead));
+            else mma_commit(empty_bar(s));
           }
-          if constexpr (MC) mma_commit_pair(empty_bar(s), (uint16_t)(0x3u << lead));
-          else mma_commit(empty_bar(s));
+          __syncwarp();
         }
-        if constexpr (MC) mma_commit_pair(tfull_bar(acc), (uint16_t)(0x3u << lead));
-        else mma_commit(tfull_bar(acc));
+        if (elect_one()) {
+          if constexpr (MC) mma_commit_pair(tfull_bar(acc), (uint16_t)(0x3u << lead));
+          else mma_commit(tfull_bar(acc));
+        }
+        __syncwarp();
       }
     }
   } else {
