@@ -54,9 +54,9 @@ METRIC = "tokens/s per B300, BF16/FP8 vs FP32 at >=99.9% label match; p50/p99 la
 # prefix; reported only while the source is unchanged. A, C and the residual
 # scale with the rows, so a launch of R rows moves about
 # mean(bytes) * R / 65,536.
-GEMM_TRAFFIC = {"source_sha256": "2d587374f11ccc47", "rows": 65536,
-                "bytes": {"qkv": 103788800 + 247970560, "attn_out": 302105088 + 245901312,
-                          "ffn1": 105139968 + 347319552, "ffn2": 614247936 + 256188672}}
+GEMM_TRAFFIC = {"source_sha256": "e10ec2661dc09526", "rows": 65536,
+                "bytes": {"qkv": 104232704 + 249455360, "attn_out": 303499008 + 247745280,
+                          "ffn1": 105460480 + 348832000, "ffn2": 617227776 + 257250560}}
 
 
 def parse():
