@@ -294,38 +294,56 @@ constexpr float kRescaleSlack = 8.0f;
 struct Work {
   int L, row0, q0, h, n_t;
 };
-__device__ __forceinline__ int2 item_at(const Params& p, int u) { return __ldg(p.items + u / p.n_heads); }
 __device__ __forceinline__ bool item_empty(int2 it) { return (it.y & 0xFFFF) == 0; }
 
 // A CTA's walk over its units (u = b, b + grid, ...), skipping padding items
-// the same way in every role. The descriptor of the unit after the current
-// one is loaded when the current one starts, so that a unit boundary does not
-// wait on a global load (it is only read a whole unit later).
+// the same way in every role. Unit u is (item u / heads, head u % heads); the
+// pair is carried along the walk (two divisions at the start, none after).
+// The descriptor of the unit after the current one is loaded when the current
+// one starts, so that a unit boundary does not wait on a global load (it is
+// only read a whole unit later).
 struct UnitWalk {
   int u = 0, n = 0, step = 0;
+  int item = 0, h = 0, nh = 1, step_item = 0, step_h = 0;
   int2 cur{0, 0}, nxt{0, 0};
+  __device__ __forceinline__ void fwd() {
+    u += step;
+    item += step_item;
+    h += step_h;
+    if (h >= nh) {
+      h -= nh;
+      ++item;
+    }
+  }
+  // item of unit u + step
+  __device__ __forceinline__ int next_item() const { return item + step_item + (h + step_h >= nh ? 1 : 0); }
   __device__ __forceinline__ void start(const Params& p, int n_units) {
     n = n_units;
+    nh = p.n_heads;
     step = (int)gridDim.x;
+    step_item = step / nh;
+    step_h = step - step_item * nh;
     u = (int)blockIdx.x;
-    while (u < n && item_empty(cur = item_at(p, u))) u += step;
-    if (u < n && u + step < n) nxt = item_at(p, u + step);
+    item = u / nh;
+    h = u - item * nh;
+    while (u < n && item_empty(cur = __ldg(p.items + item))) fwd();
+    if (u < n && u + step < n) nxt = __ldg(p.items + next_item());
   }
   __device__ __forceinline__ void advance(const Params& p) {
-    u += step;
+    fwd();
     if (u >= n) return;
     cur = nxt;
     if (item_empty(cur)) {
-      do u += step;
-      while (u < n && item_empty(cur = item_at(p, u)));
+      do fwd();
+      while (u < n && item_empty(cur = __ldg(p.items + item)));
       if (u >= n) return;
     }
-    if (u + step < n) nxt = item_at(p, u + step);
+    if (u + step < n) nxt = __ldg(p.items + next_item());
   }
   __device__ __forceinline__ bool done() const { return u >= n; }
-  __device__ __forceinline__ Work work(const Params& p) const {
+  __device__ __forceinline__ Work work(const Params&) const {
     Work w;
-    w.h = u % p.n_heads;
+    w.h = h;
     w.row0 = cur.x;
     w.L = cur.y & 0xFFFF;
     w.q0 = cur.y >> 16;
