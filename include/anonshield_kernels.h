@@ -79,6 +79,15 @@ as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start
                             const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
                             void* stream);
 
+/* The tcgen05 attention with E4M3 output, as the FP8 encoder uses it: out8
+ * [rows][d] bytes, the E4M3 code (round to nearest even, saturating at +-448)
+ * of each output value divided by out_scale (> 0; AS_ERR_ARG otherwise).
+ * Rows outside every sequence are not written. Same inputs and checks as
+ * as_k_attention_tc. */
+as_status as_k_attention_tc_e4m3(const void* qkv, void* out8, float out_scale, const int32_t* seq_start,
+                                 const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model,
+                                 int32_t n_heads, void* stream);
+
 /* Row LayerNorm (biased variance, eps 1e-5): out_f32 = LN(in) * g + b, and
  * a BF16 copy in out_bf16 when it is not NULL. in/out_f32 may alias. */
 as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16,

@@ -142,7 +142,7 @@ EXPORTED = ["as_create", "as_destroy", "as_anonymize", "as_output_records", "as_
             "as_output_free", "as_map_export", "as_map_import", "as_map_merge", "as_map_clear", "as_debug_trace", "as_last_error",
             "as_free", "as_version", "as_get_stream", "as_profile", "as_profile_read", "as_tokenize_static", "as_calibrate",
             "as_get_scales", "as_set_scales", "as_anonymize_stream", "as_anonymize_fields", "as_anonymize_jsonl", "as_reidentify", "as_autotune", "as_set_tiles", "as_get_tiles", "as_serve_start", "as_submit", "as_poll", "as_serve_stats",
-            "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_layernorm", "as_k_launch_count",
+            "as_serve_stop", "as_k_gemm", "as_k_gemm_fp8", "as_k_attention", "as_k_attention_tc", "as_k_attention_tc_e4m3", "as_k_layernorm", "as_k_launch_count",
             "as_k_last_error"]
 
 _lib = None
@@ -207,6 +207,7 @@ def load() -> C.CDLL:
                                        C.c_float, C.c_int, P]
     lib.as_k_attention.argtypes = [C.c_int, P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_attention_tc.argtypes = [P, P, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
+    lib.as_k_attention_tc_e4m3.argtypes = [P, P, C.c_float, P, P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, P]
     lib.as_k_layernorm.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P]
     lib.as_k_launch_count.restype = C.c_uint64
     lib.as_k_last_error.restype = C.c_char_p
@@ -287,6 +288,13 @@ def attention_tc(qkv, out, seq_start, seq_len, d_model: int, n_heads: int, strea
     _check_k(load().as_k_attention_tc(_ptr(qkv), _ptr(out), _ptr(seq_start), _ptr(seq_len),
                                       int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
     return out
+
+
+def attention_tc_e4m3(qkv, out8, out_scale: float, seq_start, seq_len, d_model: int, n_heads: int, stream=None):
+    """tcgen05 attention with E4M3 output (codes of value / out_scale) over packed sequences."""
+    _check_k(load().as_k_attention_tc_e4m3(_ptr(qkv), _ptr(out8), float(out_scale), _ptr(seq_start), _ptr(seq_len),
+                                           int(seq_len.numel()), int(qkv.shape[0]), d_model, n_heads, stream))
+    return out8
 
 
 def layernorm(x, g, b, out_f32, out_bf16=None, stream=None):

@@ -80,9 +80,14 @@ as_status as_k_attention(int precision, const void* qkv, void* out, const int32_
   return AS_ERR_ARG;
 }
 
-as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start,
-                            const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
-                            void* stream) {
+}  // extern "C"
+
+namespace {
+// Work items from the host copies of the sequence table, then one tcgen05
+// attention launch (BF16 output, or E4M3 of value / out_scale when out8).
+as_status attention_tc_entry(const char* name, bool out8, const void* qkv, void* out, float out_scale,
+                             const int32_t* seq_start, const int32_t* seq_len, int32_t n_seq, int64_t rows,
+                             int32_t d_model, int32_t n_heads, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::vector<int32_t> lens(n_seq > 0 ? n_seq : 0), starts(n_seq > 0 ? n_seq : 0);
   if (n_seq > 0) {
@@ -93,7 +98,7 @@ as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start
   int32_t mx = 0;
   for (int32_t i = 0; i < n_seq; ++i) {
     if (starts[i] < 0 || lens[i] < 0 || (int64_t)starts[i] + lens[i] > rows) {
-      set_k_error("as_k_attention_tc: every sequence must lie inside the rows");
+      set_k_error(std::string(name) + ": every sequence must lie inside the rows");
       return AS_ERR_ARG;
     }
     mx = lens[i] > mx ? lens[i] : mx;
@@ -105,12 +110,34 @@ as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start
   AS_CUDA_OK(cudaMallocAsync(reinterpret_cast<void**>(&d_items), items.size() * 4, st));
   cudaError_t e = cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st);
   as_status s = e == cudaSuccess ? AS_OK : AS_ERR_CUDA;
-  if (s == AS_OK)
-    s = attention_tcgen05(static_cast<const __nv_bfloat16*>(qkv), static_cast<__nv_bfloat16*>(out), d_items,
-                          (int32_t)(items.size() / 2), mx, rows, d_model, n_heads, nullptr, st);
+  if (s == AS_OK) {
+    const auto* q = static_cast<const __nv_bfloat16*>(qkv);
+    const int32_t n_items = (int32_t)(items.size() / 2);
+    s = out8 ? attention_tcgen05_e4m3(q, static_cast<uint8_t*>(out), out_scale, d_items, n_items, mx, rows, d_model,
+                                      n_heads, nullptr, st)
+             : attention_tcgen05(q, static_cast<__nv_bfloat16*>(out), d_items, n_items, mx, rows, d_model, n_heads,
+                                 nullptr, st);
+  }
   cudaFreeAsync(d_items, st);
-  if (e != cudaSuccess) set_k_error(std::string("as_k_attention_tc: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) set_k_error(std::string(name) + ": " + cudaGetErrorString(e));
   return s;
+}
+}  // namespace
+
+extern "C" {
+
+as_status as_k_attention_tc(const void* qkv, void* out, const int32_t* seq_start,
+                            const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model, int32_t n_heads,
+                            void* stream) {
+  return attention_tc_entry("as_k_attention_tc", false, qkv, out, 1.0f, seq_start, seq_len, n_seq, rows, d_model,
+                            n_heads, stream);
+}
+
+as_status as_k_attention_tc_e4m3(const void* qkv, void* out8, float out_scale, const int32_t* seq_start,
+                                 const int32_t* seq_len, int32_t n_seq, int64_t rows, int32_t d_model,
+                                 int32_t n_heads, void* stream) {
+  return attention_tc_entry("as_k_attention_tc_e4m3", true, qkv, out8, out_scale, seq_start, seq_len, n_seq, rows,
+                            d_model, n_heads, stream);
 }
 
 as_status as_k_layernorm(const float* in, const float* g, const float* b, float* out_f32, void* out_bf16, int64_t rows,

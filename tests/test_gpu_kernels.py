@@ -190,6 +190,40 @@ def test_attention_ignores_rows_outside_sequences(engine, lens):
         assert (got - ref[s0:s0 + L]).abs().max().item() < 2.5e-2
 
 
+@pytest.mark.parametrize("lens", [[1, 5, 64, 65, 300, 512, 17, 128], [63, 64, 65, 191, 192, 193, 33, 1000]])
+def test_attention_tcgen05_e4m3_output(lens):
+    """E4M3 output of the tcgen05 attention (the FP8 encoder's form): each code is
+    the value / out_scale rounded to E4M3, so the decoded value times out_scale
+    is the attention within one E4M3 rounding (relative 2^-4) plus the BF16
+    attention error. Rows between sequences keep their sentinel bytes."""
+    d, h, gap = 768, 12, 3
+    g = torch.Generator(device="cpu").manual_seed(len(lens) + 11)
+    starts, acc = [], 0
+    for L in lens:
+        starts.append(acc)
+        acc += L + gap
+    rows = acc
+    qkv = torch.randn(rows, 3 * d, generator=g).to(DEV).to(torch.bfloat16)
+    out8 = torch.full((rows, d), 0x5A, device=DEV, dtype=torch.uint8)
+    st = torch.tensor(starts, dtype=torch.int32)
+    ln = torch.tensor(lens, dtype=torch.int32)
+    scale = 0.02   # |value| / scale stays far below the E4M3 maximum of 448
+    api.attention_tc_e4m3(qkv, out8, scale, st.to(DEV), ln.to(DEV), d, h)
+    torch.cuda.synchronize()
+    ref = _ref_attention(qkv, st, ln, d, h)
+    got = out8.view(torch.float8_e4m3fn).float() * scale
+    written = torch.zeros(rows, dtype=torch.bool, device=DEV)
+    for s0, L in zip(starts, lens):
+        written[s0:s0 + L] = True
+        err = (got[s0:s0 + L] - ref[s0:s0 + L]).abs()
+        assert torch.isfinite(got[s0:s0 + L]).all()
+        # E4M3 rounding (half a spacing: 2^-4 relative) of a value within 2.5e-2 of ref
+        assert (err <= ref[s0:s0 + L].abs() * 2.0 ** -4 + 3e-2).all(), err.max().item()
+    assert (out8[~written] == 0x5A).all()
+    with pytest.raises(api.AnonShieldError):
+        api.attention_tc_e4m3(qkv, out8, 0.0, st.to(DEV), ln.to(DEV), d, h)
+
+
 def test_attention_tcgen05_large_logits():
     """Scores far apart (raises of the running maximum by more than 2^8) stay exact."""
     d, h, L = 128, 2, 700
