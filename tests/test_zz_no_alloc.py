@@ -8,8 +8,9 @@ through the C ABI twice in a row, the second time on a smaller batch so that
 stale contents left in the shared array by the first call would show, and
 compares every output with the tokens the allocating entry point
 (as_anonymize) produces for the same records: token ids, offsets, lengths,
-record token ranges and the token count, exactly. It also checks that a
-batch over the size limit is refused. This file is collected last on
+record token ranges and the token count, exactly; and, record by record,
+with the oracle's tokenizer (ids, offsets within the record, lengths). It
+also checks that a batch over the size limit is refused. This file is collected last on
 purpose, so that a failure here does not hide any other test.
 """
 import numpy as np
@@ -18,11 +19,12 @@ import torch
 
 import synth
 import paper_2606_15650_b300.api as api
+from oracle.tokenizer import tokenize
 
 pytestmark = pytest.mark.gpu
 
 
-def test_static_tokenizer_matches_allocating_path(vocab_words):
+def test_static_tokenizer_matches_allocating_path(vocab_words, vocab_index):
     dims = synth.C1.dims
     blob = synth.pack_blob(dims, synth.make_weights(dims, seed=3))
     ctx = api.Context(dims, blob, vocab_words, precision="fp32", keep_trace=True)
@@ -42,6 +44,18 @@ def test_static_tokenizer_matches_allocating_path(vocab_words):
         assert np.array_equal(got["tok_off"][:T].cpu().numpy().astype(np.uint32), ref["tok_off"])
         assert np.array_equal(got["tok_len"][:T].cpu().numpy().astype(np.uint32), ref["tok_len"])
         assert np.array_equal(got["rec_tok"].cpu().numpy().astype(np.uint64), ref["rec_tok"])
+        # and the oracle's tokenizer, record by record
+        rt = got["rec_tok"].cpu().numpy().astype(np.int64)
+        ids = got["tok_ids"][:T].cpu().numpy().astype(np.int64)
+        off = got["tok_off"][:T].cpu().numpy().astype(np.int64)
+        ln = got["tok_len"][:T].cpu().numpy().astype(np.int64)
+        for r in range(recs.n):
+            a, b = int(rt[r]), int(rt[r + 1])
+            o_ids, o_off, o_len = tokenize(recs.record(r), vocab_index)
+            base = int(recs.offsets[r])
+            assert ids[a:b].tolist() == o_ids, f"record {r}: ids"
+            assert (off[a:b] - base).tolist() == o_off, f"record {r}: offsets"
+            assert ln[a:b].tolist() == o_len, f"record {r}: lengths"
 
 
 def test_static_tokenizer_rejects_oversize(vocab_words):
